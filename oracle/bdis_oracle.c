@@ -1,0 +1,734 @@
+/*
+ * bdis_oracle.c -- plain, slow FP64 CPU restatement of BDIS
+ * (Bayesian Dense Inverse Search, arXiv 2205.03133).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the parity oracle for the CUDA
+ * path and the timed CPU baseline.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may load it.  It shares no code, header,
+ * table or constant generator with the CUDA library.
+ *
+ * Every step follows the paper's order and notation, in plain loops, FP64:
+ *   pyramid + x-gradient (Sec. III, Fig. 1; Sec. III-A)
+ *   fast inverse-compositional LK per patch (Sec. III-A, Eq. 1)
+ *   window energies, saddle / unconverged rejection (Sec. III-B, Eq. 4-6;
+ *     Sec. IV technical details)
+ *   dynamic sigma_r (Sec. III-B, text after Eq. 6)
+ *   patch posterior in the small window (Eq. 5, Eq. 6)
+ *   coarse-to-fine propagation (Sec. III-D, Eq. 10, Eq. 11)
+ *   sGMM spatial kernel (Sec. III-C, Eq. 8, Eq. 9) and fusion (Eq. 12)
+ *   optional PDF fit per patch (Sec. III-E, Eq. 14-16) and pixel variance
+ *     (Eq. 17, disparity part)
+ * Where the paper is silent the reading used is stated beside the code.
+ *
+ * Parity status: every function here is pinned by the CPU tests (closed
+ * forms, invariants, brute force); agreement with the authors' own C++ is
+ * unpinned (no code or data of theirs is available).
+ *
+ * Conventions: disparity d >= 0 with I_r(x - d, y) ~= I_l(x, y), i.e. the
+ * paper's u = -d.  Level 0 is full resolution; level l+1 has ceil(n/2) pixels
+ * per axis.  Images are row-major, dense (row stride = width).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OB_MAX_LEVELS 8
+
+/* storage emulation for the pyramid and gradient images */
+enum { OB_STORE_F64 = 0, OB_STORE_F32 = 1, OB_STORE_F16 = 2 };
+enum { OB_SIGMA_R_POOLED = 0, OB_SIGMA_R_LITERAL = 1, OB_SIGMA_R_FIXED = 2 };
+
+/* patch rejection reasons (bit flags; a patch is valid iff flags == 0) */
+enum {
+    OB_F_FLAT = 1u << 0,        /* Hessian below threshold: no texture        */
+    OB_F_UNCONVERGED = 1u << 1, /* last GN update above conv_eps              */
+    OB_F_MOVED = 1u << 2,       /* |d - d_init| above the search radius       */
+    OB_F_OUTSIDE = 1u << 3,     /* too few in-image samples (gamma)           */
+    OB_F_SADDLE = 1u << 4,      /* centre not the window minimum              */
+    OB_F_NONFINITE = 1u << 5
+};
+/* PDF-fit exceptions (Sec. III-E) */
+enum {
+    OB_PDF_NOT_PEAK = 1u << 0,  /* probability at u_k not the strict maximum */
+    OB_PDF_FAILED = 1u << 1,    /* GN left the domain or produced non-finite  */
+    OB_PDF_RESIDUAL = 1u << 2   /* RMS log residual above pdf_resid           */
+};
+
+typedef struct {
+    int patch, stride, levels, iters;
+    double sigma_s;        /* sGMM spatial sigma (px), paper: 4              */
+    double window_step;    /* window offsets {0, +-h, +-2h}, paper: h = 0.5  */
+    double conv_eps;       /* convergence threshold on |last update|, 0.05   */
+    double valid_gamma;    /* minimum in-image sample ratio, 0.75            */
+    double pix_thresh;     /* pixel threshold on the fused probability, 0.15 */
+    double search_radius;  /* tau (px at each level); <= 0 means = patch     */
+    int sigma_r_mode;
+    double sigma_r_floor;
+    double sigma_r_fixed;
+    int variance, pdf_iters;
+    double pdf_resid;
+    int storage;
+    double hess_eps;       /* per-pixel Hessian threshold: H < hess_eps*P^2  */
+    int use_sgmm, use_c2f; /* ablation switches (Table VII)                  */
+} ob_params;
+
+typedef struct {
+    double d, dinit, E[5], H, cT, dlast;
+    int nout;
+    uint32_t flags;
+    double pi, rho, sig2;
+    uint32_t pdf_flags;
+} ob_patch;
+
+/* Per-level buffers the caller may ask for (any pointer may be NULL). */
+typedef struct {
+    double *L[OB_MAX_LEVELS], *R[OB_MAX_LEVELS], *G[OB_MAX_LEVELS];
+    double *D[OB_MAX_LEVELS], *Q[OB_MAX_LEVELS];
+    ob_patch *patches[OB_MAX_LEVELS];
+    double sigma_r[OB_MAX_LEVELS];
+} ob_trace;
+
+/* ------------------------------------------------------------------ */
+/* storage emulation                                                    */
+/* ------------------------------------------------------------------ */
+
+/* Round to the nearest IEEE-754 binary16 value, ties to even.  Written from
+ * the format's definition: 10 fraction bits, normal exponents -14..15,
+ * subnormal spacing 2^-24, overflow to infinity at >= 65520. */
+double ob_round_f16(double v)
+{
+    if (isnan(v)) return v;
+    double a = fabs(v);
+    if (a >= 65520.0) return copysign(INFINITY, v);
+    if (a == 0.0) return v;
+    int e;
+    frexp(a, &e);          /* a = m * 2^e, m in [0.5, 1): a in [2^(e-1), 2^e) */
+    int E = e - 1;
+    if (E < -14) E = -14;  /* subnormal range keeps the spacing of 2^-14 binade */
+    double ulp = ldexp(1.0, E - 10);
+    double q = nearbyint(a / ulp); /* default rounding mode: nearest, ties even */
+    return copysign(q * ulp, v);
+}
+
+double ob_round_storage(double v, int storage)
+{
+    if (storage == OB_STORE_F32) return (double)(float)v;
+    if (storage == OB_STORE_F16) return ob_round_f16(v);
+    return v;
+}
+
+/* ------------------------------------------------------------------ */
+/* geometry                                                             */
+/* ------------------------------------------------------------------ */
+
+int ob_level_dim(int n, int l)
+{
+    for (int i = 0; i < l; ++i) n = (n + 1) / 2;
+    return n;
+}
+
+static int reflect101(int i, int n)
+{
+    /* reflect about the edge pixel without repeating it: -1 -> 1, n -> n-2 */
+    while (i < 0 || i >= n) {
+        if (i < 0) i = -i;
+        if (i >= n) i = 2 * (n - 1) - i;
+    }
+    return i;
+}
+
+/* Patch origins along one axis of length n: 0, S, 2S, ... <= n-P, plus one
+ * extra origin at n-P when (n-P) is not a multiple of S, so every pixel is
+ * covered (patch grid of Sec. III-A with overlap 1 - S/P). */
+int ob_origins(int n, int P, int S, int *out)
+{
+    if (n < P) return 0;
+    int k = 0;
+    for (int o = 0; o <= n - P; o += S) {
+        if (out) out[k] = o;
+        ++k;
+    }
+    if ((n - P) % S != 0) {
+        if (out) out[k] = n - P;
+        ++k;
+    }
+    return k;
+}
+
+/* Gamma weight of level n (the formula following Eq. 11):
+ * 2^n / sum_{m in levels} 2^m. */
+double ob_gamma_weight(int n, int levels)
+{
+    double s = 0.0;
+    for (int m = 0; m < levels; ++m) s += ldexp(1.0, m);
+    return ldexp(1.0, n) / s;
+}
+
+/* ------------------------------------------------------------------ */
+/* pyramid and x-gradient                                               */
+/* ------------------------------------------------------------------ */
+
+/* One pyramid step: 5-tap binomial blur [1 4 6 4 1]/16 in both axes,
+ * reflect-101 border, keep the even samples.  The paper does not state the
+ * filter (it only says level n pixels stand for 2^n x 2^n patches, Sec. III-B);
+ * this is the reading used. */
+void ob_pyr_down(const double *src, int w, int h, double *dst, int storage)
+{
+    static const double k[5] = {1.0 / 16, 4.0 / 16, 6.0 / 16, 4.0 / 16, 1.0 / 16};
+    int w2 = (w + 1) / 2, h2 = (h + 1) / 2;
+    for (int Y = 0; Y < h2; ++Y)
+        for (int X = 0; X < w2; ++X) {
+            double acc = 0.0;
+            for (int j = -2; j <= 2; ++j)
+                for (int i = -2; i <= 2; ++i) {
+                    int yy = reflect101(2 * Y + j, h), xx = reflect101(2 * X + i, w);
+                    acc += k[j + 2] * k[i + 2] * src[(size_t)yy * w + xx];
+                }
+            dst[(size_t)Y * w2 + X] = ob_round_storage(acc, storage);
+        }
+}
+
+/* x-gradient of the left image used as the fixed inverse-compositional
+ * Jacobian (Sec. III-A): Sobel-x divided by 8 (columns [-1 0 1], rows
+ * [1 2 1]), reflect-101 border. */
+void ob_sobel_x(const double *src, int w, int h, double *g, int storage)
+{
+    static const double wr[3] = {1.0, 2.0, 1.0};
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            double acc = 0.0;
+            for (int j = -1; j <= 1; ++j) {
+                int yy = reflect101(y + j, h);
+                acc += wr[j + 1] * (src[(size_t)yy * w + reflect101(x + 1, w)] -
+                                    src[(size_t)yy * w + reflect101(x - 1, w)]);
+            }
+            g[(size_t)y * w + x] = ob_round_storage(acc / 8.0, storage);
+        }
+}
+
+/* ------------------------------------------------------------------ */
+/* sampling                                                             */
+/* ------------------------------------------------------------------ */
+
+/* Right image at (X, row) by linear interpolation along x; the coordinate
+ * is clamped to [0, w-1] (rows are integer for rectified stereo, so the
+ * bilinear lookup of Eq. 1 reduces to linear). */
+static double sample_row(const double *img, int w, int row, double X)
+{
+    if (X < 0.0) X = 0.0;
+    if (X > w - 1.0) X = w - 1.0;
+    int x0 = (int)floor(X);
+    double t = X - x0;
+    int x1 = x0 + 1 < w ? x0 + 1 : w - 1;
+    const double *r = img + (size_t)row * w;
+    return (1.0 - t) * r[x0] + t * r[x1];
+}
+
+/* Bilinear lookup of a coarse map at fine position (x, y) of the next finer
+ * level: coarse coordinate = (x + 0.5)/2 - 0.5, clamped to the map. */
+static double coarse_lookup(const double *m, int wc, int hc, double x, double y)
+{
+    double X = (x + 0.5) / 2.0 - 0.5, Y = (y + 0.5) / 2.0 - 0.5;
+    if (X < 0.0) X = 0.0;
+    if (X > wc - 1.0) X = wc - 1.0;
+    if (Y < 0.0) Y = 0.0;
+    if (Y > hc - 1.0) Y = hc - 1.0;
+    int x0 = (int)floor(X), y0 = (int)floor(Y);
+    int x1 = x0 + 1 < wc ? x0 + 1 : wc - 1, y1 = y0 + 1 < hc ? y0 + 1 : hc - 1;
+    double fx = X - x0, fy = Y - y0;
+    double a = (1.0 - fx) * m[(size_t)y0 * wc + x0] + fx * m[(size_t)y0 * wc + x1];
+    double b = (1.0 - fx) * m[(size_t)y1 * wc + x0] + fx * m[(size_t)y1 * wc + x1];
+    return (1.0 - fy) * a + fy * b;
+}
+
+static double search_radius(const ob_params *p)
+{
+    return p->search_radius > 0.0 ? p->search_radius : (double)p->patch;
+}
+
+/* ------------------------------------------------------------------ */
+/* per-patch search (Sec. III-A, Eq. 1) and window energies (Eq. 6)     */
+/* ------------------------------------------------------------------ */
+
+/* Window offsets delta_i of the small window P' (Sec. III-B and the
+ * parameter list of Sec. IV-A: 5 samples, disturbances 0.5 and 1 px):
+ * index 0 is the converged estimate itself. */
+void ob_window_offsets(double h, double *delta)
+{
+    delta[0] = 0.0;
+    delta[1] = -h;
+    delta[2] = h;
+    delta[3] = -2.0 * h;
+    delta[4] = 2.0 * h;
+}
+
+/* Search one patch with origin (ox, oy) at a level of size w x h.
+ * L, R, G: left, right, left x-gradient of the level.
+ * dinit: initial disparity (from the coarser level, 0 at the coarsest).
+ *
+ * Inverse compositional Gauss-Newton on the mean-normalised residual
+ * r_i = (s_i - mean s) - (T_i - mean T), s_i = I_r(x_i - d): the template
+ * warp is linearised once, with Jacobian the centred gradient
+ * gt_i = g_i - mean g and scalar Hessian H = sum gt_i^2.  Because
+ * sum gt_i = 0 the step is  delta = (sum gt_i s_i - sum gt_i T_i) / H  and the
+ * warp update composes to d <- d + delta.  The iteration count is fixed. */
+void ob_search_patch(const ob_params *p, const double *L, const double *R,
+                     const double *G, int w, int h, int ox, int oy, double dinit,
+                     ob_patch *out)
+{
+    const int P = p->patch;
+    const int N = P * P;
+    double *T = (double *)malloc(sizeof(double) * N);
+    double *gt = (double *)malloc(sizeof(double) * N);
+    double gbar = 0.0;
+    for (int r = 0; r < P; ++r)
+        for (int c = 0; c < P; ++c) {
+            T[r * P + c] = L[(size_t)(oy + r) * w + ox + c];
+            gt[r * P + c] = G[(size_t)(oy + r) * w + ox + c];
+            gbar += gt[r * P + c];
+        }
+    gbar /= N;
+    double H = 0.0, cT = 0.0;
+    for (int i = 0; i < N; ++i) {
+        gt[i] -= gbar;
+        H += gt[i] * gt[i];
+        cT += gt[i] * T[i];
+    }
+    memset(out, 0, sizeof(*out));
+    out->H = H;
+    out->cT = cT;
+    out->dinit = dinit;
+    double d = dinit, dlast = 0.0;
+    const double dlim = (double)w + 2.0 * P; /* beyond this every sample is clamped */
+    int flat = !(H >= p->hess_eps * N);
+    if (!flat) {
+        for (int it = 0; it < p->iters; ++it) {
+            double acc = 0.0;
+            for (int r = 0; r < P; ++r)
+                for (int c = 0; c < P; ++c)
+                    acc += gt[r * P + c] * sample_row(R, w, oy + r, (double)(ox + c) - d);
+            double delta = (acc - cT) / H;
+            d += delta;
+            if (d > dlim) d = dlim;
+            if (d < -dlim) d = -dlim;
+            dlast = delta;
+        }
+    }
+    out->d = d;
+    out->dlast = dlast;
+
+    /* window energies E(delta_i) = sum_j (a_j - mean a)^2 with
+     * a_j = I_r(x_j - d - delta_i) - T_j (mean-normalised SSD, Eq. 6 numerator) */
+    double delta[5];
+    ob_window_offsets(p->window_step, delta);
+    double *a = (double *)malloc(sizeof(double) * N);
+    for (int k = 0; k < 5; ++k) {
+        double mean = 0.0;
+        for (int r = 0; r < P; ++r)
+            for (int c = 0; c < P; ++c) {
+                a[r * P + c] = sample_row(R, w, oy + r, (double)(ox + c) - d - delta[k]) - T[r * P + c];
+                mean += a[r * P + c];
+            }
+        mean /= N;
+        double E = 0.0;
+        for (int i = 0; i < N; ++i) E += (a[i] - mean) * (a[i] - mean);
+        out->E[k] = E;
+    }
+    int nout = 0;
+    for (int r = 0; r < P; ++r)
+        for (int c = 0; c < P; ++c) {
+            double X = (double)(ox + c) - d;
+            if (X < 0.0 || X > w - 1.0) ++nout;
+        }
+    out->nout = nout;
+
+    uint32_t f = 0;
+    if (flat) f |= OB_F_FLAT;
+    if (!isfinite(d) || !isfinite(H)) f |= OB_F_NONFINITE;
+    if (fabs(dlast) > p->conv_eps) f |= OB_F_UNCONVERGED;
+    if (fabs(d - dinit) > search_radius(p)) f |= OB_F_MOVED;
+    if ((double)(N - nout) < p->valid_gamma * N) f |= OB_F_OUTSIDE;
+    double emin = out->E[1];
+    for (int k = 2; k < 5; ++k) emin = out->E[k] < emin ? out->E[k] : emin;
+    if (out->E[0] > emin) f |= OB_F_SADDLE; /* a tie keeps the patch */
+    out->flags = f;
+    free(a);
+    free(T);
+    free(gt);
+}
+
+/* ------------------------------------------------------------------ */
+/* dynamic sigma_r (text after Eq. 6)                                   */
+/* ------------------------------------------------------------------ */
+
+/* The paper sets sigma_r^(n) to "the standard deviation" of the converged
+ * patch residual.  Default reading (pooled): the standard deviation of the
+ * per-pixel normalised residual pooled over the valid patches of the level,
+ * sqrt(sum_k E_k(0) / (N_valid P^2)), floored.  LITERAL: population std of
+ * E_k(0) over valid patches.  FIXED: the constant of the ablation (8). */
+double ob_sigma_r(const ob_params *p, const ob_patch *pt, int n)
+{
+    if (p->sigma_r_mode == OB_SIGMA_R_FIXED) return p->sigma_r_fixed;
+    double s = 0.0;
+    long cnt = 0;
+    for (int k = 0; k < n; ++k)
+        if (pt[k].flags == 0) {
+            s += pt[k].E[0];
+            ++cnt;
+        }
+    double sr;
+    if (cnt == 0) {
+        sr = 0.0;
+    } else if (p->sigma_r_mode == OB_SIGMA_R_LITERAL) {
+        double mean = s / cnt, v = 0.0;
+        for (int k = 0; k < n; ++k)
+            if (pt[k].flags == 0) v += (pt[k].E[0] - mean) * (pt[k].E[0] - mean);
+        sr = sqrt(v / cnt);
+    } else {
+        sr = sqrt(s / ((double)cnt * p->patch * p->patch));
+    }
+    return sr > p->sigma_r_floor ? sr : p->sigma_r_floor;
+}
+
+/* ------------------------------------------------------------------ */
+/* PDF fit (Sec. III-E, Eq. 14-16)                                      */
+/* ------------------------------------------------------------------ */
+
+/* Fit  ln c - 1/2 ln(2 pi sigma^2) - delta_i^2 / (2 sigma^2)  to the window
+ * log-probabilities lnp[i] by Gauss-Newton on (sigma, c), the 2x2 normal
+ * equations solved by Cholesky, from (sqrt(0.1), 1), a fixed number of
+ * iterations.  Reading: a step that would leave sigma > 0, c > 0 is halved
+ * until it stays inside (the paper does not say how the state is kept in its
+ * domain).  Exceptions (Sec. III-E): probability at the estimate not the
+ * strict maximum, GN failure, RMS residual above pdf_resid -> sigma = tau.
+ * A fitted sigma above tau is capped at tau.  Returns sigma_k^2. */
+double ob_pdf_fit(const double *lnp, const double *delta, int iters, double resid_max,
+                  double tau, uint32_t *flags_out, double *sigma_out, double *c_out,
+                  double *rms_out)
+{
+    uint32_t flags = 0;
+    for (int i = 1; i < 5; ++i)
+        if (!(lnp[0] > lnp[i])) flags |= OB_PDF_NOT_PEAK;
+    double sg = sqrt(0.1), c = 1.0;
+    const double ln2pi = log(2.0 * M_PI);
+    for (int it = 0; it < iters && !(flags & OB_PDF_FAILED); ++it) {
+        double A11 = 0, A12 = 0, A22 = 0, b1 = 0, b2 = 0;
+        for (int i = 0; i < 5; ++i) {
+            double d2 = delta[i] * delta[i];
+            double m = log(c) - 0.5 * (ln2pi + log(sg * sg)) - d2 / (2.0 * sg * sg);
+            double r = m - lnp[i];
+            double js = -1.0 / sg + d2 / (sg * sg * sg);
+            double jc = 1.0 / c;
+            A11 += js * js;
+            A12 += js * jc;
+            A22 += jc * jc;
+            b1 -= js * r;
+            b2 -= jc * r;
+        }
+        /* Cholesky A = L L^T */
+        if (!(A11 > 0.0)) { flags |= OB_PDF_FAILED; break; }
+        double l11 = sqrt(A11), l21 = A12 / l11, s22 = A22 - l21 * l21;
+        if (!(s22 > 0.0)) { flags |= OB_PDF_FAILED; break; }
+        double l22 = sqrt(s22);
+        double y1 = b1 / l11, y2 = (b2 - l21 * y1) / l22;
+        double dc = y2 / l22, ds = (y1 - l21 * dc) / l11;
+        int halvings = 0;
+        while (!(sg + ds > 0.0 && c + dc > 0.0) && halvings < 60) {
+            ds *= 0.5;
+            dc *= 0.5;
+            ++halvings;
+        }
+        if (!(sg + ds > 0.0 && c + dc > 0.0)) { flags |= OB_PDF_FAILED; break; }
+        sg += ds;
+        c += dc;
+        if (!isfinite(sg) || !isfinite(c)) { flags |= OB_PDF_FAILED; break; }
+    }
+    double ss = 0.0;
+    for (int i = 0; i < 5; ++i) {
+        double d2 = delta[i] * delta[i];
+        double m = log(c) - 0.5 * (ln2pi + log(sg * sg)) - d2 / (2.0 * sg * sg);
+        ss += (m - lnp[i]) * (m - lnp[i]);
+    }
+    double rms = sqrt(ss / 5.0);
+    if (!isfinite(rms)) flags |= OB_PDF_FAILED;
+    else if (rms > resid_max) flags |= OB_PDF_RESIDUAL;
+    if (sigma_out) *sigma_out = sg;
+    if (c_out) *c_out = c;
+    if (rms_out) *rms_out = rms;
+    if (flags_out) *flags_out = flags;
+    double s = (flags != 0) ? tau : (sg < tau ? sg : tau);
+    return s * s;
+}
+
+/* ------------------------------------------------------------------ */
+/* posterior (Eq. 5, 6) and coarse-to-fine propagation (Eq. 10, 11)     */
+/* ------------------------------------------------------------------ */
+
+/* Window posterior of the converged estimate: with the Boltzmann prior of
+ * Eq. 6, p_i = exp(-E_i / (2 sigma_r^2 s^2)) for the s = 5 window samples,
+ * and Eq. 5 with r = 1:  pi_k = p_0 / sum_i p_i. */
+void ob_posterior(const ob_params *p, int level, ob_patch *pt, int n, double sigma_r,
+                  const double *Qc, int wc, int hc, const int *ox, const int *oy,
+                  int npx)
+{
+    const double s = 5.0;
+    const double scale = 2.0 * sigma_r * sigma_r * s * s;
+    const double wl = ob_gamma_weight(level, p->levels);
+    const double tau0 = search_radius(p);
+    double delta[5];
+    ob_window_offsets(p->window_step, delta);
+    for (int k = 0; k < n; ++k) {
+        ob_patch *q = &pt[k];
+        q->pi = q->rho = q->sig2 = 0.0;
+        q->pdf_flags = 0;
+        if (q->flags != 0) continue;
+        double e[5], Z = 0.0;
+        for (int i = 0; i < 5; ++i) {
+            e[i] = -(q->E[i] - q->E[0]) / scale; /* ln p_i - ln p_0 */
+            Z += exp(e[i]);
+        }
+        q->pi = 1.0 / Z;
+        if (p->use_c2f) {
+            /* rho = Gamma_n pi + propagated probability of the coarser levels,
+             * read from the fused coarse probability map at the patch centre
+             * (reading of Eq. 10: a superposition over levels) */
+            double prop = 0.0;
+            if (Qc) {
+                double cx = ox[k % npx] + (p->patch - 1) / 2.0;
+                double cy = oy[k / npx] + (p->patch - 1) / 2.0;
+                prop = coarse_lookup(Qc, wc, hc, cx, cy);
+            }
+            q->rho = wl * q->pi + prop;
+        } else {
+            q->rho = q->pi;
+        }
+        if (level == 0 && p->variance) {
+            double lnp[5], lnZ = log(Z);
+            for (int i = 0; i < 5; ++i) lnp[i] = e[i] - lnZ;
+            q->sig2 = ob_pdf_fit(lnp, delta, p->pdf_iters, p->pdf_resid, tau0,
+                                 &q->pdf_flags, NULL, NULL, NULL);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* sGMM kernel (Eq. 8) and fusion (Eq. 12, Eq. 17)                      */
+/* ------------------------------------------------------------------ */
+
+/* M[b][a] = sum over the patch pixels x_i of exp(-|x - x_i|^2 / (2 sigma_s^2))
+ * for x at offset (a, b) inside the patch: Eq. 8 written out literally. */
+void ob_sgmm_table(int P, double sigma_s, double *M)
+{
+    for (int b = 0; b < P; ++b)
+        for (int a = 0; a < P; ++a) {
+            double s = 0.0;
+            for (int j = 0; j < P; ++j)
+                for (int i = 0; i < P; ++i) {
+                    double dx = a - i, dy = b - j;
+                    s += exp(-(dx * dx + dy * dy) / (2.0 * sigma_s * sigma_s));
+                }
+            M[b * P + a] = s;
+        }
+}
+
+/* Fuse the valid patches of one level into dense maps.  For pixel x with
+ * covering valid patches Omega(x): omega_k = rho_k M[x - o_k],
+ * D = sum omega_k d_k / sum omega_k, Q = sum omega_k rho_k / sum omega_k,
+ * V = sum omega_k^2 sigma_k^2 / (sum omega_k)^2.  Pixels with no valid
+ * covering patch take the upsampled coarser disparity (0 at the coarsest
+ * level) and Q = 0, V = 0, and are marked invalid (cnt = 0). */
+void ob_densify(const ob_params *p, const ob_patch *pt, const int *ox, int npx,
+                const int *oy, int npy, int w, int h, const double *Dc, int wc, int hc,
+                double *D, double *Q, double *V, int *cnt)
+{
+    const int P = p->patch;
+    double *M = (double *)malloc(sizeof(double) * P * P);
+    if (p->use_sgmm) {
+        ob_sgmm_table(P, p->sigma_s, M);
+    } else {
+        for (int i = 0; i < P * P; ++i) M[i] = 1.0; /* equal pixel weights */
+    }
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            double sw = 0.0, swd = 0.0, swr = 0.0, sw2s = 0.0;
+            int n = 0;
+            for (int ky = 0; ky < npy; ++ky) {
+                if (!(oy[ky] <= y && y < oy[ky] + P)) continue;
+                for (int kx = 0; kx < npx; ++kx) {
+                    if (!(ox[kx] <= x && x < ox[kx] + P)) continue;
+                    const ob_patch *q = &pt[ky * npx + kx];
+                    if (q->flags != 0) continue;
+                    double om = q->rho * M[(y - oy[ky]) * P + (x - ox[kx])];
+                    sw += om;
+                    swd += om * q->d;
+                    swr += om * q->rho;
+                    sw2s += om * om * q->sig2;
+                    ++n;
+                }
+            }
+            size_t i = (size_t)y * w + x;
+            if (n > 0 && sw > 0.0) {
+                D[i] = swd / sw;
+                Q[i] = swr / sw;
+                if (V) V[i] = sw2s / (sw * sw);
+            } else {
+                D[i] = Dc ? 2.0 * coarse_lookup(Dc, wc, hc, x, y) : 0.0;
+                Q[i] = 0.0;
+                if (V) V[i] = 0.0;
+                n = 0;
+            }
+            if (cnt) cnt[i] = n;
+        }
+    free(M);
+}
+
+/* ------------------------------------------------------------------ */
+/* one level and the whole coarse-to-fine pipeline (Fig. 1)             */
+/* ------------------------------------------------------------------ */
+
+int ob_num_patches(const ob_params *p, int w, int h, int level, int *npx, int *npy)
+{
+    int wl = ob_level_dim(w, level), hl = ob_level_dim(h, level);
+    int a = ob_origins(wl, p->patch, p->stride, NULL);
+    int b = ob_origins(hl, p->patch, p->stride, NULL);
+    if (npx) *npx = a;
+    if (npy) *npy = b;
+    return a * b;
+}
+
+int ob_check(const ob_params *p, int w, int h)
+{
+    if (p->patch < 2 || p->stride < 1 || p->levels < 1 || p->levels > OB_MAX_LEVELS ||
+        p->iters < 0)
+        return 1;
+    int wl = ob_level_dim(w, p->levels - 1), hl = ob_level_dim(h, p->levels - 1);
+    if (wl < p->patch || hl < p->patch || wl < 3 || hl < 3) return 1;
+    return 0;
+}
+
+/* Search all patches of one level given its images and the coarser fused
+ * disparity Dc (NULL at the coarsest level). */
+void ob_search_level(const ob_params *p, const double *L, const double *R, const double *G,
+                     int w, int h, const double *Dc, int wc, int hc, ob_patch *out)
+{
+    int npx, npy;
+    int *ox = (int *)malloc(sizeof(int) * (w + 2));
+    int *oy = (int *)malloc(sizeof(int) * (h + 2));
+    npx = ob_origins(w, p->patch, p->stride, ox);
+    npy = ob_origins(h, p->patch, p->stride, oy);
+    for (int ky = 0; ky < npy; ++ky)
+        for (int kx = 0; kx < npx; ++kx) {
+            double cx = ox[kx] + (p->patch - 1) / 2.0, cy = oy[ky] + (p->patch - 1) / 2.0;
+            double dinit = Dc ? 2.0 * coarse_lookup(Dc, wc, hc, cx, cy) : 0.0;
+            ob_search_patch(p, L, R, G, w, h, ox[kx], oy[ky], dinit, &out[ky * npx + kx]);
+        }
+    free(ox);
+    free(oy);
+}
+
+/* Full BDIS on one pair of level-0 images (values already in the storage
+ * type; 8-bit inputs are exact in every storage type).
+ * Outputs (w*h each): disp (NaN where invalid), var (NaN where invalid or
+ * variance off; may be NULL), valid (0/1). */
+int ob_match(const ob_params *p, const double *L0, const double *R0, int w, int h,
+             double *disp, double *var, uint8_t *valid, ob_trace *tr)
+{
+    if (ob_check(p, w, h)) return 1;
+    const int NL = p->levels;
+    double *Lv[OB_MAX_LEVELS], *Rv[OB_MAX_LEVELS], *Gv[OB_MAX_LEVELS];
+    int W[OB_MAX_LEVELS], Hh[OB_MAX_LEVELS];
+    for (int l = 0; l < NL; ++l) {
+        W[l] = ob_level_dim(w, l);
+        Hh[l] = ob_level_dim(h, l);
+        size_t n = (size_t)W[l] * Hh[l];
+        Lv[l] = (double *)malloc(sizeof(double) * n);
+        Rv[l] = (double *)malloc(sizeof(double) * n);
+        Gv[l] = (double *)malloc(sizeof(double) * n);
+    }
+    memcpy(Lv[0], L0, sizeof(double) * w * h);
+    memcpy(Rv[0], R0, sizeof(double) * w * h);
+    for (int l = 0; l + 1 < NL; ++l) {
+        ob_pyr_down(Lv[l], W[l], Hh[l], Lv[l + 1], p->storage);
+        ob_pyr_down(Rv[l], W[l], Hh[l], Rv[l + 1], p->storage);
+    }
+    for (int l = 0; l < NL; ++l) ob_sobel_x(Lv[l], W[l], Hh[l], Gv[l], p->storage);
+
+    double *Dprev = NULL, *Qprev = NULL;
+    int wprev = 0, hprev = 0;
+    for (int l = NL - 1; l >= 0; --l) {
+        const int wl = W[l], hl = Hh[l];
+        int *ox = (int *)malloc(sizeof(int) * (wl + 2));
+        int *oy = (int *)malloc(sizeof(int) * (hl + 2));
+        int npx = ob_origins(wl, p->patch, p->stride, ox);
+        int npy = ob_origins(hl, p->patch, p->stride, oy);
+        int np = npx * npy;
+        ob_patch *pt = (ob_patch *)calloc((size_t)np, sizeof(ob_patch));
+        ob_search_level(p, Lv[l], Rv[l], Gv[l], wl, hl, Dprev, wprev, hprev, pt);
+        double sr = ob_sigma_r(p, pt, np);
+        ob_posterior(p, l, pt, np, sr, Qprev, wprev, hprev, ox, oy, npx);
+        size_t n = (size_t)wl * hl;
+        double *D = (double *)malloc(sizeof(double) * n);
+        double *Q = (double *)malloc(sizeof(double) * n);
+        double *V = (l == 0) ? (double *)malloc(sizeof(double) * n) : NULL;
+        int *cnt = (int *)malloc(sizeof(int) * n);
+        ob_densify(p, pt, ox, npx, oy, npy, wl, hl, Dprev, wprev, hprev, D, Q, V, cnt);
+        if (tr) {
+            tr->sigma_r[l] = sr;
+            if (tr->patches[l]) memcpy(tr->patches[l], pt, sizeof(ob_patch) * np);
+            if (tr->D[l]) memcpy(tr->D[l], D, sizeof(double) * n);
+            if (tr->Q[l]) memcpy(tr->Q[l], Q, sizeof(double) * n);
+            if (tr->L[l]) memcpy(tr->L[l], Lv[l], sizeof(double) * n);
+            if (tr->R[l]) memcpy(tr->R[l], Rv[l], sizeof(double) * n);
+            if (tr->G[l]) memcpy(tr->G[l], Gv[l], sizeof(double) * n);
+        }
+        if (l == 0) {
+            /* finest level: a pixel is valid iff it has a valid covering
+             * patch and its fused probability reaches the pixel threshold */
+            for (size_t i = 0; i < n; ++i) {
+                int ok = cnt[i] > 0 && Q[i] >= p->pix_thresh;
+                valid[i] = (uint8_t)ok;
+                disp[i] = ok ? D[i] : NAN;
+                if (var) var[i] = (ok && p->variance) ? V[i] : NAN;
+            }
+        }
+        free(Dprev);
+        free(Qprev);
+        free(V);
+        free(cnt);
+        free(pt);
+        free(ox);
+        free(oy);
+        Dprev = D;
+        Qprev = Q;
+        wprev = wl;
+        hprev = hl;
+    }
+    free(Dprev);
+    free(Qprev);
+    for (int l = 0; l < NL; ++l) {
+        free(Lv[l]);
+        free(Rv[l]);
+        free(Gv[l]);
+    }
+    return 0;
+}
+
+/* 8-bit entry point: converts to double and runs ob_match. */
+int ob_match_u8(const ob_params *p, const uint8_t *L, const uint8_t *R, int w, int h,
+                double *disp, double *var, uint8_t *valid, ob_trace *tr)
+{
+    size_t n = (size_t)w * h;
+    double *a = (double *)malloc(sizeof(double) * n), *b = (double *)malloc(sizeof(double) * n);
+    for (size_t i = 0; i < n; ++i) {
+        a[i] = L[i];
+        b[i] = R[i];
+    }
+    int rc = ob_match(p, a, b, w, h, disp, var, valid, tr);
+    free(a);
+    free(b);
+    return rc;
+}
+
+int ob_sizeof_patch(void) { return (int)sizeof(ob_patch); }
+int ob_sizeof_params(void) { return (int)sizeof(ob_params); }
