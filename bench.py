@@ -1,0 +1,510 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the BDIS hot path on GB300.
+
+Default workload: one 640x480 surgical-like stereo pair (generator G2), 12x12
+patches at stride 6, 4 pyramid levels, 8 Gauss-Newton iterations, variance
+(PDF) estimate on, FP32 pyramids.  One step = one full coarse-to-fine pass
+(pyramid, search, sigma_r, posterior + PDF, densify at every level) through
+the C ABI.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 is launched with torch.distributed.run; every rank processes its own
+independent pair (seed = rank), so the work shards with no collective in the
+data path (weak scaling); only the timing uses a barrier and a max-reduce.
+The reference arm (--impl reference) is the FP64 CPU oracle timed on the host
+cores on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "dense-disparity Mpix/s (fps @640x480) fwd and fwd+bwd, batched vs plain, at oracle match"
+UNIT = "Mpix/s"
+WORKLOAD = dict(workload="plain_640x480_var", generator="G2 surgical-like (seed = rank)",
+                w=640, h=480, patch=12, stride=6, levels=4, iters=8, variance=1, storage="f32")
+PARAMS = dict(patch=12, stride=6, levels=4, iters=8, variance=1, storage="f32")
+BATCH_PARAMS = dict(patch=8, stride=4, levels=3, iters=8, variance=0, storage="f16")
+L2_FLUSH_BYTES = 256 << 20   # larger than the 129 MB L2
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws, backend):
+    if ws > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group(backend=backend)
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, ws, device=None):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.index = str(device)
+        try:
+            import torch
+            u = str(torch.cuda.get_device_properties(device).uuid)
+            self.index = u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:
+            pass
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", self.index, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        time.sleep(0.3)
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def stop(self):
+        if self.p is not None:
+            time.sleep(0.2)
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "samples": 0}
+        loaded = [r for r in rows if r[4].isdigit() and int(r[4]) > 0] or rows
+        sm = [float(r[1]) for r in loaded if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in loaded for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(loaded)}
+
+
+# ---------------------------------------------------------------- roofline bookkeeping
+
+def level_geometry(w, h, P, S, L):
+    out = []
+    for l in range(L):
+        wl, hl = w, h
+        for _ in range(l):
+            wl, hl = (wl + 1) // 2, (hl + 1) // 2
+        nx = (wl - P) // S + 1 + (1 if (wl - P) % S else 0)
+        ny = (hl - P) // S + 1 + (1 if (hl - P) % S else 0)
+        out.append((wl, hl, nx * ny))
+    return out
+
+
+def algorithmic_bytes(kernel, w, h, prm):
+    """Bytes one pass of `kernel` over all levels must move (per pair).
+    Image element sizes: level 0 u8, levels >= 1 and gradients the storage
+    type; patch record 64 B; fusion record 16 B; fused maps 8 B/px."""
+    P, S, L = prm["patch"], prm["stride"], prm["levels"]
+    b = 2 if prm["storage"] == "f16" else 4
+    geo = level_geometry(w, h, P, S, L)
+    tot = 0
+    for l, (wl, hl, npch) in enumerate(geo):
+        img = 1 if l == 0 else b
+        px = wl * hl
+        if kernel == "pyramid":
+            nxt = geo[l + 1][0] * geo[l + 1][1] if l + 1 < L else 0
+            tot += 2 * img * px + b * px + 2 * b * nxt     # read L, R; write G, next L, R
+        elif kernel == "search":
+            coarse = 4 * geo[l + 1][0] * geo[l + 1][1] if l + 1 < L else 0
+            tot += 2 * img * px + b * px + coarse + 64 * npch  # read L, R, G, coarse D; write records
+        elif kernel == "posterior":
+            coarse = 4 * geo[l + 1][0] * geo[l + 1][1] if l + 1 < L else 0
+            tot += 64 * npch + coarse + 16 * npch + 16 * npch  # read/update records, write fuse
+        elif kernel == "densify":
+            out = 9 if l == 0 else 8
+            coarse = 4 * geo[l + 1][0] * geo[l + 1][1] if l + 1 < L else 0
+            tot += 16 * npch + coarse + out * px
+        elif kernel == "sigma_r":
+            tot += 64 * npch
+    return tot
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------- CPU baseline (oracle)
+
+def cpu_baseline(pair, prm, budget_s=12.0, gpu_out=None):
+    """The FP64 C oracle as it stands, one thread, on full pairs of the
+    workload until `budget_s` of CPU time is spent (at least one run)."""
+    import numpy as np
+
+    import oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    op = oracle.make_params(**{k: v for k, v in prm.items()})
+    oracle.build()
+    runs, t0 = 0, time.perf_counter()
+    first = None
+    while True:
+        out = oracle.match(op, pair.left, pair.right, trace=gpu_out is not None and runs == 0)
+        first = first or out
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or runs >= 200:
+            break
+    px = pair.left.size * runs
+    res = {"value": round(px / el / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{runs} full {pair.left.shape[1]}x{pair.left.shape[0]} pairs "
+                     f"(all {prm['levels']} levels, variance on), FP64 C, 1 thread, {el:.1f} s"}
+    if gpu_out is not None:
+        from parity import compare_outputs
+        disp, var, valid, rec0, gp = gpu_out
+        m = compare_outputs(gp, first, disp, var, valid, rec0)
+        res["parity_vs_gpu"] = {k: (round(v, 8) if isinstance(v, float) else v) for k, v in m.items()}
+    return res
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    pair = synth.config_pair("plain_640x480_var", seed=0)
+    op = oracle.make_params(**PARAMS)
+    oracle.build()
+    t = time.perf_counter()
+    oracle.match(op, pair.left, pair.right)
+    t_full = time.perf_counter() - t
+    # each step: a bounded sample of the workload (a full-width crop of the
+    # pair) so that warm-up + timed steps stay near one minute in total
+    budget = 60.0 / max(1, args.steps + args.warmup)
+    hmin = 12 * 8 + 12
+    hc = 480 if t_full <= budget else max(hmin, int(480 * budget / t_full) // 8 * 8)
+    L, R = pair.left[:hc].copy(), pair.right[:hc].copy()
+    for _ in range(max(0, args.warmup - 1)):
+        oracle.match(op, L, R)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.match(op, L, R)
+        times.append(time.perf_counter() - t)
+    tot = sum(times)
+    px = L.size * args.steps
+    val = px / tot / 1e6
+    sample = (f"each step a 640x{hc} crop of the 640x480 pair (full coarse-to-fine, variance on); "
+              f"FP64 C oracle, 1 thread")
+    line = {"impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(tot / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, crop_h=hc),
+            "cpu_baseline": {"value": round(val, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(val, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- ours
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import paper_2205_03133_gb300 as bd
+    import synth
+    from paper_2205_03133_gb300 import build as _build
+    _build.build()
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    init_dist(ws, "nccl")
+    dev = torch.device("cuda", local)
+    B = bd.B
+
+    pair = synth.config_pair("plain_640x480_var", seed=rank)
+    h, w = pair.left.shape
+    Ld = torch.from_numpy(pair.left).to(dev)
+    Rd = torch.from_numpy(pair.right).to(dev)
+    out = (torch.empty((h, w), dtype=torch.float32, device=dev),
+           torch.empty((h, w), dtype=torch.float32, device=dev),
+           torch.empty((h, w), dtype=torch.uint8, device=dev))
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    m = bd.BDIS(**PARAMS)
+    launches_per_step = 5 * PARAMS["levels"]
+
+    def step():
+        m.match(Ld, Rd, out=out, stream=stream)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            step()
+    torch.cuda.synchronize()
+
+    # ---- timed: device time of exactly K steps, L2 flushed between steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.mark("t0")
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks.mark("t1")
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    dev_ms_max = max_over_ranks(dev_ms, ws, dev)
+    value = ws * w * h * args.steps / (dev_ms_max / 1e3) / 1e6
+
+    # ---- per-kernel event times (profiling pass, plain launches)
+    B.lib().bdis_set_option(m._h, B.OPT_PROFILE, 1)
+    prof = B.bdis_profile()
+    B.lib().bdis_get_profile(m._h, prof, 1)
+    n_prof = max(20, min(args.steps, 200))
+    with torch.cuda.stream(stream):
+        for _ in range(n_prof):
+            flush.zero_()
+            step()
+    torch.cuda.synchronize()
+    B.check(B.lib().bdis_get_profile(m._h, prof, 1), m._h)
+    B.lib().bdis_set_option(m._h, B.OPT_PROFILE, 0)
+    kernels = {}
+    for i, name in enumerate(B.KERNEL_NAMES):
+        if prof.launches[i]:
+            kernels[name] = {"launches_per_step": prof.launches[i] // n_prof,
+                             "ms_per_step": prof.ms[i] / n_prof,
+                             "avg_launch_us": prof.ms[i] / prof.launches[i] * 1e3}
+    tot_k = sum(k["ms_per_step"] for k in kernels.values())
+    for k in kernels.values():
+        k["share"] = round(k["ms_per_step"] / tot_k, 4)
+        k["ms_per_step"] = round(k["ms_per_step"], 5)
+        k["avg_launch_us"] = round(k["avg_launch_us"], 3)
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
+    peaks = measured_peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    per_step_bytes = algorithmic_bytes(dom, w, h, PARAMS)
+    achieved = per_step_bytes / (kernels[dom]["ms_per_step"] / 1e3) / 1e9
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 2),
+                "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 5),
+                "traffic": None,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
+                "algorithmic_bytes_per_step": per_step_bytes,
+                "launches_per_step": kernels[dom]["launches_per_step"]}
+
+    # ---- end to end through the host-buffer entry point (pinned buffers)
+    hL = torch.from_numpy(pair.left).pin_memory()
+    hR = torch.from_numpy(pair.right).pin_memory()
+    hD = torch.empty((h, w), dtype=torch.float32).pin_memory()
+    hV = torch.empty((h, w), dtype=torch.float32).pin_memory()
+    hM = torch.empty((h, w), dtype=torch.uint8).pin_memory()
+    sh = B.C.c_void_p(stream.cuda_stream)
+    e2e_steps = max(10, min(args.steps, 200))
+
+    def hstep():
+        m.match_host_ptr(hL.data_ptr(), hR.data_ptr(), w, h, hD.data_ptr(), hV.data_ptr(),
+                         hM.data_ptr(), sh)
+
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            flush.zero_()
+            hstep()
+    torch.cuda.synchronize()
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(e2e_steps)]
+    with torch.cuda.stream(stream):
+        for k in range(e2e_steps):
+            flush.zero_()
+            ev2[k][0].record(stream)
+            hstep()
+            ev2[k][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev2), ws, dev)
+    e2e = {"value": round(ws * w * h * e2e_steps / (e2e_ms / 1e3) / 1e6, 3), "unit": UNIT,
+           "h2d_bytes_per_step": 2 * w * h, "d2h_bytes_per_step": (4 + 4 + 1) * w * h,
+           "steps": e2e_steps, "api": "bdis_match_host (pinned host buffers)"}
+    clock_info = clocks.stop()
+
+    # ---- batched form: 64 uneven pairs, one launch per stage per level
+    batched = None
+    if not args.no_batched:
+        batched = bench_batched(bd, dev, stream, flush, rank, ws)
+
+    result = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu:
+            rec0 = None
+            with torch.cuda.stream(stream):
+                step()
+            torch.cuda.synchronize()
+            rec0 = m.level_view(0, 0)["patches"]
+            gpu_out = (out[0].cpu().numpy(), out[1].cpu().numpy(), out[2].cpu().numpy(), rec0,
+                       m.params)
+            cpu = cpu_baseline(pair, PARAMS, gpu_out=gpu_out)
+        result = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dev_ms_max / args.steps, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "fps": round(value / (w * h / 1e6), 2),
+            "config": dict(WORKLOAD, parallelism=f"replicas x{ws} (one pair per rank)",
+                           l2="flushed between timed steps (256 MiB write, outside the events)",
+                           graph="CUDA graph replay of the per-call launch sequence"),
+            "gpu_launches": launches_per_step * args.steps,
+            "kernels": kernels,
+            "roofline": roofline,
+            "e2e": e2e,
+            "clocks": clock_info,
+            "cpu_baseline": cpu,
+            "batched": batched,
+            "fwd_bwd": None,
+            "paper_context": "BDIS(VAR) 0.072 s per 640x480 frame (4.27 Mpix/s) on one i5-9400 "
+                             "core, finest scale 2^1 (Table VIII); 17 Hz claim (abstract)",
+        }
+        print(json.dumps(result))
+    m.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def bench_batched(bd, dev, stream, flush, rank, ws, steps=10):
+    """64 pairs of uneven sizes (24x640x480, 16x960x540, 16x1280x720,
+    8x1920x1080; G1 generator, seeds 64*rank + i) in one batched call per
+    step, against 64 sequential plain calls."""
+    import torch
+
+    import synth
+    sizes = synth.batch_sizes_uneven()
+    Ls, Rs, outs = [], [], []
+    for i, (w, h) in enumerate(sizes):
+        p = synth.g1_pair(w, h, 64 * rank + i)
+        Ls.append(torch.from_numpy(p.left).to(dev))
+        Rs.append(torch.from_numpy(p.right).to(dev))
+        outs.append((torch.empty((h, w), dtype=torch.float32, device=dev), None,
+                     torch.empty((h, w), dtype=torch.uint8, device=dev)))
+    px = sum(w * h for w, h in sizes)
+    m = bd.BDIS(**BATCH_PARAMS)
+    mp = bd.BDIS(**BATCH_PARAMS)
+
+    def run(fn, n):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(n)]
+        with torch.cuda.stream(stream):
+            for k in range(n):
+                flush.zero_()
+                ev[k][0].record(stream)
+                fn()
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / n
+
+    batched_fn = lambda: m.match_batched(Ls, Rs, outs=outs, stream=stream)  # noqa: E731
+
+    def plain_fn():
+        for i in range(len(sizes)):
+            mp.match(Ls[i], Rs[i], out=outs[i], stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            batched_fn()
+            plain_fn()
+    torch.cuda.synchronize()
+    t_b = run(batched_fn, steps)
+    t_p = run(plain_fn, max(3, steps // 2))
+    t_b = max_over_ranks(t_b, ws, dev)
+    t_p = max_over_ranks(t_p, ws, dev)
+    bd.B.lib().bdis_set_option(m._h, bd.B.OPT_PROFILE, 1)
+    prof = bd.B.bdis_profile()
+    bd.B.lib().bdis_get_profile(m._h, prof, 1)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            flush.zero_()
+            batched_fn()
+    torch.cuda.synchronize()
+    bd.B.lib().bdis_get_profile(m._h, prof, 1)
+    kern = {n: round(prof.ms[i] / 3, 4) for i, n in enumerate(bd.B.KERNEL_NAMES) if prof.launches[i]}
+    m.close()
+    mp.close()
+    return {"workload": "64 uneven pairs (24x640x480, 16x960x540, 16x1280x720, 8x1920x1080), "
+                        "P8 S4 L3, 8 iters, fp16 pyramids",
+            "value": round(ws * px / (t_b / 1e3) / 1e6, 2), "unit": UNIT,
+            "ms_per_batch": round(t_b, 4),
+            "plain_sequential_ms": round(t_p, 4),
+            "plain_sequential_value": round(ws * px / (t_p / 1e3) / 1e6, 2),
+            "speedup_vs_plain": round(t_p / t_b, 3), "kernel_ms_per_batch": kern}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,214 @@
+/*
+ * bdis.h -- C ABI of the GB300 (sm_103a) BDIS library (libbdis.so).
+ *
+ * BDIS (Bayesian Dense Inverse Search, arXiv 2205.03133) estimates a dense
+ * disparity map, and optionally a per-pixel disparity variance, for a
+ * rectified stereo pair.  Per pyramid level, coarsest first (Fig. 1):
+ *   - image pyramid and left x-gradient (Sec. III-A: the inverse-
+ *     compositional Jacobian is computed once);
+ *   - per-patch 1D inverse-compositional Gauss-Newton search (Eq. 1);
+ *   - window energies, rejection of saddle / unconverged patches, dynamic
+ *     sigma_r and the window posterior (Sec. III-B, Eq. 4-6);
+ *   - coarse-to-fine probability propagation (Sec. III-D, Eq. 10-11);
+ *   - sGMM-weighted dense fusion (Sec. III-C, Eq. 8-9, Eq. 12);
+ *   - optional per-patch PDF fit and pixel variance (Sec. III-E, Eq. 14-17).
+ *
+ * Conventions shared by every entry point
+ *   - Disparity d >= 0 with I_r(x - d, y) ~= I_l(x, y) (the paper's u = -d).
+ *   - Images are 8-bit grayscale, row-major, `pitch` bytes between rows
+ *     (pitch >= w).  Outputs are dense row-major float/uint8 arrays of w*h.
+ *   - Device pointers are caller-owned CUDA device memory on the current
+ *     device; the library never frees them.  `stream` is a cudaStream_t
+ *     (NULL = legacy default stream).  Device calls are asynchronous on that
+ *     stream: outputs are ready when the stream reaches that point.
+ *   - Errors are returned as bdis_status; nothing crosses the ABI as an
+ *     exception.  Arguments are validated before any launch; on an error no
+ *     output is written.  bdis_last_error() gives a one-line reason.
+ *   - Pixels with no valid estimate get disp = NaN, var = NaN, valid = 0.
+ *   - A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef BDIS_H
+#define BDIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BDIS_OK = 0,
+    BDIS_EINVAL = 1,        /* bad argument (null pointer, size, parameter) */
+    BDIS_ENOMEM = 2,        /* device or pinned host allocation failed       */
+    BDIS_ECUDA = 3,         /* a CUDA runtime call or a launch failed        */
+    BDIS_EUNSUPPORTED = 4   /* valid request outside what this build handles */
+} bdis_status;
+
+/* Storage type of the pyramid levels 1..L-1 and of the x-gradient images.
+ * Level 0 is the caller's 8-bit image.  Arithmetic is FP32 in every case. */
+typedef enum { BDIS_STORE_F32 = 0, BDIS_STORE_F16 = 1 } bdis_storage;
+
+/* Reading of the dynamic scale sigma_r^(n) (text after Eq. 6):
+ * POOLED  sqrt(sum_valid E_k(0) / (N_valid P^2)) -- the default;
+ * LITERAL population std over valid patches of E_k(0);
+ * FIXED   sigma_r_fixed (the ablation of Table VII uses 8). */
+typedef enum {
+    BDIS_SIGMA_R_POOLED = 0,
+    BDIS_SIGMA_R_LITERAL = 1,
+    BDIS_SIGMA_R_FIXED = 2
+} bdis_sigma_r_mode;
+
+typedef struct {
+    int patch;            /* P: patch side (px), 4..16                       */
+    int stride;           /* S: patch stride (px), 1..P                      */
+    int levels;           /* L: pyramid levels incl. full resolution, 1..8   */
+    int iters;            /* Gauss-Newton iterations per patch (fixed), >= 0 */
+    float sigma_s;        /* sGMM spatial sigma (Eq. 8), paper: 4            */
+    float window_step;    /* window offsets {0, +-h, +-2h} (Sec. IV-A: 0.5)  */
+    float conv_eps;       /* max |last GN update| of a kept patch, 0.05      */
+    float valid_gamma;    /* min in-image sample ratio of a kept patch, 0.75 */
+    float pix_thresh;     /* min fused probability of a valid pixel, 0.15    */
+    float search_radius;  /* tau: max |d - d_init| (px at the level); <= 0: P */
+    int sigma_r_mode;     /* bdis_sigma_r_mode                               */
+    float sigma_r_floor;  /* lower bound of sigma_r (DN), default 0.5        */
+    float sigma_r_fixed;  /* value for BDIS_SIGMA_R_FIXED, default 8         */
+    int variance;         /* 1: per-patch PDF fit + pixel variance (Eq. 14-17) */
+    int pdf_iters;        /* GN iterations of the PDF fit (Sec. III-E: 10)   */
+    float pdf_resid;      /* max RMS log residual of the fit (Sec. III-E: 0.1) */
+    int storage;          /* bdis_storage                                    */
+    float hess_eps;       /* patch rejected as flat if H < hess_eps * P^2    */
+    int use_sgmm;         /* 0: equal pixel weights (ablation, Table VII)    */
+    int use_c2f;          /* 0: no coarse-to-fine probability (ablation)     */
+} bdis_params;
+
+typedef struct bdis_handle bdis_handle;
+
+/* One stereo pair of a batch; all pointers are device memory. */
+typedef struct {
+    const uint8_t *left, *right;  /* w x h, `pitch` bytes per row           */
+    int w, h, pitch;
+    float *disp;                  /* w*h out                                 */
+    float *var;                   /* w*h out, may be NULL (or variance off)  */
+    uint8_t *valid;               /* w*h out                                 */
+} bdis_pair;
+
+/* Per-call counters of the last completed call on a handle. */
+typedef struct {
+    int levels, pairs;
+    int patches[8];          /* patches searched per level (all pairs)       */
+    int valid_patches[8];    /* patches kept per level (all pairs)           */
+    float sigma_r[8];        /* sigma_r per level of the first pair           */
+    long long valid_pixels;  /* valid output pixels (all pairs)              */
+} bdis_stats;
+
+/* Fills `p` with the defaults (8x8 patches, stride 4, 3 levels, 8 iterations,
+ * paper values from Sec. IV-A / III-E for the rest, FP32 pyramids). */
+void bdis_default_params(bdis_params *p);
+
+/* Validates `p` and creates a handle.  The handle owns a device scratch
+ * arena (pyramids, patch records, coarse maps) that grows on demand and is
+ * freed by bdis_destroy.  No CUDA call is made here. */
+bdis_status bdis_create(const bdis_params *p, bdis_handle **out);
+void bdis_destroy(bdis_handle *h);
+const char *bdis_strerror(bdis_status s);
+/* One-line description of the last error on this handle (never NULL). */
+const char *bdis_last_error(const bdis_handle *h);
+/* Copies the handle's parameters (with search_radius resolved). */
+bdis_status bdis_get_params(const bdis_handle *h, bdis_params *out);
+
+/* Dense BDIS on one pair of device images (the whole pipeline, Fig. 1).
+ * w, h must leave the coarsest level at least `patch` pixels per axis:
+ * ceil(w / 2^(L-1)) >= P and ceil(h / 2^(L-1)) >= P.  `var` may be NULL;
+ * it is written only when params.variance is 1.  Asynchronous on `stream`. */
+bdis_status bdis_match(bdis_handle *h, const uint8_t *left, const uint8_t *right, int w,
+                       int hgt, int pitch, float *disp, float *var, uint8_t *valid,
+                       void *stream);
+
+/* Same computation with HOST buffers: the inputs are copied to the device,
+ * the pipeline runs, and the outputs are copied back, all on `stream`; the
+ * call returns after the stream has finished (host outputs are ready).
+ * Pinned (page-locked) host memory gives the fastest copies. */
+bdis_status bdis_match_host(bdis_handle *h, const uint8_t *left, const uint8_t *right, int w,
+                            int hgt, int pitch, float *disp, float *var, uint8_t *valid,
+                            void *stream);
+
+/* Many pairs of possibly different sizes in one pass: every stage runs as
+ * one launch per pyramid level over all pairs (work decomposed through a
+ * per-level descriptor table).  All pairs share the handle's parameters.
+ * Results are identical to calling bdis_match on each pair. */
+bdis_status bdis_match_batched(bdis_handle *h, int n, const bdis_pair *pairs, void *stream);
+
+/* Counters of the last call (synchronises `stream` to read them). */
+bdis_status bdis_get_stats(bdis_handle *h, bdis_stats *out, void *stream);
+
+/* ---- execution options ---- */
+
+typedef enum {
+    /* 1 (default): when a call repeats the previous call's geometry and
+     * pointers on a non-default stream, replay the captured CUDA graph of its
+     * launch sequence instead of launching each kernel; 0: plain launches. */
+    BDIS_OPT_GRAPH = 1,
+    /* 1: bracket every kernel launch with CUDA events on the call's stream
+     * and accumulate per-kernel device time (graph replay is off while on). */
+    BDIS_OPT_PROFILE = 2
+} bdis_option;
+
+bdis_status bdis_set_option(bdis_handle *h, int option, int value);
+
+enum { BDIS_K_PYRAMID = 0, BDIS_K_SEARCH = 1, BDIS_K_SIGMA_R = 2, BDIS_K_POSTERIOR = 3,
+       BDIS_K_DENSIFY = 4, BDIS_K_COUNT = 5 };
+
+typedef struct {
+    int launches[BDIS_K_COUNT];   /* launches per kernel since the last reset */
+    double ms[BDIS_K_COUNT];      /* summed CUDA-event time per kernel (ms)   */
+} bdis_profile;
+
+/* Per-kernel launch counts and event times accumulated while
+ * BDIS_OPT_PROFILE is on (waits for the recorded events); reset != 0 clears. */
+bdis_status bdis_get_profile(bdis_handle *h, bdis_profile *out, int reset);
+
+/* ---- inspection of the last call's intermediate buffers (tests) ---- */
+
+/* Per-patch record, as written by the search and posterior stages. */
+typedef struct {
+    float d, dinit, dlast, H;      /* estimate, initial value, last GN step, Hessian */
+    float E[5];                    /* E[0] = E(0); E[k] = E(delta_k) - E(0) for the
+                                      window offsets delta = {-h, +h, -2h, +2h}        */
+    float cT;                      /* sum of centred gradient x template             */
+    uint32_t flags;                /* rejection bits (0 = kept), see BDIS_F_*         */
+    int32_t nout;                  /* samples outside the image at the estimate      */
+    float pi, rho, sig2;           /* window posterior, propagated probability, var  */
+    uint32_t pdf_flags;            /* PDF-fit exception bits, see BDIS_PDF_*          */
+} bdis_patch_record;
+
+enum {
+    BDIS_F_FLAT = 1u << 0, BDIS_F_UNCONVERGED = 1u << 1, BDIS_F_MOVED = 1u << 2,
+    BDIS_F_OUTSIDE = 1u << 3, BDIS_F_SADDLE = 1u << 4, BDIS_F_NONFINITE = 1u << 5
+};
+enum { BDIS_PDF_NOT_PEAK = 1u << 0, BDIS_PDF_FAILED = 1u << 1, BDIS_PDF_RESIDUAL = 1u << 2 };
+
+typedef struct {
+    int w, h;                 /* level size                                    */
+    int npx, npy;             /* patch grid                                    */
+    int image_pitch;          /* elements per row of left/right                */
+    int grad_pitch;           /* elements per row of grad                      */
+    int storage;              /* element type of left/right/grad (level 0: u8) */
+    const void *left, *right, *grad;   /* device pointers (level 0: caller's)  */
+    const bdis_patch_record *records;  /* npx*npy records, row-major           */
+    const float *D, *Q;       /* fused maps (w*h), NULL at level 0             */
+    const float *sigma_r;     /* one float                                     */
+} bdis_level_view;
+
+/* Device pointers into the handle's arena for (pair, level) of the last call.
+ * Valid until the next call on the handle. */
+bdis_status bdis_level_view_get(const bdis_handle *h, int pair, int level,
+                                bdis_level_view *out);
+
+/* cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, stream) + sync. */
+bdis_status bdis_copy(void *dst, const void *src, size_t bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BDIS_H */

@@ -1,0 +1,175 @@
+"""GB300 (sm_103a) BDIS -- Bayesian Dense Inverse Search for rectified stereo
+(arXiv 2205.03133) behind the C ABI of ``include/bdis.h``.
+
+PyTorch supplies device memory and streams; every step of the pipeline runs
+in the library's CUDA kernels.  Example::
+
+    import torch, paper_2205_03133_gb300 as bd
+    m = bd.BDIS(patch=12, stride=6, levels=4, variance=1)
+    disp, var, valid = m.match(left_u8_cuda, right_u8_cuda)
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _binding as B
+from ._binding import BdisError
+
+__all__ = ["BDIS", "BdisError", "default_params", "B"]
+
+_STORAGE = {"f32": B.STORE_F32, "f16": B.STORE_F16}
+_SIGMA_R = {"pooled": B.SIGMA_R_POOLED, "literal": B.SIGMA_R_LITERAL, "fixed": B.SIGMA_R_FIXED}
+
+
+def default_params() -> B.bdis_params:
+    p = B.bdis_params()
+    B.lib().bdis_default_params(C.byref(p))
+    return p
+
+
+def _params(**kw) -> B.bdis_params:
+    p = default_params()
+    for k, v in kw.items():
+        if k == "storage" and isinstance(v, str):
+            v = _STORAGE[v]
+        if k == "sigma_r_mode" and isinstance(v, str):
+            v = _SIGMA_R[v]
+        if not hasattr(p, k):
+            raise TypeError(f"unknown BDIS parameter {k!r}")
+        setattr(p, k, v)
+    return p
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class BDIS:
+    """One library handle (owns a device scratch arena)."""
+
+    def __init__(self, **params):
+        self.params = _params(**params)
+        h = C.c_void_p()
+        B.check(B.lib().bdis_create(C.byref(self.params), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            B.lib().bdis_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ device API
+    def match(self, left, right, out=None, stream=None):
+        """left, right: (h, w) uint8 CUDA tensors (row stride >= w).
+        Returns (disp float32, var float32 or None, valid uint8) CUDA tensors."""
+        import torch
+        assert left.dtype == torch.uint8 and right.dtype == torch.uint8
+        assert left.is_cuda and right.is_cuda and left.shape == right.shape
+        assert left.stride(1) == 1 and right.stride(1) == 1 and left.stride(0) == right.stride(0)
+        h, w = left.shape
+        if out is None:
+            disp = torch.empty((h, w), dtype=torch.float32, device=left.device)
+            var = (torch.empty((h, w), dtype=torch.float32, device=left.device)
+                   if self.params.variance else None)
+            valid = torch.empty((h, w), dtype=torch.uint8, device=left.device)
+        else:
+            disp, var, valid = out
+        st = B.lib().bdis_match(self._h, left.data_ptr(), right.data_ptr(), w, h, left.stride(0),
+                                disp.data_ptr(), var.data_ptr() if var is not None else None,
+                                valid.data_ptr(), _stream_handle(stream))
+        B.check(st, self._h)
+        return disp, var, valid
+
+    def match_batched(self, lefts, rights, outs=None, stream=None):
+        """Lists of (h_i, w_i) uint8 CUDA tensors; returns a list of
+        (disp, var, valid) per pair."""
+        import torch
+        n = len(lefts)
+        arr = (B.bdis_pair * n)()
+        results = []
+        for i, (l, r) in enumerate(zip(lefts, rights)):
+            h, w = l.shape
+            if outs is None:
+                d = torch.empty((h, w), dtype=torch.float32, device=l.device)
+                v = (torch.empty((h, w), dtype=torch.float32, device=l.device)
+                     if self.params.variance else None)
+                m = torch.empty((h, w), dtype=torch.uint8, device=l.device)
+            else:
+                d, v, m = outs[i]
+            arr[i] = B.bdis_pair(l.data_ptr(), r.data_ptr(), w, h, l.stride(0), d.data_ptr(),
+                                 v.data_ptr() if v is not None else None, m.data_ptr())
+            results.append((d, v, m))
+        B.check(B.lib().bdis_match_batched(self._h, n, arr, _stream_handle(stream)), self._h)
+        return results
+
+    # ------------------------------------------------------------ host API
+    def match_host(self, left: np.ndarray, right: np.ndarray, out=None, stream=None):
+        """numpy uint8 (h, w) inputs (ideally pinned); returns numpy outputs."""
+        left = np.ascontiguousarray(left, dtype=np.uint8)
+        right = np.ascontiguousarray(right, dtype=np.uint8)
+        h, w = left.shape
+        if out is None:
+            disp = np.empty((h, w), np.float32)
+            var = np.empty((h, w), np.float32) if self.params.variance else None
+            valid = np.empty((h, w), np.uint8)
+        else:
+            disp, var, valid = out
+        st = B.lib().bdis_match_host(
+            self._h, left.ctypes.data, right.ctypes.data, w, h, w, disp.ctypes.data,
+            var.ctypes.data if var is not None else None, valid.ctypes.data,
+            _stream_handle(stream) if stream is not None else None)
+        B.check(st, self._h)
+        return disp, var, valid
+
+    def match_host_ptr(self, left_ptr, right_ptr, w, h, disp_ptr, var_ptr, valid_ptr, stream):
+        """Raw host-pointer form (pinned torch tensors' data_ptr())."""
+        st = B.lib().bdis_match_host(self._h, left_ptr, right_ptr, w, h, w, disp_ptr, var_ptr,
+                                     valid_ptr, stream)
+        B.check(st, self._h)
+
+    # ------------------------------------------------------------ inspection
+    def stats(self, stream=None) -> dict:
+        s = B.bdis_stats()
+        B.check(B.lib().bdis_get_stats(self._h, C.byref(s), _stream_handle(stream)), self._h)
+        return dict(levels=s.levels, pairs=s.pairs, patches=list(s.patches)[:s.levels],
+                    valid_patches=list(s.valid_patches)[:s.levels],
+                    sigma_r=list(s.sigma_r)[:s.levels], valid_pixels=s.valid_pixels)
+
+    def level_view(self, pair: int, level: int) -> dict:
+        """Copies of the last call's intermediate buffers of (pair, level)."""
+        v = B.bdis_level_view()
+        B.check(B.lib().bdis_level_view_get(self._h, pair, level, C.byref(v)), self._h)
+        out = dict(w=v.w, h=v.h, npx=v.npx, npy=v.npy)
+
+        def cp(ptr, dtype, shape):
+            a = np.empty(shape, dtype=dtype)
+            B.check(B.lib().bdis_copy(a.ctypes.data, ptr, a.nbytes, None))
+            return a
+
+        rec = np.dtype([("d", "f4"), ("dinit", "f4"), ("dlast", "f4"), ("H", "f4"),
+                        ("E", "f4", (5,)), ("cT", "f4"), ("flags", "u4"), ("nout", "i4"),
+                        ("pi", "f4"), ("rho", "f4"), ("sig2", "f4"), ("pdf_flags", "u4")])
+        assert rec.itemsize == C.sizeof(B.bdis_patch_record)
+        out["patches"] = cp(v.records, rec, (v.npy, v.npx))
+        sr = cp(v.sigma_r, np.float32, (1,))
+        out["sigma_r"] = float(sr[0])
+        if level > 0:
+            out["D"] = cp(v.D, np.float32, (v.h, v.w))
+            out["Q"] = cp(v.Q, np.float32, (v.h, v.w))
+            dt = np.float16 if v.storage == B.STORE_F16 else np.float32
+            pitch = v.image_pitch
+            for key, ptr in (("L", v.left), ("R", v.right)):
+                out[key] = cp(ptr, dt, (v.h, pitch))[:, :v.w].astype(np.float64)
+        gdt = np.float16 if self.params.storage == B.STORE_F16 else np.float32
+        out["G"] = cp(v.grad, gdt, (v.h, v.grad_pitch))[:, :v.w].astype(np.float64)
+        return out

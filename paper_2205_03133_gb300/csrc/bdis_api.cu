@@ -1,0 +1,734 @@
+// bdis_api.cu -- host side of libbdis: argument checks, the per-call plan
+// (level geometry, arena layout, per-level descriptor tables), the device
+// scratch arena and the coarse-to-fine launch sequence (Fig. 1 of
+// arXiv 2205.03133: coarsest level first; each level's fused map seeds the
+// next finer level).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "bdis_internal.cuh"
+
+using namespace bdis;
+
+struct bdis_handle {
+    bdis_params p{};
+    std::string err = "no error";
+    // device scratch arena (grows, never shrinks)
+    char *arena = nullptr;
+    size_t arena_cap = 0;
+    // pinned staging for the descriptor upload
+    char *pinned = nullptr;
+    size_t pinned_cap = 0;
+    cudaEvent_t upload_done = nullptr;
+    std::vector<char> last_upload;
+    // the last call's layout (for views and stats)
+    std::vector<LevelDesc> descs;  // [level][pair]
+    int npairs = 0;
+    int levels = 0;
+    int in_type = E_U8;
+    LevelDesc *d_descs = nullptr;
+    size_t smem_prepared = 0;
+    int prepared_P = 0;
+    // CUDA graph of the last launch sequence and the descriptors it bakes in
+    bool use_graph = true;
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<char> graph_descs;
+    // per-kernel event timing
+    bool profile = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, size_t>> ev_marks;  // (kernel id, index of start event)
+    int prof_launches[BDIS_K_COUNT] = {0};
+    double prof_ms[BDIS_K_COUNT] = {0};
+};
+
+namespace {
+
+const char *kStatusText[] = {"ok", "invalid argument", "out of memory", "CUDA error",
+                             "unsupported"};
+
+bdis_status fail(bdis_handle *h, bdis_status s, const std::string &msg) {
+    if (h) h->err = msg;
+    return s;
+}
+
+bdis_status cuda_fail(bdis_handle *h, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(h, BDIS_ECUDA, m);
+}
+
+int level_dim(int n, int l) {
+    for (int i = 0; i < l; ++i) n = (n + 1) / 2;
+    return n;
+}
+
+int num_origins(int n, int P, int S, int *kreg) {
+    const int r = (n - P) / S + 1;
+    if (kreg) *kreg = r;
+    return r + ((n - P) % S != 0 ? 1 : 0);
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+bool finite_nonneg(float v) { return std::isfinite(v) && v >= 0.f; }
+
+std::string check_params(const bdis_params &p) {
+    if (p.patch < kMinPatch || p.patch > kMaxPatch) return "patch must be in [4, 16]";
+    if (p.stride < 1 || p.stride > p.patch) return "stride must be in [1, patch]";
+    if (p.levels < 1 || p.levels > kMaxLevels) return "levels must be in [1, 8]";
+    if (p.iters < 0 || p.iters > 1000) return "iters must be in [0, 1000]";
+    if (!(std::isfinite(p.sigma_s) && p.sigma_s > 0.f)) return "sigma_s must be > 0";
+    if (!(std::isfinite(p.window_step) && p.window_step > 0.f)) return "window_step must be > 0";
+    if (!finite_nonneg(p.conv_eps)) return "conv_eps must be >= 0";
+    if (!(finite_nonneg(p.valid_gamma) && p.valid_gamma <= 1.f)) return "valid_gamma must be in [0, 1]";
+    if (!finite_nonneg(p.pix_thresh)) return "pix_thresh must be >= 0";
+    if (!std::isfinite(p.search_radius)) return "search_radius must be finite";
+    if (p.sigma_r_mode < 0 || p.sigma_r_mode > 2) return "bad sigma_r_mode";
+    if (!finite_nonneg(p.sigma_r_floor)) return "sigma_r_floor must be >= 0";
+    if (!(std::isfinite(p.sigma_r_fixed) && p.sigma_r_fixed > 0.f)) return "sigma_r_fixed must be > 0";
+    if (p.sigma_r_mode != BDIS_SIGMA_R_FIXED && !(p.sigma_r_floor > 0.f))
+        return "sigma_r_floor must be > 0 for the dynamic modes";
+    if (p.variance != 0 && p.variance != 1) return "variance must be 0 or 1";
+    if (p.pdf_iters < 0 || p.pdf_iters > 100) return "pdf_iters must be in [0, 100]";
+    if (!finite_nonneg(p.pdf_resid)) return "pdf_resid must be >= 0";
+    if (p.storage != BDIS_STORE_F32 && p.storage != BDIS_STORE_F16) return "bad storage";
+    if (!finite_nonneg(p.hess_eps)) return "hess_eps must be >= 0";
+    if (p.use_sgmm != 0 && p.use_sgmm != 1) return "use_sgmm must be 0 or 1";
+    if (p.use_c2f != 0 && p.use_c2f != 1) return "use_c2f must be 0 or 1";
+    return "";
+}
+
+std::string check_pair(const bdis_params &p, const bdis_pair &q) {
+    if (!q.left || !q.right || !q.disp || !q.valid) return "null image or output pointer";
+    if (q.w < 1 || q.h < 1 || q.w > 32768 || q.h > 32768) return "w, h must be in [1, 32768]";
+    if (q.pitch < q.w) return "pitch must be >= w";
+    const int wl = level_dim(q.w, p.levels - 1), hl = level_dim(q.h, p.levels - 1);
+    if (wl < p.patch || hl < p.patch)
+        return "image too small: the coarsest level must be at least patch pixels per axis";
+    return "";
+}
+
+// smem of one search block for a level whose widest pair is `wmax`
+void search_smem(int P, int S, int wmax, int &band_pitch, int &chunk_pitch, size_t &bytes) {
+    band_pitch = (int)align_up((size_t)wmax, 32) + 1;  // rows land in different banks
+    const int chunk = search_chunk(P);
+    chunk_pitch = (chunk - 1) * S + P;
+    if ((chunk_pitch & 1) == 0) chunk_pitch += 1;
+    bytes = sizeof(float) * ((size_t)P * band_pitch + 2 * (size_t)P * chunk_pitch);
+}
+
+void fill_sgmm(const bdis_params &p, float *m) {
+    // 1D factor of Eq. 8: m[a] = sum_{j<P} exp(-(a - j)^2 / (2 sigma_s^2)),
+    // the 2D kernel being m[a] m[b]
+    for (int a = 0; a < kMaxPatch; ++a) {
+        double s = 0.0;
+        if (a < p.patch)
+            for (int j = 0; j < p.patch; ++j)
+                s += std::exp(-(double)(a - j) * (a - j) / (2.0 * p.sigma_s * p.sigma_s));
+        m[a] = (float)s;
+    }
+}
+
+float tau_at(const bdis_params &p) { return p.search_radius > 0.f ? p.search_radius : (float)p.patch; }
+
+LaunchArgs base_args(const bdis_params &p, int level, const LevelDesc *descs, int npairs) {
+    LaunchArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.descs = descs;
+    a.npairs = npairs;
+    a.level = level;
+    a.levels = p.levels;
+    a.P = p.patch;
+    a.S = p.stride;
+    a.iters = p.iters;
+    a.window_step = p.window_step;
+    a.conv_eps = p.conv_eps;
+    a.valid_gamma = p.valid_gamma;
+    a.pix_thresh = p.pix_thresh;
+    a.tau = tau_at(p);
+    a.tau0 = tau_at(p);
+    a.hess_eps = p.hess_eps;
+    double s = 0.0;
+    for (int m = 0; m < p.levels; ++m) s += std::ldexp(1.0, m);
+    a.gamma_w = (float)(std::ldexp(1.0, level) / s);
+    a.sigma_r_mode = p.sigma_r_mode;
+    a.sigma_r_floor = p.sigma_r_floor;
+    a.sigma_r_fixed = p.sigma_r_fixed;
+    a.variance = p.variance;
+    a.pdf_iters = p.pdf_iters;
+    a.pdf_resid = p.pdf_resid;
+    a.use_c2f = p.use_c2f;
+    a.use_sgmm = p.use_sgmm;
+    a.chunk = search_chunk(p.patch);
+    fill_sgmm(p, a.m);
+    return a;
+}
+
+// Arena layout and descriptor tables of one call.
+struct Plan {
+    size_t bytes = 0;
+    size_t off_desc = 0;
+    std::vector<LevelDesc> descs;  // [level][pair]
+    int wmax[kMaxLevels] = {0};
+    int units[kMaxLevels][W_COUNT] = {{0}};
+    // arena offsets, index level * n + pair
+    std::vector<size_t> oG, oL, oR, oD, oQ, oRec, oFuse, oSr;
+};
+
+struct Bump {
+    size_t off = 0;
+    size_t take(size_t n) {
+        off = align_up(off, 256);
+        size_t r = off;
+        off += n;
+        return r;
+    }
+};
+
+// Phase 1: geometry, work ranges and arena offsets.
+void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, Plan &pl) {
+    const int NL = p.levels, P = p.patch, S = p.stride;
+    const size_t esz = p.storage == BDIS_STORE_F16 ? 2 : 4;
+    const size_t cnt = (size_t)NL * n;
+    pl.descs.assign(cnt, LevelDesc{});
+    for (auto *v : {&pl.oG, &pl.oL, &pl.oR, &pl.oD, &pl.oQ, &pl.oRec, &pl.oFuse, &pl.oSr})
+        v->assign(cnt, 0);
+    Bump b;
+    pl.off_desc = b.take(sizeof(LevelDesc) * cnt);
+    const int chunk = search_chunk(P);
+    for (int l = 0; l < NL; ++l) {
+        int begin[W_COUNT] = {0, 0, 0, 0};
+        pl.wmax[l] = 0;
+        for (int i = 0; i < n; ++i) {
+            const size_t k = (size_t)l * n + i;
+            LevelDesc &d = pl.descs[k];
+            d.w = level_dim(pairs[i].w, l);
+            d.h = level_dim(pairs[i].h, l);
+            pl.wmax[l] = std::max(pl.wmax[l], d.w);
+            d.npx = num_origins(d.w, P, S, &d.kxreg);
+            d.npy = num_origins(d.h, P, S, &d.kyreg);
+            d.nchunks = (d.npx + chunk - 1) / chunk;
+            const int units[W_COUNT] = {
+                (((d.w + 1) / 2) * ((d.h + 1) / 2) + 255) / 256,  // pyramid: one thread per 2x2
+                d.npy * d.nchunks,                                // search: chunks of a patch row
+                (d.npx * d.npy + 255) / 256,                      // posterior: patches
+                (d.w * d.h + 255) / 256,                          // densify: pixels
+            };
+            for (int q = 0; q < W_COUNT; ++q) {
+                d.work_begin[q] = begin[q];
+                begin[q] += units[q];
+            }
+            const size_t gp = align_up((size_t)d.w * esz, 128) / esz;
+            d.gpitch = (int)gp;
+            pl.oG[k] = b.take(gp * esz * d.h);
+            if (l == 0) {
+                d.pitch = pairs[i].pitch;
+            } else {
+                d.pitch = (int)gp;
+                pl.oL[k] = b.take(gp * esz * d.h);
+                pl.oR[k] = b.take(gp * esz * d.h);
+                pl.oD[k] = b.take(sizeof(float) * (size_t)d.w * d.h);
+                pl.oQ[k] = b.take(sizeof(float) * (size_t)d.w * d.h);
+            }
+            const size_t np = (size_t)d.npx * d.npy;
+            pl.oRec[k] = b.take(sizeof(bdis_patch_record) * np);
+            pl.oFuse[k] = b.take(sizeof(float4) * np);
+            pl.oSr[k] = b.take(sizeof(float));
+        }
+        for (int q = 0; q < W_COUNT; ++q) pl.units[l][q] = begin[q];
+    }
+    pl.bytes = align_up(b.off, 256);
+}
+
+// Phase 2: pointers, once the arena base is known.
+void plan_pointers(const bdis_params &p, int n, const bdis_pair *pairs, char *base, Plan &pl) {
+    const int NL = p.levels;
+    for (int l = 0; l < NL; ++l)
+        for (int i = 0; i < n; ++i) {
+            const size_t k = (size_t)l * n + i;
+            LevelDesc &d = pl.descs[k];
+            d.G = base + pl.oG[k];
+            if (l == 0) {
+                d.L = pairs[i].left;
+                d.R = pairs[i].right;
+                d.D = d.Q = nullptr;
+                d.disp = pairs[i].disp;
+                d.var = pairs[i].var;
+                d.valid = pairs[i].valid;
+            } else {
+                d.L = base + pl.oL[k];
+                d.R = base + pl.oR[k];
+                d.D = (float *)(base + pl.oD[k]);
+                d.Q = (float *)(base + pl.oQ[k]);
+                d.disp = d.var = nullptr;
+                d.valid = nullptr;
+            }
+            d.rec = (bdis_patch_record *)(base + pl.oRec[k]);
+            d.fuse = (float4 *)(base + pl.oFuse[k]);
+            d.sigma_r = (float *)(base + pl.oSr[k]);
+        }
+    for (int l = 0; l < NL; ++l)
+        for (int i = 0; i < n; ++i) {
+            LevelDesc &d = pl.descs[(size_t)l * n + i];
+            if (l + 1 < NL) {
+                const LevelDesc &c = pl.descs[(size_t)(l + 1) * n + i];
+                d.Ln = (void *)c.L;
+                d.Rn = (void *)c.R;
+                d.wn = d.wc = c.w;
+                d.hn = d.hc = c.h;
+                d.pitchn = c.pitch;
+                d.Dc = c.D;
+                d.Qc = c.Q;
+            } else {
+                d.Ln = d.Rn = nullptr;
+                d.Dc = d.Qc = nullptr;
+                d.wn = d.hn = d.pitchn = d.wc = d.hc = 0;
+            }
+        }
+}
+
+bdis_status ensure_arena(bdis_handle *h, size_t bytes) {
+    if (bytes <= h->arena_cap) return BDIS_OK;
+    cudaError_t e;
+    if (h->arena) {
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaDeviceSynchronize");
+        cudaFree(h->arena);
+        h->arena = nullptr;
+        h->arena_cap = 0;
+    }
+    const size_t cap = align_up(bytes + bytes / 4, 1 << 20);
+    e = cudaMalloc((void **)&h->arena, cap);
+    if (e != cudaSuccess) {
+        h->arena = nullptr;
+        cudaGetLastError();
+        return fail(h, BDIS_ENOMEM, "cudaMalloc of the scratch arena failed");
+    }
+    h->arena_cap = cap;
+    h->last_upload.clear();
+    return BDIS_OK;
+}
+
+bdis_status ensure_pinned(bdis_handle *h, size_t bytes) {
+    if (!h->upload_done) {
+        cudaError_t e = cudaEventCreateWithFlags(&h->upload_done, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventCreate");
+    }
+    if (bytes <= h->pinned_cap) return BDIS_OK;
+    cudaError_t e = cudaEventSynchronize(h->upload_done);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
+    if (h->pinned) cudaFreeHost(h->pinned);
+    h->pinned = nullptr;
+    h->pinned_cap = 0;
+    const size_t cap = align_up(bytes, 1 << 16);
+    e = cudaMallocHost((void **)&h->pinned, cap);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, BDIS_ENOMEM, "cudaMallocHost of the descriptor staging failed");
+    }
+    h->pinned_cap = cap;
+    return BDIS_OK;
+}
+
+int sm_count() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+// Runs the whole coarse-to-fine pipeline for n pairs.  `extra` bytes are
+// reserved after the plan's arena (host-buffer staging).
+bdis_status run(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, cudaStream_t st) {
+    const bdis_params &p = h->p;
+    const int NL = p.levels;
+    Plan pl;
+    plan_layout(p, n, pairs, pl);
+    int band_pitch = 0, chunk_pitch = 0;
+    size_t smem = 0;
+    search_smem(p.patch, p.stride, pl.wmax[0], band_pitch, chunk_pitch, smem);
+    if (smem > 227 * 1024)
+        return fail(h, BDIS_EUNSUPPORTED,
+                    "image too wide for the shared-memory row band of the patch search");
+    bdis_status s = ensure_arena(h, pl.bytes);
+    if (s != BDIS_OK) return s;
+    plan_pointers(p, n, pairs, h->arena, pl);
+    if (h->prepared_P != p.patch || h->smem_prepared < smem) {
+        const size_t want = h->prepared_P == p.patch ? std::max(smem, h->smem_prepared) : smem;
+        cudaError_t e = prepare_search(p.patch, want);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute");
+        h->smem_prepared = want;
+        h->prepared_P = p.patch;
+    }
+    // upload the descriptor table unless identical to the last upload
+    const size_t tbytes = sizeof(LevelDesc) * pl.descs.size();
+    LevelDesc *d_descs = (LevelDesc *)(h->arena + pl.off_desc);
+    const bool same = h->last_upload.size() == tbytes &&
+                      std::memcmp(h->last_upload.data(), pl.descs.data(), tbytes) == 0;
+    if (!same) {
+        s = ensure_pinned(h, tbytes);
+        if (s != BDIS_OK) return s;
+        cudaError_t e = cudaEventSynchronize(h->upload_done);  // staging free again
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
+        std::memcpy(h->pinned, pl.descs.data(), tbytes);
+        e = cudaMemcpyAsync(d_descs, h->pinned, tbytes, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "descriptor upload");
+        e = cudaEventRecord(h->upload_done, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
+        h->last_upload.assign((const char *)pl.descs.data(),
+                              (const char *)pl.descs.data() + tbytes);
+    }
+
+    const int st_type = p.storage == BDIS_STORE_F16 ? E_F16 : E_F32;
+    // one kernel launch, optionally bracketed by profiling events
+    auto timed = [&](int kid, auto &&fn) -> cudaError_t {
+        size_t i0 = 0;
+        if (h->profile) {
+            i0 = h->ev_marks.empty() ? 0 : h->ev_marks.back().second + 2;
+            while (h->ev_pool.size() < i0 + 2) {
+                cudaEvent_t ev;
+                cudaError_t e = cudaEventCreate(&ev);
+                if (e != cudaSuccess) return e;
+                h->ev_pool.push_back(ev);
+            }
+            cudaError_t e = cudaEventRecord(h->ev_pool[i0], st);
+            if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = fn();
+        if (e != cudaSuccess) return e;
+        if (h->profile) {
+            e = cudaEventRecord(h->ev_pool[i0 + 1], st);
+            if (e != cudaSuccess) return e;
+            h->ev_marks.emplace_back(kid, i0);
+        }
+        return cudaSuccess;
+    };
+    auto launch_all = [&]() -> bdis_status {
+        cudaError_t e;
+        // gradients of every level and the pyramid, finest to coarsest
+        for (int l = 0; l < NL; ++l) {
+            LaunchArgs a = base_args(p, l, d_descs + (size_t)l * n, n);
+            a.total = pl.units[l][W_PYR];
+            e = timed(BDIS_K_PYRAMID, [&] { return launch_pyramid(a, l == 0 ? in_type : st_type, st_type, st); });
+            if (e != cudaSuccess) return cuda_fail(h, e, "pyramid launch");
+        }
+        // coarse-to-fine levels
+        for (int l = NL - 1; l >= 0; --l) {
+            LaunchArgs a = base_args(p, l, d_descs + (size_t)l * n, n);
+            size_t sm;
+            search_smem(p.patch, p.stride, pl.wmax[l], a.band_pitch, a.chunk_pitch, sm);
+            a.total = pl.units[l][W_SEARCH];
+            const int itype = l == 0 ? in_type : st_type;
+            const int occ = search_occupancy(p.patch, itype, st_type, sm);
+            const int grid = std::max(1, std::min(a.total, sm_count() * occ));
+            e = timed(BDIS_K_SEARCH, [&] { return launch_search(a, itype, st_type, sm, grid, st); });
+            if (e != cudaSuccess) return cuda_fail(h, e, "search launch");
+            e = timed(BDIS_K_SIGMA_R, [&] { return launch_sigma_r(a, st); });
+            if (e != cudaSuccess) return cuda_fail(h, e, "sigma_r launch");
+            a.total = pl.units[l][W_POST];
+            e = timed(BDIS_K_POSTERIOR, [&] { return launch_posterior(a, st); });
+            if (e != cudaSuccess) return cuda_fail(h, e, "posterior launch");
+            a.total = pl.units[l][W_DENSE];
+            e = timed(BDIS_K_DENSIFY, [&] { return launch_densify(a, st); });
+            if (e != cudaSuccess) return cuda_fail(h, e, "densify launch");
+        }
+        return BDIS_OK;
+    };
+
+    // Graph replay: only on a non-default stream that is not already being
+    // captured by the caller, and only for the exact descriptors captured.
+    bool can_graph = h->use_graph && !h->profile && st != nullptr;
+    if (can_graph) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+            can_graph = false;
+        cudaGetLastError();
+    }
+    const bool graph_hit = can_graph && h->graph_exec != nullptr &&
+                           h->graph_descs.size() == tbytes &&
+                           std::memcmp(h->graph_descs.data(), pl.descs.data(), tbytes) == 0;
+    if (graph_hit) {
+        cudaError_t e = cudaGraphLaunch(h->graph_exec, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+    } else if (can_graph) {
+        if (h->graph_exec) {
+            cudaGraphExecDestroy(h->graph_exec);
+            h->graph_exec = nullptr;
+            h->graph_descs.clear();
+        }
+        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            s = launch_all();
+            if (s != BDIS_OK) return s;
+        } else {
+            s = launch_all();
+            cudaGraph_t g = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(st, &g);
+            if (s != BDIS_OK) {
+                if (g) cudaGraphDestroy(g);
+                return s;
+            }
+            if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
+            e2 = cudaGraphInstantiate(&h->graph_exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e2 != cudaSuccess) {
+                h->graph_exec = nullptr;
+                return cuda_fail(h, e2, "cudaGraphInstantiate");
+            }
+            h->graph_descs.assign((const char *)pl.descs.data(),
+                                  (const char *)pl.descs.data() + tbytes);
+            e2 = cudaGraphLaunch(h->graph_exec, st);
+            if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaGraphLaunch");
+        }
+    } else {
+        s = launch_all();
+        if (s != BDIS_OK) return s;
+    }
+    h->descs = pl.descs;
+    h->npairs = n;
+    h->levels = NL;
+    h->in_type = in_type;
+    h->d_descs = d_descs;
+    return BDIS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void bdis_default_params(bdis_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->patch = 8;
+    p->stride = 4;
+    p->levels = 3;
+    p->iters = 8;
+    p->sigma_s = 4.0f;       // Sec. IV-A
+    p->window_step = 0.5f;   // Sec. IV-A: disturbances 0.5 and 1 px
+    p->conv_eps = 0.05f;     // Sec. IV-A: early-stopping 0.05
+    p->valid_gamma = 0.75f;  // Sec. IV-A
+    p->pix_thresh = 0.15f;   // Sec. IV-A
+    p->search_radius = 0.f;  // = patch
+    p->sigma_r_mode = BDIS_SIGMA_R_POOLED;
+    p->sigma_r_floor = 0.5f;
+    p->sigma_r_fixed = 8.0f;  // Table VII ablation value
+    p->variance = 0;
+    p->pdf_iters = 10;        // Sec. III-E
+    p->pdf_resid = 0.1f;      // Sec. III-E
+    p->storage = BDIS_STORE_F32;
+    p->hess_eps = 1e-4f;
+    p->use_sgmm = 1;
+    p->use_c2f = 1;
+}
+
+bdis_status bdis_create(const bdis_params *p, bdis_handle **out) {
+    if (!out) return BDIS_EINVAL;
+    *out = nullptr;
+    bdis_params q;
+    if (p) q = *p; else bdis_default_params(&q);
+    if (!check_params(q).empty()) return BDIS_EINVAL;
+    bdis_handle *h = new (std::nothrow) bdis_handle();
+    if (!h) return BDIS_ENOMEM;
+    h->p = q;
+    *out = h;
+    return BDIS_OK;
+}
+
+void bdis_destroy(bdis_handle *h) {
+    if (!h) return;
+    if (h->upload_done) {
+        cudaEventSynchronize(h->upload_done);
+        cudaEventDestroy(h->upload_done);
+    }
+    if (h->arena) {
+        cudaDeviceSynchronize();
+        cudaFree(h->arena);
+    }
+    if (h->pinned) cudaFreeHost(h->pinned);
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
+    delete h;
+}
+
+bdis_status bdis_set_option(bdis_handle *h, int option, int value) {
+    if (!h) return BDIS_EINVAL;
+    if (option == BDIS_OPT_GRAPH) {
+        h->use_graph = value != 0;
+        return BDIS_OK;
+    }
+    if (option == BDIS_OPT_PROFILE) {
+        h->profile = value != 0;
+        return BDIS_OK;
+    }
+    return fail(h, BDIS_EINVAL, "unknown option");
+}
+
+bdis_status bdis_get_profile(bdis_handle *h, bdis_profile *out, int reset) {
+    if (!h || !out) return BDIS_EINVAL;
+    for (const auto &mk : h->ev_marks) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(h->ev_pool[mk.second + 1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, h->ev_pool[mk.second], h->ev_pool[mk.second + 1]);
+        if (e != cudaSuccess) return cuda_fail(h, e, "profile events");
+        h->prof_launches[mk.first] += 1;
+        h->prof_ms[mk.first] += ms;
+    }
+    h->ev_marks.clear();
+    for (int k = 0; k < BDIS_K_COUNT; ++k) {
+        out->launches[k] = h->prof_launches[k];
+        out->ms[k] = h->prof_ms[k];
+        if (reset) {
+            h->prof_launches[k] = 0;
+            h->prof_ms[k] = 0.0;
+        }
+    }
+    return BDIS_OK;
+}
+
+const char *bdis_strerror(bdis_status s) {
+    if ((int)s < 0 || (int)s > 4) return "unknown status";
+    return kStatusText[(int)s];
+}
+
+const char *bdis_last_error(const bdis_handle *h) { return h ? h->err.c_str() : "null handle"; }
+
+bdis_status bdis_get_params(const bdis_handle *h, bdis_params *out) {
+    if (!h || !out) return BDIS_EINVAL;
+    *out = h->p;
+    out->search_radius = tau_at(h->p);
+    return BDIS_OK;
+}
+
+bdis_status bdis_match_batched(bdis_handle *h, int n, const bdis_pair *pairs, void *stream) {
+    if (!h) return BDIS_EINVAL;
+    if (n < 1 || !pairs) return fail(h, BDIS_EINVAL, "need at least one pair");
+    for (int i = 0; i < n; ++i) {
+        std::string m = check_pair(h->p, pairs[i]);
+        if (!m.empty()) return fail(h, BDIS_EINVAL, "pair " + std::to_string(i) + ": " + m);
+    }
+    return run(h, n, pairs, E_U8, (cudaStream_t)stream);
+}
+
+bdis_status bdis_match(bdis_handle *h, const uint8_t *left, const uint8_t *right, int w,
+                       int hgt, int pitch, float *disp, float *var, uint8_t *valid,
+                       void *stream) {
+    bdis_pair q{left, right, w, hgt, pitch, disp, var, valid};
+    return bdis_match_batched(h, 1, &q, stream);
+}
+
+bdis_status bdis_match_host(bdis_handle *h, const uint8_t *left, const uint8_t *right, int w,
+                            int hgt, int pitch, float *disp, float *var, uint8_t *valid,
+                            void *stream) {
+    if (!h) return BDIS_EINVAL;
+    bdis_pair q{left, right, w, hgt, pitch, disp, var, valid};
+    std::string m = check_pair(h->p, q);
+    if (!m.empty()) return fail(h, BDIS_EINVAL, m);
+    cudaStream_t st = (cudaStream_t)stream;
+    // device staging for the inputs and outputs, after the pipeline's arena
+    Plan pl;
+    plan_layout(h->p, 1, &q, pl);
+    const size_t img = align_up((size_t)w * hgt, 256);
+    const size_t fo = align_up(sizeof(float) * (size_t)w * hgt, 256);
+    const size_t extra = 2 * img + 2 * fo + img;
+    const size_t base = align_up(pl.bytes, 256);
+    bdis_status s = ensure_arena(h, base + extra);
+    if (s != BDIS_OK) return s;
+    char *dl = h->arena + base;
+    char *dr = dl + img;
+    float *dd = (float *)(dr + img);
+    float *dv = (float *)((char *)dd + fo);
+    uint8_t *dm = (uint8_t *)((char *)dv + fo);
+    cudaError_t e = cudaMemcpy2DAsync(dl, w, left, pitch, w, hgt, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(dr, w, right, pitch, w, hgt, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "input copy");
+    bdis_pair dq{(const uint8_t *)dl, (const uint8_t *)dr, w, hgt, w, dd,
+                 (var && h->p.variance) ? dv : nullptr, dm};
+    s = run(h, 1, &dq, E_U8, st);
+    if (s != BDIS_OK) return s;
+    const size_t npx = (size_t)w * hgt;
+    e = cudaMemcpyAsync(disp, dd, sizeof(float) * npx, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && var && h->p.variance)
+        e = cudaMemcpyAsync(var, dv, sizeof(float) * npx, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(valid, dm, npx, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "output copy");
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    return BDIS_OK;
+}
+
+bdis_status bdis_level_view_get(const bdis_handle *h, int pair, int level, bdis_level_view *out) {
+    if (!h || !out) return BDIS_EINVAL;
+    if (pair < 0 || pair >= h->npairs || level < 0 || level >= h->levels) return BDIS_EINVAL;
+    const LevelDesc &d = h->descs[(size_t)level * h->npairs + pair];
+    out->w = d.w;
+    out->h = d.h;
+    out->npx = d.npx;
+    out->npy = d.npy;
+    out->image_pitch = d.pitch;
+    out->grad_pitch = d.gpitch;
+    out->storage = level == 0 ? -1 : h->p.storage;
+    out->left = d.L;
+    out->right = d.R;
+    out->grad = d.G;
+    out->records = d.rec;
+    out->D = d.D;
+    out->Q = d.Q;
+    out->sigma_r = d.sigma_r;
+    return BDIS_OK;
+}
+
+bdis_status bdis_get_stats(bdis_handle *h, bdis_stats *out, void *stream) {
+    if (!h || !out) return BDIS_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    if (h->npairs == 0) return fail(h, BDIS_EINVAL, "no call yet");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    out->levels = h->levels;
+    out->pairs = h->npairs;
+    std::vector<bdis_patch_record> recs;
+    for (int l = 0; l < h->levels; ++l) {
+        for (int i = 0; i < h->npairs; ++i) {
+            const LevelDesc &d = h->descs[(size_t)l * h->npairs + i];
+            const size_t np = (size_t)d.npx * d.npy;
+            recs.resize(np);
+            e = cudaMemcpy(recs.data(), d.rec, sizeof(bdis_patch_record) * np, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(h, e, "stats copy");
+            out->patches[l] += (int)np;
+            for (const auto &r : recs) out->valid_patches[l] += r.flags == 0u ? 1 : 0;
+            if (i == 0) {
+                e = cudaMemcpy(&out->sigma_r[l], d.sigma_r, sizeof(float), cudaMemcpyDeviceToHost);
+                if (e != cudaSuccess) return cuda_fail(h, e, "stats copy");
+            }
+        }
+    }
+    std::vector<uint8_t> v;
+    for (int i = 0; i < h->npairs; ++i) {
+        const LevelDesc &d = h->descs[(size_t)i];
+        v.resize((size_t)d.w * d.h);
+        e = cudaMemcpy(v.data(), d.valid, v.size(), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(h, e, "stats copy");
+        for (uint8_t b : v) out->valid_pixels += b;
+    }
+    return BDIS_OK;
+}
+
+bdis_status bdis_copy(void *dst, const void *src, size_t bytes, void *stream) {
+    if (!dst || !src) return BDIS_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st) != cudaSuccess) return BDIS_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return BDIS_ECUDA;
+    return BDIS_OK;
+}
+
+}  // extern "C"

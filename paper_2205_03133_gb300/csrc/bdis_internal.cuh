@@ -1,0 +1,86 @@
+// bdis_internal.cuh -- device-side descriptors shared by the kernels and the
+// host library of libbdis.  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "bdis.h"
+
+namespace bdis {
+
+constexpr int kMaxLevels = 8;
+constexpr int kMinPatch = 4;
+constexpr int kMaxPatch = 16;
+constexpr int kWindow = 5;  // samples of the small window P' (Sec. III-B, s = 5)
+
+// Work spaces of the per-level kernels.  Each (pair, level) owns the
+// half-open unit range [work_begin[k], work_begin[k] + units) of kernel k.
+enum WorkKind { W_PYR = 0, W_SEARCH = 1, W_POST = 2, W_DENSE = 3, W_COUNT = 4 };
+
+// Element types of the level images.
+enum ElemType { E_U8 = 0, E_F32 = 1, E_F16 = 2 };
+
+// One (pair, level).  All pointers are device pointers.
+struct alignas(16) LevelDesc {
+    const void *L, *R;        // level images (level 0: caller's 8-bit images)
+    void *G;                  // x-gradient of L at this level (storage type)
+    void *Ln, *Rn;            // next coarser level to build (nullptr at the coarsest)
+    float *D, *Q;             // fused disparity / probability maps (levels >= 1)
+    const float *Dc, *Qc;     // coarser fused maps (nullptr at the coarsest level)
+    float *disp, *var;        // finest-level outputs (var may be nullptr)
+    uint8_t *valid;
+    bdis_patch_record *rec;   // npx * npy records of this pair at this level
+    float4 *fuse;             // (d, rho, sig2, kept) per patch for the fusion gather
+    float *sigma_r;           // one float
+    int w, h, pitch;          // level size, row pitch (elements) of L and R
+    int gpitch;               // row pitch (elements) of G
+    int wn, hn, pitchn;       // next coarser level size and pitch
+    int wc, hc;               // coarser map size (levels < L-1)
+    int npx, npy, kxreg, kyreg;
+    int nchunks;              // search chunks per patch row
+    int work_begin[W_COUNT];
+};
+
+// Per-launch arguments (passed by value).
+struct LaunchArgs {
+    const LevelDesc *descs;   // the npairs descriptors of this level
+    int npairs;
+    int total;                // total work units of this launch
+    int level, levels;
+    int P, S, iters;
+    float window_step, conv_eps, valid_gamma, pix_thresh;
+    float tau;                // search radius at this level (px)
+    float tau0;               // search radius at level 0 (PDF exception value)
+    float hess_eps;
+    float gamma_w;            // Gamma weight of this level (Eq. 11)
+    int sigma_r_mode;
+    float sigma_r_floor, sigma_r_fixed;
+    int variance, pdf_iters;
+    float pdf_resid;
+    int use_c2f, use_sgmm;
+    int chunk;                // patches per search chunk
+    int band_pitch;           // floats per row of the staged right band
+    int chunk_pitch;          // floats per row of the staged left / gradient band
+    float m[kMaxPatch];       // 1D sGMM factors m[a] (Eq. 8 is separable)
+};
+
+// Kernel launchers (bdis_kernels.cu).  Each returns cudaGetLastError().
+cudaError_t launch_pyramid(const LaunchArgs &a, int in_type, int out_type, cudaStream_t s);
+cudaError_t launch_search(const LaunchArgs &a, int in_type, int g_type, size_t smem, int grid,
+                          cudaStream_t s);
+cudaError_t launch_sigma_r(const LaunchArgs &a, cudaStream_t s);
+cudaError_t launch_posterior(const LaunchArgs &a, cudaStream_t s);
+cudaError_t launch_densify(const LaunchArgs &a, cudaStream_t s);
+// Opt-in to large dynamic shared memory for every search instance.
+cudaError_t prepare_search(int P, size_t smem_bytes);
+// Number of resident search blocks per SM for (P, image type, gradient type, smem).
+int search_occupancy(int P, int in_type, int g_type, size_t smem_bytes);
+bool search_supported(int P);
+int search_group(int P);      // lanes per patch
+int search_chunk(int P);      // patches per chunk
+
+}  // namespace bdis

@@ -1,0 +1,111 @@
+"""Helpers that run the CUDA path and the FP64 oracle on the same seeded
+inputs and compare them element by element.
+
+Tolerances (the gate, stated once here and used by every parity test):
+  * disparity: |d_gpu - d_oracle| <= 1e-3 px on >= 99.9% of the pixels valid
+    in both, and <= 0.05 px on every such pixel not covered by a level-0
+    patch whose discrete decision (kept / rejected, PDF exception) differs
+    between the two sides in a way that changes its estimate ("flipped");
+  * variance: relative difference <= 1e-3 on the same pixels;
+  * validity masks equal outside the footprints of flipped patches;
+  * the kept / rejected decision of each patch equal on >= 99.9% of the
+    patches of every level (at most 2 disagreements on small levels).
+Where a floating-point comparison decides an integer (a rejection flag),
+both sides take it in their own arithmetic (FP32 on the GPU, FP64 in the
+oracle); the rare disagreements are counted as flips and reported.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+D_TOL = 1e-3
+D_FRAC = 0.999
+D_MAX = 0.05
+V_RTOL = 1e-3
+
+STORE_NAMES = {0: "f32", 1: "f16"}
+
+
+def oracle_params(gp, storage_override=None):
+    """Oracle parameters equal to a GPU bdis_params (field by field)."""
+    st = storage_override or STORE_NAMES[gp.storage]
+    return oracle.make_params(
+        patch=gp.patch, stride=gp.stride, levels=gp.levels, iters=gp.iters,
+        sigma_s=gp.sigma_s, window_step=gp.window_step, conv_eps=gp.conv_eps,
+        valid_gamma=gp.valid_gamma, pix_thresh=gp.pix_thresh, search_radius=gp.search_radius,
+        sigma_r_mode={0: "pooled", 1: "literal", 2: "fixed"}[gp.sigma_r_mode],
+        sigma_r_floor=gp.sigma_r_floor, sigma_r_fixed=gp.sigma_r_fixed, variance=gp.variance,
+        pdf_iters=gp.pdf_iters, pdf_resid=gp.pdf_resid, storage=st, hess_eps=gp.hess_eps,
+        use_sgmm=gp.use_sgmm, use_c2f=gp.use_c2f)
+
+
+def footprint(mask_patches, w, h, P, S):
+    """Pixels covered by the patches marked in the (npy, npx) mask."""
+    ox = oracle.origins(w, P, S)
+    oy = oracle.origins(h, P, S)
+    out = np.zeros((h, w), bool)
+    for ky, kx in zip(*np.nonzero(mask_patches)):
+        out[oy[ky]:oy[ky] + P, ox[kx]:ox[kx] + P] = True
+    return out
+
+
+def compare_outputs(gp, o, disp, var, valid, rec_gpu0):
+    """Final-output comparison; returns a metrics dict."""
+    h, w = disp.shape
+    P, S = gp.patch, gp.stride
+    rec_o0 = o["levels"][0]["patches"]
+    flip = (rec_o0["flags"] == 0) != (rec_gpu0["flags"] == 0)
+    both_kept = (rec_o0["flags"] == 0) & (rec_gpu0["flags"] == 0)
+    if gp.variance:
+        # a PDF exception on one side only counts when it changes sigma_k
+        # (an exception and a fit capped at tau both give sigma_k = tau)
+        s2o = rec_o0["sig2"].astype(np.float64)
+        s2g = rec_gpu0["sig2"].astype(np.float64)
+        differs = np.abs(s2g - s2o) > V_RTOL * np.maximum(s2o, 1e-12)
+        flip |= both_kept & ((rec_o0["pdf_flags"] != 0) != (rec_gpu0["pdf_flags"] != 0)) & differs
+    fp = footprint(flip, w, h, P, S)
+    vo = o["valid"]
+    vg = valid.astype(bool)
+    both = vo & vg
+    dd = np.abs(disp.astype(np.float64) - o["disp"])
+    m = dict(
+        pixels=w * h, valid_oracle=int(vo.sum()), valid_gpu=int(vg.sum()),
+        mask_mismatch=int((vo != vg).sum()), mask_mismatch_outside_flips=int(((vo != vg) & ~fp).sum()),
+        flipped_patches=int(flip.sum()), patches=int(flip.size),
+        frac_within_tol=float((dd[both] <= D_TOL).mean()) if both.any() else 1.0,
+        max_dd=float(dd[both].max()) if both.any() else 0.0,
+        max_dd_outside_flips=float(dd[both & ~fp].max()) if (both & ~fp).any() else 0.0,
+    )
+    if gp.variance:
+        vv = np.abs(var.astype(np.float64) - o["var"]) / np.maximum(np.abs(o["var"]), 1e-12)
+        sel = both & ~fp
+        m["var_max_rel_outside_flips"] = float(vv[sel].max()) if sel.any() else 0.0
+        m["var_frac_within"] = float((vv[both] <= V_RTOL).mean()) if both.any() else 1.0
+    return m
+
+
+def assert_gate(m):
+    assert m["frac_within_tol"] >= D_FRAC, m
+    assert m["max_dd_outside_flips"] <= D_MAX, m
+    assert m["mask_mismatch_outside_flips"] == 0, m
+    assert m["flipped_patches"] <= max(2, int(0.001 * m["patches"])), m
+    if "var_max_rel_outside_flips" in m:
+        assert m["var_max_rel_outside_flips"] <= V_RTOL, m
+
+
+def compare_records(rg, ro):
+    """Per-patch comparison at one level.  The decision that reaches the
+    outputs is kept / rejected; which rejection bits are set on a patch both
+    sides reject (e.g. a flat patch whose window energies tie) is reported
+    but not gated."""
+    fg, fo = rg["flags"], ro["flags"]
+    decision_flips = (fg == 0) != (fo == 0)
+    both = (fg == 0) & (fo == 0)
+    dd = np.abs(rg["d"].astype(np.float64) - ro["d"])
+    return dict(patches=int(fg.size), decision_flips=int(decision_flips.sum()),
+                flag_bits_agree=float((fg == fo).mean()),
+                kept_gpu=int((fg == 0).sum()), kept_oracle=int((fo == 0).sum()),
+                d_frac_within=float((dd[both] <= D_TOL).mean()) if both.any() else 1.0,
+                d_max=float(dd[both].max()) if both.any() else 0.0)

@@ -1,0 +1,77 @@
+"""The C-ABI library builds, loads and exports every function that
+include/bdis.h declares; argument checks run on the host (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+def _declared_functions():
+    names = []
+    for hp in HEADERS:
+        text = open(hp).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ \*]*?\b(bdis_[a-z0-9_]+)\s*\(",
+                             text, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2205_03133_gb300 import build
+    build.build()
+    from paper_2205_03133_gb300 import _binding
+    return _binding.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert len(names) >= 12, names
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/*.h but not exported"
+
+
+def test_binding_covers_the_header():
+    from paper_2205_03133_gb300 import _binding
+    bound = {n for n, _, _ in _binding.EXPORTS}
+    assert set(_declared_functions()) == bound
+
+
+def test_struct_sizes_match_header(lib):
+    from paper_2205_03133_gb300 import _binding as B
+    assert C.sizeof(B.bdis_patch_record) == 64
+    p = B.bdis_params()
+    lib.bdis_default_params(C.byref(p))
+    assert (p.patch, p.stride, p.levels, p.iters) == (8, 4, 3, 8)
+    assert p.sigma_s == 4.0 and p.window_step == 0.5 and p.pdf_iters == 10
+
+
+def test_host_side_argument_checks(lib):
+    import paper_2205_03133_gb300 as bd
+    with pytest.raises(bd.BdisError):
+        bd.BDIS(patch=3)
+    with pytest.raises(bd.BdisError):
+        bd.BDIS(stride=9)
+    with pytest.raises(bd.BdisError):
+        bd.BDIS(levels=9)
+    m = bd.BDIS(patch=12, stride=6, levels=4)
+    B = bd.B
+    # null pointers
+    st = lib.bdis_match(m._h, None, None, 640, 480, 640, None, None, None, None)
+    assert st == B.BDIS_EINVAL
+    # too small for the pyramid: coarsest level below the patch size
+    st = lib.bdis_match(m._h, 16, 16, 80, 60, 80, 16, None, 16, None)
+    assert st == B.BDIS_EINVAL and b"too small" in lib.bdis_last_error(m._h)
+    # pitch below width
+    st = lib.bdis_match(m._h, 16, 16, 640, 480, 600, 16, None, 16, None)
+    assert st == B.BDIS_EINVAL
+    assert lib.bdis_strerror(B.BDIS_EUNSUPPORTED) == b"unsupported"
+    # level views before any call
+    v = B.bdis_level_view()
+    assert lib.bdis_level_view_get(m._h, 0, 0, C.byref(v)) == B.BDIS_EINVAL
