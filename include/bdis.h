@@ -139,6 +139,31 @@ bdis_status bdis_match_host(bdis_handle *h, const uint8_t *left, const uint8_t *
  * Results are identical to calling bdis_match on each pair. */
 bdis_status bdis_match_batched(bdis_handle *h, int n, const bdis_pair *pairs, void *stream);
 
+/* Allocation-free variant of bdis_match (the paper has no counterpart: it
+ * exists for callers that cannot allocate device memory).  Callers such as a
+ * video pipeline whose memory pool owns the whole device, a process with a
+ * fixed device-memory budget, or a latency-critical loop that cannot take
+ * the device-wide synchronisation of cudaMalloc/cudaFree, get the same
+ * result as bdis_match without any allocation: no handle, no cudaMalloc,
+ * cudaFree or pinned staging.  The scratch (pyramids, patch records, coarse
+ * maps, descriptor table) lives in one static device array of 32 MiB that
+ * every GPU loading the library holds until the process exits; the caller
+ * passes inputs and outputs as for bdis_match (device pointers).
+ *   - Returns BDIS_EUNSUPPORTED, before any launch, when the pair needs more
+ *     than that 32 MiB (e.g. 1920x1080 with FP32 pyramids); a 640x480 pair
+ *     fits with any settings, a 1280x720 pair with 8x8 patches, stride 4,
+ *     3 levels.  BDIS_EINVAL for invalid parameters or sizes.
+ *   - The first call on each device resolves the array's device address
+ *     (cudaGetSymbolAddress with that device current); make that first call
+ *     before any stream capture.
+ *   - All calls share the one array, which keeps the last call's contents:
+ *     calls that overlap on the GPU (other streams or host threads) race and
+ *     must be serialised by the caller.
+ *   - Asynchronous on `stream`; no bdis_last_error text (no handle). */
+bdis_status bdis_match_noalloc(const bdis_params *p, const uint8_t *left, const uint8_t *right,
+                               int w, int hgt, int pitch, float *disp, float *var,
+                               uint8_t *valid, void *stream);
+
 /* Counters of the last call (synchronises `stream` to read them). */
 bdis_status bdis_get_stats(bdis_handle *h, bdis_stats *out, void *stream);
 

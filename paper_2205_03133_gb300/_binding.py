@@ -91,6 +91,8 @@ EXPORTS = [
     ("bdis_copy", C.c_int, [_vp, _vp, C.c_size_t, _vp]),
     ("bdis_set_option", C.c_int, [_h, C.c_int, C.c_int]),
     ("bdis_get_profile", C.c_int, [_h, C.POINTER(bdis_profile), C.c_int]),
+    ("bdis_match_noalloc", C.c_int, [C.POINTER(bdis_params), _vp, _vp, C.c_int, C.c_int, C.c_int,
+                                     _vp, _vp, _vp, _vp]),
 ]
 
 _lib = None
