@@ -264,6 +264,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--only", default="all", choices=["all", "batched"],
+                    help="batched: only the 64-pair batched form (used for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -283,6 +285,14 @@ def main():
     init_dist(ws, "nccl")
     dev = torch.device("cuda", local)
     B = bd.B
+    if args.only == "batched":
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+        stream = torch.cuda.Stream(device=dev)
+        res = bench_batched(bd, dev, stream, flush, rank, ws, steps=args.steps,
+                            warmup=args.warmup, compare_plain=False)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "batched": res}))
+        return 0
 
     pair = synth.config_pair("plain_640x480_var", seed=rank)
     h, w = pair.left.shape
@@ -439,7 +449,7 @@ def main():
     return 0
 
 
-def bench_batched(bd, dev, stream, flush, rank, ws, steps=10):
+def bench_batched(bd, dev, stream, flush, rank, ws, steps=10, warmup=3, compare_plain=True):
     """64 pairs of uneven sizes (24x640x480, 16x960x540, 16x1280x720,
     8x1920x1080; G1 generator, seeds 64*rank + i) in one batched call per
     step, against 64 sequential plain calls."""
@@ -477,14 +487,18 @@ def bench_batched(bd, dev, stream, flush, rank, ws, steps=10):
             mp.match(Ls[i], Rs[i], out=outs[i], stream=stream)
 
     with torch.cuda.stream(stream):
-        for _ in range(3):
+        for _ in range(warmup):
             batched_fn()
-            plain_fn()
+            if compare_plain:
+                plain_fn()
     torch.cuda.synchronize()
-    t_b = run(batched_fn, steps)
-    t_p = run(plain_fn, max(3, steps // 2))
-    t_b = max_over_ranks(t_b, ws, dev)
-    t_p = max_over_ranks(t_p, ws, dev)
+    t_b = max_over_ranks(run(batched_fn, steps), ws, dev)
+    if not compare_plain:
+        m.close()
+        mp.close()
+        return {"value": round(ws * px / (t_b / 1e3) / 1e6, 2), "unit": UNIT,
+                "ms_per_batch": round(t_b, 4)}
+    t_p = max_over_ranks(run(plain_fn, max(3, steps // 2)), ws, dev)
     bd.B.lib().bdis_set_option(m._h, bd.B.OPT_PROFILE, 1)
     prof = bd.B.bdis_profile()
     bd.B.lib().bdis_get_profile(m._h, prof, 1)
