@@ -59,7 +59,7 @@ class Params(C.Structure):
 PATCH_DTYPE = np.dtype([
     ("d", "f8"), ("dinit", "f8"), ("E", "f8", (5,)), ("H", "f8"), ("cT", "f8"),
     ("dlast", "f8"), ("nout", "i4"), ("flags", "u4"), ("pi", "f8"), ("rho", "f8"),
-    ("sig2", "f8"), ("pdf_flags", "u4"),
+    ("sig2", "f8"), ("prop", "f8"), ("pdf_flags", "u4"),
 ], align=True)
 
 
@@ -289,3 +289,58 @@ def match(p: Params, left: np.ndarray, right: np.ndarray, trace: bool = False):
             out["levels"].append({k: keep[(k, l)] for k in ("L", "R", "G", "D", "Q", "patches")}
                                  | {"sigma_r": tr.sigma_r[l]})
     return out
+
+
+# ---------------------------------------------------------------- differentiable form
+
+def frozen_state(p: Params, out: dict) -> dict:
+    """Level-0 discrete state of a traced forward (oracle.match(..., trace=True)):
+    kept patches, initial disparities, inherited coarse probabilities, valid
+    pixels, and whether sigma_r sat at its floor."""
+    lv0 = out["levels"][0]
+    rec = lv0["patches"]
+    return dict(kept=np.ascontiguousarray((rec["flags"] == 0).astype(np.uint8).ravel()),
+                dinit=np.ascontiguousarray(rec["dinit"].ravel()),
+                prop=np.ascontiguousarray(rec["prop"].ravel()),
+                valid=np.ascontiguousarray(out["valid"].astype(np.uint8)),
+                sr_const=int(lv0["sigma_r"] <= p.sigma_r_floor))
+
+
+def _diff_sigs(L):
+    vp = C.c_void_p
+    common = [C.POINTER(Params), vp, vp, C.c_int, C.c_int, vp, vp, vp, vp, C.c_int, C.c_double]
+    L.ob_diff_forward.restype = C.c_double
+    L.ob_diff_forward.argtypes = common + [vp, vp, vp]
+    L.ob_diff_grad.restype = C.c_double
+    L.ob_diff_grad.argtypes = common + [vp, vp, vp, vp]
+
+
+def diff_forward(p: Params, left, right, st: dict, lam: float = 0.1, d_override=None):
+    """Frozen-state level-0 function: returns (loss, D, d_k)."""
+    L = lib()
+    _diff_sigs(L)
+    Lf = np.ascontiguousarray(left, dtype=np.float64)
+    Rf = np.ascontiguousarray(right, dtype=np.float64)
+    h, w = Lf.shape
+    D = np.zeros((h, w))
+    dk = np.zeros(st["kept"].size)
+    do = None if d_override is None else np.ascontiguousarray(d_override, dtype=np.float64)
+    loss = L.ob_diff_forward(C.byref(p), _ptr(Lf), _ptr(Rf), w, h, _ptr(st["kept"]), _ptr(st["dinit"]),
+                             _ptr(st["prop"]), _ptr(st["valid"]), st["sr_const"], lam, _ptr(do),
+                             _ptr(D), _ptr(dk))
+    return loss, D, dk
+
+
+def diff_grad(p: Params, left, right, st: dict, lam: float = 0.1):
+    """Analytic gradient: returns (loss, dL/dI_l, dL/dI_r, dL/dd_k, dL/dD)."""
+    L = lib()
+    _diff_sigs(L)
+    Lf = np.ascontiguousarray(left, dtype=np.float64)
+    Rf = np.ascontiguousarray(right, dtype=np.float64)
+    h, w = Lf.shape
+    gL = np.zeros((h, w)); gR = np.zeros((h, w)); gD = np.zeros((h, w))
+    gdk = np.zeros(st["kept"].size)
+    loss = L.ob_diff_grad(C.byref(p), _ptr(Lf), _ptr(Rf), w, h, _ptr(st["kept"]), _ptr(st["dinit"]),
+                          _ptr(st["prop"]), _ptr(st["valid"]), st["sr_const"], lam, _ptr(gL), _ptr(gR),
+                          _ptr(gdk), _ptr(gD))
+    return loss, gL, gR, gdk, gD

@@ -78,6 +78,7 @@ typedef struct {
     int nout;
     uint32_t flags;
     double pi, rho, sig2;
+    double prop;           /* coarse probability inherited at the centre (Eq. 10) */
     uint32_t pdf_flags;
 } ob_patch;
 
@@ -480,7 +481,7 @@ void ob_posterior(const ob_params *p, int level, ob_patch *pt, int n, double sig
     ob_window_offsets(p->window_step, delta);
     for (int k = 0; k < n; ++k) {
         ob_patch *q = &pt[k];
-        q->pi = q->rho = q->sig2 = 0.0;
+        q->pi = q->rho = q->sig2 = q->prop = 0.0;
         q->pdf_flags = 0;
         if (q->flags != 0) continue;
         double e[5], Z = 0.0;
@@ -500,6 +501,7 @@ void ob_posterior(const ob_params *p, int level, ob_patch *pt, int n, double sig
                 prop = coarse_lookup(Qc, wc, hc, cx, cy);
             }
             q->rho = wl * q->pi + prop;
+            q->prop = prop;
         } else {
             q->rho = q->pi;
         }
@@ -732,3 +734,393 @@ int ob_match_u8(const ob_params *p, const uint8_t *L, const uint8_t *R, int w, i
 
 int ob_sizeof_patch(void) { return (int)sizeof(ob_patch); }
 int ob_sizeof_params(void) { return (int)sizeof(ob_params); }
+
+/* ================================================================== */
+/* Differentiable form (finest level, discrete state frozen)           */
+/* ================================================================== */
+/*
+ * The function differentiated, given float images I_l, I_r of level 0 and
+ * the discrete state of a forward pass (which level-0 patches were kept,
+ * each patch's initial disparity d_init and inherited coarse probability
+ * prop, the valid pixels, and whether sigma_r sat at its floor):
+ *   g     = Sobel-x/8 of I_l
+ *   d_k   = `iters` Gauss-Newton steps from d_init (Eq. 1), kept patches
+ *   E_k   = window energies at d_k + delta_i
+ *   sigma_r (pooled, or the floor / fixed value as a constant)
+ *   pi_k  = window posterior (Eq. 5-6), rho_k = Gamma_0 pi_k + prop_k
+ *   D(x)  = sum_k omega_k d_k / sum_k omega_k over kept covering patches (Eq. 12)
+ *   loss  = ( sum_{x valid} |I_r(x - D(x)) - I_l(x)|
+ *           + lambda sum_{valid 4-neighbour pairs (p, q)} |D(p) - D(q)| ) / (w h)
+ * The analytic gradient treats each d_k as the root of
+ *   F_k(d) = sum_i gt_i (I_r(x_i - d) - T_i) = 0
+ * (implicit-function rule dd/dtheta = -(dF/dd)^-1 dF/dtheta), which is exact
+ * where the Gauss-Newton iterate has converged.
+ */
+
+/* right-sided slope of the clamped linear interpolation of a row at X */
+static double slope_row(const double *img, int w, int row, double X)
+{
+    if (X < 0.0 || X >= w - 1.0) return 0.0;
+    int x0 = (int)floor(X);
+    const double *r = img + (size_t)row * w;
+    return r[x0 + 1] - r[x0];
+}
+
+/* interpolation taps of a row sample at X (after clamping) */
+static void taps_row(int w, double X, int *x0, int *x1, double *t)
+{
+    if (X < 0.0) X = 0.0;
+    if (X > w - 1.0) X = w - 1.0;
+    *x0 = (int)floor(X);
+    *t = X - *x0;
+    *x1 = *x0 + 1 < w ? *x0 + 1 : w - 1;
+}
+
+typedef struct {
+    double d, E[5], e[5], pik[5], pi, rho, Fd, sigma_prop;
+} ob_dpatch;
+
+/* forward of the frozen level-0 function; fills the per-patch values, D,
+ * the weight sums W and the loss.  d_override (may be NULL) replaces the
+ * Gauss-Newton estimates (the patch disparities as free variables). */
+static double diff_forward(const ob_params *p, const double *L, const double *R, int w, int h,
+                           const uint8_t *kept, const double *dinit, const double *prop,
+                           const uint8_t *valid, int sr_const, double lambda,
+                           const double *d_override, double *G, ob_dpatch *dp, double *sr_out,
+                           double *D, double *W, double *M)
+{
+    const int P = p->patch, N = P * P;
+    int *ox = (int *)malloc(sizeof(int) * (w + 2)), *oy = (int *)malloc(sizeof(int) * (h + 2));
+    int npx = ob_origins(w, P, p->stride, ox), npy = ob_origins(h, P, p->stride, oy);
+    ob_sobel_x(L, w, h, G, OB_STORE_F64);
+    double delta[5];
+    ob_window_offsets(p->window_step, delta);
+    double *T = (double *)malloc(sizeof(double) * N), *gt = (double *)malloc(sizeof(double) * N);
+    double sumE0 = 0.0;
+    int nk = 0;
+    for (int k = 0; k < npx * npy; ++k) {
+        if (!kept[k]) continue;
+        const int x0 = ox[k % npx], y0 = oy[k / npx];
+        double gbar = 0.0;
+        for (int r = 0; r < P; ++r)
+            for (int c = 0; c < P; ++c) {
+                T[r * P + c] = L[(size_t)(y0 + r) * w + x0 + c];
+                gt[r * P + c] = G[(size_t)(y0 + r) * w + x0 + c];
+                gbar += gt[r * P + c];
+            }
+        gbar /= N;
+        double H = 0.0, cT = 0.0;
+        for (int i = 0; i < N; ++i) {
+            gt[i] -= gbar;
+            H += gt[i] * gt[i];
+            cT += gt[i] * T[i];
+        }
+        double d = dinit[k];
+        if (d_override) {
+            d = d_override[k];
+        } else {
+            const double dlim = (double)w + 2.0 * P;
+            for (int it = 0; it < p->iters; ++it) {
+                double acc = 0.0;
+                for (int r = 0; r < P; ++r)
+                    for (int c = 0; c < P; ++c)
+                        acc += gt[r * P + c] * sample_row(R, w, y0 + r, (double)(x0 + c) - d);
+                d += (acc - cT) / H;
+                if (d > dlim) d = dlim;
+                if (d < -dlim) d = -dlim;
+            }
+        }
+        ob_dpatch *q = &dp[k];
+        q->d = d;
+        double Fd = 0.0;
+        for (int r = 0; r < P; ++r)
+            for (int c = 0; c < P; ++c)
+                Fd -= gt[r * P + c] * slope_row(R, w, y0 + r, (double)(x0 + c) - d);
+        q->Fd = Fd;
+        for (int i = 0; i < 5; ++i) {
+            double mean = 0.0, E = 0.0;
+            for (int r = 0; r < P; ++r)
+                for (int c = 0; c < P; ++c)
+                    mean += sample_row(R, w, y0 + r, (double)(x0 + c) - d - delta[i]) - T[r * P + c];
+            mean /= N;
+            for (int r = 0; r < P; ++r)
+                for (int c = 0; c < P; ++c) {
+                    double a = sample_row(R, w, y0 + r, (double)(x0 + c) - d - delta[i]) -
+                               T[r * P + c] - mean;
+                    E += a * a;
+                }
+            q->E[i] = E;
+        }
+        sumE0 += q->E[0];
+        ++nk;
+    }
+    double sr;
+    if (sr_const || p->sigma_r_mode == OB_SIGMA_R_FIXED || nk == 0)
+        sr = p->sigma_r_mode == OB_SIGMA_R_FIXED ? p->sigma_r_fixed : p->sigma_r_floor;
+    else
+        sr = sqrt(sumE0 / ((double)nk * P * P));
+    *sr_out = sr;
+    const double S2 = 2.0 * sr * sr * 25.0;
+    const double w0 = ob_gamma_weight(0, p->levels);
+    for (int k = 0; k < npx * npy; ++k) {
+        if (!kept[k]) continue;
+        ob_dpatch *q = &dp[k];
+        double Z = 0.0;
+        for (int i = 0; i < 5; ++i) {
+            q->e[i] = -(q->E[i] - q->E[0]) / S2;
+            Z += exp(q->e[i]);
+        }
+        for (int i = 0; i < 5; ++i) q->pik[i] = exp(q->e[i]) / Z;
+        q->pi = 1.0 / Z;
+        q->rho = p->use_c2f ? w0 * q->pi + prop[k] : q->pi;
+    }
+    if (p->use_sgmm) ob_sgmm_table(P, p->sigma_s, M);
+    else for (int i = 0; i < N; ++i) M[i] = 1.0;
+    for (size_t i = 0; i < (size_t)w * h; ++i) { D[i] = 0.0; W[i] = 0.0; }
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            if (!valid[(size_t)y * w + x]) continue;
+            double sw = 0.0, swd = 0.0;
+            for (int ky = 0; ky < npy; ++ky) {
+                if (!(oy[ky] <= y && y < oy[ky] + P)) continue;
+                for (int kx = 0; kx < npx; ++kx) {
+                    if (!(ox[kx] <= x && x < ox[kx] + P)) continue;
+                    int k = ky * npx + kx;
+                    if (!kept[k]) continue;
+                    double om = dp[k].rho * M[(y - oy[ky]) * P + (x - ox[kx])];
+                    sw += om;
+                    swd += om * dp[k].d;
+                }
+            }
+            D[(size_t)y * w + x] = sw > 0.0 ? swd / sw : 0.0;
+            W[(size_t)y * w + x] = sw;
+        }
+    double loss = 0.0;
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            size_t i = (size_t)y * w + x;
+            if (!valid[i]) continue;
+            loss += fabs(sample_row(R, w, y, x - D[i]) - L[i]);
+            if (x + 1 < w && valid[i + 1]) loss += lambda * fabs(D[i] - D[i + 1]);
+            if (y + 1 < h && valid[i + w]) loss += lambda * fabs(D[i] - D[i + w]);
+        }
+    free(T);
+    free(gt);
+    free(ox);
+    free(oy);
+    return loss / ((double)w * h);
+}
+
+static double sgn(double v) { return v > 0.0 ? 1.0 : (v < 0.0 ? -1.0 : 0.0); }
+
+/* Frozen-state forward: returns the loss; D (w*h) and dk (patches) may be NULL. */
+double ob_diff_forward(const ob_params *p, const double *L, const double *R, int w, int h,
+                       const uint8_t *kept, const double *dinit, const double *prop,
+                       const uint8_t *valid, int sr_const, double lambda,
+                       const double *d_override, double *D_out, double *dk_out)
+{
+    const int P = p->patch;
+    int npx = ob_origins(w, P, p->stride, NULL), npy = ob_origins(h, P, p->stride, NULL);
+    ob_dpatch *dp = (ob_dpatch *)calloc((size_t)npx * npy, sizeof(ob_dpatch));
+    double *G = (double *)malloc(sizeof(double) * w * h), *D = (double *)malloc(sizeof(double) * w * h);
+    double *W = (double *)malloc(sizeof(double) * w * h), *M = (double *)malloc(sizeof(double) * P * P);
+    double sr;
+    double loss = diff_forward(p, L, R, w, h, kept, dinit, prop, valid, sr_const, lambda, d_override,
+                               G, dp, &sr, D, W, M);
+    if (D_out) memcpy(D_out, D, sizeof(double) * w * h);
+    if (dk_out)
+        for (int k = 0; k < npx * npy; ++k) dk_out[k] = kept[k] ? dp[k].d : 0.0;
+    free(dp);
+    free(G);
+    free(D);
+    free(W);
+    free(M);
+    return loss;
+}
+
+/* Analytic gradient of ob_diff_forward with respect to I_l, I_r (w*h each,
+ * overwritten) and to the patch disparities d_k as free variables (gdk,
+ * patches).  gD (w*h, may be NULL) receives dloss/dD. */
+double ob_diff_grad(const ob_params *p, const double *L, const double *R, int w, int h,
+                    const uint8_t *kept, const double *dinit, const double *prop,
+                    const uint8_t *valid, int sr_const, double lambda, double *gL, double *gR,
+                    double *gdk, double *gD_out)
+{
+    const int P = p->patch, N = P * P;
+    int *ox = (int *)malloc(sizeof(int) * (w + 2)), *oy = (int *)malloc(sizeof(int) * (h + 2));
+    int npx = ob_origins(w, P, p->stride, ox), npy = ob_origins(h, P, p->stride, oy);
+    const int np = npx * npy;
+    ob_dpatch *dp = (ob_dpatch *)calloc((size_t)np, sizeof(ob_dpatch));
+    double *G = (double *)malloc(sizeof(double) * w * h), *D = (double *)malloc(sizeof(double) * w * h);
+    double *W = (double *)malloc(sizeof(double) * w * h), *M = (double *)malloc(sizeof(double) * N);
+    double *gD = (double *)calloc((size_t)w * h, sizeof(double));
+    double *gG = (double *)calloc((size_t)w * h, sizeof(double));
+    double sr;
+    const double loss = diff_forward(p, L, R, w, h, kept, dinit, prop, valid, sr_const, lambda, NULL,
+                                     G, dp, &sr, D, W, M);
+    const double inv = 1.0 / ((double)w * h);
+    for (size_t i = 0; i < (size_t)w * h; ++i) { gL[i] = 0.0; gR[i] = 0.0; }
+
+    /* 1. loss -> D, and the direct image terms */
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            size_t i = (size_t)y * w + x;
+            if (!valid[i]) continue;
+            double X = x - D[i];
+            double r = sample_row(R, w, y, X) - L[i];
+            double s = sgn(r) * inv;
+            gD[i] += -s * slope_row(R, w, y, X);
+            int a0, a1;
+            double t;
+            taps_row(w, X, &a0, &a1, &t);
+            gR[(size_t)y * w + a0] += s * (1.0 - t);
+            gR[(size_t)y * w + a1] += s * t;
+            gL[i] += -s;
+            if (x + 1 < w && valid[i + 1]) {
+                double q = lambda * inv * sgn(D[i] - D[i + 1]);
+                gD[i] += q;
+                gD[i + 1] -= q;
+            }
+            if (y + 1 < h && valid[i + w]) {
+                double q = lambda * inv * sgn(D[i] - D[i + w]);
+                gD[i] += q;
+                gD[i + w] -= q;
+            }
+        }
+    if (gD_out) memcpy(gD_out, gD, sizeof(double) * w * h);
+
+    /* 2. fusion (Eq. 12) -> d_k and rho_k */
+    double *gd = (double *)calloc((size_t)np, sizeof(double));
+    double *gpi = (double *)calloc((size_t)np, sizeof(double));
+    for (int k = 0; k < np; ++k) {
+        if (!kept[k]) continue;
+        const int x0 = ox[k % npx], y0 = oy[k / npx];
+        double grho = 0.0;
+        for (int r = 0; r < P; ++r)
+            for (int c = 0; c < P; ++c) {
+                size_t i = (size_t)(y0 + r) * w + x0 + c;
+                if (!valid[i]) continue;
+                double m = M[r * P + c];
+                gd[k] += gD[i] * dp[k].rho * m / W[i];
+                grho += gD[i] * m * (dp[k].d - D[i]) / W[i];
+            }
+        gpi[k] = p->use_c2f ? ob_gamma_weight(0, p->levels) * grho : grho;
+    }
+
+    /* 3. posterior (Eq. 5-6) -> window energies and sigma_r */
+    double delta[5];
+    ob_window_offsets(p->window_step, delta);
+    const double S2 = 2.0 * sr * sr * 25.0;
+    int nk = 0;
+    double gsr = 0.0;
+    double *gE = (double *)calloc((size_t)np * 5, sizeof(double));
+    for (int k = 0; k < np; ++k) {
+        if (!kept[k]) continue;
+        ++nk;
+        const ob_dpatch *q = &dp[k];
+        for (int i = 1; i < 5; ++i) {
+            /* dpi/de_i = -pi pik_i; de_i/dE_i = -1/S2; de_i/dE_0 = 1/S2 */
+            double g = gpi[k] * q->pi * q->pik[i] / S2;
+            gE[k * 5 + i] += g;
+            gE[k * 5 + 0] -= g;
+            /* de_i/dsigma_r = -2 e_i / sigma_r */
+            gsr += gpi[k] * (-q->pi * q->pik[i]) * (-2.0 * q->e[i] / sr);
+        }
+    }
+    const int sr_free = !(sr_const || p->sigma_r_mode == OB_SIGMA_R_FIXED) && nk > 0;
+    if (sr_free)
+        for (int k = 0; k < np; ++k)
+            if (kept[k]) gE[k * 5 + 0] += gsr / (2.0 * sr * (double)nk * P * P);
+
+    /* 4. window energies and the patch solve (implicit function) -> images */
+    double *T = (double *)malloc(sizeof(double) * N), *gt = (double *)malloc(sizeof(double) * N);
+    double *a = (double *)malloc(sizeof(double) * N);
+    for (int k = 0; k < np; ++k) {
+        if (!kept[k]) continue;
+        const int x0 = ox[k % npx], y0 = oy[k / npx];
+        const double d = dp[k].d;
+        double gbar = 0.0;
+        for (int r = 0; r < P; ++r)
+            for (int c = 0; c < P; ++c) {
+                T[r * P + c] = L[(size_t)(y0 + r) * w + x0 + c];
+                gt[r * P + c] = G[(size_t)(y0 + r) * w + x0 + c];
+                gbar += gt[r * P + c];
+            }
+        gbar /= N;
+        for (int i = 0; i < N; ++i) gt[i] -= gbar;
+        double gdt = gd[k];
+        for (int i = 0; i < 5; ++i) {
+            const double ge = gE[k * 5 + i];
+            double mean = 0.0;
+            for (int r = 0; r < P; ++r)
+                for (int c = 0; c < P; ++c) {
+                    a[r * P + c] = sample_row(R, w, y0 + r, (double)(x0 + c) - d - delta[i]) - T[r * P + c];
+                    mean += a[r * P + c];
+                }
+            mean /= N;
+            for (int r = 0; r < P; ++r)
+                for (int c = 0; c < P; ++c) {
+                    double X = (double)(x0 + c) - d - delta[i];
+                    double dE_da = 2.0 * (a[r * P + c] - mean);
+                    gdt += ge * dE_da * (-slope_row(R, w, y0 + r, X));
+                    int a0, a1;
+                    double t;
+                    taps_row(w, X, &a0, &a1, &t);
+                    gR[(size_t)(y0 + r) * w + a0] += ge * dE_da * (1.0 - t);
+                    gR[(size_t)(y0 + r) * w + a1] += ge * dE_da * t;
+                    gL[(size_t)(y0 + r) * w + x0 + c] += -ge * dE_da;
+                }
+        }
+        gdk[k] = gdt;
+        /* implicit function: v = -gdt / (dF/dd) */
+        const double v = -gdt / dp[k].Fd;
+        double mres = 0.0;
+        for (int r = 0; r < P; ++r)
+            for (int c = 0; c < P; ++c)
+                mres += sample_row(R, w, y0 + r, (double)(x0 + c) - d) - T[r * P + c];
+        mres /= N;
+        for (int r = 0; r < P; ++r)
+            for (int c = 0; c < P; ++c) {
+                double X = (double)(x0 + c) - d;
+                int a0, a1;
+                double t;
+                taps_row(w, X, &a0, &a1, &t);
+                gR[(size_t)(y0 + r) * w + a0] += v * gt[r * P + c] * (1.0 - t);
+                gR[(size_t)(y0 + r) * w + a1] += v * gt[r * P + c] * t;
+                gL[(size_t)(y0 + r) * w + x0 + c] += -v * gt[r * P + c];
+                double res = sample_row(R, w, y0 + r, X) - T[r * P + c];
+                gG[(size_t)(y0 + r) * w + x0 + c] += v * (res - mres);
+            }
+    }
+    for (int k = 0; k < np; ++k)
+        if (!kept[k]) gdk[k] = 0.0;
+
+    /* 5. x-gradient (Sobel-x/8, reflect-101) -> I_l */
+    static const double wr[3] = {1.0, 2.0, 1.0};
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            double g = gG[(size_t)y * w + x];
+            if (g == 0.0) continue;
+            for (int j = -1; j <= 1; ++j) {
+                int yy = reflect101(y + j, h);
+                gL[(size_t)yy * w + reflect101(x + 1, w)] += g * wr[j + 1] / 8.0;
+                gL[(size_t)yy * w + reflect101(x - 1, w)] -= g * wr[j + 1] / 8.0;
+            }
+        }
+    free(T);
+    free(gt);
+    free(a);
+    free(gE);
+    free(gd);
+    free(gpi);
+    free(dp);
+    free(G);
+    free(D);
+    free(W);
+    free(M);
+    free(gD);
+    free(gG);
+    free(ox);
+    free(oy);
+    return loss;
+}
