@@ -406,8 +406,10 @@ def main():
 
     # ---- batched form: 64 uneven pairs, one launch per stage per level
     batched = None
+    fwd_bwd = None
     if not args.no_batched:
         batched = bench_batched(bd, dev, stream, flush, rank, ws)
+        fwd_bwd = bench_fwd_bwd(bd, dev, stream, flush, rank, ws)
 
     result = None
     if rank == 0:
@@ -437,7 +439,7 @@ def main():
             "clocks": clock_info,
             "cpu_baseline": cpu,
             "batched": batched,
-            "fwd_bwd": None,
+            "fwd_bwd": fwd_bwd,
             "paper_context": "BDIS(VAR) 0.072 s per 640x480 frame (4.27 Mpix/s) on one i5-9400 "
                              "core, finest scale 2^1 (Table VIII); 17 Hz claim (abstract)",
         }
@@ -447,6 +449,71 @@ def main():
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+DIFF_PARAMS = dict(patch=8, stride=4, levels=3, iters=8, variance=0, storage="f32")
+
+
+def bench_fwd_bwd(bd, dev, stream, flush, rank, ws, steps=10, warmup=3):
+    """Differentiable form: 16 float pairs of 640x480 (G1, seeds 16*rank + i),
+    one step = batched forward + L1 reprojection / smoothness loss + adjoint
+    (gradients w.r.t. both images and the patch disparities)."""
+    import torch
+
+    import synth
+    n, w, h = 16, 640, 480
+    Ls, Rs = [], []
+    for i in range(n):
+        p = synth.g1_pair(w, h, 16 * rank + i)
+        Ls.append(torch.from_numpy(p.left.astype("float32")).to(dev))
+        Rs.append(torch.from_numpy(p.right.astype("float32")).to(dev))
+    m = bd.BDIS(**DIFF_PARAMS)
+    B = bd.B
+    outs = [(torch.empty((h, w), device=dev), None, torch.empty((h, w), dtype=torch.uint8, device=dev))
+            for _ in range(n)]
+
+    def fwd():
+        m.match_f32(Ls, Rs, outs=outs, stream=stream)
+
+    bufs = None
+
+    def fwd_bwd():
+        nonlocal bufs
+        fwd()
+        if bufs is None:
+            bufs = m.loss_and_grad(0.1, stream=stream)
+            return
+        arr = bd._grad_table(m, bufs)
+        st = B.C.c_void_p(stream.cuda_stream)
+        B.check(B.lib().bdis_loss(m._h, B.C.c_float(0.1), arr, st), m._h)
+        B.check(B.lib().bdis_backward(m._h, arr, st), m._h)
+
+    def run(fn, k):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(k)]
+        with torch.cuda.stream(stream):
+            for i in range(k):
+                flush.zero_()
+                ev[i][0].record(stream)
+                fn()
+                ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / k
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            fwd_bwd()
+    torch.cuda.synchronize()
+    t_fb = max_over_ranks(run(fwd_bwd, steps), ws, dev)
+    t_f = max_over_ranks(run(fwd, steps), ws, dev)
+    loss = float(torch.stack([b["loss"] for b in bufs]).mean().item())
+    m.close()
+    px = n * w * h
+    return {"workload": "16 float pairs 640x480 (G1), P8 S4 L3, 8 iters, loss = L1 reprojection "
+                        "+ 0.1 smoothness; grads w.r.t. both images and patch disparities",
+            "value": round(ws * px / (t_fb / 1e3) / 1e6, 2), "unit": UNIT,
+            "ms_per_step": round(t_fb, 4), "fwd_only_value": round(ws * px / (t_f / 1e3) / 1e6, 2),
+            "fwd_only_ms": round(t_f, 4), "mean_loss": round(loss, 5)}
 
 
 def bench_batched(bd, dev, stream, flush, rank, ws, steps=10, warmup=3, compare_plain=True):

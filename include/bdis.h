@@ -167,6 +167,60 @@ bdis_status bdis_match_noalloc(const bdis_params *p, const uint8_t *left, const 
 /* Counters of the last call (synchronises `stream` to read them). */
 bdis_status bdis_get_stats(bdis_handle *h, bdis_stats *out, void *stream);
 
+/* ---- differentiable form (finest level) ----
+ * A forward on float images followed by a loss and its adjoint.  The
+ * function differentiated is the finest level with the forward's discrete
+ * state frozen (kept patches, their initial estimates and inherited coarse
+ * probabilities, valid pixels, sigma_r at its floor or not):
+ *   d_k  root of F_k(d) = sum_i gt_i (I_r(x_i - d) - T_i) (Eq. 1), reached by
+ *        the forward's Gauss-Newton iterations;
+ *   E_k, pi_k, rho_k (Eq. 5-6, 10-11), D = sum omega_k d_k / sum omega_k (Eq. 12).
+ * The patch adjoint is the implicit-function rule
+ *   dd_k/dtheta = -(dF_k/dd)^-1 dF_k/dtheta,
+ * exact where the iteration has converged.  The coarser levels are frozen.
+ * The paper has no loss or gradient: they are the extension that makes BDIS
+ * usable inside a learned pipeline. */
+
+typedef struct {
+    const float *left, *right;    /* w x h float images, `pitch` ELEMENTS per row */
+    int w, h, pitch;
+    float *disp, *var;            /* w*h out (var may be NULL)                    */
+    uint8_t *valid;               /* w*h out                                      */
+} bdis_pair_f32;
+
+/* Forward on float images (same pipeline as bdis_match; the level-0 images
+ * are read as float).  Required before bdis_loss / bdis_backward. */
+bdis_status bdis_match_f32(bdis_handle *h, const float *left, const float *right, int w, int hgt,
+                           int pitch, float *disp, float *var, uint8_t *valid, void *stream);
+bdis_status bdis_match_batched_f32(bdis_handle *h, int n, const bdis_pair_f32 *pairs,
+                                   void *stream);
+
+/* Per-pair gradient buffers (device, dense w*h unless stated). */
+typedef struct {
+    float *loss;          /* 1 float: the pair's loss (bdis_loss)                   */
+    float *g_disp;        /* dloss/dD (written by bdis_loss, read by bdis_backward) */
+    float *g_left;        /* dloss/dI_l                                            */
+    float *g_right;       /* dloss/dI_r                                            */
+    float *g_patch_disp;  /* npx*npy level-0 patches: dloss/dd_k with the images
+                             held fixed (bdis_backward); may be NULL              */
+} bdis_grad;
+
+/* Loss of the last forward (bdis_match_f32 / _batched_f32), for every pair:
+ *   loss = ( sum_{valid x} |I_r(x - D(x)) - I_l(x)|
+ *          + lambda sum_{valid 4-neighbour pairs} |D(p) - D(q)| ) / (w h)
+ * (I_r sampled by clamped linear interpolation along x).  Writes loss,
+ * g_disp, and the direct image terms: g_left is overwritten, g_right is
+ * zeroed and then accumulated.  `g` has one entry per pair of that call. */
+bdis_status bdis_loss(bdis_handle *h, float lambda, const bdis_grad *g, void *stream);
+
+/* Adjoint of the last forward: reads g_disp (from bdis_loss or from the
+ * caller's own loss), ADDS dloss/dI_l and dloss/dI_r to g_left / g_right
+ * (zero them first when g_disp comes from another loss) and writes
+ * g_patch_disp.  Needs the pooled or fixed sigma_r (BDIS_EUNSUPPORTED for
+ * LITERAL).  Image gradients are accumulated with float atomics, so their
+ * last bits may differ from run to run. */
+bdis_status bdis_backward(bdis_handle *h, const bdis_grad *g, void *stream);
+
 /* ---- execution options ---- */
 
 typedef enum {

@@ -913,6 +913,15 @@ static double diff_forward(const ob_params *p, const double *L, const double *R,
 
 static double sgn(double v) { return v > 0.0 ? 1.0 : (v < 0.0 ? -1.0 : 0.0); }
 
+/* Subgradient of |D_p - D_q| used for the smoothness term: 0 at a tie.
+ * Pixels covered by the same patches along one axis have exactly equal D in
+ * exact arithmetic (the common sGMM factor cancels, Eq. 12), so ties are
+ * structural; a difference within 1e-6 (|D_p| + |D_q|) counts as a tie. */
+static double sgn_tie(double a, double dp, double dq)
+{
+    return fabs(a) <= 1e-6 * (fabs(dp) + fabs(dq)) ? 0.0 : sgn(a);
+}
+
 /* Frozen-state forward: returns the loss; D (w*h) and dk (patches) may be NULL. */
 double ob_diff_forward(const ob_params *p, const double *L, const double *R, int w, int h,
                        const uint8_t *kept, const double *dinit, const double *prop,
@@ -977,12 +986,12 @@ double ob_diff_grad(const ob_params *p, const double *L, const double *R, int w,
             gR[(size_t)y * w + a1] += s * t;
             gL[i] += -s;
             if (x + 1 < w && valid[i + 1]) {
-                double q = lambda * inv * sgn(D[i] - D[i + 1]);
+                double q = lambda * inv * sgn_tie(D[i] - D[i + 1], D[i], D[i + 1]);
                 gD[i] += q;
                 gD[i + 1] -= q;
             }
             if (y + 1 < h && valid[i + w]) {
-                double q = lambda * inv * sgn(D[i] - D[i + w]);
+                double q = lambda * inv * sgn_tie(D[i] - D[i + w], D[i], D[i + w]);
                 gD[i] += q;
                 gD[i + w] -= q;
             }

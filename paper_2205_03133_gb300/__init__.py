@@ -17,7 +17,7 @@ import numpy as np
 from . import _binding as B
 from ._binding import BdisError
 
-__all__ = ["BDIS", "BdisError", "default_params", "B"]
+__all__ = ["BDIS", "BdisError", "default_params", "B", "_grad_table"]
 
 _STORAGE = {"f32": B.STORE_F32, "f16": B.STORE_F16}
 _SIGMA_R = {"pooled": B.SIGMA_R_POOLED, "literal": B.SIGMA_R_LITERAL, "fixed": B.SIGMA_R_FIXED}
@@ -173,3 +173,136 @@ class BDIS:
         gdt = np.float16 if self.params.storage == B.STORE_F16 else np.float32
         out["G"] = cp(v.grad, gdt, (v.h, v.grad_pitch))[:, :v.w].astype(np.float64)
         return out
+
+
+# ---------------------------------------------------------------- differentiable form
+
+def _f32_pair(l, r, d, v, m):
+    h, w = l.shape
+    return B.bdis_pair_f32(l.data_ptr(), r.data_ptr(), w, h, l.stride(0), d.data_ptr(),
+                           v.data_ptr() if v is not None else None, m.data_ptr())
+
+
+def _match_f32(self, lefts, rights, outs=None, stream=None):
+    """Forward on float32 CUDA images (lists of (h, w) tensors); returns a list
+    of (disp, var, valid) (preallocated `outs` are filled if given).
+    Required before loss_and_grad / backward."""
+    import torch
+    n = len(lefts)
+    arr = (B.bdis_pair_f32 * n)()
+    res = []
+    for i, (l, r) in enumerate(zip(lefts, rights)):
+        assert l.dtype == torch.float32 and r.dtype == torch.float32 and l.is_cuda
+        assert l.stride(1) == 1 and l.stride(0) == r.stride(0)
+        h, w = l.shape
+        if outs is not None:
+            d, v, m = outs[i]
+        else:
+            d = torch.empty((h, w), dtype=torch.float32, device=l.device)
+            v = (torch.empty((h, w), dtype=torch.float32, device=l.device)
+                 if self.params.variance else None)
+            m = torch.empty((h, w), dtype=torch.uint8, device=l.device)
+        arr[i] = _f32_pair(l, r, d, v, m)
+        res.append((d, v, m))
+    B.check(B.lib().bdis_match_batched_f32(self._h, n, arr, _stream_handle(stream)), self._h)
+    self._f32_shapes = [tuple(l.shape) for l in lefts]
+    # the loss and the adjoint read the forward's images and outputs: keep
+    # them alive until the next forward on this handle
+    self._f32_keep = (list(lefts), list(rights), res)
+    return res
+
+
+def _grad_table(self, bufs):
+    """ctypes table of per-pair gradient buffers (dicts of CUDA tensors)."""
+    n = len(bufs)
+    arr = (B.bdis_grad * n)()
+    for i, b in enumerate(bufs):
+        arr[i] = B.bdis_grad(*(t.data_ptr() if t is not None else None for t in
+                               (b.get("loss"), b["g_disp"], b["g_left"], b["g_right"],
+                                b.get("g_patch_disp"))))
+    return arr
+
+
+def _loss_and_grad(self, lam=0.1, stream=None):
+    """L1 reprojection + lam * smoothness of the last float forward and its
+    gradients.  Returns per pair dict(loss, g_disp, g_left, g_right,
+    g_patch_disp) (CUDA tensors)."""
+    import torch
+    bufs = []
+    for i, (h, w) in enumerate(self._f32_shapes):
+        v = B.bdis_level_view()
+        B.check(B.lib().bdis_level_view_get(self._h, i, 0, C.byref(v)), self._h)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        bufs.append(dict(loss=torch.empty(1, device=dev), g_disp=torch.empty((h, w), device=dev),
+                         g_left=torch.empty((h, w), device=dev),
+                         g_right=torch.empty((h, w), device=dev),
+                         g_patch_disp=torch.empty((v.npy, v.npx), device=dev)))
+    arr = _grad_table(self, bufs)
+    st = _stream_handle(stream)
+    B.check(B.lib().bdis_loss(self._h, C.c_float(lam), arr, st), self._h)
+    B.check(B.lib().bdis_backward(self._h, arr, st), self._h)
+    return bufs
+
+
+def _backward(self, g_disps, stream=None):
+    """Adjoint of the last float forward for caller-supplied dL/dD (list of
+    (h, w) tensors); returns (g_left, g_right, g_patch_disp) per pair."""
+    import torch
+    bufs = []
+    for i, gd in enumerate(g_disps):
+        h, w = gd.shape
+        v = B.bdis_level_view()
+        B.check(B.lib().bdis_level_view_get(self._h, i, 0, C.byref(v)), self._h)
+        bufs.append(dict(g_disp=torch.nan_to_num(gd.float(), nan=0.0).contiguous(),
+                         g_left=torch.zeros((h, w), device=gd.device),
+                         g_right=torch.zeros((h, w), device=gd.device),
+                         g_patch_disp=torch.empty((v.npy, v.npx), device=gd.device)))
+    arr = _grad_table(self, bufs)
+    B.check(B.lib().bdis_backward(self._h, arr, _stream_handle(stream)), self._h)
+    return [(b["g_left"], b["g_right"], b["g_patch_disp"]) for b in bufs]
+
+
+BDIS.match_f32 = _match_f32
+BDIS.loss_and_grad = _loss_and_grad
+BDIS.backward = _backward
+
+
+def disparity(model: "BDIS", left, right):
+    """Differentiable dense disparity of one float32 pair (torch autograd).
+    Returns (disp, valid); disp is NaN at invalid pixels and the gradient
+    flows to `left` and `right` through the library's adjoint.  The model's
+    handle keeps the forward state: run the backward before the next forward
+    on the same model."""
+    return _Disparity.apply(model, left, right)
+
+
+def _autograd_cls():
+    import torch
+
+    class Disparity(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, model, left, right):
+            (d, _, m), = model.match_f32([left.detach().contiguous()], [right.detach().contiguous()])
+            ctx.model = model
+            ctx.mark_non_differentiable(m)
+            return d, m
+
+        @staticmethod
+        def backward(ctx, g_disp, g_valid):
+            (gl, gr, _), = ctx.model.backward([g_disp])
+            return None, gl, gr
+
+    return Disparity
+
+
+class _Lazy:
+    cls = None
+
+    def apply(self, *a):
+        if _Lazy.cls is None:
+            _Lazy.cls = _autograd_cls()
+        return _Lazy.cls.apply(*a)
+
+
+_Disparity = _Lazy()
+__all__ += ["disparity"]

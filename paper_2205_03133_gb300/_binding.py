@@ -65,6 +65,18 @@ class bdis_level_view(C.Structure):
     ]
 
 
+class bdis_pair_f32(C.Structure):
+    _fields_ = [
+        ("left", C.c_void_p), ("right", C.c_void_p), ("w", C.c_int), ("h", C.c_int),
+        ("pitch", C.c_int), ("disp", C.c_void_p), ("var", C.c_void_p), ("valid", C.c_void_p),
+    ]
+
+
+class bdis_grad(C.Structure):
+    _fields_ = [("loss", C.c_void_p), ("g_disp", C.c_void_p), ("g_left", C.c_void_p),
+                ("g_right", C.c_void_p), ("g_patch_disp", C.c_void_p)]
+
+
 class bdis_profile(C.Structure):
     _fields_ = [("launches", C.c_int * 5), ("ms", C.c_double * 5)]
 
@@ -91,6 +103,10 @@ EXPORTS = [
     ("bdis_copy", C.c_int, [_vp, _vp, C.c_size_t, _vp]),
     ("bdis_set_option", C.c_int, [_h, C.c_int, C.c_int]),
     ("bdis_get_profile", C.c_int, [_h, C.POINTER(bdis_profile), C.c_int]),
+    ("bdis_match_f32", C.c_int, [_h, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp]),
+    ("bdis_match_batched_f32", C.c_int, [_h, C.c_int, C.POINTER(bdis_pair_f32), _vp]),
+    ("bdis_loss", C.c_int, [_h, C.c_float, C.POINTER(bdis_grad), _vp]),
+    ("bdis_backward", C.c_int, [_h, C.POINTER(bdis_grad), _vp]),
     ("bdis_match_noalloc", C.c_int, [C.POINTER(bdis_params), _vp, _vp, C.c_int, C.c_int, C.c_int,
                                      _vp, _vp, _vp, _vp]),
 ]

@@ -38,6 +38,9 @@ struct bdis_handle {
     bool use_graph = true;
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<char> graph_descs;
+    // scratch of the backward pass (grows, never shrinks)
+    char *garena = nullptr;
+    size_t garena_cap = 0;
     // per-kernel event timing
     bool profile = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -555,6 +558,7 @@ void bdis_destroy(bdis_handle *h) {
     }
     if (h->pinned) cudaFreeHost(h->pinned);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->garena) cudaFree(h->garena);
     for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
     delete h;
 }
@@ -728,6 +732,199 @@ bdis_status bdis_copy(void *dst, const void *src, size_t bytes, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st) != cudaSuccess) return BDIS_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return BDIS_ECUDA;
+    return BDIS_OK;
+}
+
+bdis_status bdis_match_batched_f32(bdis_handle *h, int n, const bdis_pair_f32 *pairs,
+                                   void *stream) {
+    if (!h) return BDIS_EINVAL;
+    if (n < 1 || !pairs) return fail(h, BDIS_EINVAL, "need at least one pair");
+    std::vector<bdis_pair> q((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        const bdis_pair_f32 &f = pairs[i];
+        // level 0 is indexed in elements; check_pair only needs pitch >= w
+        q[i] = bdis_pair{(const uint8_t *)f.left, (const uint8_t *)f.right, f.w, f.h, f.pitch,
+                         f.disp, f.var, f.valid};
+        std::string m = check_pair(h->p, q[i]);
+        if (!m.empty()) return fail(h, BDIS_EINVAL, "pair " + std::to_string(i) + ": " + m);
+    }
+    return run(h, n, q.data(), E_F32, (cudaStream_t)stream);
+}
+
+bdis_status bdis_match_f32(bdis_handle *h, const float *left, const float *right, int w, int hgt,
+                           int pitch, float *disp, float *var, uint8_t *valid, void *stream) {
+    bdis_pair_f32 q{left, right, w, hgt, pitch, disp, var, valid};
+    return bdis_match_batched_f32(h, 1, &q, stream);
+}
+
+namespace {
+
+// Builds and uploads the per-pair descriptors of the backward pass.
+bdis_status grad_setup(bdis_handle *h, const bdis_grad *g, bool need_loss, cudaStream_t st,
+                       GradArgs &a, std::vector<GradDesc> &gd, size_t &gG_off, size_t &gG_bytes,
+                       int totals[G_COUNT]) {
+    if (!g) return fail(h, BDIS_EINVAL, "null gradient table");
+    if (h->npairs < 1 || h->in_type != E_F32)
+        return fail(h, BDIS_EINVAL, "no float-image forward to differentiate (call bdis_match_f32)");
+    const bdis_params &p = h->p;
+    const int n = h->npairs;
+    for (int i = 0; i < n; ++i) {
+        if (!g[i].g_disp || !g[i].g_left || !g[i].g_right)
+            return fail(h, BDIS_EINVAL, "null gradient buffer");
+        if (need_loss && !g[i].loss) return fail(h, BDIS_EINVAL, "null loss pointer");
+    }
+    gd.assign((size_t)n, GradDesc{});
+    Bump b;
+    const size_t off_desc = b.take(sizeof(GradDesc) * n);
+    std::vector<size_t> oDw(n), oG(n), od(n), opi(n), osp(n), oce(n), olp(n);
+    const int ngrp = 256 / search_group(p.patch);
+    int begin[G_COUNT] = {0, 0, 0};
+    for (int i = 0; i < n; ++i) {
+        const LevelDesc &d = h->descs[(size_t)i];  // level 0
+        GradDesc &q = gd[i];
+        q.w = d.w;
+        q.h = d.h;
+        q.pitch = d.pitch;
+        q.gpitch = d.gpitch;
+        q.gtype = p.storage == BDIS_STORE_F16 ? E_F16 : E_F32;
+        q.npx = d.npx;
+        q.npy = d.npy;
+        q.kxreg = d.kxreg;
+        q.kyreg = d.kyreg;
+        const size_t px = (size_t)d.w * d.h, np = (size_t)d.npx * d.npy;
+        const int units[G_COUNT] = {(int)((px + 255) / 256), (int)((np + 255) / 256),
+                                    (int)((np + ngrp - 1) / ngrp)};
+        for (int k = 0; k < G_COUNT; ++k) {
+            q.work_begin[k] = begin[k];
+            begin[k] += units[k];
+        }
+        oDw[i] = b.take(sizeof(float) * px);
+        od[i] = b.take(sizeof(float) * np);
+        opi[i] = b.take(sizeof(float) * np);
+        osp[i] = b.take(sizeof(float) * 2 * ((np + 255) / 256));
+        oce[i] = b.take(sizeof(float));
+        olp[i] = b.take(sizeof(float) * ((px + 255) / 256));
+    }
+    // the gradient images of all pairs are contiguous (one memset)
+    gG_off = b.take(0);
+    for (int i = 0; i < n; ++i) oG[i] = b.take(sizeof(float) * (size_t)gd[i].w * gd[i].h);
+    gG_bytes = b.off - gG_off;
+    const size_t bytes = align_up(b.off, 256);
+    if (bytes > h->garena_cap) {
+        if (h->garena) {
+            cudaError_t e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaDeviceSynchronize");
+            cudaFree(h->garena);
+            h->garena = nullptr;
+            h->garena_cap = 0;
+        }
+        const size_t cap = align_up(bytes + bytes / 4, 1 << 20);
+        if (cudaMalloc((void **)&h->garena, cap) != cudaSuccess) {
+            cudaGetLastError();
+            h->garena = nullptr;
+            return fail(h, BDIS_ENOMEM, "cudaMalloc of the backward scratch failed");
+        }
+        h->garena_cap = cap;
+    }
+    char *base = h->garena;
+    for (int i = 0; i < n; ++i) {
+        const LevelDesc &d = h->descs[(size_t)i];
+        GradDesc &q = gd[i];
+        q.L = (const float *)d.L;
+        q.R = (const float *)d.R;
+        q.G = d.G;
+        q.disp = d.disp;
+        q.valid = d.valid;
+        q.rec = d.rec;
+        q.fuse = d.fuse;
+        q.sigma_r = d.sigma_r;
+        q.gDisp = g[i].g_disp;
+        q.gL = g[i].g_left;
+        q.gR = g[i].g_right;
+        q.gPatch = g[i].g_patch_disp;
+        q.loss = g[i].loss;
+        q.gDw = (float *)(base + oDw[i]);
+        q.gG = (float *)(base + oG[i]);
+        q.gd = (float *)(base + od[i]);
+        q.gpi = (float *)(base + opi[i]);
+        q.sig_part = (float *)(base + osp[i]);
+        q.coefE0 = (float *)(base + oce[i]);
+        q.loss_part = (float *)(base + olp[i]);
+    }
+    const size_t tbytes = sizeof(GradDesc) * n;
+    bdis_status s = ensure_pinned(h, std::max(tbytes, h->last_upload.size()));
+    if (s != BDIS_OK) return s;
+    cudaError_t e = cudaEventSynchronize(h->upload_done);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
+    std::memcpy(h->pinned, gd.data(), tbytes);
+    GradDesc *d_desc = (GradDesc *)(base + off_desc);
+    e = cudaMemcpyAsync(d_desc, h->pinned, tbytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "gradient descriptor upload");
+    e = cudaEventRecord(h->upload_done, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
+    std::memset(&a, 0, sizeof(a));
+    a.descs = d_desc;
+    a.npairs = n;
+    a.P = p.patch;
+    a.S = p.stride;
+    a.window_step = p.window_step;
+    double gsum = 0.0;
+    for (int m = 0; m < p.levels; ++m) gsum += std::ldexp(1.0, m);
+    a.gamma_w = (float)(1.0 / gsum);
+    a.sigma_r_mode = p.sigma_r_mode;
+    a.sigma_r_floor = p.sigma_r_floor;
+    a.use_sgmm = p.use_sgmm;
+    a.use_c2f = p.use_c2f;
+    fill_sgmm(p, a.m);
+    for (int k = 0; k < G_COUNT; ++k) totals[k] = begin[k];
+    a.total = begin[G_PIX];
+    return BDIS_OK;
+}
+
+}  // namespace
+
+bdis_status bdis_loss(bdis_handle *h, float lambda, const bdis_grad *g, void *stream) {
+    if (!h) return BDIS_EINVAL;
+    if (!std::isfinite(lambda) || lambda < 0.f) return fail(h, BDIS_EINVAL, "lambda must be >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    GradArgs a;
+    std::vector<GradDesc> gd;
+    size_t goff, gbytes;
+    int tot[G_COUNT];
+    bdis_status s = grad_setup(h, g, true, st, a, gd, goff, gbytes, tot);
+    if (s != BDIS_OK) return s;
+    a.lambda = lambda;
+    for (size_t i = 0; i < gd.size(); ++i) {
+        cudaError_t e = cudaMemsetAsync(gd[i].gR, 0, sizeof(float) * (size_t)gd[i].w * gd[i].h, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
+    }
+    a.total = tot[G_PIX];
+    cudaError_t e = launch_loss(a, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "loss launch");
+    return BDIS_OK;
+}
+
+bdis_status bdis_backward(bdis_handle *h, const bdis_grad *g, void *stream) {
+    if (!h) return BDIS_EINVAL;
+    if (h->p.sigma_r_mode == BDIS_SIGMA_R_LITERAL)
+        return fail(h, BDIS_EUNSUPPORTED, "no adjoint for the LITERAL sigma_r reading");
+    cudaStream_t st = (cudaStream_t)stream;
+    GradArgs a;
+    std::vector<GradDesc> gd;
+    size_t goff, gbytes;
+    int tot[G_COUNT];
+    bdis_status s = grad_setup(h, g, false, st, a, gd, goff, gbytes, tot);
+    if (s != BDIS_OK) return s;
+    cudaError_t e = cudaMemsetAsync(h->garena + goff, 0, gbytes, st);  // gradient images
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
+    a.total = tot[G_PIX];
+    if ((e = launch_bwd_pix(a, st)) != cudaSuccess) return cuda_fail(h, e, "backward launch");
+    a.total = tot[G_PATCH];
+    if ((e = launch_bwd_dens(a, st)) != cudaSuccess) return cuda_fail(h, e, "backward launch");
+    a.total = tot[G_GROUP];
+    if ((e = launch_bwd_patch(a, st)) != cudaSuccess) return cuda_fail(h, e, "backward launch");
+    a.total = tot[G_PIX];
+    if ((e = launch_bwd_sobel(a, st)) != cudaSuccess) return cuda_fail(h, e, "backward launch");
     return BDIS_OK;
 }
 

@@ -1,0 +1,75 @@
+// bdis_device.cuh -- small device helpers shared by the kernels of libbdis.
+#pragma once
+
+#include <cmath>
+
+#include "bdis_internal.cuh"
+
+namespace bdis {
+namespace {
+
+__device__ __forceinline__ float ldf(const uint8_t *p) { return (float)__ldg(p); }
+__device__ __forceinline__ float ldf(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float ldf(const __half *p) { return __half2float(__ldg(p)); }
+
+__device__ __forceinline__ void stf(float *p, float v) { *p = v; }
+__device__ __forceinline__ void stf(__half *p, float v) { *p = __float2half_rn(v); }
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
+
+// reflect about the edge pixel without repeating it (-1 -> 1, n -> n-2); n >= 3
+__device__ __forceinline__ int refl(int i, int n) {
+    i = i < 0 ? -i : i;
+    return i >= n ? 2 * (n - 1) - i : i;
+}
+
+// Patch origin k along an axis of length n: k*S for the regular origins,
+// n-P for the extra ragged one.
+__device__ __forceinline__ int origin(int k, int n, int P, int S, int kreg) {
+    return k < kreg ? k * S : n - P;
+}
+
+// Largest descriptor whose work range starts at or before `unit`.
+__device__ __forceinline__ int find_pair(const LevelDesc *d, int n, int unit, int kind) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (d[mid].work_begin[kind] <= unit) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Bilinear lookup of a coarse map at fine position (x, y): coarse
+// coordinate (x + 0.5)/2 - 0.5, clamped to the map.
+__device__ __forceinline__ float coarse_bilin(const float *__restrict__ m, int wc, int hc,
+                                              float x, float y) {
+    float X = (x + 0.5f) * 0.5f - 0.5f, Y = (y + 0.5f) * 0.5f - 0.5f;
+    X = fminf(fmaxf(X, 0.f), (float)(wc - 1));
+    Y = fminf(fmaxf(Y, 0.f), (float)(hc - 1));
+    int x0 = (int)floorf(X), y0 = (int)floorf(Y);
+    int x1 = min(x0 + 1, wc - 1), y1 = min(y0 + 1, hc - 1);
+    float fx = X - (float)x0, fy = Y - (float)y0;
+    float a = (1.f - fx) * __ldg(m + (size_t)y0 * wc + x0) + fx * __ldg(m + (size_t)y0 * wc + x1);
+    float b = (1.f - fx) * __ldg(m + (size_t)y1 * wc + x0) + fx * __ldg(m + (size_t)y1 * wc + x1);
+    return (1.f - fy) * a + fy * b;
+}
+
+template <int G>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Split x - d into an integer base and a fraction: x - d = base + t with
+// t in [0, 1), computed from d alone so it is exact for any x.
+__device__ __forceinline__ void split_shift(float d, int &off, float &t) {
+    float fl = floorf(d);
+    float f = d - fl;                 // exact
+    int di = (int)fl;
+    if (f > 0.f) { off = -di - 1; t = 1.f - f; }
+    else { off = -di; t = 0.f; }
+}
+
+}  // namespace
+}  // namespace bdis

@@ -1,0 +1,492 @@
+// bdis_grad.cu -- adjoint kernels of the differentiable finest level.
+//
+// The function differentiated is the level-0 pipeline of a forward pass on
+// float images with its discrete state frozen (kept patches, their initial
+// estimates and inherited coarse probabilities, valid pixels, whether sigma_r
+// sat at its floor):
+//   g = Sobel-x/8(I_l); d_k solves F_k(d) = sum_i gt_i (I_r(x_i - d) - T_i) = 0
+//   (Eq. 1); E_k(delta) window energies; sigma_r pooled; pi_k (Eq. 5-6);
+//   rho_k = Gamma_0 pi_k + prop_k (Eq. 10-11); D = sum omega d / sum omega (Eq. 12).
+// The loss is L1 photometric reprojection plus lambda times first-order
+// smoothness, both summed over valid pixels and divided by w h.  The patch
+// adjoint is the implicit-function rule dd/dtheta = -(dF/dd)^-1 dF/dtheta.
+//
+// Image gradients are accumulated with float atomics (the sample positions
+// of different patches overlap), so their last bits depend on the order in
+// which the hardware serves the atomics.
+#include "bdis_device.cuh"
+
+namespace bdis {
+namespace {
+
+__device__ __forceinline__ float sgnf(float v) { return v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f); }
+
+// subgradient of |D_p - D_q|: 0 at a tie (pixels covered by the same patches
+// along one axis have equal D in exact arithmetic; a difference within
+// 1e-6 (|D_p| + |D_q|) is a tie)
+__device__ __forceinline__ float sgn_tie(float dp, float dq) {
+    const float a = dp - dq;
+    return fabsf(a) <= 1e-6f * (fabsf(dp) + fabsf(dq)) ? 0.f : sgnf(a);
+}
+
+// Sample of a row at x - d = base + t (clamped linear interpolation), its
+// taps and the right-sided slope (0 where the coordinate is clamped).
+struct Tap {
+    int x0, x1;
+    float t, v, slope;
+};
+
+__device__ __forceinline__ Tap tap_row(const float *__restrict__ row, int w, int base, float t) {
+    Tap q;
+    if (base < 0) {
+        q.x0 = q.x1 = 0;
+        q.t = 0.f;
+        q.v = __ldg(row);
+        q.slope = 0.f;
+    } else if (base >= w - 1) {
+        q.x0 = q.x1 = w - 1;
+        q.t = 0.f;
+        q.v = __ldg(row + w - 1);
+        q.slope = 0.f;
+    } else {
+        q.x0 = base;
+        q.x1 = base + 1;
+        q.t = t;
+        const float a = __ldg(row + base), b = __ldg(row + base + 1);
+        q.v = fmaf(t, b - a, a);
+        q.slope = b - a;
+    }
+    return q;
+}
+
+// tap of the sample x - d of pixel x
+__device__ __forceinline__ Tap tap_at(const float *__restrict__ row, int w, int x, float d) {
+    int off;
+    float t;
+    split_shift(d, off, t);
+    return tap_row(row, w, x + off, t);
+}
+
+__device__ __forceinline__ int find_pair_g(const GradDesc *d, int n, int unit, int kind) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d[mid].work_begin[kind] <= unit) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ float ldg_grad(const GradDesc &g, int row, int col) {
+    const size_t i = (size_t)row * g.gpitch + col;
+    return g.gtype == E_F16 ? __half2float(__ldg((const __half *)g.G + i))
+                            : __ldg((const float *)g.G + i);
+}
+
+// Sum of the sGMM weights over the kept patches covering pixel (x, y).
+__device__ float weight_sum(const GradDesc &g, const GradArgs &a, int x, int y) {
+    const int P = a.P, S = a.S;
+    const int kxlo = x - P + 1 > 0 ? (x - P + 1 + S - 1) / S : 0;
+    const int kxhi = min(g.kxreg - 1, x / S);
+    const bool kxext = g.npx > g.kxreg && x >= g.w - P;
+    const int kylo = y - P + 1 > 0 ? (y - P + 1 + S - 1) / S : 0;
+    const int kyhi = min(g.kyreg - 1, y / S);
+    const bool kyext = g.npy > g.kyreg && y >= g.h - P;
+    const int nky = kyhi - kylo + 1 + (kyext ? 1 : 0);
+    const int nkx = kxhi - kxlo + 1 + (kxext ? 1 : 0);
+    float sw = 0.f;
+    for (int iy = 0; iy < nky; ++iy) {
+        const int ky = (kylo + iy <= kyhi) ? kylo + iy : g.npy - 1;
+        const int oy = origin(ky, g.h, P, S, g.kyreg);
+        const float my = a.use_sgmm ? a.m[y - oy] : 1.f;
+        for (int ix = 0; ix < nkx; ++ix) {
+            const int kx = (kxlo + ix <= kxhi) ? kxlo + ix : g.npx - 1;
+            const int ox = origin(kx, g.w, P, S, g.kxreg);
+            const float4 f = __ldg(g.fuse + (size_t)ky * g.npx + kx);
+            if (f.w == 0.f) continue;
+            sw += f.y * (my * (a.use_sgmm ? a.m[x - ox] : 1.f));
+        }
+    }
+    return sw;
+}
+
+__device__ __forceinline__ float block_sum256(float v, float *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    float s = 0.f;
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    return s;
+}
+
+// ---------------------------------------------------------------- loss (K6)
+
+// Per pixel: loss terms, dL/dD, the direct dL/dI_l (written) and dL/dI_r
+// (scattered into a zeroed buffer); one loss partial per block.
+__global__ void __launch_bounds__(256) k_loss(GradArgs a) {
+    __shared__ float red[32];
+    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) {
+        const int pi = find_pair_g(a.descs, a.npairs, unit, G_PIX);
+        const GradDesc &g = a.descs[pi];
+        const int local = unit - g.work_begin[G_PIX];
+        const int idx = local * blockDim.x + threadIdx.x;
+        float part = 0.f;
+        if (idx < g.w * g.h) {
+            const int x = idx % g.w, y = idx / g.w;
+            const float inv = 1.f / ((float)g.w * (float)g.h);
+            float gD = 0.f, gLd = 0.f;
+            if (g.valid[idx]) {
+                const float D = g.disp[idx];
+                const float *rrow = g.R + (size_t)y * g.pitch;
+                const Tap q = tap_at(rrow, g.w, x, D);
+                const float r = q.v - __ldg(g.L + (size_t)y * g.pitch + x);
+                const float s = sgnf(r) * inv;
+                part += fabsf(r);
+                gD -= s * q.slope;
+                gLd = -s;
+                atomicAdd(g.gR + (size_t)y * g.w + q.x0, s * (1.f - q.t));
+                atomicAdd(g.gR + (size_t)y * g.w + q.x1, s * q.t);
+                const float li = a.lambda * inv;
+                if (x + 1 < g.w && g.valid[idx + 1]) {
+                    part += a.lambda * fabsf(D - g.disp[idx + 1]);
+                    gD += li * sgn_tie(D, g.disp[idx + 1]);
+                }
+                if (y + 1 < g.h && g.valid[idx + g.w]) {
+                    part += a.lambda * fabsf(D - g.disp[idx + g.w]);
+                    gD += li * sgn_tie(D, g.disp[idx + g.w]);
+                }
+                if (x > 0 && g.valid[idx - 1]) gD += li * sgn_tie(D, g.disp[idx - 1]);
+                if (y > 0 && g.valid[idx - g.w]) gD += li * sgn_tie(D, g.disp[idx - g.w]);
+            }
+            g.gDisp[idx] = gD;
+            g.gL[(size_t)y * g.w + x] = gLd;
+        }
+        const float bs = block_sum256(part, red);
+        if (threadIdx.x == 0) g.loss_part[local] = bs;
+    }
+}
+
+// One block per pair: loss = sum of the partials / (w h), in a fixed order.
+__global__ void __launch_bounds__(256) k_loss_reduce(GradArgs a) {
+    __shared__ float red[32];
+    for (int pair = blockIdx.x; pair < a.npairs; pair += gridDim.x) {
+        const GradDesc &g = a.descs[pair];
+        const int n = (g.w * g.h + 255) / 256;
+        float s = 0.f;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) s += g.loss_part[i];
+        const float t = block_sum256(s, red);
+        if (threadIdx.x == 0 && g.loss) *g.loss = t / ((float)g.w * (float)g.h);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- fusion adjoint
+
+// Per pixel: dL/dD / sum omega (0 at invalid pixels).
+__global__ void __launch_bounds__(256) k_bwd_pix(GradArgs a) {
+    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) {
+        const GradDesc &g = a.descs[find_pair_g(a.descs, a.npairs, unit, G_PIX)];
+        const int idx = (unit - g.work_begin[G_PIX]) * blockDim.x + threadIdx.x;
+        if (idx >= g.w * g.h) continue;
+        float v = 0.f;
+        if (g.valid[idx]) {
+            const float sw = weight_sum(g, a, idx % g.w, idx / g.w);
+            v = sw > 0.f ? g.gDisp[idx] / sw : 0.f;
+        }
+        g.gDw[idx] = v;
+    }
+}
+
+// Per kept patch: dL/dd_k = sum_x gDw rho_k M, dL/drho_k = sum_x gDw M (d_k - D),
+// dL/dpi_k, and the patch's share of dL/dsigma_r (block partials).
+__global__ void __launch_bounds__(256) k_bwd_dens(GradArgs a) {
+    __shared__ float red[32];
+    const int P = a.P, S = a.S;
+    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) {
+        const int pi = find_pair_g(a.descs, a.npairs, unit, G_PATCH);
+        const GradDesc &g = a.descs[pi];
+        const int local = unit - g.work_begin[G_PATCH];
+        const int k = local * blockDim.x + threadIdx.x;
+        float gsr = 0.f, cnt = 0.f;
+        if (k < g.npx * g.npy) {
+            const bdis_patch_record &rc = g.rec[k];
+            float gd = 0.f, gpi = 0.f;
+            if (rc.flags == 0u) {
+                const int ox = origin(k % g.npx, g.w, P, S, g.kxreg);
+                const int oy = origin(k / g.npx, g.h, P, S, g.kyreg);
+                float grho = 0.f;
+                for (int r = 0; r < P; ++r) {
+                    const float my = a.use_sgmm ? a.m[r] : 1.f;
+                    for (int c = 0; c < P; ++c) {
+                        const size_t i = (size_t)(oy + r) * g.w + ox + c;
+                        const float w = __ldg(g.gDw + i);
+                        if (w == 0.f) continue;
+                        const float M = my * (a.use_sgmm ? a.m[c] : 1.f);
+                        gd = fmaf(w * rc.rho, M, gd);
+                        grho = fmaf(w * M, rc.d - __ldg(g.disp + i), grho);
+                    }
+                }
+                gpi = a.use_c2f ? a.gamma_w * grho : grho;
+                // dpi/dsigma_r = (2 pi / sigma_r) sum_i pi_i e_i
+                const float sr = __ldg(g.sigma_r);
+                const float S2 = 2.f * sr * sr * (float)(kWindow * kWindow);
+                float e[5], Z = 1.f;
+                e[0] = 0.f;
+#pragma unroll
+                for (int i = 1; i < 5; ++i) {
+                    e[i] = -rc.E[i] / S2;
+                    Z += expf(e[i]);
+                }
+                float se = 0.f;
+#pragma unroll
+                for (int i = 1; i < 5; ++i) se += expf(e[i]) / Z * e[i];
+                gsr = gpi * (2.f * rc.pi / sr) * se;
+                cnt = 1.f;
+            }
+            g.gd[k] = gd;
+            g.gpi[k] = gpi;
+        }
+        const float s1 = block_sum256(gsr, red);
+        const float s2 = block_sum256(cnt, red);
+        if (threadIdx.x == 0) {
+            g.sig_part[2 * local] = s1;
+            g.sig_part[2 * local + 1] = s2;
+        }
+    }
+}
+
+// One block per pair: dL/dsigma_r -> the coefficient added to every kept
+// patch's dL/dE(0) (pooled sigma_r: dsigma_r/dE_k(0) = 1/(2 sigma_r N P^2)).
+__global__ void __launch_bounds__(256) k_bwd_sigma(GradArgs a) {
+    __shared__ float red[32];
+    for (int pair = blockIdx.x; pair < a.npairs; pair += gridDim.x) {
+        const GradDesc &g = a.descs[pair];
+        const int n = (g.npx * g.npy + 255) / 256;
+        float s = 0.f, c = 0.f;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            s += g.sig_part[2 * i];
+            c += g.sig_part[2 * i + 1];
+        }
+        const float S = block_sum256(s, red);
+        const float Cn = block_sum256(c, red);
+        if (threadIdx.x == 0) {
+            const float sr = *g.sigma_r;
+            const bool free_sr = a.sigma_r_mode == BDIS_SIGMA_R_POOLED && sr > a.sigma_r_floor &&
+                                 Cn > 0.f;
+            *g.coefE0 = free_sr ? S / (2.f * sr * Cn * (float)(a.P * a.P)) : 0.f;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- patch adjoint
+
+// A group of G lanes per kept patch, lane = patch row (as in the search).
+// Window energies and the implicit-function rule through F_k.
+template <int P>
+__global__ void __launch_bounds__(256) k_bwd_patch(GradArgs a) {
+    constexpr int G = P <= 8 ? 8 : 16;
+    constexpr int N = P * P;
+    constexpr float invN = 1.f / (float)N;
+    const int tid = threadIdx.x;
+    const int gl = tid & (G - 1);
+    const int grp = tid / G;
+    const int ngrp = blockDim.x / G;
+    const bool row_on = gl < P;
+    const float h = a.window_step;
+    const float dl[5] = {0.f, -h, h, -2.f * h, 2.f * h};
+    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) {
+        const GradDesc &g = a.descs[find_pair_g(a.descs, a.npairs, unit, G_GROUP)];
+        const int k = (unit - g.work_begin[G_GROUP]) * ngrp + grp;
+        const bool active_patch = k < g.npx * g.npy && g.rec[min(k, g.npx * g.npy - 1)].flags == 0u;
+        const int kk = min(k, g.npx * g.npy - 1);
+        const bdis_patch_record rc = g.rec[kk];
+        const int ox = origin(kk % g.npx, g.w, P, a.S, g.kxreg);
+        const int oy = origin(kk / g.npx, g.h, P, a.S, g.kyreg);
+        const int row = oy + (row_on ? gl : 0);
+        const float *Lrow = g.L + (size_t)row * g.pitch + ox;
+        const float *Rrow = g.R + (size_t)row * g.pitch;
+        float T[P], gt[P];
+        float gs = 0.f;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            T[j] = __ldg(Lrow + j);
+            gt[j] = row_on ? ldg_grad(g, row, ox + j) : 0.f;
+            gs += gt[j];
+        }
+        const float gbar = group_sum<G>(gs) * invN;
+#pragma unroll
+        for (int j = 0; j < P; ++j) gt[j] = row_on ? gt[j] - gbar : 0.f;
+        const float d = rc.d;
+        // residual at d, and dF/dd
+        float sres = 0.f, fd = 0.f;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            const Tap q = tap_at(Rrow, g.w, ox + j, d);
+            sres += row_on ? q.v - T[j] : 0.f;
+            fd -= gt[j] * q.slope;
+        }
+        const float mres = group_sum<G>(sres) * invN;
+        const float Fd = group_sum<G>(fd);
+        // dE_i/dd and the means of the window residuals
+        float abar[5], dEdd[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            float sa = 0.f;
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                const Tap q = tap_at(Rrow, g.w, ox + j, d + dl[i]);
+                sa += row_on ? q.v - T[j] : 0.f;
+            }
+            abar[i] = group_sum<G>(sa) * invN;
+        }
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            float s = 0.f;
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                const Tap q = tap_at(Rrow, g.w, ox + j, d + dl[i]);
+                s += row_on ? 2.f * (q.v - T[j] - abar[i]) * (-q.slope) : 0.f;
+            }
+            dEdd[i] = group_sum<G>(s);
+        }
+        // dL/dE_i from dL/dpi_k and sigma_r
+        const float sr = __ldg(g.sigma_r);
+        const float S2 = 2.f * sr * sr * (float)(kWindow * kWindow);
+        float pik[5], Z = 1.f;
+        pik[0] = 1.f;
+#pragma unroll
+        for (int i = 1; i < 5; ++i) {
+            pik[i] = expf(-rc.E[i] / S2);
+            Z += pik[i];
+        }
+        const float gpi = g.gpi[kk];
+        float gE[5];
+        gE[0] = __ldg(g.coefE0);
+#pragma unroll
+        for (int i = 1; i < 5; ++i) {
+            gE[i] = gpi * rc.pi * (pik[i] / Z) / S2;
+            gE[0] -= gE[i];
+        }
+        float gdt = g.gd[kk];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) gdt = fmaf(gE[i], dEdd[i], gdt);
+        const float v = -gdt / Fd;
+        if (active_patch && gl == 0 && g.gPatch) g.gPatch[kk] = gdt;
+        if (!(active_patch && row_on)) continue;
+        // scatter: window energies, the solve F, the gradient image
+        float *gRrow = g.gR + (size_t)row * g.w;
+        float *gLrow = g.gL + (size_t)row * g.w + ox;
+        float *gGrow = g.gG + (size_t)row * g.w + ox;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            float tsum = 0.f;
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                const Tap q = tap_at(Rrow, g.w, ox + j, d + dl[i]);
+                const float c = gE[i] * 2.f * (q.v - T[j] - abar[i]);
+                atomicAdd(gRrow + q.x0, c * (1.f - q.t));
+                atomicAdd(gRrow + q.x1, c * q.t);
+                tsum += c;
+            }
+            const Tap q = tap_at(Rrow, g.w, ox + j, d);
+            atomicAdd(gRrow + q.x0, v * gt[j] * (1.f - q.t));
+            atomicAdd(gRrow + q.x1, v * gt[j] * q.t);
+            atomicAdd(gLrow + j, -tsum - v * gt[j]);
+            atomicAdd(gGrow + j, v * ((q.v - T[j]) - mres));
+        }
+    }
+}
+
+// dL/dg -> dL/dI_l through Sobel-x/8 (reflect-101), scattered.
+__global__ void __launch_bounds__(256) k_bwd_sobel(GradArgs a) {
+    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) {
+        const GradDesc &g = a.descs[find_pair_g(a.descs, a.npairs, unit, G_PIX)];
+        const int idx = (unit - g.work_begin[G_PIX]) * blockDim.x + threadIdx.x;
+        if (idx >= g.w * g.h) continue;
+        const float v = g.gG[idx];
+        if (v == 0.f) continue;
+        const int x = idx % g.w, y = idx / g.w;
+        const int xp = refl(x + 1, g.w), xm = refl(x - 1, g.w);
+#pragma unroll
+        for (int j = -1; j <= 1; ++j) {
+            const float wgt = (j == 0 ? 2.f : 1.f) * 0.125f * v;
+            float *row = g.gL + (size_t)refl(y + j, g.h) * g.w;
+            atomicAdd(row + xp, wgt);
+            atomicAdd(row + xm, -wgt);
+        }
+    }
+}
+
+int grad_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+int ggrid(int total) {
+    const int cap = grad_sms() * 8;
+    return total < 1 ? 1 : (total < cap ? total : cap);
+}
+
+}  // namespace
+
+cudaError_t launch_loss(const GradArgs &a, cudaStream_t s) {
+    k_loss<<<ggrid(a.total), 256, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_loss_reduce<<<ggrid(a.npairs), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_pix(const GradArgs &a, cudaStream_t s) {
+    k_bwd_pix<<<ggrid(a.total), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_dens(const GradArgs &a, cudaStream_t s) {
+    k_bwd_dens<<<ggrid(a.total), 256, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_bwd_sigma<<<ggrid(a.npairs), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_patch(const GradArgs &a, cudaStream_t s) {
+    const int grid = ggrid(a.total);
+    switch (a.P) {
+        case 4: k_bwd_patch<4><<<grid, 256, 0, s>>>(a); break;
+        case 5: k_bwd_patch<5><<<grid, 256, 0, s>>>(a); break;
+        case 6: k_bwd_patch<6><<<grid, 256, 0, s>>>(a); break;
+        case 7: k_bwd_patch<7><<<grid, 256, 0, s>>>(a); break;
+        case 8: k_bwd_patch<8><<<grid, 256, 0, s>>>(a); break;
+        case 9: k_bwd_patch<9><<<grid, 256, 0, s>>>(a); break;
+        case 10: k_bwd_patch<10><<<grid, 256, 0, s>>>(a); break;
+        case 11: k_bwd_patch<11><<<grid, 256, 0, s>>>(a); break;
+        case 12: k_bwd_patch<12><<<grid, 256, 0, s>>>(a); break;
+        case 13: k_bwd_patch<13><<<grid, 256, 0, s>>>(a); break;
+        case 14: k_bwd_patch<14><<<grid, 256, 0, s>>>(a); break;
+        case 15: k_bwd_patch<15><<<grid, 256, 0, s>>>(a); break;
+        case 16: k_bwd_patch<16><<<grid, 256, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_sobel(const GradArgs &a, cudaStream_t s) {
+    k_bwd_sobel<<<ggrid(a.total), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace bdis

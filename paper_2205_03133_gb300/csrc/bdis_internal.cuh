@@ -68,6 +68,44 @@ struct LaunchArgs {
     float m[kMaxPatch];       // 1D sGMM factors m[a] (Eq. 8 is separable)
 };
 
+// ---- differentiable finest level (bdis_grad.cu)
+
+enum GradWork { G_PIX = 0, G_PATCH = 1, G_GROUP = 2, G_COUNT = 3 };
+
+// One pair of the backward pass.  Images are the level-0 float images of the
+// forward; gradients are dense w*h arrays.
+struct alignas(16) GradDesc {
+    const float *L, *R;            // level-0 images, `pitch` elements per row
+    const void *G;                 // level-0 x-gradient (storage type)
+    const float *disp;             // forward disparity (valid pixels)
+    const uint8_t *valid;
+    const bdis_patch_record *rec;  // level-0 records
+    const float4 *fuse;            // level-0 fusion records
+    const float *sigma_r;
+    float *gDisp, *gL, *gR, *gPatch, *loss;        // caller buffers
+    float *gDw, *gG, *gd, *gpi, *sig_part, *coefE0, *loss_part;  // scratch
+    int w, h, pitch, gpitch, gtype;
+    int npx, npy, kxreg, kyreg;
+    int work_begin[G_COUNT];
+};
+
+struct GradArgs {
+    const GradDesc *descs;
+    int npairs, total;
+    int P, S;
+    float window_step, lambda, gamma_w;
+    int sigma_r_mode;
+    float sigma_r_floor;
+    int use_sgmm, use_c2f;
+    float m[kMaxPatch];
+};
+
+cudaError_t launch_loss(const GradArgs &a, cudaStream_t s);        // + per-pair reduce
+cudaError_t launch_bwd_pix(const GradArgs &a, cudaStream_t s);
+cudaError_t launch_bwd_dens(const GradArgs &a, cudaStream_t s);    // + sigma_r adjoint
+cudaError_t launch_bwd_patch(const GradArgs &a, cudaStream_t s);
+cudaError_t launch_bwd_sobel(const GradArgs &a, cudaStream_t s);
+
 // Kernel launchers (bdis_kernels.cu).  Each returns cudaGetLastError().
 cudaError_t launch_pyramid(const LaunchArgs &a, int in_type, int out_type, cudaStream_t s);
 cudaError_t launch_search(const LaunchArgs &a, int in_type, int g_type, size_t smem, int grid,

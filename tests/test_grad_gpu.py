@@ -1,0 +1,142 @@
+"""GPU adjoint of the differentiable finest level against the oracle's
+analytic gradient (itself pinned to FP64 central differences on CPU), on the
+same seeded float images, through the C ABI.
+
+Tolerance: per element |g_gpu - g_oracle| <= 1e-4 * max|g_oracle| (+ a
+FP32 floor), on all elements for the small case and on >= 99.9 % of them at
+640x480, where FP32 and FP64 can take a different side of a kink of the L1
+terms (sign of a residual or of a disparity difference within rounding of
+zero) at a handful of pixels."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity import oracle_params
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def bd():
+    import paper_2205_03133_gb300 as bd
+    from paper_2205_03133_gb300 import build
+    build.build()
+    return bd
+
+
+def _gpu(bd, kw, L32, R32, lam=0.1):
+    import torch
+    m = bd.BDIS(**kw)
+    Lt = torch.from_numpy(L32).cuda()
+    Rt = torch.from_numpy(R32).cuda()
+    (d, v, ok), = m.match_f32([Lt], [Rt])
+    g, = m.loss_and_grad(lam)
+    torch.cuda.synchronize()
+    rec = m.level_view(0, 0)["patches"]
+    out = {k: t.cpu().numpy() for k, t in g.items()}
+    out.update(disp=d.cpu().numpy(), valid=ok.cpu().numpy().astype(bool), rec=rec, params=m.params)
+    m.close()
+    return out
+
+
+def _oracle(gp, L, R, lam=0.1):
+    op = oracle_params(gp)
+    o = oracle.match(op, L, R, trace=True)
+    st = oracle.frozen_state(op, o)
+    loss, gL, gR, gdk, gD = oracle.diff_grad(op, L, R, st, lam)
+    return dict(loss=loss, g_left=gL, g_right=gR, g_patch=gdk, g_disp=gD, out=o, st=st)
+
+
+def _close(a, b, frac=1.0):
+    scale = np.abs(b).max()
+    err = np.abs(a.astype(np.float64) - b)
+    ok = err <= REL * scale + 1e-9
+    return ok.mean() >= frac, dict(frac_ok=float(ok.mean()), max_rel=float(err.max() / scale))
+
+
+@pytest.mark.parametrize("kw", [
+    dict(patch=8, stride=4, levels=3, iters=50),
+    dict(patch=8, stride=4, levels=3, iters=50, sigma_r_mode="fixed"),
+    dict(patch=12, stride=4, levels=2, iters=50, use_sgmm=0),
+])
+def test_adjoint_matches_oracle_small(bd, kw):
+    pr = synth.g1_pair(64, 48, 3, d0=1.0, d1=3.0, amp=1.0, as_float=True)
+    L32, R32 = pr.left.astype(np.float32), pr.right.astype(np.float32)
+    L, R = L32.astype(np.float64), R32.astype(np.float64)
+    g = _gpu(bd, kw, L32, R32)
+    o = _oracle(g["params"], L, R)
+    # same discrete state on both sides
+    assert np.array_equal(g["valid"], o["out"]["valid"])
+    assert np.array_equal(g["rec"]["flags"].ravel() == 0, o["st"]["kept"].astype(bool))
+    assert abs(float(g["loss"][0]) - o["loss"]) <= 1e-5 * o["loss"]
+    for key, okey in (("g_disp", "g_disp"), ("g_left", "g_left"), ("g_right", "g_right")):
+        good, info = _close(g[key], o[okey])
+        assert good, (key, info)
+    kept = o["st"]["kept"].astype(bool)
+    good, info = _close(g["g_patch_disp"].ravel()[kept], o["g_patch"][kept])
+    assert good, ("g_patch_disp", info)
+
+
+def test_adjoint_matches_oracle_640x480(bd):
+    # a pair of the 16-pair differentiable workload: 640x480 G1, 8x8 patches,
+    # stride 4, 3 levels, 8 Gauss-Newton iterations
+    pr = synth.g1_pair(640, 480, 0)
+    L32, R32 = pr.left.astype(np.float32), pr.right.astype(np.float32)
+    kw = dict(patch=8, stride=4, levels=3, iters=8)
+    g = _gpu(bd, kw, L32, R32)
+    o = _oracle(g["params"], L32.astype(np.float64), R32.astype(np.float64))
+    kept_g = g["rec"]["flags"].ravel() == 0
+    kept_o = o["st"]["kept"].astype(bool)
+    flips = int((kept_g != kept_o).sum())
+    assert flips <= max(2, int(0.001 * kept_o.size))
+    assert abs(float(g["loss"][0]) - o["loss"]) <= 1e-4 * o["loss"]
+    for key in ("g_left", "g_right", "g_disp"):
+        good, info = _close(g[key], o[key], frac=0.999)
+        print(key, info, "flips", flips)
+        assert good, (key, info)
+
+
+def test_batched_backward_equals_per_pair(bd):
+    import torch
+    kw = dict(patch=8, stride=4, levels=2, iters=8)
+    pairs = [synth.g1_pair(w, h, 40 + i, d0=1.0, d1=3.0, amp=1.0, as_float=True)
+             for i, (w, h) in enumerate([(96, 64), (128, 80), (96, 64)])]
+    Ls = [torch.from_numpy(p.left.astype(np.float32)).cuda() for p in pairs]
+    Rs = [torch.from_numpy(p.right.astype(np.float32)).cuda() for p in pairs]
+    m = bd.BDIS(**kw)
+    m.match_f32(Ls, Rs)
+    gb = m.loss_and_grad(0.1)
+    torch.cuda.synchronize()
+    gb = [{k: t.cpu().numpy() for k, t in g.items()} for g in gb]
+    for i in range(3):
+        m.match_f32([Ls[i]], [Rs[i]])
+        g1, = m.loss_and_grad(0.1)
+        torch.cuda.synchronize()
+        for k in ("loss", "g_disp", "g_patch_disp"):
+            np.testing.assert_allclose(g1[k].cpu().numpy(), gb[i][k], rtol=1e-5, atol=1e-9)
+        for k in ("g_left", "g_right"):   # atomics: order of accumulation may differ
+            a, b = g1[k].cpu().numpy(), gb[i][k]
+            assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max()
+
+
+def test_autograd_function(bd):
+    import torch
+    pr = synth.g1_pair(96, 64, 7, d0=1.0, d1=3.0, amp=1.0, as_float=True)
+    L = torch.from_numpy(pr.left.astype(np.float32)).cuda().requires_grad_(True)
+    R = torch.from_numpy(pr.right.astype(np.float32)).cuda().requires_grad_(True)
+    m = bd.BDIS(patch=8, stride=4, levels=2, iters=30)
+    d, valid = bd.disparity(m, L, R)
+    w = torch.linspace(0, 1, d.shape[1], device=d.device)[None, :].expand_as(d)
+    loss = (torch.nan_to_num(d, nan=0.0) * w).sum()
+    loss.backward()
+    # the same gradient from the C ABI with dL/dD = w on valid pixels
+    m2 = bd.BDIS(patch=8, stride=4, levels=2, iters=30)
+    m2.match_f32([L.detach()], [R.detach()])
+    (gl, gr, _), = m2.backward([torch.where(valid.bool(), w, torch.zeros_like(w))])
+    torch.cuda.synchronize()
+    assert torch.allclose(L.grad, gl, rtol=1e-4, atol=1e-6 * gl.abs().max().item())
+    assert torch.allclose(R.grad, gr, rtol=1e-4, atol=1e-6 * gr.abs().max().item())
+    assert L.grad.abs().sum() > 0 and R.grad.abs().sum() > 0
