@@ -58,6 +58,17 @@ def barrier(ws):
         dist.barrier()
 
 
+def aggregate_value(ws, units_per_rank, steps, max_ms):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (Mpix/s when units are pixels)."""
+    return ws * units_per_rank * steps / (max_ms / 1e3) / 1e6
+
+
+def rank_seed(rank, i=0, per_rank=1):
+    """Each rank works on its own independent pairs: seed = per_rank*rank + i."""
+    return per_rank * rank + i
+
+
 def max_over_ranks(v, ws, device=None):
     if ws == 1:
         return v
@@ -294,7 +305,7 @@ def main():
             print(json.dumps({"metric": METRIC, "batched": res}))
         return 0
 
-    pair = synth.config_pair("plain_640x480_var", seed=rank)
+    pair = synth.config_pair("plain_640x480_var", seed=rank_seed(rank))
     h, w = pair.left.shape
     Ld = torch.from_numpy(pair.left).to(dev)
     Rd = torch.from_numpy(pair.right).to(dev)
@@ -334,7 +345,7 @@ def main():
     clocks.mark("t1")
     dev_ms = sum(a.elapsed_time(b) for a, b in ev)
     dev_ms_max = max_over_ranks(dev_ms, ws, dev)
-    value = ws * w * h * args.steps / (dev_ms_max / 1e3) / 1e6
+    value = aggregate_value(ws, w * h, args.steps, dev_ms_max)
 
     # ---- per-kernel event times (profiling pass, plain launches)
     B.lib().bdis_set_option(m._h, B.OPT_PROFILE, 1)
@@ -464,7 +475,7 @@ def bench_fwd_bwd(bd, dev, stream, flush, rank, ws, steps=10, warmup=3):
     n, w, h = 16, 640, 480
     Ls, Rs = [], []
     for i in range(n):
-        p = synth.g1_pair(w, h, 16 * rank + i)
+        p = synth.g1_pair(w, h, rank_seed(rank, i, 16))
         Ls.append(torch.from_numpy(p.left.astype("float32")).to(dev))
         Rs.append(torch.from_numpy(p.right.astype("float32")).to(dev))
     m = bd.BDIS(**DIFF_PARAMS)
@@ -526,7 +537,7 @@ def bench_batched(bd, dev, stream, flush, rank, ws, steps=10, warmup=3, compare_
     sizes = synth.batch_sizes_uneven()
     Ls, Rs, outs = [], [], []
     for i, (w, h) in enumerate(sizes):
-        p = synth.g1_pair(w, h, 64 * rank + i)
+        p = synth.g1_pair(w, h, rank_seed(rank, i, 64))
         Ls.append(torch.from_numpy(p.left).to(dev))
         Rs.append(torch.from_numpy(p.right).to(dev))
         outs.append((torch.empty((h, w), dtype=torch.float32, device=dev), None,
