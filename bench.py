@@ -169,15 +169,12 @@ def algorithmic_bytes(kernel, w, h, prm):
         elif kernel == "search":
             coarse = 4 * geo[l + 1][0] * geo[l + 1][1] if l + 1 < L else 0
             tot += 2 * img * px + b * px + coarse + 64 * npch  # read L, R, G, coarse D; write records
-        elif kernel == "posterior":
-            coarse = 4 * geo[l + 1][0] * geo[l + 1][1] if l + 1 < L else 0
-            tot += 64 * npch + coarse + 16 * npch + 16 * npch  # read/update records, write fuse
-        elif kernel == "densify":
+        elif kernel == "fuse":
+            # read records, update posterior fields, write fusion records;
+            # coarse D and Q; write D, Q (disp, var, valid at level 0)
             out = 9 if l == 0 else 8
-            coarse = 4 * geo[l + 1][0] * geo[l + 1][1] if l + 1 < L else 0
-            tot += 16 * npch + coarse + out * px
-        elif kernel == "sigma_r":
-            tot += 64 * npch
+            coarse = 8 * geo[l + 1][0] * geo[l + 1][1] if l + 1 < L else 0
+            tot += 64 * npch + 16 * npch + 16 * npch + coarse + out * px
     return tot
 
 
@@ -315,7 +312,7 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
     m = bd.BDIS(**PARAMS)
-    launches_per_step = 5 * PARAMS["levels"]
+    launches_per_step = 3 * PARAMS["levels"]
 
     def step():
         m.match(Ld, Rd, out=out, stream=stream)

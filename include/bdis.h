@@ -235,8 +235,8 @@ typedef enum {
 
 bdis_status bdis_set_option(bdis_handle *h, int option, int value);
 
-enum { BDIS_K_PYRAMID = 0, BDIS_K_SEARCH = 1, BDIS_K_SIGMA_R = 2, BDIS_K_POSTERIOR = 3,
-       BDIS_K_DENSIFY = 4, BDIS_K_COUNT = 5 };
+/* kernels: pyramid + gradient; patch search; fused sigma_r + posterior + densify */
+enum { BDIS_K_PYRAMID = 0, BDIS_K_SEARCH = 1, BDIS_K_FUSE = 2, BDIS_K_COUNT = 3 };
 
 typedef struct {
     int launches[BDIS_K_COUNT];   /* launches per kernel since the last reset */

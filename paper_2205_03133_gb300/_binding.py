@@ -78,11 +78,11 @@ class bdis_grad(C.Structure):
 
 
 class bdis_profile(C.Structure):
-    _fields_ = [("launches", C.c_int * 5), ("ms", C.c_double * 5)]
+    _fields_ = [("launches", C.c_int * 3), ("ms", C.c_double * 3)]
 
 
 OPT_GRAPH, OPT_PROFILE = 1, 2
-KERNEL_NAMES = ["pyramid", "search", "sigma_r", "posterior", "densify"]
+KERNEL_NAMES = ["pyramid", "search", "fuse"]
 
 
 # (name, restype, argtypes) of every exported function of include/bdis.h

@@ -115,15 +115,6 @@ std::string check_pair(const bdis_params &p, const bdis_pair &q) {
     return "";
 }
 
-// smem of one search block for a level whose widest pair is `wmax`
-void search_smem(int P, int S, int wmax, int &band_pitch, int &chunk_pitch, size_t &bytes) {
-    band_pitch = (int)align_up((size_t)wmax, 32) + 1;  // rows land in different banks
-    const int chunk = search_chunk(P);
-    chunk_pitch = (chunk - 1) * S + P;
-    if ((chunk_pitch & 1) == 0) chunk_pitch += 1;
-    bytes = sizeof(float) * ((size_t)P * band_pitch + 2 * (size_t)P * chunk_pitch);
-}
-
 void fill_sgmm(const bdis_params &p, float *m) {
     // 1D factor of Eq. 8: m[a] = sum_{j<P} exp(-(a - j)^2 / (2 sigma_s^2)),
     // the 2D kernel being m[a] m[b]
@@ -179,7 +170,7 @@ struct Plan {
     int wmax[kMaxLevels] = {0};
     int units[kMaxLevels][W_COUNT] = {{0}};
     // arena offsets, index level * n + pair
-    std::vector<size_t> oG, oL, oR, oD, oQ, oRec, oFuse, oSr;
+    std::vector<size_t> oG, oL, oR, oD, oQ, oRec, oFuse, oSr, oSp;
 };
 
 struct Bump {
@@ -198,13 +189,13 @@ void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, Plan &pl) 
     const size_t esz = p.storage == BDIS_STORE_F16 ? 2 : 4;
     const size_t cnt = (size_t)NL * n;
     pl.descs.assign(cnt, LevelDesc{});
-    for (auto *v : {&pl.oG, &pl.oL, &pl.oR, &pl.oD, &pl.oQ, &pl.oRec, &pl.oFuse, &pl.oSr})
+    for (auto *v : {&pl.oG, &pl.oL, &pl.oR, &pl.oD, &pl.oQ, &pl.oRec, &pl.oFuse, &pl.oSr, &pl.oSp})
         v->assign(cnt, 0);
     Bump b;
     pl.off_desc = b.take(sizeof(LevelDesc) * cnt);
     const int chunk = search_chunk(P);
     for (int l = 0; l < NL; ++l) {
-        int begin[W_COUNT] = {0, 0, 0, 0};
+        int begin[W_COUNT] = {0, 0, 0};
         pl.wmax[l] = 0;
         for (int i = 0; i < n; ++i) {
             const size_t k = (size_t)l * n + i;
@@ -215,11 +206,11 @@ void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, Plan &pl) 
             d.npx = num_origins(d.w, P, S, &d.kxreg);
             d.npy = num_origins(d.h, P, S, &d.kyreg);
             d.nchunks = (d.npx + chunk - 1) / chunk;
+            d.tiles_x = (d.w + kFuseTileW - 1) / kFuseTileW;
             const int units[W_COUNT] = {
                 (((d.w + 1) / 2) * ((d.h + 1) / 2) + 255) / 256,  // pyramid: one thread per 2x2
                 d.npy * d.nchunks,                                // search: chunks of a patch row
-                (d.npx * d.npy + 255) / 256,                      // posterior: patches
-                (d.w * d.h + 255) / 256,                          // densify: pixels
+                d.tiles_x * ((d.h + kFuseTileH - 1) / kFuseTileH),  // fuse: pixel tiles
             };
             for (int q = 0; q < W_COUNT; ++q) {
                 d.work_begin[q] = begin[q];
@@ -241,6 +232,7 @@ void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, Plan &pl) 
             pl.oRec[k] = b.take(sizeof(bdis_patch_record) * np);
             pl.oFuse[k] = b.take(sizeof(float4) * np);
             pl.oSr[k] = b.take(sizeof(float));
+            pl.oSp[k] = b.take(sizeof(float4) * (size_t)d.npy * d.nchunks);
         }
         for (int q = 0; q < W_COUNT; ++q) pl.units[l][q] = begin[q];
     }
@@ -273,6 +265,7 @@ void plan_pointers(const bdis_params &p, int n, const bdis_pair *pairs, char *ba
             d.rec = (bdis_patch_record *)(base + pl.oRec[k]);
             d.fuse = (float4 *)(base + pl.oFuse[k]);
             d.sigma_r = (float *)(base + pl.oSr[k]);
+            d.spart = (float4 *)(base + pl.oSp[k]);
         }
     for (int l = 0; l < NL; ++l)
         for (int i = 0; i < n; ++i) {
@@ -355,20 +348,22 @@ bdis_status run(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, cuda
     const int NL = p.levels;
     Plan pl;
     plan_layout(p, n, pairs, pl);
-    int band_pitch = 0, chunk_pitch = 0;
+    int band_pitch = 0, band_cap = 0, chunk_pitch = 0;
     size_t smem = 0;
-    search_smem(p.patch, p.stride, pl.wmax[0], band_pitch, chunk_pitch, smem);
-    if (smem > 227 * 1024)
-        return fail(h, BDIS_EUNSUPPORTED,
-                    "image too wide for the shared-memory row band of the patch search");
+    search_layout(p.patch, p.stride, tau_at(p), p.window_step, band_pitch, band_cap, chunk_pitch,
+                  smem);
+    const size_t fsmem = fuse_smem(p.patch, p.stride);
+    if (smem > 227 * 1024 || fsmem > 227 * 1024)
+        return fail(h, BDIS_EUNSUPPORTED, "search radius too large for the shared-memory band");
     bdis_status s = ensure_arena(h, pl.bytes);
     if (s != BDIS_OK) return s;
     plan_pointers(p, n, pairs, h->arena, pl);
     if (h->prepared_P != p.patch || h->smem_prepared < smem) {
-        const size_t want = h->prepared_P == p.patch ? std::max(smem, h->smem_prepared) : smem;
-        cudaError_t e = prepare_search(p.patch, want);
+        // limits are only raised, so other handles' settings stay valid
+        cudaError_t e = prepare_search(p.patch, smem);
+        if (e == cudaSuccess) e = prepare_fuse(fsmem);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute");
-        h->smem_prepared = want;
+        h->smem_prepared = smem;
         h->prepared_P = p.patch;
     }
     // upload the descriptor table unless identical to the last upload
@@ -423,25 +418,21 @@ bdis_status run(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, cuda
             e = timed(BDIS_K_PYRAMID, [&] { return launch_pyramid(a, l == 0 ? in_type : st_type, st_type, st); });
             if (e != cudaSuccess) return cuda_fail(h, e, "pyramid launch");
         }
-        // coarse-to-fine levels
+        // coarse-to-fine levels: search, then sigma_r + posterior + fusion
         for (int l = NL - 1; l >= 0; --l) {
             LaunchArgs a = base_args(p, l, d_descs + (size_t)l * n, n);
-            size_t sm;
-            search_smem(p.patch, p.stride, pl.wmax[l], a.band_pitch, a.chunk_pitch, sm);
+            a.band_pitch = band_pitch;
+            a.band_cap = band_cap;
+            a.chunk_pitch = chunk_pitch;
             a.total = pl.units[l][W_SEARCH];
             const int itype = l == 0 ? in_type : st_type;
-            const int occ = search_occupancy(p.patch, itype, st_type, sm);
+            const int occ = search_occupancy(p.patch, itype, st_type, smem);
             const int grid = std::max(1, std::min(a.total, sm_count() * occ));
-            e = timed(BDIS_K_SEARCH, [&] { return launch_search(a, itype, st_type, sm, grid, st); });
+            e = timed(BDIS_K_SEARCH, [&] { return launch_search(a, itype, st_type, smem, grid, st); });
             if (e != cudaSuccess) return cuda_fail(h, e, "search launch");
-            e = timed(BDIS_K_SIGMA_R, [&] { return launch_sigma_r(a, st); });
-            if (e != cudaSuccess) return cuda_fail(h, e, "sigma_r launch");
-            a.total = pl.units[l][W_POST];
-            e = timed(BDIS_K_POSTERIOR, [&] { return launch_posterior(a, st); });
-            if (e != cudaSuccess) return cuda_fail(h, e, "posterior launch");
-            a.total = pl.units[l][W_DENSE];
-            e = timed(BDIS_K_DENSIFY, [&] { return launch_densify(a, st); });
-            if (e != cudaSuccess) return cuda_fail(h, e, "densify launch");
+            a.total = pl.units[l][W_FUSE];
+            e = timed(BDIS_K_FUSE, [&] { return launch_fuse(a, fsmem, st); });
+            if (e != cudaSuccess) return cuda_fail(h, e, "fuse launch");
         }
         return BDIS_OK;
     };

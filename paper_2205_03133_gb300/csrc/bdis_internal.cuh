@@ -19,7 +19,14 @@ constexpr int kWindow = 5;  // samples of the small window P' (Sec. III-B, s = 5
 
 // Work spaces of the per-level kernels.  Each (pair, level) owns the
 // half-open unit range [work_begin[k], work_begin[k] + units) of kernel k.
-enum WorkKind { W_PYR = 0, W_SEARCH = 1, W_POST = 2, W_DENSE = 3, W_COUNT = 4 };
+enum WorkKind { W_PYR = 0, W_SEARCH = 1, W_FUSE = 2, W_COUNT = 3 };
+
+// Pixel tile of the fused posterior / densify kernel.
+constexpr int kFuseTileW = 32;
+constexpr int kFuseTileH = 16;
+// Extra columns of the search's right band for the spread of the initial
+// estimates inside one chunk (wider spreads read the image directly).
+constexpr int kBandSpread = 64;
 
 // Element types of the level images.
 enum ElemType { E_U8 = 0, E_F32 = 1, E_F16 = 2 };
@@ -36,12 +43,14 @@ struct alignas(16) LevelDesc {
     bdis_patch_record *rec;   // npx * npy records of this pair at this level
     float4 *fuse;             // (d, rho, sig2, kept) per patch for the fusion gather
     float *sigma_r;           // one float
+    float4 *spart;            // per search unit: (sum E(0), count, sum E(0)^2) of kept patches
     int w, h, pitch;          // level size, row pitch (elements) of L and R
     int gpitch;               // row pitch (elements) of G
     int wn, hn, pitchn;       // next coarser level size and pitch
     int wc, hc;               // coarser map size (levels < L-1)
     int npx, npy, kxreg, kyreg;
     int nchunks;              // search chunks per patch row
+    int tiles_x;              // fuse tiles per row
     int work_begin[W_COUNT];
 };
 
@@ -64,6 +73,7 @@ struct LaunchArgs {
     int use_c2f, use_sgmm;
     int chunk;                // patches per search chunk
     int band_pitch;           // floats per row of the staged right band
+    int band_cap;             // usable columns of the right band
     int chunk_pitch;          // floats per row of the staged left / gradient band
     float m[kMaxPatch];       // 1D sGMM factors m[a] (Eq. 8 is separable)
 };
@@ -110,10 +120,13 @@ cudaError_t launch_bwd_sobel(const GradArgs &a, cudaStream_t s);
 cudaError_t launch_pyramid(const LaunchArgs &a, int in_type, int out_type, cudaStream_t s);
 cudaError_t launch_search(const LaunchArgs &a, int in_type, int g_type, size_t smem, int grid,
                           cudaStream_t s);
-cudaError_t launch_sigma_r(const LaunchArgs &a, cudaStream_t s);
-cudaError_t launch_posterior(const LaunchArgs &a, cudaStream_t s);
-cudaError_t launch_densify(const LaunchArgs &a, cudaStream_t s);
-// Opt-in to large dynamic shared memory for every search instance.
+cudaError_t launch_fuse(const LaunchArgs &a, size_t smem, cudaStream_t s);
+// Shared-memory layout of the search (band pitch and capacity, chunk pitch, bytes).
+void search_layout(int P, int S, float tau, float window_step, int &band_pitch, int &band_cap,
+                   int &chunk_pitch, size_t &bytes);
+size_t fuse_smem(int P, int S);
+cudaError_t prepare_fuse(size_t smem_bytes);
+// Raise (never lower) the dynamic shared-memory limit of every search instance.
 cudaError_t prepare_search(int P, size_t smem_bytes);
 // Number of resident search blocks per SM for (P, image type, gradient type, smem).
 int search_occupancy(int P, int in_type, int g_type, size_t smem_bytes);

@@ -1,18 +1,18 @@
-// bdis_kernels.cu -- sm_103a kernels of the BDIS pipeline.
+// bdis_kernels.cu -- sm_103a kernels of the BDIS forward pipeline.
 //
 // Every kernel processes one pyramid level of a whole batch of pairs: work
 // units are flattened over the pairs through LevelDesc::work_begin, and each
 // block strides over the units (grid sized to the SM count), so the plain
-// single-pair call and the batched call run the same code.
-//
-// Stage map (arXiv 2205.03133):
+// single-pair call and the batched call run the same code.  Two launches per
+// level after the pyramid:
 //   k_pyramid   image pyramid + Sobel-x/8 of the left image (Sec. III-A)
-//   k_search    inverse-compositional GN per patch (Eq. 1), window energies
-//               and rejection flags (Sec. III-B, Sec. IV technical details)
-//   k_sigma_r   dynamic sigma_r^(n) (text after Eq. 6)
-//   k_posterior window posterior (Eq. 5-6), coarse-to-fine rho (Eq. 10-11),
-//               PDF fit (Eq. 14-16)
-//   k_densify   sGMM fusion gather (Eq. 8-9, Eq. 12) and pixel variance (Eq. 17)
+//   k_search    inverse-compositional GN per patch (Eq. 1), window energies,
+//               rejection flags (Sec. III-B, Sec. IV technical details), and
+//               per-chunk partial sums for the dynamic sigma_r (text after Eq. 6)
+//   k_fuse      per 32x16 pixel tile: sigma_r, window posterior (Eq. 5-6),
+//               coarse-to-fine rho (Eq. 10-11) and PDF fit (Eq. 14-16) of the
+//               patches overlapping the tile, then the sGMM fusion gather
+//               (Eq. 8-9, Eq. 12) and pixel variance (Eq. 17)
 #include <cfloat>
 #include <cmath>
 
@@ -82,31 +82,66 @@ __global__ void __launch_bounds__(256) k_pyramid(LaunchArgs a) {
 
 // ---------------------------------------------------------------- patch search
 
+// Block-wide min and max (all threads get the result).
+__device__ __forceinline__ void block_minmax(float &lo, float &hi, float *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red[wid] = lo;
+        red[8 + wid] = hi;
+    }
+    __syncthreads();
+    lo = red[0];
+    hi = red[8];
+#pragma unroll
+    for (int i = 1; i < 8; ++i) {
+        lo = fminf(lo, red[i]);
+        hi = fmaxf(hi, red[8 + i]);
+    }
+    __syncthreads();
+}
+
 // A block owns one chunk of consecutive patches of one patch row.  It stages
-// the P right-image rows of that patch row over the full level width (any
-// estimate d samples inside them after clamping), and the left image and
-// gradient over the chunk's columns, in shared memory.  A group of G lanes
-// handles one patch, lane r owning patch row r; reductions are xor shuffles
-// inside the group.  The iteration count is fixed, so every lane of a warp
-// executes the same instruction stream.
+// in shared memory the left image and gradient over the chunk's columns and
+// the right image over the column window that the chunk's estimates can
+// reach: [cx0 - max d_init - margin, cx0 + cw - min d_init + margin], each
+// shared column holding the image column clamped to [0, w-1], so the inner
+// loops read with immediate offsets and no clamping.  A patch whose estimate
+// leaves the window reads the image directly (same clamped values).  A group
+// of G lanes handles one patch, lane r owning patch row r; reductions are
+// xor shuffles inside the group; the iteration count is fixed, so every lane
+// of a warp executes the same instruction stream.  The groups of a warp take
+// patches spaced so that their rows fall in different shared-memory banks.
 template <int P, typename TI, typename TG>
 __global__ void __launch_bounds__(256) k_search(LaunchArgs a) {
     constexpr int G = P <= 8 ? 8 : 16;
     constexpr int N = P * P;
+    constexpr int GPW = 32 / G;  // groups per warp
     constexpr float invN = 1.f / (float)N;
     extern __shared__ float smem[];
-    const int bp = a.band_pitch, cp = a.chunk_pitch;
+    const int bp = a.band_pitch, cp = a.chunk_pitch, cap = a.band_cap;
     float *Rb = smem;
     float *Lb = Rb + P * bp;
     float *Gb = Lb + P * cp;
+    float *dsh = Gb + P * cp;            // chunk d_init
+    float *pe = dsh + a.chunk;           // chunk sigma_r terms: E(0), count, E(0)^2
+    float *red = pe + 3 * a.chunk;       // 16 floats
     const int tid = threadIdx.x;
     const int gl = tid & (G - 1);
-    const int grp = tid / G;
-    const int ngrp = blockDim.x / G;
+    const int q = (tid & 31) / G;
+    const int warp = tid >> 5;
     const bool row_on = gl < P;
     const int S = a.S;
     const float h = a.window_step;
     const float dl[4] = {-h, h, -2.f * h, 2.f * h};
+    // patch spacing between the groups of a warp (a power of two dividing 16)
+    int sp = (32 / GPW) / S;
+    sp = sp >= 16 ? 16 : sp >= 8 ? 8 : sp >= 4 ? 4 : sp >= 2 ? 2 : 1;
+    const int margin = (int)ceilf(a.tau) + (int)ceilf(2.f * h) + 3;
 
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) {
         const LevelDesc &D = a.descs[find_pair(a.descs, a.npairs, unit, W_SEARCH)];
@@ -115,6 +150,7 @@ __global__ void __launch_bounds__(256) k_search(LaunchArgs a) {
         const int oy = origin(py, D.h, P, S, D.kyreg);
         const int k0 = ch * a.chunk;
         const int k1 = min(k0 + a.chunk, D.npx);
+        const int nk = k1 - k0;
         const int cx0 = origin(k0, D.w, P, S, D.kxreg);
         const int cw = origin(k1 - 1, D.w, P, S, D.kxreg) + P - cx0;
         const int w = D.w;
@@ -123,25 +159,52 @@ __global__ void __launch_bounds__(256) k_search(LaunchArgs a) {
         const TG *Gi = (const TG *)D.G;
 
         __syncthreads();  // the previous unit's readers are done with smem
-        for (int i = tid; i < P * w; i += blockDim.x) {
-            const int r = i / w, c = i - r * w;
-            Rb[r * bp + c] = ldf(R + (size_t)(oy + r) * D.pitch + c);
+        // initial estimates of the chunk (coarser fused map at the centre)
+        float dlo = FLT_MAX, dhi = -FLT_MAX;
+        for (int t = tid; t < nk; t += blockDim.x) {
+            float di = 0.f;
+            if (D.Dc != nullptr) {
+                const float cxp = (float)origin(k0 + t, w, P, S, D.kxreg) + 0.5f * (float)(P - 1);
+                const float cyp = (float)oy + 0.5f * (float)(P - 1);
+                di = 2.f * coarse_bilin(D.Dc, D.wc, D.hc, cxp, cyp);
+            }
+            dsh[t] = di;
+            dlo = fminf(dlo, di);
+            dhi = fmaxf(dhi, di);
         }
-        for (int i = tid; i < P * cw; i += blockDim.x) {
-            const int r = i / cw, c = i - r * cw;
-            Lb[r * cp + c] = ldf(L + (size_t)(oy + r) * D.pitch + cx0 + c);
-            Gb[r * cp + c] = ldf(Gi + (size_t)(oy + r) * D.gpitch + cx0 + c);
+        block_minmax(dlo, dhi, red);
+        // column window of the right band
+        dhi = fminf(fmaxf(dhi, -(float)(2 * w)), (float)(2 * w));
+        dlo = fminf(fmaxf(dlo, -(float)(2 * w)), (float)(2 * w));
+        const int xlo = cx0 - (int)ceilf(dhi) - margin;
+        const int xhi = cx0 + cw - (int)floorf(dlo) + margin;
+        const int wwin = min(xhi - xlo, cap);
+        for (int r = 0; r < P; ++r) {
+            const TI *src = R + (size_t)(oy + r) * D.pitch;
+            for (int c = tid; c < wwin; c += blockDim.x)
+                Rb[r * bp + c] = ldf(src + clampi(xlo + c, 0, w - 1));
+            const TI *lsrc = L + (size_t)(oy + r) * D.pitch + cx0;
+            const TG *gsrc = Gi + (size_t)(oy + r) * D.gpitch + cx0;
+            for (int c = tid; c < cw; c += blockDim.x) {
+                Lb[r * cp + c] = ldf(lsrc + c);
+                Gb[r * cp + c] = ldf(gsrc + c);
+            }
         }
         __syncthreads();
 
-        for (int kk = grp; kk < a.chunk; kk += ngrp) {
-            const bool active = k0 + kk < k1;
-            const int kx = min(k0 + kk, k1 - 1);
+        const int passes = a.chunk / (8 * GPW);
+        for (int pass = 0; pass < passes; ++pass) {
+            const int uu = pass * 8 + warp;
+            const int kk = (uu / sp) * (sp * GPW) + (uu % sp) + sp * q;  // patch slot in chunk
+            const bool active = kk < nk;
+            const int kl = min(kk, nk - 1);
+            const int kx = k0 + kl;
             const int ox = origin(kx, w, P, S, D.kxreg);
             const int rr = row_on ? gl : 0;
             const float *Lrow = Lb + rr * cp + (ox - cx0);
             const float *Grow = Gb + rr * cp + (ox - cx0);
-            const float *Rrow = Rb + rr * bp;
+            const float *Rs = Rb + rr * bp;
+            const TI *Rg = R + (size_t)(oy + rr) * D.pitch;
 
             // template, centred gradient, Hessian (computed once, Sec. III-A)
             float T[P], gt[P];
@@ -153,21 +216,33 @@ __global__ void __launch_bounds__(256) k_search(LaunchArgs a) {
                 gs += gt[j];
             }
             const float gbar = group_sum<G>(gs) * invN;
-            float hp = 0.f, cp_ = 0.f;
+            float hp = 0.f, cpart = 0.f;
 #pragma unroll
             for (int j = 0; j < P; ++j) {
                 gt[j] = row_on ? gt[j] - gbar : 0.f;
                 hp = fmaf(gt[j], gt[j], hp);
-                cp_ = fmaf(gt[j], T[j], cp_);
+                cpart = fmaf(gt[j], T[j], cpart);
             }
             const float H = group_sum<G>(hp);
-            const float cT = group_sum<G>(cp_);
+            const float cT = group_sum<G>(cpart);
             const bool flat = !(H >= a.hess_eps * (float)N);
-
-            const float cxp = (float)ox + 0.5f * (float)(P - 1);
-            const float cyp = (float)oy + 0.5f * (float)(P - 1);
-            const float dinit = D.Dc != nullptr ? 2.f * coarse_bilin(D.Dc, D.wc, D.hc, cxp, cyp) : 0.f;
+            const float invH = flat ? 0.f : 1.f / H;
+            const float dinit = dsh[kl];
             const float dlim = (float)w + 2.f * (float)P;
+
+            // right-image samples of this lane's row at x - d = base + j (+ t):
+            // the P + 1 values base .. base + P
+            auto load_row = [&](int base, float (&v)[P + 1]) {
+                const int o = base - xlo;
+                if (o >= 0 && o + P < wwin) {
+                    const float *p = Rs + o;
+#pragma unroll
+                    for (int j = 0; j <= P; ++j) v[j] = p[j];
+                } else {
+#pragma unroll
+                    for (int j = 0; j <= P; ++j) v[j] = ldf(Rg + clampi(base + j, 0, w - 1));
+                }
+            };
 
             // Gauss-Newton: d <- d + (sum gt_i s_i - cT) / H, s_i = I_r(x_i - d)
             float d = dinit, dlast = 0.f;
@@ -175,19 +250,17 @@ __global__ void __launch_bounds__(256) k_search(LaunchArgs a) {
                 int off;
                 float t;
                 split_shift(d, off, t);
-                const int base = ox + off;
+                float v[P + 1];
+                load_row(ox + off, v);
                 float A = 0.f, B = 0.f;
-                float v = Rrow[clampi(base, 0, w - 1)];
 #pragma unroll
                 for (int j = 0; j < P; ++j) {
-                    const float vn = Rrow[clampi(base + j + 1, 0, w - 1)];
-                    A = fmaf(gt[j], v, A);
-                    B = fmaf(gt[j], vn, B);
-                    v = vn;
+                    A = fmaf(gt[j], v[j], A);
+                    B = fmaf(gt[j], v[j + 1], B);
                 }
                 const float s = group_sum<G>(fmaf(t, B - A, A));
                 if (!flat) {
-                    const float delta = (s - cT) / H;
+                    const float delta = (s - cT) * invH;
                     d = fminf(fmaxf(d + delta, -dlim), dlim);
                     dlast = delta;
                 }
@@ -206,23 +279,22 @@ __global__ void __launch_bounds__(256) k_search(LaunchArgs a) {
             float sa = 0.f;
             int nout = 0;
             {
-                float v = Rrow[clampi(base0, 0, w - 1)];
+                float v[P + 1];
+                load_row(base0, v);
 #pragma unroll
                 for (int j = 0; j < P; ++j) {
-                    const float vn = Rrow[clampi(base0 + j + 1, 0, w - 1)];
-                    s0[j] = fmaf(t0, vn - v, v);
+                    s0[j] = fmaf(t0, v[j + 1] - v[j], v[j]);
                     sa += row_on ? s0[j] - T[j] : 0.f;
                     const int xi = base0 + j;
                     nout += (row_on && (xi < 0 || xi > w - 1 || (xi == w - 1 && t0 > 0.f))) ? 1 : 0;
-                    v = vn;
                 }
             }
             const float mean0 = group_sum<G>(sa) * invN;
             float e0 = 0.f;
 #pragma unroll
             for (int j = 0; j < P; ++j) {
-                const float q = row_on ? (s0[j] - T[j]) - mean0 : 0.f;
-                e0 = fmaf(q, q, e0);
+                const float qv = row_on ? (s0[j] - T[j]) - mean0 : 0.f;
+                e0 = fmaf(qv, qv, e0);
             }
             float su[4], suu[4], suc[4];
 #pragma unroll
@@ -230,18 +302,16 @@ __global__ void __launch_bounds__(256) k_search(LaunchArgs a) {
                 int off;
                 float t;
                 split_shift(d + dl[k], off, t);
-                const int base = ox + off;
-                float v = Rrow[clampi(base, 0, w - 1)];
+                float v[P + 1];
+                load_row(ox + off, v);
                 float p1 = 0.f, p2 = 0.f, p3 = 0.f;
 #pragma unroll
                 for (int j = 0; j < P; ++j) {
-                    const float vn = Rrow[clampi(base + j + 1, 0, w - 1)];
-                    const float u = row_on ? fmaf(t, vn - v, v) - s0[j] : 0.f;
+                    const float uj = row_on ? fmaf(t, v[j + 1] - v[j], v[j]) - s0[j] : 0.f;
                     const float c = row_on ? (s0[j] - T[j]) - mean0 : 0.f;
-                    p1 += u;
-                    p2 = fmaf(u, u, p2);
-                    p3 = fmaf(u, c, p3);
-                    v = vn;
+                    p1 += uj;
+                    p2 = fmaf(uj, uj, p2);
+                    p3 = fmaf(uj, c, p3);
                 }
                 su[k] = p1;
                 suu[k] = p2;
@@ -283,70 +353,33 @@ __global__ void __launch_bounds__(256) k_search(LaunchArgs a) {
                 rec.sig2 = 0.f;
                 rec.pdf_flags = 0u;
                 D.rec[(size_t)py * D.npx + kx] = rec;
+                const bool kept = f == 0u;
+                pe[3 * kk] = kept ? E[0] : 0.f;
+                pe[3 * kk + 1] = kept ? 1.f : 0.f;
+                pe[3 * kk + 2] = kept ? E[0] * E[0] : 0.f;
             }
         }
-    }
-}
-
-// ---------------------------------------------------------------- sigma_r
-
-__device__ __forceinline__ float block_sum(float v, float *red) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    float s = 0.f;
-    if (threadIdx.x < 32) {
-        s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    }
-    return s;  // valid in thread 0
-}
-
-// One block per pair: sigma_r of this level from the kept patches
-// (deterministic order: fixed per-thread partial sums, then a tree).
-__global__ void __launch_bounds__(256) k_sigma_r(LaunchArgs a) {
-    __shared__ float red[32];
-    __shared__ float bc[2];
-    for (int pair = blockIdx.x; pair < a.npairs; pair += gridDim.x) {
-        const LevelDesc &D = a.descs[pair];
-        const int n = D.npx * D.npy;
-        float s = 0.f, c = 0.f;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const bdis_patch_record &r = D.rec[i];
-            if (r.flags == 0u) { s += r.E[0]; c += 1.f; }
-        }
-        const float S = block_sum(s, red);
-        const float C = block_sum(c, red);
-        if (threadIdx.x == 0) { bc[0] = S; bc[1] = C; }
         __syncthreads();
-        float sr;
-        if (a.sigma_r_mode == BDIS_SIGMA_R_FIXED) {
-            sr = a.sigma_r_fixed;
-        } else if (bc[1] == 0.f) {
-            sr = 0.f;
-        } else if (a.sigma_r_mode == BDIS_SIGMA_R_LITERAL) {
-            const float mean = bc[0] / bc[1];
-            float v = 0.f;
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                const bdis_patch_record &r = D.rec[i];
-                if (r.flags == 0u) v += (r.E[0] - mean) * (r.E[0] - mean);
+        // chunk partial sums for sigma_r, fixed order (warp 0)
+        if (warp == 0) {
+            float s1 = 0.f, s2 = 0.f, s3 = 0.f;
+            for (int i = tid; i < nk; i += 32) {
+                s1 += pe[3 * i];
+                s2 += pe[3 * i + 1];
+                s3 += pe[3 * i + 2];
             }
-            const float V = block_sum(v, red);
-            sr = sqrtf(V / bc[1]);
-        } else {
-            sr = sqrtf(bc[0] / (bc[1] * (float)(a.P * a.P)));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+                s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+            }
+            if (tid == 0) D.spart[u] = make_float4(s1, s2, s3, 0.f);
         }
-        if (a.sigma_r_mode != BDIS_SIGMA_R_FIXED) sr = fmaxf(sr, a.sigma_r_floor);
-        if (threadIdx.x == 0) *D.sigma_r = sr;
-        __syncthreads();
     }
 }
 
-// ---------------------------------------------------------------- posterior + PDF
+// ---------------------------------------------------------------- posterior, fusion
 
 // Gauss-Newton fit of ln c - 1/2 ln(2 pi sigma^2) - delta^2/(2 sigma^2) to
 // the window log-probabilities, state (sigma, c) from (sqrt(0.1), 1), steps
@@ -419,127 +452,215 @@ __device__ float pdf_fit(const float lnp[5], const float dlt[5], int iters, floa
     return s * s;
 }
 
-// One thread per patch: pi_k = p_0 / sum_i p_i with p_i = exp(-E_i/(2 sigma_r^2 s^2)),
-// rho_k = Gamma_n pi_k + Q^(n+1)(centre), and at the finest level with
-// variance on the PDF fit.  Writes the compact fusion record.
-__global__ void __launch_bounds__(256) k_posterior(LaunchArgs a) {
-    const float h = a.window_step;
-    const float dlt[5] = {0.f, -h, h, -2.f * h, 2.f * h};
-    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) {
-        const LevelDesc &D = a.descs[find_pair(a.descs, a.npairs, unit, W_POST)];
-        const int idx = (unit - D.work_begin[W_POST]) * blockDim.x + threadIdx.x;
-        const int n = D.npx * D.npy;
-        if (idx >= n) continue;
-        bdis_patch_record *rec = D.rec + idx;
-        const uint32_t flags = rec->flags;
-        if (flags != 0u) {
+// One thread per patch of a tile's patch set: pi_k = p_0 / sum_i p_i with
+// p_i = exp(-E_i/(2 sigma_r^2 s^2)), rho_k = Gamma_n pi_k + Q^(n+1)(centre),
+// and at the finest level with variance on the PDF fit.
+__device__ float4 posterior_of(const LaunchArgs &a, const LevelDesc &D, int kx, int ky, float sr,
+                               bool write) {
+    const int k = ky * D.npx + kx;
+    bdis_patch_record *rec = D.rec + k;
+    if (rec->flags != 0u) {
+        if (write) {
             rec->pi = rec->rho = rec->sig2 = 0.f;
             rec->pdf_flags = 0u;
-            D.fuse[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
-            continue;
+            D.fuse[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        const float sr = __ldg(D.sigma_r);
-        const float scale = 2.f * sr * sr * (float)(kWindow * kWindow);
-        // ln p_i - ln p_0 = -(E_i - E_0) / (2 sigma_r^2 s^2); the record holds E_i - E_0
-        float e[5], Z = 1.f;
-        e[0] = 0.f;
+        return make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float h = a.window_step;
+    const float dlt[5] = {0.f, -h, h, -2.f * h, 2.f * h};
+    const float scale = 2.f * sr * sr * (float)(kWindow * kWindow);
+    // ln p_i - ln p_0 = -(E_i - E_0) / (2 sigma_r^2 s^2); the record holds E_i - E_0
+    float e[5], Z = 1.f;
+    e[0] = 0.f;
 #pragma unroll
-        for (int i = 1; i < 5; ++i) {
-            e[i] = -rec->E[i] / scale;
-            Z += expf(e[i]);
+    for (int i = 1; i < 5; ++i) {
+        e[i] = -rec->E[i] / scale;
+        Z += expf(e[i]);
+    }
+    const float pi = 1.f / Z;
+    float rho;
+    if (a.use_c2f) {
+        float prop = 0.f;
+        if (D.Qc != nullptr) {
+            const float cx = (float)origin(kx, D.w, a.P, a.S, D.kxreg) + 0.5f * (float)(a.P - 1);
+            const float cy = (float)origin(ky, D.h, a.P, a.S, D.kyreg) + 0.5f * (float)(a.P - 1);
+            prop = coarse_bilin(D.Qc, D.wc, D.hc, cx, cy);
         }
-        const float pi = 1.f / Z;
-        float rho;
-        if (a.use_c2f) {
-            float prop = 0.f;
-            if (D.Qc != nullptr) {
-                const int kx = idx % D.npx, ky = idx / D.npx;
-                const float cx = (float)origin(kx, D.w, a.P, a.S, D.kxreg) + 0.5f * (float)(a.P - 1);
-                const float cy = (float)origin(ky, D.h, a.P, a.S, D.kyreg) + 0.5f * (float)(a.P - 1);
-                prop = coarse_bilin(D.Qc, D.wc, D.hc, cx, cy);
-            }
-            rho = a.gamma_w * pi + prop;
-        } else {
-            rho = pi;
-        }
-        float sig2 = 0.f;
-        uint32_t pf = 0u;
-        if (a.level == 0 && a.variance) {
-            const float lnZ = logf(Z);
-            float lnp[5];
+        rho = a.gamma_w * pi + prop;
+    } else {
+        rho = pi;
+    }
+    float sig2 = 0.f;
+    uint32_t pf = 0u;
+    if (a.level == 0 && a.variance) {
+        const float lnZ = logf(Z);
+        float lnp[5];
 #pragma unroll
-            for (int i = 0; i < 5; ++i) lnp[i] = e[i] - lnZ;
-            sig2 = pdf_fit(lnp, dlt, a.pdf_iters, a.pdf_resid, a.tau0, pf);
-        }
+        for (int i = 0; i < 5; ++i) lnp[i] = e[i] - lnZ;
+        sig2 = pdf_fit(lnp, dlt, a.pdf_iters, a.pdf_resid, a.tau0, pf);
+    }
+    const float4 fz = make_float4(rec->d, rho, sig2, 1.f);
+    if (write) {
         rec->pi = pi;
         rec->rho = rho;
         rec->sig2 = sig2;
         rec->pdf_flags = pf;
-        D.fuse[idx] = make_float4(rec->d, rho, sig2, 1.f);
+        D.fuse[k] = fz;
     }
+    return fz;
 }
 
-// ---------------------------------------------------------------- densify
+__device__ __forceinline__ float block_sum(float v, float *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += red[i];
+    return s;  // every thread, same fixed order
+}
 
-// One thread per pixel: gather the kept patches covering it (no atomics):
-// omega_k = rho_k m[x - ox] m[y - oy], D = sum omega d / sum omega,
-// Q = sum omega rho / sum omega, V = sum omega^2 sig2 / (sum omega)^2.
-__global__ void __launch_bounds__(256) k_densify(LaunchArgs a) {
+// Covering patch indices of pixel coordinate x along one axis: regular k
+// with kS <= x < kS + P, plus the ragged one.
+__device__ __forceinline__ void cover(int x, int n, int P, int S, int kreg, int np, int &lo,
+                                      int &hi, bool &ext) {
+    lo = x - P + 1 > 0 ? (x - P + 1 + S - 1) / S : 0;
+    hi = min(kreg - 1, x / S);
+    ext = np > kreg && x >= n - P;
+}
+
+// A block owns a TW x TH pixel tile.  It derives sigma_r of its pair from
+// the search's chunk partials (fixed order, identical in every block),
+// computes the posterior of every patch overlapping the tile into shared
+// memory (the tile containing a patch's origin writes its record), then
+// fuses its pixels by a gather over the covering kept patches (no atomics):
+//   omega_k = rho_k m[x - ox] m[y - oy], D = sum omega d / sum omega,
+//   Q = sum omega rho / sum omega, V = sum omega^2 sig2 / (sum omega)^2.
+__global__ void __launch_bounds__(256) k_fuse(LaunchArgs a) {
+    constexpr int TW = kFuseTileW, TH = kFuseTileH;
+    extern __shared__ float4 fz[];
+    __shared__ float red[8];
+    __shared__ float srs;
     const int P = a.P, S = a.S;
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) {
-        const LevelDesc &D = a.descs[find_pair(a.descs, a.npairs, unit, W_DENSE)];
-        const int idx = (unit - D.work_begin[W_DENSE]) * blockDim.x + threadIdx.x;
-        if (idx >= D.w * D.h) continue;
-        const int x = idx % D.w, y = idx / D.w;
-        // covering origins: regular k with kS <= x < kS + P, plus the ragged one
-        const int kxlo = x - P + 1 > 0 ? (x - P + 1 + S - 1) / S : 0;
-        const int kxhi = min(D.kxreg - 1, x / S);
-        const bool kxext = D.npx > D.kxreg && x >= D.w - P;
-        const int kylo = y - P + 1 > 0 ? (y - P + 1 + S - 1) / S : 0;
-        const int kyhi = min(D.kyreg - 1, y / S);
-        const bool kyext = D.npy > D.kyreg && y >= D.h - P;
-        float sw = 0.f, swd = 0.f, swr = 0.f, sw2 = 0.f;
-        int n = 0;
-        const int nky = kyhi - kylo + 1 + (kyext ? 1 : 0);
-        const int nkx = kxhi - kxlo + 1 + (kxext ? 1 : 0);
-        for (int iy = 0; iy < nky; ++iy) {
-            const int ky = (kylo + iy <= kyhi) ? kylo + iy : D.npy - 1;
+        const LevelDesc &D = a.descs[find_pair(a.descs, a.npairs, unit, W_FUSE)];
+        const int tile = unit - D.work_begin[W_FUSE];
+        const int tx = tile % D.tiles_x, ty = tile / D.tiles_x;
+        const int x0 = tx * TW, y0 = ty * TH;
+        const int x1 = min(x0 + TW, D.w) - 1, y1 = min(y0 + TH, D.h) - 1;
+
+        // sigma_r of the pair
+        const int nu = D.npy * D.nchunks;
+        float s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        for (int i = threadIdx.x; i < nu; i += blockDim.x) {
+            const float4 v = D.spart[i];
+            s1 += v.x;
+            s2 += v.y;
+            s3 += v.z;
+        }
+        const float S1 = block_sum(s1, red);
+        const float S2 = block_sum(s2, red);
+        const float S3 = block_sum(s3, red);
+        if (threadIdx.x == 0) {
+            float sr;
+            if (a.sigma_r_mode == BDIS_SIGMA_R_FIXED) {
+                sr = a.sigma_r_fixed;
+            } else if (S2 == 0.f) {
+                sr = a.sigma_r_floor;
+            } else if (a.sigma_r_mode == BDIS_SIGMA_R_LITERAL) {
+                const float mean = S1 / S2;
+                sr = fmaxf(sqrtf(fmaxf(S3 / S2 - mean * mean, 0.f)), a.sigma_r_floor);
+            } else {
+                sr = fmaxf(sqrtf(S1 / (S2 * (float)(P * P))), a.sigma_r_floor);
+            }
+            srs = sr;
+            if (tile == 0) *D.sigma_r = sr;
+        }
+        __syncthreads();
+        const float sr = srs;
+
+        // patches overlapping the tile
+        int kxlo, kxhi, kylo, kyhi, tmp;
+        bool kxext, kyext, bext;
+        cover(x0, D.w, P, S, D.kxreg, D.npx, kxlo, tmp, bext);
+        cover(x1, D.w, P, S, D.kxreg, D.npx, tmp, kxhi, kxext);
+        cover(y0, D.h, P, S, D.kyreg, D.npy, kylo, tmp, bext);
+        cover(y1, D.h, P, S, D.kyreg, D.npy, tmp, kyhi, kyext);
+        const int nkxr = max(0, kxhi - kxlo + 1), nkyr = max(0, kyhi - kylo + 1);
+        const int nkx = nkxr + (kxext ? 1 : 0);
+        const int nky = nkyr + (kyext ? 1 : 0);
+        for (int i = threadIdx.x; i < nkx * nky; i += blockDim.x) {
+            const int ix = i % nkx, iy = i / nkx;
+            const int kx = ix < nkxr ? kxlo + ix : D.npx - 1;
+            const int ky = iy < nkyr ? kylo + iy : D.npy - 1;
+            const int ox = origin(kx, D.w, P, S, D.kxreg);
             const int oy = origin(ky, D.h, P, S, D.kyreg);
-            const float my = a.use_sgmm ? a.m[y - oy] : 1.f;
-            for (int ix = 0; ix < nkx; ++ix) {
-                const int kx = (kxlo + ix <= kxhi) ? kxlo + ix : D.npx - 1;
-                const int ox = origin(kx, D.w, P, S, D.kxreg);
-                const float4 f = __ldg(D.fuse + (size_t)ky * D.npx + kx);
-                if (f.w == 0.f) continue;
-                const float mx = a.use_sgmm ? a.m[x - ox] : 1.f;
-                const float om = f.y * (my * mx);
-                sw += om;
-                swd = fmaf(om, f.x, swd);
-                swr = fmaf(om, f.y, swr);
-                sw2 = fmaf(om * om, f.z, sw2);
-                ++n;
+            const bool owner = ox >= x0 && ox < x0 + TW && oy >= y0 && oy < y0 + TH;
+            fz[i] = posterior_of(a, D, kx, ky, sr, owner);
+        }
+        __syncthreads();
+
+        // fuse the tile's pixels
+        for (int pix = threadIdx.x; pix < TW * TH; pix += blockDim.x) {
+            const int x = x0 + pix % TW, y = y0 + pix / TW;
+            if (x > x1 || y > y1) continue;
+            int pxlo, pxhi, pylo, pyhi;
+            bool pxext, pyext;
+            cover(x, D.w, P, S, D.kxreg, D.npx, pxlo, pxhi, pxext);
+            cover(y, D.h, P, S, D.kyreg, D.npy, pylo, pyhi, pyext);
+            const int nxx = pxhi - pxlo + 1 + (pxext ? 1 : 0);
+            const int nyy = pyhi - pylo + 1 + (pyext ? 1 : 0);
+            float sw = 0.f, swd = 0.f, swr = 0.f, sw2 = 0.f;
+            int n = 0;
+            for (int iy = 0; iy < nyy; ++iy) {
+                const bool ex = pylo + iy > pyhi;
+                const int ky = ex ? D.npy - 1 : pylo + iy;
+                const int ly = ex ? nky - 1 : ky - kylo;
+                const int oy = origin(ky, D.h, P, S, D.kyreg);
+                const float my = a.use_sgmm ? a.m[y - oy] : 1.f;
+                for (int ix = 0; ix < nxx; ++ix) {
+                    const bool exx = pxlo + ix > pxhi;
+                    const int kx = exx ? D.npx - 1 : pxlo + ix;
+                    const int lx = exx ? nkx - 1 : kx - kxlo;
+                    const int ox = origin(kx, D.w, P, S, D.kxreg);
+                    const float4 f = fz[ly * nkx + lx];
+                    if (f.w == 0.f) continue;
+                    const float mx = a.use_sgmm ? a.m[x - ox] : 1.f;
+                    const float om = f.y * (my * mx);
+                    sw += om;
+                    swd = fmaf(om, f.x, swd);
+                    swr = fmaf(om, f.y, swr);
+                    sw2 = fmaf(om * om, f.z, sw2);
+                    ++n;
+                }
+            }
+            const size_t idx = (size_t)y * D.w + x;
+            float Dv, Qv, Vv;
+            if (n > 0 && sw > 0.f) {
+                Dv = swd / sw;
+                Qv = swr / sw;
+                Vv = sw2 / (sw * sw);
+            } else {
+                Dv = D.Dc != nullptr ? 2.f * coarse_bilin(D.Dc, D.wc, D.hc, (float)x, (float)y) : 0.f;
+                Qv = 0.f;
+                Vv = 0.f;
+                n = 0;
+            }
+            if (a.level == 0) {
+                const bool ok = n > 0 && Qv >= a.pix_thresh;
+                D.valid[idx] = ok ? 1 : 0;
+                D.disp[idx] = ok ? Dv : __int_as_float(0x7fc00000);
+                if (D.var != nullptr && a.variance) D.var[idx] = ok ? Vv : __int_as_float(0x7fc00000);
+            } else {
+                D.D[idx] = Dv;
+                D.Q[idx] = Qv;
             }
         }
-        float Dv, Qv, Vv;
-        if (n > 0 && sw > 0.f) {
-            Dv = swd / sw;
-            Qv = swr / sw;
-            Vv = sw2 / (sw * sw);
-        } else {
-            Dv = D.Dc != nullptr ? 2.f * coarse_bilin(D.Dc, D.wc, D.hc, (float)x, (float)y) : 0.f;
-            Qv = 0.f;
-            Vv = 0.f;
-            n = 0;
-        }
-        if (a.level == 0) {
-            const bool ok = n > 0 && Qv >= a.pix_thresh;
-            D.valid[idx] = ok ? 1 : 0;
-            D.disp[idx] = ok ? Dv : __int_as_float(0x7fc00000);
-            if (D.var != nullptr && a.variance) D.var[idx] = ok ? Vv : __int_as_float(0x7fc00000);
-        } else {
-            D.D[idx] = Dv;
-            D.Q[idx] = Qv;
-        }
+        __syncthreads();
     }
 }
 
@@ -595,9 +716,39 @@ int grid_for(int total, int per_sm) {
 
 }  // namespace
 
+cudaError_t raise_smem_limit(const void *f, size_t bytes);
+
 bool search_supported(int P) { return P >= kMinPatch && P <= kMaxPatch; }
+
+void search_layout(int P, int S, float tau, float window_step, int &band_pitch, int &band_cap,
+                   int &chunk_pitch, size_t &bytes) {
+    const int chunk = search_chunk(P);
+    const int cw = (chunk - 1) * S + P;
+    const int margin = (int)ceilf(tau) + (int)ceilf(2.f * window_step) + 3;
+    band_cap = cw + 2 * margin + kBandSpread;
+    band_pitch = (band_cap + 31) / 32 * 32 + 1;  // rows land in different banks
+    chunk_pitch = cw | 1;
+    bytes = sizeof(float) * ((size_t)P * band_pitch + 2 * (size_t)P * chunk_pitch + 4 * (size_t)chunk + 16);
+}
+
+size_t fuse_smem(int P, int S) {
+    const int nkx = (kFuseTileW + P - 2) / S + 2, nky = (kFuseTileH + P - 2) / S + 2;
+    return sizeof(float4) * (size_t)nkx * nky;
+}
+
+cudaError_t prepare_fuse(size_t smem_bytes) { return raise_smem_limit((const void *)k_fuse, smem_bytes); }
 int search_group(int P) { return P <= 8 ? 8 : 16; }
 int search_chunk(int P) { return 2 * (256 / search_group(P)); }
+
+// Raises (never lowers) a kernel's dynamic shared-memory limit to `bytes`.
+cudaError_t raise_smem_limit(const void *f, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    cudaFuncAttributes at;
+    cudaError_t e = cudaFuncGetAttributes(&at, f);
+    if (e != cudaSuccess) return e;
+    if ((size_t)at.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
 
 cudaError_t prepare_search(int P, size_t smem_bytes) {
     const int combos[5][2] = {{E_U8, E_F32}, {E_U8, E_F16}, {E_F32, E_F32}, {E_F32, E_F16},
@@ -605,8 +756,7 @@ cudaError_t prepare_search(int P, size_t smem_bytes) {
     for (const auto &c : combos) {
         const void *f = search_kernel(P, c[0], c[1]);
         if (f == nullptr) return cudaErrorInvalidValue;
-        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem_bytes);
+        cudaError_t e = raise_smem_limit(f, smem_bytes);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -642,18 +792,8 @@ cudaError_t launch_search(const LaunchArgs &a, int in_type, int g_type, size_t s
     return cudaLaunchKernel(f, dim3(grid), dim3(256), args, smem, s);
 }
 
-cudaError_t launch_sigma_r(const LaunchArgs &a, cudaStream_t s) {
-    k_sigma_r<<<grid_for(a.npairs, 8), 256, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_posterior(const LaunchArgs &a, cudaStream_t s) {
-    k_posterior<<<grid_for(a.total, 8), 256, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_densify(const LaunchArgs &a, cudaStream_t s) {
-    k_densify<<<grid_for(a.total, 8), 256, 0, s>>>(a);
+cudaError_t launch_fuse(const LaunchArgs &a, size_t smem, cudaStream_t s) {
+    k_fuse<<<grid_for(a.total, 8), 256, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -122,7 +122,7 @@ extern "C" bdis_status bdis_match_noalloc(const bdis_params *pp, const uint8_t *
     const int chunk = search_chunk(P);
     size_t off = na_align(sizeof(LevelDesc) * kMaxLevels, 256);
     size_t oG[kMaxLevels], oL[kMaxLevels], oR[kMaxLevels], oD[kMaxLevels], oQ[kMaxLevels];
-    size_t oRec[kMaxLevels], oFuse[kMaxLevels], oSr[kMaxLevels];
+    size_t oRec[kMaxLevels], oFuse[kMaxLevels], oSr[kMaxLevels], oSp[kMaxLevels];
     int units[kMaxLevels][W_COUNT];
     auto take = [&](size_t n) {
         off = na_align(off, 256);
@@ -139,10 +139,10 @@ extern "C" bdis_status bdis_match_noalloc(const bdis_params *pp, const uint8_t *
         d.npx = d.kxreg + ((d.w - P) % S != 0 ? 1 : 0);
         d.npy = d.kyreg + ((d.h - P) % S != 0 ? 1 : 0);
         d.nchunks = (d.npx + chunk - 1) / chunk;
+        d.tiles_x = (d.w + kFuseTileW - 1) / kFuseTileW;
         units[l][W_PYR] = (((d.w + 1) / 2) * ((d.h + 1) / 2) + 255) / 256;
         units[l][W_SEARCH] = d.npy * d.nchunks;
-        units[l][W_POST] = (d.npx * d.npy + 255) / 256;
-        units[l][W_DENSE] = (d.w * d.h + 255) / 256;
+        units[l][W_FUSE] = d.tiles_x * ((d.h + kFuseTileH - 1) / kFuseTileH);
         const size_t gp = na_align((size_t)d.w * esz, 128) / esz;
         d.gpitch = (int)gp;
         d.pitch = l == 0 ? pitch : (int)gp;
@@ -157,18 +157,17 @@ extern "C" bdis_status bdis_match_noalloc(const bdis_params *pp, const uint8_t *
         oRec[l] = take(sizeof(bdis_patch_record) * np);
         oFuse[l] = take(sizeof(float4) * np);
         oSr[l] = take(sizeof(float));
+        oSp[l] = take(sizeof(float4) * (size_t)d.npy * d.nchunks);
     }
     if (off > kNoAllocScratchBytes) return BDIS_EUNSUPPORTED;  // needs more than the static maximum
 
-    // search shared memory of the widest level
-    auto smem_of = [&](int wl, int &bp, int &cp) {
-        bp = (int)na_align((size_t)wl, 32) + 1;
-        cp = (chunk - 1) * S + P;
-        if ((cp & 1) == 0) cp += 1;
-        return sizeof(float) * ((size_t)P * bp + 2 * (size_t)P * cp);
-    };
-    int bp0, cp0;
-    if (smem_of(w, bp0, cp0) > 227 * 1024) return BDIS_EUNSUPPORTED;
+    // shared memory of the search and fuse blocks
+    const float tau = p.search_radius > 0.f ? p.search_radius : (float)P;
+    int band_pitch, band_cap, chunk_pitch;
+    size_t smem;
+    search_layout(P, S, tau, p.window_step, band_pitch, band_cap, chunk_pitch, smem);
+    const size_t fsmem = fuse_smem(P, S);
+    if (smem > 227 * 1024 || fsmem > 227 * 1024) return BDIS_EUNSUPPORTED;
 
     void *scratch = nullptr;
     const bdis_status ss = na_scratch(&scratch);
@@ -194,6 +193,7 @@ extern "C" bdis_status bdis_match_noalloc(const bdis_params *pp, const uint8_t *
         d.rec = (bdis_patch_record *)(base + oRec[l]);
         d.fuse = (float4 *)(base + oFuse[l]);
         d.sigma_r = (float *)(base + oSr[l]);
+        d.spart = (float4 *)(base + oSp[l]);
     }
     for (int l = 0; l + 1 < NL; ++l) {
         LevelDesc &d = tab.d[l];
@@ -214,8 +214,10 @@ extern "C" bdis_status bdis_match_noalloc(const bdis_params *pp, const uint8_t *
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
-    // only ever raise the opt-in limit of the shared search kernels
-    if (prepare_search(P, (size_t)optin) != cudaSuccess) return BDIS_ECUDA;
+    // the kernels' shared-memory limits are only ever raised, never lowered
+    (void)optin;
+    if (prepare_search(P, smem) != cudaSuccess) return BDIS_ECUDA;
+    if (prepare_fuse(fsmem) != cudaSuccess) return BDIS_ECUDA;
     k_noalloc_write_descs<<<1, 32, 0, st>>>(tab, d_descs);
     if (cudaGetLastError() != cudaSuccess) return BDIS_ECUDA;
 
@@ -261,19 +263,18 @@ extern "C" bdis_status bdis_match_noalloc(const bdis_params *pp, const uint8_t *
         a.descs = d_descs + l;
         a.level = l;
         a.gamma_w = (float)(std::ldexp(1.0, l) / gsum);
-        const size_t sm = smem_of(tab.d[l].w, a.band_pitch, a.chunk_pitch);
+        a.band_pitch = band_pitch;
+        a.band_cap = band_cap;
+        a.chunk_pitch = chunk_pitch;
         a.total = units[l][W_SEARCH];
         const int itype = l == 0 ? E_U8 : st_type;
-        int occ = search_occupancy(P, itype, st_type, sm);
+        int occ = search_occupancy(P, itype, st_type, smem);
         if (occ < 1) occ = 1;
         const int grid = a.total < sms * occ ? a.total : sms * occ;
-        if (launch_search(a, itype, st_type, sm, grid > 0 ? grid : 1, st) != cudaSuccess)
+        if (launch_search(a, itype, st_type, smem, grid > 0 ? grid : 1, st) != cudaSuccess)
             return BDIS_ECUDA;
-        if (launch_sigma_r(a, st) != cudaSuccess) return BDIS_ECUDA;
-        a.total = units[l][W_POST];
-        if (launch_posterior(a, st) != cudaSuccess) return BDIS_ECUDA;
-        a.total = units[l][W_DENSE];
-        if (launch_densify(a, st) != cudaSuccess) return BDIS_ECUDA;
+        a.total = units[l][W_FUSE];
+        if (launch_fuse(a, fsmem, st) != cudaSuccess) return BDIS_ECUDA;
     }
     return BDIS_OK;
 }
