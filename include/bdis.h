@@ -230,7 +230,14 @@ typedef enum {
     BDIS_OPT_GRAPH = 1,
     /* 1: bracket every kernel launch with CUDA events on the call's stream
      * and accumulate per-kernel device time (graph replay is off while on). */
-    BDIS_OPT_PROFILE = 2
+    BDIS_OPT_PROFILE = 2,
+    /* 1 (default): on the first call of a geometry (pair count and sizes),
+     * time the candidate launch configurations (search patches per block,
+     * fusion tile size) level by level and keep the fastest; the call waits
+     * for the timing runs.  All configurations compute identical results.
+     * 0: the default configuration.  Never tunes while the stream is being
+     * captured. */
+    BDIS_OPT_AUTOTUNE = 3
 } bdis_option;
 
 bdis_status bdis_set_option(bdis_handle *h, int option, int value);

@@ -81,7 +81,7 @@ class bdis_profile(C.Structure):
     _fields_ = [("launches", C.c_int * 3), ("ms", C.c_double * 3)]
 
 
-OPT_GRAPH, OPT_PROFILE = 1, 2
+OPT_GRAPH, OPT_PROFILE, OPT_AUTOTUNE = 1, 2, 3
 KERNEL_NAMES = ["pyramid", "search", "fuse"]
 
 

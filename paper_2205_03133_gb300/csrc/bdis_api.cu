@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -41,6 +42,9 @@ struct bdis_handle {
     // scratch of the backward pass (grows, never shrinks)
     char *garena = nullptr;
     size_t garena_cap = 0;
+    // autotuner: per-level launch configuration cached per geometry key
+    bool autotune = true;
+    std::map<std::string, std::vector<LevelCfg>> tuned;
     // per-kernel event timing
     bool profile = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -157,7 +161,6 @@ LaunchArgs base_args(const bdis_params &p, int level, const LevelDesc *descs, in
     a.pdf_resid = p.pdf_resid;
     a.use_c2f = p.use_c2f;
     a.use_sgmm = p.use_sgmm;
-    a.chunk = search_chunk(p.patch);
     fill_sgmm(p, a.m);
     return a;
 }
@@ -166,11 +169,12 @@ LaunchArgs base_args(const bdis_params &p, int level, const LevelDesc *descs, in
 struct Plan {
     size_t bytes = 0;
     size_t off_desc = 0;
+    size_t off_acc = 0, acc_count = 0;  // sigma_r accumulators, contiguous
     std::vector<LevelDesc> descs;  // [level][pair]
     int wmax[kMaxLevels] = {0};
     int units[kMaxLevels][W_COUNT] = {{0}};
     // arena offsets, index level * n + pair
-    std::vector<size_t> oG, oL, oR, oD, oQ, oRec, oFuse, oSr, oSp;
+    std::vector<size_t> oG, oL, oR, oD, oQ, oRec, oFuse, oSr;
 };
 
 struct Bump {
@@ -184,17 +188,20 @@ struct Bump {
 };
 
 // Phase 1: geometry, work ranges and arena offsets.
-void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, Plan &pl) {
+void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, const LevelCfg *cfg,
+                 Plan &pl) {
     const int NL = p.levels, P = p.patch, S = p.stride;
     const size_t esz = p.storage == BDIS_STORE_F16 ? 2 : 4;
     const size_t cnt = (size_t)NL * n;
     pl.descs.assign(cnt, LevelDesc{});
-    for (auto *v : {&pl.oG, &pl.oL, &pl.oR, &pl.oD, &pl.oQ, &pl.oRec, &pl.oFuse, &pl.oSr, &pl.oSp})
+    for (auto *v : {&pl.oG, &pl.oL, &pl.oR, &pl.oD, &pl.oQ, &pl.oRec, &pl.oFuse, &pl.oSr})
         v->assign(cnt, 0);
     Bump b;
     pl.off_desc = b.take(sizeof(LevelDesc) * cnt);
-    const int chunk = search_chunk(P);
+    pl.acc_count = 3 * cnt;
+    pl.off_acc = b.take(sizeof(unsigned long long) * pl.acc_count);
     for (int l = 0; l < NL; ++l) {
+        const int chunk = search_chunk(P, cfg[l].passes);
         int begin[W_COUNT] = {0, 0, 0};
         pl.wmax[l] = 0;
         for (int i = 0; i < n; ++i) {
@@ -206,11 +213,11 @@ void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, Plan &pl) 
             d.npx = num_origins(d.w, P, S, &d.kxreg);
             d.npy = num_origins(d.h, P, S, &d.kyreg);
             d.nchunks = (d.npx + chunk - 1) / chunk;
-            d.tiles_x = (d.w + kFuseTileW - 1) / kFuseTileW;
+            d.tiles_x = (d.w + cfg[l].tile_w - 1) / cfg[l].tile_w;
             const int units[W_COUNT] = {
-                (((d.w + 1) / 2) * ((d.h + 1) / 2) + 255) / 256,  // pyramid: one thread per 2x2
+                ((d.w + 63) / 64) * ((d.h + 31) / 32),             // pyramid: 64 x 32 tiles
                 d.npy * d.nchunks,                                // search: chunks of a patch row
-                d.tiles_x * ((d.h + kFuseTileH - 1) / kFuseTileH),  // fuse: pixel tiles
+                d.tiles_x * ((d.h + cfg[l].tile_h - 1) / cfg[l].tile_h),  // fuse: pixel tiles
             };
             for (int q = 0; q < W_COUNT; ++q) {
                 d.work_begin[q] = begin[q];
@@ -232,7 +239,6 @@ void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, Plan &pl) 
             pl.oRec[k] = b.take(sizeof(bdis_patch_record) * np);
             pl.oFuse[k] = b.take(sizeof(float4) * np);
             pl.oSr[k] = b.take(sizeof(float));
-            pl.oSp[k] = b.take(sizeof(float4) * (size_t)d.npy * d.nchunks);
         }
         for (int q = 0; q < W_COUNT; ++q) pl.units[l][q] = begin[q];
     }
@@ -265,7 +271,7 @@ void plan_pointers(const bdis_params &p, int n, const bdis_pair *pairs, char *ba
             d.rec = (bdis_patch_record *)(base + pl.oRec[k]);
             d.fuse = (float4 *)(base + pl.oFuse[k]);
             d.sigma_r = (float *)(base + pl.oSr[k]);
-            d.spart = (float4 *)(base + pl.oSp[k]);
+            d.acc = (unsigned long long *)(base + pl.off_acc) + 3 * k;
         }
     for (int l = 0; l < NL; ++l)
         for (int i = 0; i < n; ++i) {
@@ -341,30 +347,37 @@ int sm_count() {
     return sms;
 }
 
-// Runs the whole coarse-to-fine pipeline for n pairs.  `extra` bytes are
-// reserved after the plan's arena (host-buffer staging).
-bdis_status run(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, cudaStream_t st) {
+const LevelCfg kDefaultCfg{2, 32, 16};
+const LevelCfg kSearchCands[3] = {{1, 32, 16}, {2, 64, 32}, {4, 32, 16}};
+
+// The whole coarse-to-fine pipeline for n pairs with per-level launch
+// configuration cfg.  graph: replay / capture allowed; prof: bracket each
+// launch with events (kernel id and level recorded in h->ev_marks).
+bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, cudaStream_t st,
+                    const LevelCfg *cfg, bool graph, bool prof) {
     const bdis_params &p = h->p;
     const int NL = p.levels;
     Plan pl;
-    plan_layout(p, n, pairs, pl);
-    int band_pitch = 0, band_cap = 0, chunk_pitch = 0;
-    size_t smem = 0;
-    search_layout(p.patch, p.stride, tau_at(p), p.window_step, band_pitch, band_cap, chunk_pitch,
-                  smem);
-    const size_t fsmem = fuse_smem(p.patch, p.stride);
-    if (smem > 227 * 1024 || fsmem > 227 * 1024)
+    plan_layout(p, n, pairs, cfg, pl);
+    int bpitch[kMaxLevels], bcap[kMaxLevels], cpitch[kMaxLevels];
+    size_t ssm[kMaxLevels], fsm[kMaxLevels], smax = 0, fmax = 0;
+    for (int l = 0; l < NL; ++l) {
+        search_layout(p.patch, p.stride, tau_at(p), p.window_step, cfg[l].passes, bpitch[l], bcap[l],
+                      cpitch[l], ssm[l]);
+        fsm[l] = fuse_smem(p.patch, p.stride, cfg[l].tile_w, cfg[l].tile_h);
+        smax = std::max(smax, ssm[l]);
+        fmax = std::max(fmax, fsm[l]);
+    }
+    if (smax > 227 * 1024 || fmax > 227 * 1024)
         return fail(h, BDIS_EUNSUPPORTED, "search radius too large for the shared-memory band");
     bdis_status s = ensure_arena(h, pl.bytes);
     if (s != BDIS_OK) return s;
     plan_pointers(p, n, pairs, h->arena, pl);
-    if (h->prepared_P != p.patch || h->smem_prepared < smem) {
+    {
         // limits are only raised, so other handles' settings stay valid
-        cudaError_t e = prepare_search(p.patch, smem);
-        if (e == cudaSuccess) e = prepare_fuse(fsmem);
+        cudaError_t e = prepare_search(p.patch, smax);
+        if (e == cudaSuccess) e = prepare_fuse(fmax);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute");
-        h->smem_prepared = smem;
-        h->prepared_P = p.patch;
     }
     // upload the descriptor table unless identical to the last upload
     const size_t tbytes = sizeof(LevelDesc) * pl.descs.size();
@@ -389,7 +402,7 @@ bdis_status run(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, cuda
     // one kernel launch, optionally bracketed by profiling events
     auto timed = [&](int kid, auto &&fn) -> cudaError_t {
         size_t i0 = 0;
-        if (h->profile) {
+        if (prof) {
             i0 = h->ev_marks.empty() ? 0 : h->ev_marks.back().second + 2;
             while (h->ev_pool.size() < i0 + 2) {
                 cudaEvent_t ev;
@@ -402,7 +415,7 @@ bdis_status run(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, cuda
         }
         cudaError_t e = fn();
         if (e != cudaSuccess) return e;
-        if (h->profile) {
+        if (prof) {
             e = cudaEventRecord(h->ev_pool[i0 + 1], st);
             if (e != cudaSuccess) return e;
             h->ev_marks.emplace_back(kid, i0);
@@ -415,23 +428,30 @@ bdis_status run(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, cuda
         for (int l = 0; l < NL; ++l) {
             LaunchArgs a = base_args(p, l, d_descs + (size_t)l * n, n);
             a.total = pl.units[l][W_PYR];
+            if (l == 0) {
+                a.acc_zero = (unsigned long long *)(h->arena + pl.off_acc);
+                a.acc_count = (int)pl.acc_count;
+            }
             e = timed(BDIS_K_PYRAMID, [&] { return launch_pyramid(a, l == 0 ? in_type : st_type, st_type, st); });
             if (e != cudaSuccess) return cuda_fail(h, e, "pyramid launch");
         }
         // coarse-to-fine levels: search, then sigma_r + posterior + fusion
         for (int l = NL - 1; l >= 0; --l) {
             LaunchArgs a = base_args(p, l, d_descs + (size_t)l * n, n);
-            a.band_pitch = band_pitch;
-            a.band_cap = band_cap;
-            a.chunk_pitch = chunk_pitch;
+            a.chunk = search_chunk(p.patch, cfg[l].passes);
+            a.tile_w = cfg[l].tile_w;
+            a.tile_h = cfg[l].tile_h;
+            a.band_pitch = bpitch[l];
+            a.band_cap = bcap[l];
+            a.chunk_pitch = cpitch[l];
             a.total = pl.units[l][W_SEARCH];
             const int itype = l == 0 ? in_type : st_type;
-            const int occ = search_occupancy(p.patch, itype, st_type, smem);
+            const int occ = search_occupancy(p.patch, itype, st_type, ssm[l]);
             const int grid = std::max(1, std::min(a.total, sm_count() * occ));
-            e = timed(BDIS_K_SEARCH, [&] { return launch_search(a, itype, st_type, smem, grid, st); });
+            e = timed(BDIS_K_SEARCH, [&] { return launch_search(a, itype, st_type, ssm[l], grid, st); });
             if (e != cudaSuccess) return cuda_fail(h, e, "search launch");
             a.total = pl.units[l][W_FUSE];
-            e = timed(BDIS_K_FUSE, [&] { return launch_fuse(a, fsmem, st); });
+            e = timed(BDIS_K_FUSE, [&] { return launch_fuse(a, fsm[l], st); });
             if (e != cudaSuccess) return cuda_fail(h, e, "fuse launch");
         }
         return BDIS_OK;
@@ -439,7 +459,7 @@ bdis_status run(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, cuda
 
     // Graph replay: only on a non-default stream that is not already being
     // captured by the caller, and only for the exact descriptors captured.
-    bool can_graph = h->use_graph && !h->profile && st != nullptr;
+    bool can_graph = graph && h->use_graph && !prof && st != nullptr;
     if (can_graph) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
@@ -493,6 +513,83 @@ bdis_status run(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, cuda
     h->in_type = in_type;
     h->d_descs = d_descs;
     return BDIS_OK;
+}
+
+std::string geometry_key(const bdis_handle *h, int n, const bdis_pair *pairs, int in_type) {
+    std::string k = std::to_string(in_type) + ":" + std::to_string(n);
+    for (int i = 0; i < n; ++i) k += ":" + std::to_string(pairs[i].w) + "x" + std::to_string(pairs[i].h);
+    (void)h;
+    return k;
+}
+
+// Autotuner: times the candidate configurations with per-launch events on
+// this geometry and keeps, per level, the fastest search passes and the
+// fastest fuse tile.  Every configuration computes identical results.
+bdis_status autotune(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, cudaStream_t st,
+                     std::vector<LevelCfg> &best) {
+    const int NL = h->p.levels;
+    std::vector<LevelCfg> cfg((size_t)NL, kDefaultCfg);
+    bdis_status s = run_cfg(h, n, pairs, in_type, st, cfg.data(), false, false);  // warm-up
+    if (s != BDIS_OK) return s;
+    double tsearch[3][kMaxLevels] = {{0}}, tfuse[3][kMaxLevels] = {{0}};
+    for (int c = 0; c < 3; ++c) {
+        for (int l = 0; l < NL; ++l) cfg[l] = kSearchCands[c];
+        const size_t m0 = h->ev_marks.size();
+        s = run_cfg(h, n, pairs, in_type, st, cfg.data(), false, true);
+        if (s != BDIS_OK) return s;
+        // marks in launch order: NL pyramids, then (search, fuse) for l = NL-1 .. 0
+        for (size_t m = m0; m < h->ev_marks.size(); ++m) {
+            float ms = 0.f;
+            const size_t ev = h->ev_marks[m].second;
+            cudaError_t e = cudaEventSynchronize(h->ev_pool[ev + 1]);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, h->ev_pool[ev], h->ev_pool[ev + 1]);
+            if (e != cudaSuccess) return cuda_fail(h, e, "autotune events");
+            const int idx = (int)(m - m0);
+            if (idx < NL) continue;
+            const int l = NL - 1 - (idx - NL) / 2;
+            if ((idx - NL) % 2 == 0) tsearch[c][l] = ms; else tfuse[c][l] = ms;
+        }
+        h->ev_marks.resize(m0);
+    }
+    best.assign((size_t)NL, kDefaultCfg);
+    for (int l = 0; l < NL; ++l) {
+        int bs = 0, bf = 0;
+        for (int c = 1; c < 3; ++c) {
+            if (tsearch[c][l] < tsearch[bs][l]) bs = c;
+            if (tfuse[c][l] < tfuse[bf][l]) bf = c;
+        }
+        best[l].passes = kSearchCands[bs].passes;
+        best[l].tile_w = kSearchCands[bf].tile_w;
+        best[l].tile_h = kSearchCands[bf].tile_h;
+    }
+    return BDIS_OK;
+}
+
+// Runs the whole pipeline for n pairs with the tuned configuration of this
+// geometry (tuned on first use unless the stream is being captured).
+bdis_status run(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, cudaStream_t st) {
+    const std::string key = geometry_key(h, n, pairs, in_type);
+    auto it = h->tuned.find(key);
+    std::vector<LevelCfg> cfg;
+    if (it != h->tuned.end()) {
+        cfg = it->second;
+    } else {
+        bool capturing = false;
+        if (st != nullptr) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+                capturing = true;
+            cudaGetLastError();
+        }
+        if (h->autotune && !capturing) {
+            bdis_status s = autotune(h, n, pairs, in_type, st, cfg);
+            if (s != BDIS_OK) return s;
+            h->tuned[key] = cfg;
+        } else {
+            cfg.assign((size_t)h->p.levels, kDefaultCfg);
+        }
+    }
+    return run_cfg(h, n, pairs, in_type, st, cfg.data(), true, h->profile);
 }
 
 }  // namespace
@@ -564,6 +661,10 @@ bdis_status bdis_set_option(bdis_handle *h, int option, int value) {
         h->profile = value != 0;
         return BDIS_OK;
     }
+    if (option == BDIS_OPT_AUTOTUNE) {
+        h->autotune = value != 0;
+        return BDIS_OK;
+    }
     return fail(h, BDIS_EINVAL, "unknown option");
 }
 
@@ -630,7 +731,8 @@ bdis_status bdis_match_host(bdis_handle *h, const uint8_t *left, const uint8_t *
     cudaStream_t st = (cudaStream_t)stream;
     // device staging for the inputs and outputs, after the pipeline's arena
     Plan pl;
-    plan_layout(h->p, 1, &q, pl);
+    std::vector<LevelCfg> dcfg((size_t)h->p.levels, LevelCfg{2, 32, 16});
+    plan_layout(h->p, 1, &q, dcfg.data(), pl);
     const size_t img = align_up((size_t)w * hgt, 256);
     const size_t fo = align_up(sizeof(float) * (size_t)w * hgt, 256);
     const size_t extra = 2 * img + 2 * fo + img;

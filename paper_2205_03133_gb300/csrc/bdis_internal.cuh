@@ -21,12 +21,21 @@ constexpr int kWindow = 5;  // samples of the small window P' (Sec. III-B, s = 5
 // half-open unit range [work_begin[k], work_begin[k] + units) of kernel k.
 enum WorkKind { W_PYR = 0, W_SEARCH = 1, W_FUSE = 2, W_COUNT = 3 };
 
-// Pixel tile of the fused posterior / densify kernel.
-constexpr int kFuseTileW = 32;
-constexpr int kFuseTileH = 16;
+// Largest pixel tile of the fused posterior / densify kernel.
+constexpr int kFuseTileWMax = 64;
+constexpr int kFuseTileHMax = 32;
+
+// Launch configuration of one level (chosen by the autotuner): search passes
+// per block (a block's chunk is passes x groups patches) and fuse tile size.
+struct LevelCfg {
+    int passes;
+    int tile_w, tile_h;
+};
 // Extra columns of the search's right band for the spread of the initial
 // estimates inside one chunk (wider spreads read the image directly).
 constexpr int kBandSpread = 64;
+// Fixed-point scale of the sigma_r sum of E(0) (E(0) <= 255^2 * 256 per patch).
+constexpr float kSigmaFix1 = 65536.f;
 
 // Element types of the level images.
 enum ElemType { E_U8 = 0, E_F32 = 1, E_F16 = 2 };
@@ -43,7 +52,7 @@ struct alignas(16) LevelDesc {
     bdis_patch_record *rec;   // npx * npy records of this pair at this level
     float4 *fuse;             // (d, rho, sig2, kept) per patch for the fusion gather
     float *sigma_r;           // one float
-    float4 *spart;            // per search unit: (sum E(0), count, sum E(0)^2) of kept patches
+    unsigned long long *acc;  // sigma_r sums of kept patches: E(0) * 2^16, count, E(0)^2
     int w, h, pitch;          // level size, row pitch (elements) of L and R
     int gpitch;               // row pitch (elements) of G
     int wn, hn, pitchn;       // next coarser level size and pitch
@@ -72,10 +81,13 @@ struct LaunchArgs {
     float pdf_resid;
     int use_c2f, use_sgmm;
     int chunk;                // patches per search chunk
+    int tile_w, tile_h;       // fuse tile
     int band_pitch;           // floats per row of the staged right band
     int band_cap;             // usable columns of the right band
     int chunk_pitch;          // floats per row of the staged left / gradient band
     float m[kMaxPatch];       // 1D sGMM factors m[a] (Eq. 8 is separable)
+    unsigned long long *acc_zero;  // finest pyramid launch: accumulators to clear
+    int acc_count;
 };
 
 // ---- differentiable finest level (bdis_grad.cu)
@@ -122,9 +134,9 @@ cudaError_t launch_search(const LaunchArgs &a, int in_type, int g_type, size_t s
                           cudaStream_t s);
 cudaError_t launch_fuse(const LaunchArgs &a, size_t smem, cudaStream_t s);
 // Shared-memory layout of the search (band pitch and capacity, chunk pitch, bytes).
-void search_layout(int P, int S, float tau, float window_step, int &band_pitch, int &band_cap,
-                   int &chunk_pitch, size_t &bytes);
-size_t fuse_smem(int P, int S);
+void search_layout(int P, int S, float tau, float window_step, int passes, int &band_pitch,
+                   int &band_cap, int &chunk_pitch, size_t &bytes);
+size_t fuse_smem(int P, int S, int tile_w, int tile_h);
 cudaError_t prepare_fuse(size_t smem_bytes);
 // Raise (never lower) the dynamic shared-memory limit of every search instance.
 cudaError_t prepare_search(int P, size_t smem_bytes);
@@ -132,6 +144,6 @@ cudaError_t prepare_search(int P, size_t smem_bytes);
 int search_occupancy(int P, int in_type, int g_type, size_t smem_bytes);
 bool search_supported(int P);
 int search_group(int P);      // lanes per patch
-int search_chunk(int P);      // patches per chunk
+int search_chunk(int P, int passes);  // patches per chunk
 
 }  // namespace bdis

@@ -5,11 +5,13 @@
 // block strides over the units (grid sized to the SM count), so the plain
 // single-pair call and the batched call run the same code.  Two launches per
 // level after the pyramid:
-//   k_pyramid   image pyramid + Sobel-x/8 of the left image (Sec. III-A)
+//   k_pyramid   image pyramid + Sobel-x/8 of the left image (Sec. III-A),
+//               tiles staged in shared memory
 //   k_search    inverse-compositional GN per patch (Eq. 1), window energies,
-//               rejection flags (Sec. III-B, Sec. IV technical details), and
-//               per-chunk partial sums for the dynamic sigma_r (text after Eq. 6)
-//   k_fuse      per 32x16 pixel tile: sigma_r, window posterior (Eq. 5-6),
+//               rejection flags (Sec. III-B, Sec. IV technical details), and the
+//               sums of the dynamic sigma_r (text after Eq. 6), accumulated in
+//               exact 64-bit fixed point
+//   k_fuse      per 32x16 pixel tile: window posterior (Eq. 5-6),
 //               coarse-to-fine rho (Eq. 10-11) and PDF fit (Eq. 14-16) of the
 //               patches overlapping the tile, then the sGMM fusion gather
 //               (Eq. 8-9, Eq. 12) and pixel variance (Eq. 17)
@@ -23,59 +25,75 @@ namespace {
 
 // ---------------------------------------------------------------- pyramid
 
-// One thread per pixel (X, Y) of the half-resolution grid of level l:
-// Sobel-x/8 of the left image at the 2x2 block (2X.., 2Y..) of level l and,
-// when a coarser level is requested, the [1 4 6 4 1]/16 blur of L and R at
-// (2X, 2Y), reflect-101 borders.
+// A block owns a 64 x 32 pixel tile of level l and the 32 x 16 tile of
+// level l+1 under it.  It stages the 68 x 36 region of L (and R when a
+// coarser level is built) with reflect-101 indices applied once, then writes
+// Sobel-x/8 of L for the 64 x 32 pixels and the [1 4 6 4 1]/16 blur of L and
+// R at the even pixels (2X, 2Y).
+constexpr int kPyrTW = 64, kPyrTH = 32;
+constexpr int kPyrSW = kPyrTW + 4, kPyrSH = kPyrTH + 4;
+
 template <typename TI, typename TO>
 __global__ void __launch_bounds__(256) k_pyramid(LaunchArgs a) {
+    __shared__ float Ls[kPyrSH][kPyrSW];
+    __shared__ float Rs[kPyrSH][kPyrSW];
+    // the finest pyramid launch runs before every search: it clears the
+    // sigma_r accumulators of all levels and pairs
+    if (blockIdx.x == 0 && a.acc_zero != nullptr)
+        for (int i = threadIdx.x; i < a.acc_count; i += blockDim.x) a.acc_zero[i] = 0ull;
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) {
         const LevelDesc &D = a.descs[find_pair(a.descs, a.npairs, unit, W_PYR)];
-        const int wq = (D.w + 1) >> 1, hq = (D.h + 1) >> 1;
-        const int idx = (unit - D.work_begin[W_PYR]) * blockDim.x + threadIdx.x;
-        if (idx >= wq * hq) continue;
-        const int X = idx % wq, Y = idx / wq;
+        const int tile = unit - D.work_begin[W_PYR];
+        const int ntx = (D.w + kPyrTW - 1) / kPyrTW;
+        const int tx = tile % ntx, ty = tile / ntx;
+        const int x0 = tx * kPyrTW - 2, y0 = ty * kPyrTH - 2;  // region origin
+        const int w = D.w, h = D.h, pitch = D.pitch;
         const TI *L = (const TI *)D.L;
         const TI *R = (const TI *)D.R;
-        const int w = D.w, h = D.h, pitch = D.pitch;
-        TO *G = (TO *)D.G;
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int y = 2 * Y + j;
-            if (y >= h) break;
-            const TI *r0 = L + (size_t)refl(y - 1, h) * pitch;
-            const TI *r1 = L + (size_t)y * pitch;
-            const TI *r2 = L + (size_t)refl(y + 1, h) * pitch;
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int x = 2 * X + i;
-                if (x >= w) break;
-                const int xm = refl(x - 1, w), xp = refl(x + 1, w);
-                float acc = (ldf(r0 + xp) - ldf(r0 + xm)) + 2.f * (ldf(r1 + xp) - ldf(r1 + xm)) +
-                            (ldf(r2 + xp) - ldf(r2 + xm));
-                stf(G + (size_t)y * D.gpitch + x, acc * 0.125f);
-            }
+        const bool next = D.Ln != nullptr;
+        __syncthreads();
+        for (int i = threadIdx.x; i < kPyrSH * kPyrSW; i += blockDim.x) {
+            const int r = i / kPyrSW, c = i - r * kPyrSW;
+            // only indices within 2 of the image are ever used by a stencil
+            const int gy = refl(min(max(y0 + r, -2), h + 1), h);
+            const int gx = refl(min(max(x0 + c, -2), w + 1), w);
+            Ls[r][c] = ldf(L + (size_t)gy * pitch + gx);
+            if (next) Rs[r][c] = ldf(R + (size_t)gy * pitch + gx);
         }
-        if (D.Ln != nullptr) {
+        __syncthreads();
+        TO *G = (TO *)D.G;
+        for (int i = threadIdx.x; i < kPyrTW * kPyrTH; i += blockDim.x) {
+            const int ly = i / kPyrTW, lx = i - ly * kPyrTW;
+            const int x = x0 + 2 + lx, y = y0 + 2 + ly;
+            if (x >= w || y >= h) continue;
+            const int cx = lx + 2, cy = ly + 2;
+            const float acc = (Ls[cy - 1][cx + 1] - Ls[cy - 1][cx - 1]) +
+                              2.f * (Ls[cy][cx + 1] - Ls[cy][cx - 1]) +
+                              (Ls[cy + 1][cx + 1] - Ls[cy + 1][cx - 1]);
+            stf(G + (size_t)y * D.gpitch + x, acc * 0.125f);
+        }
+        if (next) {
             const float k[5] = {1.f, 4.f, 6.f, 4.f, 1.f};
-            int xs[5];
+            for (int i = threadIdx.x; i < (kPyrTW / 2) * (kPyrTH / 2); i += blockDim.x) {
+                const int oy = i / (kPyrTW / 2), ox = i - oy * (kPyrTW / 2);
+                const int X = tx * (kPyrTW / 2) + ox, Y = ty * (kPyrTH / 2) + oy;
+                if (X >= D.wn || Y >= D.hn) continue;
+                const int cx = 2 * ox + 2, cy = 2 * oy + 2;
+                float accL = 0.f, accR = 0.f;
 #pragma unroll
-            for (int i = 0; i < 5; ++i) xs[i] = refl(2 * X + i - 2, w);
-            float accL = 0.f, accR = 0.f;
+                for (int j = 0; j < 5; ++j) {
+                    float sl = 0.f, sr = 0.f;
 #pragma unroll
-            for (int j = 0; j < 5; ++j) {
-                const size_t ro = (size_t)refl(2 * Y + j - 2, h) * pitch;
-                float sl = 0.f, sr = 0.f;
-#pragma unroll
-                for (int i = 0; i < 5; ++i) {
-                    sl += k[i] * ldf(L + ro + xs[i]);
-                    sr += k[i] * ldf(R + ro + xs[i]);
+                    for (int q = 0; q < 5; ++q) {
+                        sl += k[q] * Ls[cy + j - 2][cx + q - 2];
+                        sr += k[q] * Rs[cy + j - 2][cx + q - 2];
+                    }
+                    accL += k[j] * sl;
+                    accR += k[j] * sr;
                 }
-                accL += k[j] * sl;
-                accR += k[j] * sr;
+                stf((TO *)D.Ln + (size_t)Y * D.pitchn + X, accL * (1.f / 256.f));
+                stf((TO *)D.Rn + (size_t)Y * D.pitchn + X, accR * (1.f / 256.f));
             }
-            stf((TO *)D.Ln + (size_t)Y * D.pitchn + X, accL * (1.f / 256.f));
-            stf((TO *)D.Rn + (size_t)Y * D.pitchn + X, accR * (1.f / 256.f));
         }
     }
 }
@@ -141,6 +159,7 @@ __global__ void __launch_bounds__(256) k_search(LaunchArgs a) {
     // patch spacing between the groups of a warp (a power of two dividing 16)
     int sp = (32 / GPW) / S;
     sp = sp >= 16 ? 16 : sp >= 8 ? 8 : sp >= 4 ? 4 : sp >= 2 ? 2 : 1;
+    sp = min(sp, 8 * (a.chunk / (8 * GPW)));  // must divide 8 x passes
     const int margin = (int)ceilf(a.tau) + (int)ceilf(2.f * h) + 3;
 
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) {
@@ -277,7 +296,6 @@ __global__ void __launch_bounds__(256) k_search(LaunchArgs a) {
             const int base0 = ox + off0;
             float s0[P];
             float sa = 0.f;
-            int nout = 0;
             {
                 float v[P + 1];
                 load_row(base0, v);
@@ -285,16 +303,20 @@ __global__ void __launch_bounds__(256) k_search(LaunchArgs a) {
                 for (int j = 0; j < P; ++j) {
                     s0[j] = fmaf(t0, v[j + 1] - v[j], v[j]);
                     sa += row_on ? s0[j] - T[j] : 0.f;
-                    const int xi = base0 + j;
-                    nout += (row_on && (xi < 0 || xi > w - 1 || (xi == w - 1 && t0 > 0.f))) ? 1 : 0;
                 }
             }
+            // samples outside [0, w-1]: every row shares base0 and t0, so per
+            // row j < -base0 on the left and base0 + j >= w - 1 (t0 > 0) or
+            // >= w (t0 = 0) on the right
+            const int nl = min(max(-base0, 0), P);
+            const int nr = min(max(P + base0 - (t0 > 0.f ? w - 1 : w), 0), P);
+            const int nout_all = P * (nl + nr);
             const float mean0 = group_sum<G>(sa) * invN;
             float e0 = 0.f;
 #pragma unroll
             for (int j = 0; j < P; ++j) {
-                const float qv = row_on ? (s0[j] - T[j]) - mean0 : 0.f;
-                e0 = fmaf(qv, qv, e0);
+                T[j] = row_on ? (s0[j] - T[j]) - mean0 : 0.f;  // now the centred residual
+                e0 = fmaf(T[j], T[j], e0);
             }
             float su[4], suu[4], suc[4];
 #pragma unroll
@@ -308,10 +330,9 @@ __global__ void __launch_bounds__(256) k_search(LaunchArgs a) {
 #pragma unroll
                 for (int j = 0; j < P; ++j) {
                     const float uj = row_on ? fmaf(t, v[j + 1] - v[j], v[j]) - s0[j] : 0.f;
-                    const float c = row_on ? (s0[j] - T[j]) - mean0 : 0.f;
                     p1 += uj;
                     p2 = fmaf(uj, uj, p2);
-                    p3 = fmaf(uj, c, p3);
+                    p3 = fmaf(uj, T[j], p3);
                 }
                 su[k] = p1;
                 suu[k] = p2;
@@ -326,7 +347,6 @@ __global__ void __launch_bounds__(256) k_search(LaunchArgs a) {
                 const float S3 = group_sum<G>(suc[k]);
                 E[k + 1] = fmaxf(S2 - S1 * S1 * invN, 0.f) + 2.f * S3;
             }
-            const int nout_all = (int)group_sum<G>((float)nout);
 
             if (active && gl == 0) {
                 uint32_t f = 0;
@@ -360,13 +380,15 @@ __global__ void __launch_bounds__(256) k_search(LaunchArgs a) {
             }
         }
         __syncthreads();
-        // chunk partial sums for sigma_r, fixed order (warp 0)
+        // sigma_r sums of the chunk in 64-bit fixed point: integer addition is
+        // exactly associative, so the totals do not depend on the chunking or
+        // on the order in which blocks add them
         if (warp == 0) {
-            float s1 = 0.f, s2 = 0.f, s3 = 0.f;
+            unsigned long long s1 = 0ull, s2 = 0ull, s3 = 0ull;
             for (int i = tid; i < nk; i += 32) {
-                s1 += pe[3 * i];
-                s2 += pe[3 * i + 1];
-                s3 += pe[3 * i + 2];
+                s1 += (unsigned long long)__float2ll_rn(pe[3 * i] * kSigmaFix1);
+                s2 += (unsigned long long)pe[3 * i + 1];
+                s3 += (unsigned long long)__float2ll_rn(pe[3 * i + 2]);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -374,7 +396,11 @@ __global__ void __launch_bounds__(256) k_search(LaunchArgs a) {
                 s2 += __shfl_xor_sync(0xffffffffu, s2, o);
                 s3 += __shfl_xor_sync(0xffffffffu, s3, o);
             }
-            if (tid == 0) D.spart[u] = make_float4(s1, s2, s3, 0.f);
+            if (tid == 0) {
+                atomicAdd(D.acc, s1);
+                atomicAdd(D.acc + 1, s2);
+                atomicAdd(D.acc + 2, s3);
+            }
         }
     }
 }
@@ -511,19 +537,6 @@ __device__ float4 posterior_of(const LaunchArgs &a, const LevelDesc &D, int kx, 
     return fz;
 }
 
-__device__ __forceinline__ float block_sum(float v, float *red) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    float s = 0.f;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) s += red[i];
-    return s;  // every thread, same fixed order
-}
-
 // Covering patch indices of pixel coordinate x along one axis: regular k
 // with kS <= x < kS + P, plus the ragged one.
 __device__ __forceinline__ void cover(int x, int n, int P, int S, int kreg, int np, int &lo,
@@ -533,18 +546,22 @@ __device__ __forceinline__ void cover(int x, int n, int P, int S, int kreg, int 
     ext = np > kreg && x >= n - P;
 }
 
-// A block owns a TW x TH pixel tile.  It derives sigma_r of its pair from
-// the search's chunk partials (fixed order, identical in every block),
-// computes the posterior of every patch overlapping the tile into shared
-// memory (the tile containing a patch's origin writes its record), then
-// fuses its pixels by a gather over the covering kept patches (no atomics):
+// A block owns a TW x TH pixel tile.  It reads sigma_r of its pair (reduced
+// by the search), computes the posterior of every patch overlapping the tile
+// into shared memory (the tile containing a patch's origin writes its
+// record), then fuses its pixels by a gather over the covering kept patches
+// (no atomics):
 //   omega_k = rho_k m[x - ox] m[y - oy], D = sum omega d / sum omega,
 //   Q = sum omega rho / sum omega, V = sum omega^2 sig2 / (sum omega)^2.
+// The weight is separable, so the gather runs in two passes: per tile column
+// and covering patch row, sums over the covering patch columns; then per
+// pixel, sums over the covering patch rows.
 __global__ void __launch_bounds__(256) k_fuse(LaunchArgs a) {
-    constexpr int TW = kFuseTileW, TH = kFuseTileH;
-    extern __shared__ float4 fz[];
-    __shared__ float red[8];
-    __shared__ float srs;
+    const int TW = a.tile_w, TH = a.tile_h;
+    extern __shared__ float4 fz[];  // nkx * nky posteriors, then nky * TW column sums
+    __shared__ int cxlo[kFuseTileWMax], cxn[kFuseTileWMax], cxr[kFuseTileWMax];
+    __shared__ int cylo[kFuseTileHMax], cyn[kFuseTileHMax], cyr[kFuseTileHMax];
+    __shared__ float cxm[kFuseTileWMax][kMaxPatch + 2], cym[kFuseTileHMax][kMaxPatch + 2];
     const int P = a.P, S = a.S;
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) {
         const LevelDesc &D = a.descs[find_pair(a.descs, a.npairs, unit, W_FUSE)];
@@ -552,36 +569,24 @@ __global__ void __launch_bounds__(256) k_fuse(LaunchArgs a) {
         const int tx = tile % D.tiles_x, ty = tile / D.tiles_x;
         const int x0 = tx * TW, y0 = ty * TH;
         const int x1 = min(x0 + TW, D.w) - 1, y1 = min(y0 + TH, D.h) - 1;
-
-        // sigma_r of the pair
-        const int nu = D.npy * D.nchunks;
-        float s1 = 0.f, s2 = 0.f, s3 = 0.f;
-        for (int i = threadIdx.x; i < nu; i += blockDim.x) {
-            const float4 v = D.spart[i];
-            s1 += v.x;
-            s2 += v.y;
-            s3 += v.z;
-        }
-        const float S1 = block_sum(s1, red);
-        const float S2 = block_sum(s2, red);
-        const float S3 = block_sum(s3, red);
-        if (threadIdx.x == 0) {
-            float sr;
+        // sigma_r of the pair from the search's exact sums (text after Eq. 6)
+        float sr;
+        {
+            const double S1 = (double)__ldcg(D.acc) / (double)kSigmaFix1;
+            const double S2 = (double)__ldcg(D.acc + 1);
+            const double S3 = (double)__ldcg(D.acc + 2);
             if (a.sigma_r_mode == BDIS_SIGMA_R_FIXED) {
                 sr = a.sigma_r_fixed;
-            } else if (S2 == 0.f) {
+            } else if (S2 == 0.0) {
                 sr = a.sigma_r_floor;
             } else if (a.sigma_r_mode == BDIS_SIGMA_R_LITERAL) {
-                const float mean = S1 / S2;
-                sr = fmaxf(sqrtf(fmaxf(S3 / S2 - mean * mean, 0.f)), a.sigma_r_floor);
+                const float mean = (float)(S1 / S2);
+                sr = fmaxf(sqrtf(fmaxf((float)(S3 / S2) - mean * mean, 0.f)), a.sigma_r_floor);
             } else {
-                sr = fmaxf(sqrtf(S1 / (S2 * (float)(P * P))), a.sigma_r_floor);
+                sr = fmaxf(sqrtf((float)(S1 / (S2 * (double)(P * P)))), a.sigma_r_floor);
             }
-            srs = sr;
-            if (tile == 0) *D.sigma_r = sr;
+            if (tile == 0 && threadIdx.x == 0) *D.sigma_r = sr;
         }
-        __syncthreads();
-        const float sr = srs;
 
         // patches overlapping the tile
         int kxlo, kxhi, kylo, kyhi, tmp;
@@ -602,45 +607,71 @@ __global__ void __launch_bounds__(256) k_fuse(LaunchArgs a) {
             const bool owner = ox >= x0 && ox < x0 + TW && oy >= y0 && oy < y0 + TH;
             fz[i] = posterior_of(a, D, kx, ky, sr, owner);
         }
+        // covering patches (tile-local indices) and their weights per column / row
+        if (threadIdx.x < TW + TH) {
+            const bool col = threadIdx.x < TW;
+            const int c = col ? threadIdx.x : threadIdx.x - TW;
+            const int xy = (col ? x0 : y0) + c;
+            const int n = col ? D.w : D.h, kreg = col ? D.kxreg : D.kyreg, np = col ? D.npx : D.npy;
+            const int klo = col ? kxlo : kylo, nr = col ? nkxr : nkyr, nt = col ? nkx : nky;
+            int lo = 0, hi = -1;
+            bool ext = false;
+            if (xy < n) cover(xy, n, P, S, kreg, np, lo, hi, ext);
+            const int cnt = xy < n ? max(0, hi - lo + 1) + (ext ? 1 : 0) : 0;
+            float *mrow = col ? cxm[c] : cym[c];
+            for (int q = 0; q < cnt; ++q) {
+                const bool isx = lo + q > hi;  // the ragged extra patch comes last
+                const int k = isx ? np - 1 : lo + q;
+                const int o = origin(k, n, P, S, kreg);
+                mrow[q] = a.use_sgmm ? a.m[xy - o] : 1.f;
+            }
+            (col ? cxlo : cylo)[c] = lo - klo;  // first regular local index
+            (col ? cxn : cyn)[c] = cnt;
+            (col ? cxr : cyr)[c] = xy < n ? max(0, hi - lo + 1) : 0;  // regular entries
+            (void)nr;
+            (void)nt;
+        }
         __syncthreads();
 
-        // fuse the tile's pixels
+        // pass 1: per tile column x and patch row iy, sums over the covering columns
+        float4 *csum = fz + nkx * nky;  // [nky][TW] of (sum m rho d, sum m rho, sum m rho^2, sum m^2 rho^2 sig2)
+        for (int i = threadIdx.x; i < nky * TW; i += blockDim.x) {
+            const int iy = i / TW, c = i - iy * TW;
+            const int cnt = cxn[c], lo = cxlo[c], nreg = cxr[c];
+            float A = 0.f, Bw = 0.f, Cq = 0.f, V = 0.f;
+            for (int q = 0; q < cnt; ++q) {
+                const int lx = q < nreg ? lo + q : nkx - 1;
+                const float4 f = fz[iy * nkx + lx];
+                const float mr = cxm[c][q] * f.y;  // 0 for a rejected patch
+                A = fmaf(mr, f.x, A);
+                Bw += mr;
+                Cq = fmaf(mr, f.y, Cq);
+                V = fmaf(mr * mr, f.z, V);
+            }
+            csum[i] = make_float4(A, Bw, Cq, V);
+        }
+        __syncthreads();
+
+        // pass 2: per pixel, sums over the covering patch rows
         for (int pix = threadIdx.x; pix < TW * TH; pix += blockDim.x) {
-            const int x = x0 + pix % TW, y = y0 + pix / TW;
+            const int c = pix % TW, r = pix / TW;
+            const int x = x0 + c, y = y0 + r;
             if (x > x1 || y > y1) continue;
-            int pxlo, pxhi, pylo, pyhi;
-            bool pxext, pyext;
-            cover(x, D.w, P, S, D.kxreg, D.npx, pxlo, pxhi, pxext);
-            cover(y, D.h, P, S, D.kyreg, D.npy, pylo, pyhi, pyext);
-            const int nxx = pxhi - pxlo + 1 + (pxext ? 1 : 0);
-            const int nyy = pyhi - pylo + 1 + (pyext ? 1 : 0);
-            float sw = 0.f, swd = 0.f, swr = 0.f, sw2 = 0.f;
-            int n = 0;
-            for (int iy = 0; iy < nyy; ++iy) {
-                const bool ex = pylo + iy > pyhi;
-                const int ky = ex ? D.npy - 1 : pylo + iy;
-                const int ly = ex ? nky - 1 : ky - kylo;
-                const int oy = origin(ky, D.h, P, S, D.kyreg);
-                const float my = a.use_sgmm ? a.m[y - oy] : 1.f;
-                for (int ix = 0; ix < nxx; ++ix) {
-                    const bool exx = pxlo + ix > pxhi;
-                    const int kx = exx ? D.npx - 1 : pxlo + ix;
-                    const int lx = exx ? nkx - 1 : kx - kxlo;
-                    const int ox = origin(kx, D.w, P, S, D.kxreg);
-                    const float4 f = fz[ly * nkx + lx];
-                    if (f.w == 0.f) continue;
-                    const float mx = a.use_sgmm ? a.m[x - ox] : 1.f;
-                    const float om = f.y * (my * mx);
-                    sw += om;
-                    swd = fmaf(om, f.x, swd);
-                    swr = fmaf(om, f.y, swr);
-                    sw2 = fmaf(om * om, f.z, sw2);
-                    ++n;
-                }
+            const int cnt = cyn[r], lo = cylo[r], nreg = cyr[r];
+            float swd = 0.f, sw = 0.f, swr = 0.f, sw2 = 0.f;
+            for (int q = 0; q < cnt; ++q) {
+                const int ly = q < nreg ? lo + q : nky - 1;
+                const float4 cs = csum[ly * TW + c];
+                const float my = cym[r][q];
+                swd = fmaf(my, cs.x, swd);
+                sw = fmaf(my, cs.y, sw);
+                swr = fmaf(my, cs.z, swr);
+                sw2 = fmaf(my * my, cs.w, sw2);
             }
             const size_t idx = (size_t)y * D.w + x;
+            const bool any = sw > 0.f;
             float Dv, Qv, Vv;
-            if (n > 0 && sw > 0.f) {
+            if (any) {
                 Dv = swd / sw;
                 Qv = swr / sw;
                 Vv = sw2 / (sw * sw);
@@ -648,10 +679,9 @@ __global__ void __launch_bounds__(256) k_fuse(LaunchArgs a) {
                 Dv = D.Dc != nullptr ? 2.f * coarse_bilin(D.Dc, D.wc, D.hc, (float)x, (float)y) : 0.f;
                 Qv = 0.f;
                 Vv = 0.f;
-                n = 0;
             }
             if (a.level == 0) {
-                const bool ok = n > 0 && Qv >= a.pix_thresh;
+                const bool ok = any && Qv >= a.pix_thresh;
                 D.valid[idx] = ok ? 1 : 0;
                 D.disp[idx] = ok ? Dv : __int_as_float(0x7fc00000);
                 if (D.var != nullptr && a.variance) D.var[idx] = ok ? Vv : __int_as_float(0x7fc00000);
@@ -720,9 +750,9 @@ cudaError_t raise_smem_limit(const void *f, size_t bytes);
 
 bool search_supported(int P) { return P >= kMinPatch && P <= kMaxPatch; }
 
-void search_layout(int P, int S, float tau, float window_step, int &band_pitch, int &band_cap,
-                   int &chunk_pitch, size_t &bytes) {
-    const int chunk = search_chunk(P);
+void search_layout(int P, int S, float tau, float window_step, int passes, int &band_pitch,
+                   int &band_cap, int &chunk_pitch, size_t &bytes) {
+    const int chunk = search_chunk(P, passes);
     const int cw = (chunk - 1) * S + P;
     const int margin = (int)ceilf(tau) + (int)ceilf(2.f * window_step) + 3;
     band_cap = cw + 2 * margin + kBandSpread;
@@ -731,14 +761,14 @@ void search_layout(int P, int S, float tau, float window_step, int &band_pitch, 
     bytes = sizeof(float) * ((size_t)P * band_pitch + 2 * (size_t)P * chunk_pitch + 4 * (size_t)chunk + 16);
 }
 
-size_t fuse_smem(int P, int S) {
-    const int nkx = (kFuseTileW + P - 2) / S + 2, nky = (kFuseTileH + P - 2) / S + 2;
-    return sizeof(float4) * (size_t)nkx * nky;
+size_t fuse_smem(int P, int S, int tile_w, int tile_h) {
+    const int nkx = (tile_w + P - 2) / S + 2, nky = (tile_h + P - 2) / S + 2;
+    return sizeof(float4) * ((size_t)nkx * nky + (size_t)nky * tile_w);
 }
 
 cudaError_t prepare_fuse(size_t smem_bytes) { return raise_smem_limit((const void *)k_fuse, smem_bytes); }
 int search_group(int P) { return P <= 8 ? 8 : 16; }
-int search_chunk(int P) { return 2 * (256 / search_group(P)); }
+int search_chunk(int P, int passes) { return passes * (256 / search_group(P)); }
 
 // Raises (never lowers) a kernel's dynamic shared-memory limit to `bytes`.
 cudaError_t raise_smem_limit(const void *f, size_t bytes) {

@@ -19,8 +19,8 @@
 // passed to the kernels.  The first call on each device does this set-up.
 //
 // Every call shares the one array and it keeps the previous call's contents.
-// Nothing in it needs to start at zero: each stage writes every element it
-// later reads.  Calls that overlap on the GPU (different streams, or
+// Only the sigma_r accumulators must start at zero; each call's first kernel
+// clears them.  Every other element is written before it is read.  Calls that overlap on the GPU (different streams, or
 // different host threads) race on the array and must be serialised by the
 // caller.
 #include <cmath>
@@ -119,10 +119,13 @@ extern "C" bdis_status bdis_match_noalloc(const bdis_params *pp, const uint8_t *
     std::memset(&tab, 0, sizeof(tab));
     tab.n = NL;
     const size_t esz = p.storage == BDIS_STORE_F16 ? 2 : 4;
-    const int chunk = search_chunk(P);
+    const LevelCfg cfg{2, 32, 16};  // default launch configuration (no tuning here)
+    const int chunk = search_chunk(P, cfg.passes);
     size_t off = na_align(sizeof(LevelDesc) * kMaxLevels, 256);
+    const size_t off_acc = off;  // sigma_r accumulators: 3 per level, cleared by the pyramid
+    off += sizeof(unsigned long long) * 3 * kMaxLevels;
     size_t oG[kMaxLevels], oL[kMaxLevels], oR[kMaxLevels], oD[kMaxLevels], oQ[kMaxLevels];
-    size_t oRec[kMaxLevels], oFuse[kMaxLevels], oSr[kMaxLevels], oSp[kMaxLevels];
+    size_t oRec[kMaxLevels], oFuse[kMaxLevels], oSr[kMaxLevels];
     int units[kMaxLevels][W_COUNT];
     auto take = [&](size_t n) {
         off = na_align(off, 256);
@@ -139,10 +142,10 @@ extern "C" bdis_status bdis_match_noalloc(const bdis_params *pp, const uint8_t *
         d.npx = d.kxreg + ((d.w - P) % S != 0 ? 1 : 0);
         d.npy = d.kyreg + ((d.h - P) % S != 0 ? 1 : 0);
         d.nchunks = (d.npx + chunk - 1) / chunk;
-        d.tiles_x = (d.w + kFuseTileW - 1) / kFuseTileW;
-        units[l][W_PYR] = (((d.w + 1) / 2) * ((d.h + 1) / 2) + 255) / 256;
+        d.tiles_x = (d.w + cfg.tile_w - 1) / cfg.tile_w;
+        units[l][W_PYR] = ((d.w + 63) / 64) * ((d.h + 31) / 32);
         units[l][W_SEARCH] = d.npy * d.nchunks;
-        units[l][W_FUSE] = d.tiles_x * ((d.h + kFuseTileH - 1) / kFuseTileH);
+        units[l][W_FUSE] = d.tiles_x * ((d.h + cfg.tile_h - 1) / cfg.tile_h);
         const size_t gp = na_align((size_t)d.w * esz, 128) / esz;
         d.gpitch = (int)gp;
         d.pitch = l == 0 ? pitch : (int)gp;
@@ -157,7 +160,6 @@ extern "C" bdis_status bdis_match_noalloc(const bdis_params *pp, const uint8_t *
         oRec[l] = take(sizeof(bdis_patch_record) * np);
         oFuse[l] = take(sizeof(float4) * np);
         oSr[l] = take(sizeof(float));
-        oSp[l] = take(sizeof(float4) * (size_t)d.npy * d.nchunks);
     }
     if (off > kNoAllocScratchBytes) return BDIS_EUNSUPPORTED;  // needs more than the static maximum
 
@@ -165,8 +167,8 @@ extern "C" bdis_status bdis_match_noalloc(const bdis_params *pp, const uint8_t *
     const float tau = p.search_radius > 0.f ? p.search_radius : (float)P;
     int band_pitch, band_cap, chunk_pitch;
     size_t smem;
-    search_layout(P, S, tau, p.window_step, band_pitch, band_cap, chunk_pitch, smem);
-    const size_t fsmem = fuse_smem(P, S);
+    search_layout(P, S, tau, p.window_step, cfg.passes, band_pitch, band_cap, chunk_pitch, smem);
+    const size_t fsmem = fuse_smem(P, S, cfg.tile_w, cfg.tile_h);
     if (smem > 227 * 1024 || fsmem > 227 * 1024) return BDIS_EUNSUPPORTED;
 
     void *scratch = nullptr;
@@ -193,7 +195,7 @@ extern "C" bdis_status bdis_match_noalloc(const bdis_params *pp, const uint8_t *
         d.rec = (bdis_patch_record *)(base + oRec[l]);
         d.fuse = (float4 *)(base + oFuse[l]);
         d.sigma_r = (float *)(base + oSr[l]);
-        d.spart = (float4 *)(base + oSp[l]);
+        d.acc = (unsigned long long *)(base + off_acc) + 3 * l;
     }
     for (int l = 0; l + 1 < NL; ++l) {
         LevelDesc &d = tab.d[l];
@@ -243,6 +245,8 @@ extern "C" bdis_status bdis_match_noalloc(const bdis_params *pp, const uint8_t *
     a.use_c2f = p.use_c2f;
     a.use_sgmm = p.use_sgmm;
     a.chunk = chunk;
+    a.tile_w = cfg.tile_w;
+    a.tile_h = cfg.tile_h;
     for (int i = 0; i < kMaxPatch; ++i) {  // 1D sGMM factor of Eq. 8
         double s = 0.0;
         if (i < P)
@@ -257,6 +261,8 @@ extern "C" bdis_status bdis_match_noalloc(const bdis_params *pp, const uint8_t *
         a.descs = d_descs + l;
         a.level = l;
         a.total = units[l][W_PYR];
+        a.acc_zero = l == 0 ? (unsigned long long *)(base + off_acc) : nullptr;
+        a.acc_count = l == 0 ? 3 * kMaxLevels : 0;
         if (launch_pyramid(a, l == 0 ? E_U8 : st_type, st_type, st) != cudaSuccess) return BDIS_ECUDA;
     }
     for (int l = NL - 1; l >= 0; --l) {
