@@ -153,6 +153,12 @@ def level_geometry(w, h, P, S, L):
 
 
 def algorithmic_bytes(kernel, w, h, prm):
+    if kernel == "persistent":   # every stage in one launch
+        return sum(algorithmic_bytes(k, w, h, prm) for k in ("pyramid", "search", "fuse"))
+    return _stage_bytes(kernel, w, h, prm)
+
+
+def _stage_bytes(kernel, w, h, prm):
     """Bytes one pass of `kernel` over all levels must move (per pair).
     Image element sizes: level 0 u8, levels >= 1 and gradients the storage
     type; patch record 64 B; fusion record 16 B; fused maps 8 B/px."""
@@ -357,7 +363,7 @@ def main():
     B.check(B.lib().bdis_get_profile(m._h, prof, 1), m._h)
     B.lib().bdis_set_option(m._h, B.OPT_PROFILE, 0)
     kernels = {}
-    for i, name in enumerate(B.KERNEL_NAMES):
+    for i, name in enumerate(B.KERNEL_NAMES[:len(prof.launches)]):
         if prof.launches[i]:
             kernels[name] = {"launches_per_step": prof.launches[i] // n_prof,
                              "ms_per_step": prof.ms[i] / n_prof,

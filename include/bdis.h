@@ -100,6 +100,8 @@ typedef struct {
     int valid_patches[8];    /* patches kept per level (all pairs)           */
     float sigma_r[8];        /* sigma_r per level of the first pair           */
     long long valid_pixels;  /* valid output pixels (all pairs)              */
+    int persistent;          /* 1 if the call ran in the persistent form      */
+    int barrier_timeouts;    /* persistent form: a grid-barrier wait ran out  */
 } bdis_stats;
 
 /* Fills `p` with the defaults (8x8 patches, stride 4, 3 levels, 8 iterations,
@@ -237,13 +239,19 @@ typedef enum {
      * for the timing runs.  All configurations compute identical results.
      * 0: the default configuration.  Never tunes while the stream is being
      * captured. */
-    BDIS_OPT_AUTOTUNE = 3
+    BDIS_OPT_AUTOTUNE = 3,
+    /* Execution form: 0 (default) as chosen by the autotuner, 1 one launch per
+     * stage, 2 persistent (every stage in one cooperative launch with grid
+     * barriers; 8-bit inputs, patch sizes 6, 8, 10, 12, 16).  Same results. */
+    BDIS_OPT_FORM = 4
 } bdis_option;
 
 bdis_status bdis_set_option(bdis_handle *h, int option, int value);
 
-/* kernels: pyramid + gradient; patch search; fused sigma_r + posterior + densify */
-enum { BDIS_K_PYRAMID = 0, BDIS_K_SEARCH = 1, BDIS_K_FUSE = 2, BDIS_K_COUNT = 3 };
+/* kernels: pyramid + gradient; patch search; fused sigma_r + posterior + densify;
+ * the persistent form (all stages in one launch) */
+enum { BDIS_K_PYRAMID = 0, BDIS_K_SEARCH = 1, BDIS_K_FUSE = 2, BDIS_K_PERSISTENT = 3,
+       BDIS_K_COUNT = 4 };
 
 typedef struct {
     int launches[BDIS_K_COUNT];   /* launches per kernel since the last reset */

@@ -57,6 +57,9 @@ class BDIS:
         B.check(B.lib().bdis_create(C.byref(self.params), C.byref(h)))
         self._h = h
 
+    def set_option(self, option: int, value: int):
+        B.check(B.lib().bdis_set_option(self._h, option, value), self._h)
+
     def close(self):
         if getattr(self, "_h", None):
             B.lib().bdis_destroy(self._h)
@@ -143,7 +146,8 @@ class BDIS:
         B.check(B.lib().bdis_get_stats(self._h, C.byref(s), _stream_handle(stream)), self._h)
         return dict(levels=s.levels, pairs=s.pairs, patches=list(s.patches)[:s.levels],
                     valid_patches=list(s.valid_patches)[:s.levels],
-                    sigma_r=list(s.sigma_r)[:s.levels], valid_pixels=s.valid_pixels)
+                    sigma_r=list(s.sigma_r)[:s.levels], valid_pixels=s.valid_pixels,
+                    persistent=s.persistent, barrier_timeouts=s.barrier_timeouts)
 
     def level_view(self, pair: int, level: int) -> dict:
         """Copies of the last call's intermediate buffers of (pair, level)."""

@@ -44,7 +44,7 @@ class bdis_stats(C.Structure):
     _fields_ = [
         ("levels", C.c_int), ("pairs", C.c_int), ("patches", C.c_int * 8),
         ("valid_patches", C.c_int * 8), ("sigma_r", C.c_float * 8),
-        ("valid_pixels", C.c_longlong),
+        ("valid_pixels", C.c_longlong), ("persistent", C.c_int), ("barrier_timeouts", C.c_int),
     ]
 
 
@@ -78,11 +78,11 @@ class bdis_grad(C.Structure):
 
 
 class bdis_profile(C.Structure):
-    _fields_ = [("launches", C.c_int * 3), ("ms", C.c_double * 3)]
+    _fields_ = [("launches", C.c_int * 4), ("ms", C.c_double * 4)]
 
 
-OPT_GRAPH, OPT_PROFILE, OPT_AUTOTUNE = 1, 2, 3
-KERNEL_NAMES = ["pyramid", "search", "fuse"]
+OPT_GRAPH, OPT_PROFILE, OPT_AUTOTUNE, OPT_FORM = 1, 2, 3, 4
+KERNEL_NAMES = ["pyramid", "search", "fuse", "persistent"]
 
 
 # (name, restype, argtypes) of every exported function of include/bdis.h

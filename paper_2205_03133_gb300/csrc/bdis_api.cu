@@ -44,7 +44,14 @@ struct bdis_handle {
     size_t garena_cap = 0;
     // autotuner: per-level launch configuration cached per geometry key
     bool autotune = true;
-    std::map<std::string, std::vector<LevelCfg>> tuned;
+    struct Tuned {
+        std::vector<LevelCfg> cfg;
+        bool mega;
+    };
+    std::map<std::string, Tuned> tuned;
+    int *err_flag = nullptr;  // timeout flag of the persistent form
+    bool last_persistent = false;
+    int form = 0;             // BDIS_OPT_FORM
     // per-kernel event timing
     bool profile = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -170,6 +177,8 @@ struct Plan {
     size_t bytes = 0;
     size_t off_desc = 0;
     size_t off_acc = 0, acc_count = 0;  // sigma_r accumulators, contiguous
+    size_t off_stages = 0;              // stage arguments of the persistent form (3 per level)
+    size_t off_bar = 0;                 // barrier arrivals, generation, timeout flag
     std::vector<LevelDesc> descs;  // [level][pair]
     int wmax[kMaxLevels] = {0};
     int units[kMaxLevels][W_COUNT] = {{0}};
@@ -198,8 +207,10 @@ void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, const Leve
         v->assign(cnt, 0);
     Bump b;
     pl.off_desc = b.take(sizeof(LevelDesc) * cnt);
+    pl.off_stages = b.take(sizeof(LaunchArgs) * 3 * NL);
     pl.acc_count = 3 * cnt;
     pl.off_acc = b.take(sizeof(unsigned long long) * pl.acc_count);
+    pl.off_bar = b.take(4 * sizeof(unsigned));
     for (int l = 0; l < NL; ++l) {
         const int chunk = search_chunk(P, cfg[l].passes);
         int begin[W_COUNT] = {0, 0, 0};
@@ -310,6 +321,10 @@ bdis_status ensure_arena(bdis_handle *h, size_t bytes) {
         cudaGetLastError();
         return fail(h, BDIS_ENOMEM, "cudaMalloc of the scratch arena failed");
     }
+    // zero once: the barrier state of the persistent form starts at zero and
+    // every call leaves its arrival counter at zero
+    e = cudaMemset(h->arena, 0, cap);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemset");
     h->arena_cap = cap;
     h->last_upload.clear();
     return BDIS_OK;
@@ -354,7 +369,7 @@ const LevelCfg kSearchCands[3] = {{1, 32, 16}, {2, 64, 32}, {4, 32, 16}};
 // configuration cfg.  graph: replay / capture allowed; prof: bracket each
 // launch with events (kernel id and level recorded in h->ev_marks).
 bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, cudaStream_t st,
-                    const LevelCfg *cfg, bool graph, bool prof) {
+                    const LevelCfg *cfg, bool graph, bool prof, bool mega = false) {
     const bdis_params &p = h->p;
     const int NL = p.levels;
     Plan pl;
@@ -379,26 +394,62 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
         if (e == cudaSuccess) e = prepare_fuse(fmax);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute");
     }
-    // upload the descriptor table unless identical to the last upload
-    const size_t tbytes = sizeof(LevelDesc) * pl.descs.size();
+    const int st_type = p.storage == BDIS_STORE_F16 ? E_F16 : E_F32;
     LevelDesc *d_descs = (LevelDesc *)(h->arena + pl.off_desc);
-    const bool same = h->last_upload.size() == tbytes &&
-                      std::memcmp(h->last_upload.data(), pl.descs.data(), tbytes) == 0;
+    // stage list: the pyramid levels, then (search, fuse) per level coarse to fine
+    std::vector<LaunchArgs> stages;
+    std::vector<int> stage_itype;
+    for (int l = 0; l < NL; ++l) {
+        LaunchArgs a = base_args(p, l, d_descs + (size_t)l * n, n);
+        a.kind = 0;
+        a.total = pl.units[l][W_PYR];
+        if (l == 0) {
+            a.acc_zero = (unsigned long long *)(h->arena + pl.off_acc);
+            a.acc_count = (int)pl.acc_count;
+        }
+        stages.push_back(a);
+        stage_itype.push_back(l == 0 ? in_type : st_type);
+    }
+    for (int l = NL - 1; l >= 0; --l) {
+        LaunchArgs a = base_args(p, l, d_descs + (size_t)l * n, n);
+        a.chunk = search_chunk(p.patch, cfg[l].passes);
+        a.tile_w = cfg[l].tile_w;
+        a.tile_h = cfg[l].tile_h;
+        a.band_pitch = bpitch[l];
+        a.band_cap = bcap[l];
+        a.chunk_pitch = cpitch[l];
+        a.kind = 1;
+        a.total = pl.units[l][W_SEARCH];
+        stages.push_back(a);
+        stage_itype.push_back(l == 0 ? in_type : st_type);
+        a.kind = 2;
+        a.total = pl.units[l][W_FUSE];
+        stages.push_back(a);
+        stage_itype.push_back(l == 0 ? in_type : st_type);
+    }
+    // upload descriptors (and the stage list) unless identical to the last upload
+    const size_t dbytes = sizeof(LevelDesc) * pl.descs.size();
+    const size_t sbytes = sizeof(LaunchArgs) * stages.size();
+    const size_t blob = pl.off_stages - pl.off_desc + sbytes;
+    std::vector<char> host((size_t)blob, 0);
+    std::memcpy(host.data(), pl.descs.data(), dbytes);
+    std::memcpy(host.data() + (pl.off_stages - pl.off_desc), stages.data(), sbytes);
+    const size_t tbytes = dbytes;
+    const bool same = h->last_upload.size() == host.size() &&
+                      std::memcmp(h->last_upload.data(), host.data(), host.size()) == 0;
     if (!same) {
-        s = ensure_pinned(h, tbytes);
+        s = ensure_pinned(h, host.size());
         if (s != BDIS_OK) return s;
         cudaError_t e = cudaEventSynchronize(h->upload_done);  // staging free again
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
-        std::memcpy(h->pinned, pl.descs.data(), tbytes);
-        e = cudaMemcpyAsync(d_descs, h->pinned, tbytes, cudaMemcpyHostToDevice, st);
+        std::memcpy(h->pinned, host.data(), host.size());
+        e = cudaMemcpyAsync(d_descs, h->pinned, host.size(), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "descriptor upload");
         e = cudaEventRecord(h->upload_done, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
-        h->last_upload.assign((const char *)pl.descs.data(),
-                              (const char *)pl.descs.data() + tbytes);
+        h->last_upload.swap(host);
     }
 
-    const int st_type = p.storage == BDIS_STORE_F16 ? E_F16 : E_F32;
     // one kernel launch, optionally bracketed by profiling events
     auto timed = [&](int kid, auto &&fn) -> cudaError_t {
         size_t i0 = 0;
@@ -422,37 +473,47 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
         }
         return cudaSuccess;
     };
+
+    if (mega) {
+        // persistent form: one cooperative launch runs every stage
+        const size_t msm = std::max(kPyrSmemBytes, std::max(smax, fmax));
+        const int grid = mega_grid(p.patch, st_type, msm);
+        if (grid < 1) return fail(h, BDIS_EUNSUPPORTED, "persistent form unavailable");
+        MegaArgs m;
+        m.stages = (const LaunchArgs *)(h->arena + pl.off_stages);
+        m.nstages = (int)stages.size();
+        m.bar = (unsigned *)(h->arena + pl.off_bar);
+        m.err = (int *)(m.bar + 2);
+        cudaError_t e = timed(BDIS_K_PERSISTENT, [&] { return launch_mega(m, p.patch, st_type, grid, msm, st); });
+        if (e != cudaSuccess) return cuda_fail(h, e, "persistent launch");
+        h->descs = pl.descs;
+        h->npairs = n;
+        h->levels = NL;
+        h->in_type = in_type;
+        h->d_descs = d_descs;
+        h->err_flag = m.err;
+        h->last_persistent = true;
+        return BDIS_OK;
+    }
+
     auto launch_all = [&]() -> bdis_status {
         cudaError_t e;
-        // gradients of every level and the pyramid, finest to coarsest
-        for (int l = 0; l < NL; ++l) {
-            LaunchArgs a = base_args(p, l, d_descs + (size_t)l * n, n);
-            a.total = pl.units[l][W_PYR];
-            if (l == 0) {
-                a.acc_zero = (unsigned long long *)(h->arena + pl.off_acc);
-                a.acc_count = (int)pl.acc_count;
+        for (size_t k = 0; k < stages.size(); ++k) {
+            const LaunchArgs &a = stages[k];
+            const int itype = stage_itype[k];
+            if (a.kind == 0) {
+                e = timed(BDIS_K_PYRAMID, [&] { return launch_pyramid(a, itype, st_type, st); });
+                if (e != cudaSuccess) return cuda_fail(h, e, "pyramid launch");
+            } else if (a.kind == 1) {
+                const size_t sm = ssm[a.level];
+                const int occ = search_occupancy(p.patch, itype, st_type, sm);
+                const int grid = std::max(1, std::min(a.total, sm_count() * occ));
+                e = timed(BDIS_K_SEARCH, [&] { return launch_search(a, itype, st_type, sm, grid, st); });
+                if (e != cudaSuccess) return cuda_fail(h, e, "search launch");
+            } else {
+                e = timed(BDIS_K_FUSE, [&] { return launch_fuse(a, fsm[a.level], st); });
+                if (e != cudaSuccess) return cuda_fail(h, e, "fuse launch");
             }
-            e = timed(BDIS_K_PYRAMID, [&] { return launch_pyramid(a, l == 0 ? in_type : st_type, st_type, st); });
-            if (e != cudaSuccess) return cuda_fail(h, e, "pyramid launch");
-        }
-        // coarse-to-fine levels: search, then sigma_r + posterior + fusion
-        for (int l = NL - 1; l >= 0; --l) {
-            LaunchArgs a = base_args(p, l, d_descs + (size_t)l * n, n);
-            a.chunk = search_chunk(p.patch, cfg[l].passes);
-            a.tile_w = cfg[l].tile_w;
-            a.tile_h = cfg[l].tile_h;
-            a.band_pitch = bpitch[l];
-            a.band_cap = bcap[l];
-            a.chunk_pitch = cpitch[l];
-            a.total = pl.units[l][W_SEARCH];
-            const int itype = l == 0 ? in_type : st_type;
-            const int occ = search_occupancy(p.patch, itype, st_type, ssm[l]);
-            const int grid = std::max(1, std::min(a.total, sm_count() * occ));
-            e = timed(BDIS_K_SEARCH, [&] { return launch_search(a, itype, st_type, ssm[l], grid, st); });
-            if (e != cudaSuccess) return cuda_fail(h, e, "search launch");
-            a.total = pl.units[l][W_FUSE];
-            e = timed(BDIS_K_FUSE, [&] { return launch_fuse(a, fsm[l], st); });
-            if (e != cudaSuccess) return cuda_fail(h, e, "fuse launch");
         }
         return BDIS_OK;
     };
@@ -512,6 +573,7 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
     h->levels = NL;
     h->in_type = in_type;
     h->d_descs = d_descs;
+    h->last_persistent = false;
     return BDIS_OK;
 }
 
@@ -565,14 +627,39 @@ bdis_status autotune(bdis_handle *h, int n, const bdis_pair *pairs, int in_type,
     return BDIS_OK;
 }
 
+// Mean device time of `reps` back-to-back calls of one form (events).
+bdis_status time_form(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, cudaStream_t st,
+                      const LevelCfg *cfg, bool mega, int reps, float &ms) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(h, cudaGetLastError(), "cudaEventCreate");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(h, cudaGetLastError(), "cudaEventCreate");
+    }
+    bdis_status s = run_cfg(h, n, pairs, in_type, st, cfg, true, false, mega);  // warm / capture
+    if (s == BDIS_OK) {
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && s == BDIS_OK; ++r)
+            s = run_cfg(h, n, pairs, in_type, st, cfg, true, false, mega);
+        cudaEventRecord(e1, st);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (s == BDIS_OK && e != cudaSuccess) s = cuda_fail(h, e, "autotune events");
+        ms /= (float)reps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return s;
+}
+
 // Runs the whole pipeline for n pairs with the tuned configuration of this
 // geometry (tuned on first use unless the stream is being captured).
 bdis_status run(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, cudaStream_t st) {
     const std::string key = geometry_key(h, n, pairs, in_type);
     auto it = h->tuned.find(key);
-    std::vector<LevelCfg> cfg;
+    bdis_handle::Tuned t;
     if (it != h->tuned.end()) {
-        cfg = it->second;
+        t = it->second;
     } else {
         bool capturing = false;
         if (st != nullptr) {
@@ -582,14 +669,28 @@ bdis_status run(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, cuda
             cudaGetLastError();
         }
         if (h->autotune && !capturing) {
-            bdis_status s = autotune(h, n, pairs, in_type, st, cfg);
+            bdis_status s = autotune(h, n, pairs, in_type, st, t.cfg);
             if (s != BDIS_OK) return s;
-            h->tuned[key] = cfg;
+            // one persistent launch against the launch sequence, for 8-bit inputs
+            t.mega = false;
+            if (in_type == E_U8 && mega_supported(h->p.patch) && st != nullptr) {
+                float tm = 0.f, tp = 0.f;
+                s = time_form(h, n, pairs, in_type, st, t.cfg.data(), false, 5, tm);
+                if (s != BDIS_OK) return s;
+                s = time_form(h, n, pairs, in_type, st, t.cfg.data(), true, 5, tp);
+                if (s == BDIS_OK) t.mega = tp < tm;
+                else h->err = "no persistent form";
+            }
+            h->tuned[key] = t;
         } else {
-            cfg.assign((size_t)h->p.levels, kDefaultCfg);
+            t.cfg.assign((size_t)h->p.levels, kDefaultCfg);
+            t.mega = false;
         }
     }
-    return run_cfg(h, n, pairs, in_type, st, cfg.data(), true, h->profile);
+    bool mega = t.mega;
+    if (h->form == 1) mega = false;
+    if (h->form == 2) mega = in_type == E_U8 && mega_supported(h->p.patch);
+    return run_cfg(h, n, pairs, in_type, st, t.cfg.data(), true, h->profile, mega);
 }
 
 }  // namespace
@@ -663,6 +764,11 @@ bdis_status bdis_set_option(bdis_handle *h, int option, int value) {
     }
     if (option == BDIS_OPT_AUTOTUNE) {
         h->autotune = value != 0;
+        return BDIS_OK;
+    }
+    if (option == BDIS_OPT_FORM) {
+        if (value < 0 || value > 2) return fail(h, BDIS_EINVAL, "form must be 0, 1 or 2");
+        h->form = value;
         return BDIS_OK;
     }
     return fail(h, BDIS_EINVAL, "unknown option");
@@ -808,6 +914,11 @@ bdis_status bdis_get_stats(bdis_handle *h, bdis_stats *out, void *stream) {
                 if (e != cudaSuccess) return cuda_fail(h, e, "stats copy");
             }
         }
+    }
+    out->persistent = h->last_persistent ? 1 : 0;
+    if (h->err_flag) {
+        e = cudaMemcpy(&out->barrier_timeouts, h->err_flag, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(h, e, "stats copy");
     }
     std::vector<uint8_t> v;
     for (int i = 0; i < h->npairs; ++i) {

@@ -49,8 +49,9 @@ __device__ __forceinline__ float coarse_bilin(const float *__restrict__ m, int w
     int x0 = (int)floorf(X), y0 = (int)floorf(Y);
     int x1 = min(x0 + 1, wc - 1), y1 = min(y0 + 1, hc - 1);
     float fx = X - (float)x0, fy = Y - (float)y0;
-    float a = (1.f - fx) * __ldg(m + (size_t)y0 * wc + x0) + fx * __ldg(m + (size_t)y0 * wc + x1);
-    float b = (1.f - fx) * __ldg(m + (size_t)y1 * wc + x0) + fx * __ldg(m + (size_t)y1 * wc + x1);
+    // L2 loads: the map may have been written earlier in the same (persistent) launch
+    float a = (1.f - fx) * __ldcg(m + (size_t)y0 * wc + x0) + fx * __ldcg(m + (size_t)y0 * wc + x1);
+    float b = (1.f - fx) * __ldcg(m + (size_t)y1 * wc + x0) + fx * __ldcg(m + (size_t)y1 * wc + x1);
     return (1.f - fy) * a + fy * b;
 }
 

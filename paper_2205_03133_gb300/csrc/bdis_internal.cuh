@@ -88,7 +88,21 @@ struct LaunchArgs {
     float m[kMaxPatch];       // 1D sGMM factors m[a] (Eq. 8 is separable)
     unsigned long long *acc_zero;  // finest pyramid launch: accumulators to clear
     int acc_count;
+    int kind;                 // stage of the persistent form: 0 pyramid, 1 search, 2 fuse
 };
+
+// Persistent form: every stage of a call in one cooperative launch, with a
+// grid barrier between dependent stages.
+struct MegaArgs {
+    const LaunchArgs *stages;  // device array of nstages stage arguments
+    int nstages;
+    unsigned *bar;             // [0] arrivals, [1] generation (both 0 initially)
+    int *err;                  // set to 1 when a barrier wait runs out
+};
+
+// Spin limit of one grid-barrier wait (well under a second); a wait that runs out
+// sets MegaArgs::err and lets the block continue, so the kernel always ends.
+constexpr unsigned kBarrierSpinLimit = 1u << 22;
 
 // ---- differentiable finest level (bdis_grad.cu)
 
@@ -138,6 +152,12 @@ void search_layout(int P, int S, float tau, float window_step, int passes, int &
                    int &band_cap, int &chunk_pitch, size_t &bytes);
 size_t fuse_smem(int P, int S, int tile_w, int tile_h);
 cudaError_t prepare_fuse(size_t smem_bytes);
+// Persistent form: available for the patch sizes with an instance; grid =
+// co-resident blocks (0 if unavailable).
+bool mega_supported(int P);
+int mega_grid(int P, int st_type, size_t smem);
+cudaError_t launch_mega(const MegaArgs &m, int P, int st_type, int grid, size_t smem, cudaStream_t s);
+constexpr size_t kPyrSmemBytes = sizeof(float) * 2 * 36 * 68;
 // Raise (never lower) the dynamic shared-memory limit of every search instance.
 cudaError_t prepare_search(int P, size_t smem_bytes);
 // Number of resident search blocks per SM for (P, image type, gradient type, smem).

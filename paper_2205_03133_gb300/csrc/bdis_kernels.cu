@@ -34,6 +34,65 @@ constexpr int kPyrTW = 64, kPyrTH = 32;
 constexpr int kPyrSW = kPyrTW + 4, kPyrSH = kPyrTH + 4;
 
 template <typename TI, typename TO>
+__device__ __forceinline__ void pyramid_unit(const LaunchArgs &a, int unit, float (*Ls)[kPyrSW],
+                                             float (*Rs)[kPyrSW]) {
+
+    const LevelDesc &D = a.descs[find_pair(a.descs, a.npairs, unit, W_PYR)];
+    const int tile = unit - D.work_begin[W_PYR];
+    const int ntx = (D.w + kPyrTW - 1) / kPyrTW;
+    const int tx = tile % ntx, ty = tile / ntx;
+    const int x0 = tx * kPyrTW - 2, y0 = ty * kPyrTH - 2;  // region origin
+    const int w = D.w, h = D.h, pitch = D.pitch;
+    const TI *L = (const TI *)D.L;
+    const TI *R = (const TI *)D.R;
+    const bool next = D.Ln != nullptr;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kPyrSH * kPyrSW; i += blockDim.x) {
+        const int r = i / kPyrSW, c = i - r * kPyrSW;
+        // only indices within 2 of the image are ever used by a stencil
+        const int gy = refl(min(max(y0 + r, -2), h + 1), h);
+        const int gx = refl(min(max(x0 + c, -2), w + 1), w);
+        Ls[r][c] = ldf(L + (size_t)gy * pitch + gx);
+        if (next) Rs[r][c] = ldf(R + (size_t)gy * pitch + gx);
+    }
+    __syncthreads();
+    TO *G = (TO *)D.G;
+    for (int i = threadIdx.x; i < kPyrTW * kPyrTH; i += blockDim.x) {
+        const int ly = i / kPyrTW, lx = i - ly * kPyrTW;
+        const int x = x0 + 2 + lx, y = y0 + 2 + ly;
+        if (x >= w || y >= h) continue;
+        const int cx = lx + 2, cy = ly + 2;
+        const float acc = (Ls[cy - 1][cx + 1] - Ls[cy - 1][cx - 1]) +
+                          2.f * (Ls[cy][cx + 1] - Ls[cy][cx - 1]) +
+                          (Ls[cy + 1][cx + 1] - Ls[cy + 1][cx - 1]);
+        stf(G + (size_t)y * D.gpitch + x, acc * 0.125f);
+    }
+    if (next) {
+        const float k[5] = {1.f, 4.f, 6.f, 4.f, 1.f};
+        for (int i = threadIdx.x; i < (kPyrTW / 2) * (kPyrTH / 2); i += blockDim.x) {
+            const int oy = i / (kPyrTW / 2), ox = i - oy * (kPyrTW / 2);
+            const int X = tx * (kPyrTW / 2) + ox, Y = ty * (kPyrTH / 2) + oy;
+            if (X >= D.wn || Y >= D.hn) continue;
+            const int cx = 2 * ox + 2, cy = 2 * oy + 2;
+            float accL = 0.f, accR = 0.f;
+#pragma unroll
+            for (int j = 0; j < 5; ++j) {
+                float sl = 0.f, sr = 0.f;
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    sl += k[q] * Ls[cy + j - 2][cx + q - 2];
+                    sr += k[q] * Rs[cy + j - 2][cx + q - 2];
+                }
+                accL += k[j] * sl;
+                accR += k[j] * sr;
+            }
+            stf((TO *)D.Ln + (size_t)Y * D.pitchn + X, accL * (1.f / 256.f));
+            stf((TO *)D.Rn + (size_t)Y * D.pitchn + X, accR * (1.f / 256.f));
+        }
+    }
+    }
+
+template <typename TI, typename TO>
 __global__ void __launch_bounds__(256) k_pyramid(LaunchArgs a) {
     __shared__ float Ls[kPyrSH][kPyrSW];
     __shared__ float Rs[kPyrSH][kPyrSW];
@@ -41,61 +100,7 @@ __global__ void __launch_bounds__(256) k_pyramid(LaunchArgs a) {
     // sigma_r accumulators of all levels and pairs
     if (blockIdx.x == 0 && a.acc_zero != nullptr)
         for (int i = threadIdx.x; i < a.acc_count; i += blockDim.x) a.acc_zero[i] = 0ull;
-    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) {
-        const LevelDesc &D = a.descs[find_pair(a.descs, a.npairs, unit, W_PYR)];
-        const int tile = unit - D.work_begin[W_PYR];
-        const int ntx = (D.w + kPyrTW - 1) / kPyrTW;
-        const int tx = tile % ntx, ty = tile / ntx;
-        const int x0 = tx * kPyrTW - 2, y0 = ty * kPyrTH - 2;  // region origin
-        const int w = D.w, h = D.h, pitch = D.pitch;
-        const TI *L = (const TI *)D.L;
-        const TI *R = (const TI *)D.R;
-        const bool next = D.Ln != nullptr;
-        __syncthreads();
-        for (int i = threadIdx.x; i < kPyrSH * kPyrSW; i += blockDim.x) {
-            const int r = i / kPyrSW, c = i - r * kPyrSW;
-            // only indices within 2 of the image are ever used by a stencil
-            const int gy = refl(min(max(y0 + r, -2), h + 1), h);
-            const int gx = refl(min(max(x0 + c, -2), w + 1), w);
-            Ls[r][c] = ldf(L + (size_t)gy * pitch + gx);
-            if (next) Rs[r][c] = ldf(R + (size_t)gy * pitch + gx);
-        }
-        __syncthreads();
-        TO *G = (TO *)D.G;
-        for (int i = threadIdx.x; i < kPyrTW * kPyrTH; i += blockDim.x) {
-            const int ly = i / kPyrTW, lx = i - ly * kPyrTW;
-            const int x = x0 + 2 + lx, y = y0 + 2 + ly;
-            if (x >= w || y >= h) continue;
-            const int cx = lx + 2, cy = ly + 2;
-            const float acc = (Ls[cy - 1][cx + 1] - Ls[cy - 1][cx - 1]) +
-                              2.f * (Ls[cy][cx + 1] - Ls[cy][cx - 1]) +
-                              (Ls[cy + 1][cx + 1] - Ls[cy + 1][cx - 1]);
-            stf(G + (size_t)y * D.gpitch + x, acc * 0.125f);
-        }
-        if (next) {
-            const float k[5] = {1.f, 4.f, 6.f, 4.f, 1.f};
-            for (int i = threadIdx.x; i < (kPyrTW / 2) * (kPyrTH / 2); i += blockDim.x) {
-                const int oy = i / (kPyrTW / 2), ox = i - oy * (kPyrTW / 2);
-                const int X = tx * (kPyrTW / 2) + ox, Y = ty * (kPyrTH / 2) + oy;
-                if (X >= D.wn || Y >= D.hn) continue;
-                const int cx = 2 * ox + 2, cy = 2 * oy + 2;
-                float accL = 0.f, accR = 0.f;
-#pragma unroll
-                for (int j = 0; j < 5; ++j) {
-                    float sl = 0.f, sr = 0.f;
-#pragma unroll
-                    for (int q = 0; q < 5; ++q) {
-                        sl += k[q] * Ls[cy + j - 2][cx + q - 2];
-                        sr += k[q] * Rs[cy + j - 2][cx + q - 2];
-                    }
-                    accL += k[j] * sl;
-                    accR += k[j] * sr;
-                }
-                stf((TO *)D.Ln + (size_t)Y * D.pitchn + X, accL * (1.f / 256.f));
-                stf((TO *)D.Rn + (size_t)Y * D.pitchn + X, accR * (1.f / 256.f));
-            }
-        }
-    }
+    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) pyramid_unit<TI, TO>(a, unit, Ls, Rs);
 }
 
 // ---------------------------------------------------------------- patch search
@@ -135,12 +140,12 @@ __device__ __forceinline__ void block_minmax(float &lo, float &hi, float *red) {
 // of a warp executes the same instruction stream.  The groups of a warp take
 // patches spaced so that their rows fall in different shared-memory banks.
 template <int P, typename TI, typename TG>
-__global__ void __launch_bounds__(256) k_search(LaunchArgs a) {
+__device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float *smem) {
+
     constexpr int G = P <= 8 ? 8 : 16;
     constexpr int N = P * P;
     constexpr int GPW = 32 / G;  // groups per warp
     constexpr float invN = 1.f / (float)N;
-    extern __shared__ float smem[];
     const int bp = a.band_pitch, cp = a.chunk_pitch, cap = a.band_cap;
     float *Rb = smem;
     float *Lb = Rb + P * bp;
@@ -162,247 +167,252 @@ __global__ void __launch_bounds__(256) k_search(LaunchArgs a) {
     sp = min(sp, 8 * (a.chunk / (8 * GPW)));  // must divide 8 x passes
     const int margin = (int)ceilf(a.tau) + (int)ceilf(2.f * h) + 3;
 
-    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) {
-        const LevelDesc &D = a.descs[find_pair(a.descs, a.npairs, unit, W_SEARCH)];
-        const int u = unit - D.work_begin[W_SEARCH];
-        const int py = u / D.nchunks, ch = u - py * D.nchunks;
-        const int oy = origin(py, D.h, P, S, D.kyreg);
-        const int k0 = ch * a.chunk;
-        const int k1 = min(k0 + a.chunk, D.npx);
-        const int nk = k1 - k0;
-        const int cx0 = origin(k0, D.w, P, S, D.kxreg);
-        const int cw = origin(k1 - 1, D.w, P, S, D.kxreg) + P - cx0;
-        const int w = D.w;
-        const TI *R = (const TI *)D.R;
-        const TI *L = (const TI *)D.L;
-        const TG *Gi = (const TG *)D.G;
 
-        __syncthreads();  // the previous unit's readers are done with smem
-        // initial estimates of the chunk (coarser fused map at the centre)
-        float dlo = FLT_MAX, dhi = -FLT_MAX;
-        for (int t = tid; t < nk; t += blockDim.x) {
-            float di = 0.f;
-            if (D.Dc != nullptr) {
-                const float cxp = (float)origin(k0 + t, w, P, S, D.kxreg) + 0.5f * (float)(P - 1);
-                const float cyp = (float)oy + 0.5f * (float)(P - 1);
-                di = 2.f * coarse_bilin(D.Dc, D.wc, D.hc, cxp, cyp);
-            }
-            dsh[t] = di;
-            dlo = fminf(dlo, di);
-            dhi = fmaxf(dhi, di);
+    const LevelDesc &D = a.descs[find_pair(a.descs, a.npairs, unit, W_SEARCH)];
+    const int u = unit - D.work_begin[W_SEARCH];
+    const int py = u / D.nchunks, ch = u - py * D.nchunks;
+    const int oy = origin(py, D.h, P, S, D.kyreg);
+    const int k0 = ch * a.chunk;
+    const int k1 = min(k0 + a.chunk, D.npx);
+    const int nk = k1 - k0;
+    const int cx0 = origin(k0, D.w, P, S, D.kxreg);
+    const int cw = origin(k1 - 1, D.w, P, S, D.kxreg) + P - cx0;
+    const int w = D.w;
+    const TI *R = (const TI *)D.R;
+    const TI *L = (const TI *)D.L;
+    const TG *Gi = (const TG *)D.G;
+
+    __syncthreads();  // the previous unit's readers are done with smem
+    // initial estimates of the chunk (coarser fused map at the centre)
+    float dlo = FLT_MAX, dhi = -FLT_MAX;
+    for (int t = tid; t < nk; t += blockDim.x) {
+        float di = 0.f;
+        if (D.Dc != nullptr) {
+            const float cxp = (float)origin(k0 + t, w, P, S, D.kxreg) + 0.5f * (float)(P - 1);
+            const float cyp = (float)oy + 0.5f * (float)(P - 1);
+            di = 2.f * coarse_bilin(D.Dc, D.wc, D.hc, cxp, cyp);
         }
-        block_minmax(dlo, dhi, red);
-        // column window of the right band
-        dhi = fminf(fmaxf(dhi, -(float)(2 * w)), (float)(2 * w));
-        dlo = fminf(fmaxf(dlo, -(float)(2 * w)), (float)(2 * w));
-        const int xlo = cx0 - (int)ceilf(dhi) - margin;
-        const int xhi = cx0 + cw - (int)floorf(dlo) + margin;
-        const int wwin = min(xhi - xlo, cap);
-        for (int r = 0; r < P; ++r) {
-            const TI *src = R + (size_t)(oy + r) * D.pitch;
-            for (int c = tid; c < wwin; c += blockDim.x)
-                Rb[r * bp + c] = ldf(src + clampi(xlo + c, 0, w - 1));
-            const TI *lsrc = L + (size_t)(oy + r) * D.pitch + cx0;
-            const TG *gsrc = Gi + (size_t)(oy + r) * D.gpitch + cx0;
-            for (int c = tid; c < cw; c += blockDim.x) {
-                Lb[r * cp + c] = ldf(lsrc + c);
-                Gb[r * cp + c] = ldf(gsrc + c);
-            }
-        }
-        __syncthreads();
-
-        const int passes = a.chunk / (8 * GPW);
-        for (int pass = 0; pass < passes; ++pass) {
-            const int uu = pass * 8 + warp;
-            const int kk = (uu / sp) * (sp * GPW) + (uu % sp) + sp * q;  // patch slot in chunk
-            const bool active = kk < nk;
-            const int kl = min(kk, nk - 1);
-            const int kx = k0 + kl;
-            const int ox = origin(kx, w, P, S, D.kxreg);
-            const int rr = row_on ? gl : 0;
-            const float *Lrow = Lb + rr * cp + (ox - cx0);
-            const float *Grow = Gb + rr * cp + (ox - cx0);
-            const float *Rs = Rb + rr * bp;
-            const TI *Rg = R + (size_t)(oy + rr) * D.pitch;
-
-            // template, centred gradient, Hessian (computed once, Sec. III-A)
-            float T[P], gt[P];
-            float gs = 0.f;
-#pragma unroll
-            for (int j = 0; j < P; ++j) {
-                T[j] = Lrow[j];
-                gt[j] = row_on ? Grow[j] : 0.f;
-                gs += gt[j];
-            }
-            const float gbar = group_sum<G>(gs) * invN;
-            float hp = 0.f, cpart = 0.f;
-#pragma unroll
-            for (int j = 0; j < P; ++j) {
-                gt[j] = row_on ? gt[j] - gbar : 0.f;
-                hp = fmaf(gt[j], gt[j], hp);
-                cpart = fmaf(gt[j], T[j], cpart);
-            }
-            const float H = group_sum<G>(hp);
-            const float cT = group_sum<G>(cpart);
-            const bool flat = !(H >= a.hess_eps * (float)N);
-            const float invH = flat ? 0.f : 1.f / H;
-            const float dinit = dsh[kl];
-            const float dlim = (float)w + 2.f * (float)P;
-
-            // right-image samples of this lane's row at x - d = base + j (+ t):
-            // the P + 1 values base .. base + P
-            auto load_row = [&](int base, float (&v)[P + 1]) {
-                const int o = base - xlo;
-                if (o >= 0 && o + P < wwin) {
-                    const float *p = Rs + o;
-#pragma unroll
-                    for (int j = 0; j <= P; ++j) v[j] = p[j];
-                } else {
-#pragma unroll
-                    for (int j = 0; j <= P; ++j) v[j] = ldf(Rg + clampi(base + j, 0, w - 1));
-                }
-            };
-
-            // Gauss-Newton: d <- d + (sum gt_i s_i - cT) / H, s_i = I_r(x_i - d)
-            float d = dinit, dlast = 0.f;
-            for (int it = 0; it < a.iters; ++it) {
-                int off;
-                float t;
-                split_shift(d, off, t);
-                float v[P + 1];
-                load_row(ox + off, v);
-                float A = 0.f, B = 0.f;
-#pragma unroll
-                for (int j = 0; j < P; ++j) {
-                    A = fmaf(gt[j], v[j], A);
-                    B = fmaf(gt[j], v[j + 1], B);
-                }
-                const float s = group_sum<G>(fmaf(t, B - A, A));
-                if (!flat) {
-                    const float delta = (s - cT) * invH;
-                    d = fminf(fmaxf(d + delta, -dlim), dlim);
-                    dlast = delta;
-                }
-            }
-
-            // window energies.  E(0) in two passes; for the four offsets the
-            // differences dE_k = E(delta_k) - E(0) directly from the sample
-            // differences u_j = s_kj - s_0j (the template cancels):
-            //   dE_k = sum u^2 - (sum u)^2 / N + 2 sum u (a_0j - mean a_0),
-            // which keeps full relative precision when dE_k << E(0).
-            int off0;
-            float t0;
-            split_shift(d, off0, t0);
-            const int base0 = ox + off0;
-            float s0[P];
-            float sa = 0.f;
-            {
-                float v[P + 1];
-                load_row(base0, v);
-#pragma unroll
-                for (int j = 0; j < P; ++j) {
-                    s0[j] = fmaf(t0, v[j + 1] - v[j], v[j]);
-                    sa += row_on ? s0[j] - T[j] : 0.f;
-                }
-            }
-            // samples outside [0, w-1]: every row shares base0 and t0, so per
-            // row j < -base0 on the left and base0 + j >= w - 1 (t0 > 0) or
-            // >= w (t0 = 0) on the right
-            const int nl = min(max(-base0, 0), P);
-            const int nr = min(max(P + base0 - (t0 > 0.f ? w - 1 : w), 0), P);
-            const int nout_all = P * (nl + nr);
-            const float mean0 = group_sum<G>(sa) * invN;
-            float e0 = 0.f;
-#pragma unroll
-            for (int j = 0; j < P; ++j) {
-                T[j] = row_on ? (s0[j] - T[j]) - mean0 : 0.f;  // now the centred residual
-                e0 = fmaf(T[j], T[j], e0);
-            }
-            float su[4], suu[4], suc[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                int off;
-                float t;
-                split_shift(d + dl[k], off, t);
-                float v[P + 1];
-                load_row(ox + off, v);
-                float p1 = 0.f, p2 = 0.f, p3 = 0.f;
-#pragma unroll
-                for (int j = 0; j < P; ++j) {
-                    const float uj = row_on ? fmaf(t, v[j + 1] - v[j], v[j]) - s0[j] : 0.f;
-                    p1 += uj;
-                    p2 = fmaf(uj, uj, p2);
-                    p3 = fmaf(uj, T[j], p3);
-                }
-                su[k] = p1;
-                suu[k] = p2;
-                suc[k] = p3;
-            }
-            float E[5];  // E[0] = E(0); E[k] = E(delta_k) - E(0)
-            E[0] = group_sum<G>(e0);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float S1 = group_sum<G>(su[k]);
-                const float S2 = group_sum<G>(suu[k]);
-                const float S3 = group_sum<G>(suc[k]);
-                E[k + 1] = fmaxf(S2 - S1 * S1 * invN, 0.f) + 2.f * S3;
-            }
-
-            if (active && gl == 0) {
-                uint32_t f = 0;
-                if (flat) f |= BDIS_F_FLAT;
-                if (!isfinite(d) || !isfinite(H)) f |= BDIS_F_NONFINITE;
-                if (fabsf(dlast) > a.conv_eps) f |= BDIS_F_UNCONVERGED;
-                if (fabsf(d - dinit) > a.tau) f |= BDIS_F_MOVED;
-                if ((float)(N - nout_all) < a.valid_gamma * (float)N) f |= BDIS_F_OUTSIDE;
-                // saddle: E(0) above the smallest off-centre energy (a tie keeps)
-                const float dmin = fminf(fminf(E[1], E[2]), fminf(E[3], E[4]));
-                if (dmin < 0.f) f |= BDIS_F_SADDLE;
-                bdis_patch_record rec;
-                rec.d = d;
-                rec.dinit = dinit;
-                rec.dlast = dlast;
-                rec.H = H;
-#pragma unroll
-                for (int k = 0; k < 5; ++k) rec.E[k] = E[k];
-                rec.cT = cT;
-                rec.flags = f;
-                rec.nout = nout_all;
-                rec.pi = 0.f;
-                rec.rho = 0.f;
-                rec.sig2 = 0.f;
-                rec.pdf_flags = 0u;
-                D.rec[(size_t)py * D.npx + kx] = rec;
-                const bool kept = f == 0u;
-                pe[3 * kk] = kept ? E[0] : 0.f;
-                pe[3 * kk + 1] = kept ? 1.f : 0.f;
-                pe[3 * kk + 2] = kept ? E[0] * E[0] : 0.f;
-            }
-        }
-        __syncthreads();
-        // sigma_r sums of the chunk in 64-bit fixed point: integer addition is
-        // exactly associative, so the totals do not depend on the chunking or
-        // on the order in which blocks add them
-        if (warp == 0) {
-            unsigned long long s1 = 0ull, s2 = 0ull, s3 = 0ull;
-            for (int i = tid; i < nk; i += 32) {
-                s1 += (unsigned long long)__float2ll_rn(pe[3 * i] * kSigmaFix1);
-                s2 += (unsigned long long)pe[3 * i + 1];
-                s3 += (unsigned long long)__float2ll_rn(pe[3 * i + 2]);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-                s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-                s3 += __shfl_xor_sync(0xffffffffu, s3, o);
-            }
-            if (tid == 0) {
-                atomicAdd(D.acc, s1);
-                atomicAdd(D.acc + 1, s2);
-                atomicAdd(D.acc + 2, s3);
-            }
+        dsh[t] = di;
+        dlo = fminf(dlo, di);
+        dhi = fmaxf(dhi, di);
+    }
+    block_minmax(dlo, dhi, red);
+    // column window of the right band
+    dhi = fminf(fmaxf(dhi, -(float)(2 * w)), (float)(2 * w));
+    dlo = fminf(fmaxf(dlo, -(float)(2 * w)), (float)(2 * w));
+    const int xlo = cx0 - (int)ceilf(dhi) - margin;
+    const int xhi = cx0 + cw - (int)floorf(dlo) + margin;
+    const int wwin = min(xhi - xlo, cap);
+    for (int r = 0; r < P; ++r) {
+        const TI *src = R + (size_t)(oy + r) * D.pitch;
+        for (int c = tid; c < wwin; c += blockDim.x)
+            Rb[r * bp + c] = ldf(src + clampi(xlo + c, 0, w - 1));
+        const TI *lsrc = L + (size_t)(oy + r) * D.pitch + cx0;
+        const TG *gsrc = Gi + (size_t)(oy + r) * D.gpitch + cx0;
+        for (int c = tid; c < cw; c += blockDim.x) {
+            Lb[r * cp + c] = ldf(lsrc + c);
+            Gb[r * cp + c] = ldf(gsrc + c);
         }
     }
+    __syncthreads();
+
+    const int passes = a.chunk / (8 * GPW);
+    for (int pass = 0; pass < passes; ++pass) {
+        const int uu = pass * 8 + warp;
+        const int kk = (uu / sp) * (sp * GPW) + (uu % sp) + sp * q;  // patch slot in chunk
+        const bool active = kk < nk;
+        const int kl = min(kk, nk - 1);
+        const int kx = k0 + kl;
+        const int ox = origin(kx, w, P, S, D.kxreg);
+        const int rr = row_on ? gl : 0;
+        const float *Lrow = Lb + rr * cp + (ox - cx0);
+        const float *Grow = Gb + rr * cp + (ox - cx0);
+        const float *Rs = Rb + rr * bp;
+        const TI *Rg = R + (size_t)(oy + rr) * D.pitch;
+
+        // template, centred gradient, Hessian (computed once, Sec. III-A)
+        float T[P], gt[P];
+        float gs = 0.f;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            T[j] = Lrow[j];
+            gt[j] = row_on ? Grow[j] : 0.f;
+            gs += gt[j];
+        }
+        const float gbar = group_sum<G>(gs) * invN;
+        float hp = 0.f, cpart = 0.f;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            gt[j] = row_on ? gt[j] - gbar : 0.f;
+            hp = fmaf(gt[j], gt[j], hp);
+            cpart = fmaf(gt[j], T[j], cpart);
+        }
+        const float H = group_sum<G>(hp);
+        const float cT = group_sum<G>(cpart);
+        const bool flat = !(H >= a.hess_eps * (float)N);
+        const float invH = flat ? 0.f : 1.f / H;
+        const float dinit = dsh[kl];
+        const float dlim = (float)w + 2.f * (float)P;
+
+        // right-image samples of this lane's row at x - d = base + j (+ t):
+        // the P + 1 values base .. base + P
+        auto load_row = [&](int base, float (&v)[P + 1]) {
+            const int o = base - xlo;
+            if (o >= 0 && o + P < wwin) {
+                const float *p = Rs + o;
+#pragma unroll
+                for (int j = 0; j <= P; ++j) v[j] = p[j];
+            } else {
+#pragma unroll
+                for (int j = 0; j <= P; ++j) v[j] = ldf(Rg + clampi(base + j, 0, w - 1));
+            }
+        };
+
+        // Gauss-Newton: d <- d + (sum gt_i s_i - cT) / H, s_i = I_r(x_i - d)
+        float d = dinit, dlast = 0.f;
+        for (int it = 0; it < a.iters; ++it) {
+            int off;
+            float t;
+            split_shift(d, off, t);
+            float v[P + 1];
+            load_row(ox + off, v);
+            float A = 0.f, B = 0.f;
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                A = fmaf(gt[j], v[j], A);
+                B = fmaf(gt[j], v[j + 1], B);
+            }
+            const float s = group_sum<G>(fmaf(t, B - A, A));
+            if (!flat) {
+                const float delta = (s - cT) * invH;
+                d = fminf(fmaxf(d + delta, -dlim), dlim);
+                dlast = delta;
+            }
+        }
+
+        // window energies.  E(0) in two passes; for the four offsets the
+        // differences dE_k = E(delta_k) - E(0) directly from the sample
+        // differences u_j = s_kj - s_0j (the template cancels):
+        //   dE_k = sum u^2 - (sum u)^2 / N + 2 sum u (a_0j - mean a_0),
+        // which keeps full relative precision when dE_k << E(0).
+        int off0;
+        float t0;
+        split_shift(d, off0, t0);
+        const int base0 = ox + off0;
+        float s0[P];
+        float sa = 0.f;
+        {
+            float v[P + 1];
+            load_row(base0, v);
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                s0[j] = fmaf(t0, v[j + 1] - v[j], v[j]);
+                sa += row_on ? s0[j] - T[j] : 0.f;
+            }
+        }
+        // samples outside [0, w-1]: every row shares base0 and t0, so per
+        // row j < -base0 on the left and base0 + j >= w - 1 (t0 > 0) or
+        // >= w (t0 = 0) on the right
+        const int nl = min(max(-base0, 0), P);
+        const int nr = min(max(P + base0 - (t0 > 0.f ? w - 1 : w), 0), P);
+        const int nout_all = P * (nl + nr);
+        const float mean0 = group_sum<G>(sa) * invN;
+        float e0 = 0.f;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            T[j] = row_on ? (s0[j] - T[j]) - mean0 : 0.f;  // now the centred residual
+            e0 = fmaf(T[j], T[j], e0);
+        }
+        float su[4], suu[4], suc[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            int off;
+            float t;
+            split_shift(d + dl[k], off, t);
+            float v[P + 1];
+            load_row(ox + off, v);
+            float p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                const float uj = row_on ? fmaf(t, v[j + 1] - v[j], v[j]) - s0[j] : 0.f;
+                p1 += uj;
+                p2 = fmaf(uj, uj, p2);
+                p3 = fmaf(uj, T[j], p3);
+            }
+            su[k] = p1;
+            suu[k] = p2;
+            suc[k] = p3;
+        }
+        float E[5];  // E[0] = E(0); E[k] = E(delta_k) - E(0)
+        E[0] = group_sum<G>(e0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float S1 = group_sum<G>(su[k]);
+            const float S2 = group_sum<G>(suu[k]);
+            const float S3 = group_sum<G>(suc[k]);
+            E[k + 1] = fmaxf(S2 - S1 * S1 * invN, 0.f) + 2.f * S3;
+        }
+
+        if (active && gl == 0) {
+            uint32_t f = 0;
+            if (flat) f |= BDIS_F_FLAT;
+            if (!isfinite(d) || !isfinite(H)) f |= BDIS_F_NONFINITE;
+            if (fabsf(dlast) > a.conv_eps) f |= BDIS_F_UNCONVERGED;
+            if (fabsf(d - dinit) > a.tau) f |= BDIS_F_MOVED;
+            if ((float)(N - nout_all) < a.valid_gamma * (float)N) f |= BDIS_F_OUTSIDE;
+            // saddle: E(0) above the smallest off-centre energy (a tie keeps)
+            const float dmin = fminf(fminf(E[1], E[2]), fminf(E[3], E[4]));
+            if (dmin < 0.f) f |= BDIS_F_SADDLE;
+            bdis_patch_record rec;
+            rec.d = d;
+            rec.dinit = dinit;
+            rec.dlast = dlast;
+            rec.H = H;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) rec.E[k] = E[k];
+            rec.cT = cT;
+            rec.flags = f;
+            rec.nout = nout_all;
+            rec.pi = 0.f;
+            rec.rho = 0.f;
+            rec.sig2 = 0.f;
+            rec.pdf_flags = 0u;
+            D.rec[(size_t)py * D.npx + kx] = rec;
+            const bool kept = f == 0u;
+            pe[3 * kk] = kept ? E[0] : 0.f;
+            pe[3 * kk + 1] = kept ? 1.f : 0.f;
+            pe[3 * kk + 2] = kept ? E[0] * E[0] : 0.f;
+        }
+    }
+    __syncthreads();
+    // sigma_r sums of the chunk in 64-bit fixed point: integer addition is
+    // exactly associative, so the totals do not depend on the chunking or
+    // on the order in which blocks add them
+    if (warp == 0) {
+        unsigned long long s1 = 0ull, s2 = 0ull, s3 = 0ull;
+        for (int i = tid; i < nk; i += 32) {
+            s1 += (unsigned long long)__float2ll_rn(pe[3 * i] * kSigmaFix1);
+            s2 += (unsigned long long)pe[3 * i + 1];
+            s3 += (unsigned long long)__float2ll_rn(pe[3 * i + 2]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+        }
+        if (tid == 0) {
+            atomicAdd(D.acc, s1);
+            atomicAdd(D.acc + 1, s2);
+            atomicAdd(D.acc + 2, s3);
+        }
+    }
+    }
+
+template <int P, typename TI, typename TG>
+__global__ void __launch_bounds__(256) k_search(LaunchArgs a) {
+    extern __shared__ float smem[];
+    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) search_unit<P, TI, TG>(a, unit, smem);
 }
 
 // ---------------------------------------------------------------- posterior, fusion
@@ -485,7 +495,13 @@ __device__ float4 posterior_of(const LaunchArgs &a, const LevelDesc &D, int kx, 
                                bool write) {
     const int k = ky * D.npx + kx;
     bdis_patch_record *rec = D.rec + k;
-    if (rec->flags != 0u) {
+    // L2 loads: the record was written by another block, possibly earlier in
+    // the same (persistent) launch
+    const float4 r0 = __ldcg((const float4 *)rec);       // d, dinit, dlast, H
+    const float4 r1 = __ldcg((const float4 *)rec + 1);   // E0, dE1, dE2, dE3
+    const float4 r2 = __ldcg((const float4 *)rec + 2);   // dE4, cT, flags, nout
+    const uint32_t flags = __float_as_uint(r2.z);
+    if (flags != 0u) {
         if (write) {
             rec->pi = rec->rho = rec->sig2 = 0.f;
             rec->pdf_flags = 0u;
@@ -497,11 +513,12 @@ __device__ float4 posterior_of(const LaunchArgs &a, const LevelDesc &D, int kx, 
     const float dlt[5] = {0.f, -h, h, -2.f * h, 2.f * h};
     const float scale = 2.f * sr * sr * (float)(kWindow * kWindow);
     // ln p_i - ln p_0 = -(E_i - E_0) / (2 sigma_r^2 s^2); the record holds E_i - E_0
+    const float dE[5] = {0.f, r1.y, r1.z, r1.w, r2.x};
     float e[5], Z = 1.f;
     e[0] = 0.f;
 #pragma unroll
     for (int i = 1; i < 5; ++i) {
-        e[i] = -rec->E[i] / scale;
+        e[i] = -dE[i] / scale;
         Z += expf(e[i]);
     }
     const float pi = 1.f / Z;
@@ -526,7 +543,7 @@ __device__ float4 posterior_of(const LaunchArgs &a, const LevelDesc &D, int kx, 
         for (int i = 0; i < 5; ++i) lnp[i] = e[i] - lnZ;
         sig2 = pdf_fit(lnp, dlt, a.pdf_iters, a.pdf_resid, a.tau0, pf);
     }
-    const float4 fz = make_float4(rec->d, rho, sig2, 1.f);
+    const float4 fz = make_float4(r0.x, rho, sig2, 1.f);
     if (write) {
         rec->pi = pi;
         rec->rho = rho;
@@ -556,141 +573,222 @@ __device__ __forceinline__ void cover(int x, int n, int P, int S, int kreg, int 
 // The weight is separable, so the gather runs in two passes: per tile column
 // and covering patch row, sums over the covering patch columns; then per
 // pixel, sums over the covering patch rows.
-__global__ void __launch_bounds__(256) k_fuse(LaunchArgs a) {
+__device__ __forceinline__ void fuse_unit(const LaunchArgs &a, int unit, float4 *fz) {
+    // fz: nkx * nky posteriors, then nky * TW column sums (dynamic shared memory)
+
     const int TW = a.tile_w, TH = a.tile_h;
-    extern __shared__ float4 fz[];  // nkx * nky posteriors, then nky * TW column sums
     __shared__ int cxlo[kFuseTileWMax], cxn[kFuseTileWMax], cxr[kFuseTileWMax];
     __shared__ int cylo[kFuseTileHMax], cyn[kFuseTileHMax], cyr[kFuseTileHMax];
     __shared__ float cxm[kFuseTileWMax][kMaxPatch + 2], cym[kFuseTileHMax][kMaxPatch + 2];
     const int P = a.P, S = a.S;
-    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) {
-        const LevelDesc &D = a.descs[find_pair(a.descs, a.npairs, unit, W_FUSE)];
-        const int tile = unit - D.work_begin[W_FUSE];
-        const int tx = tile % D.tiles_x, ty = tile / D.tiles_x;
-        const int x0 = tx * TW, y0 = ty * TH;
-        const int x1 = min(x0 + TW, D.w) - 1, y1 = min(y0 + TH, D.h) - 1;
-        // sigma_r of the pair from the search's exact sums (text after Eq. 6)
-        float sr;
-        {
-            const double S1 = (double)__ldcg(D.acc) / (double)kSigmaFix1;
-            const double S2 = (double)__ldcg(D.acc + 1);
-            const double S3 = (double)__ldcg(D.acc + 2);
-            if (a.sigma_r_mode == BDIS_SIGMA_R_FIXED) {
-                sr = a.sigma_r_fixed;
-            } else if (S2 == 0.0) {
-                sr = a.sigma_r_floor;
-            } else if (a.sigma_r_mode == BDIS_SIGMA_R_LITERAL) {
-                const float mean = (float)(S1 / S2);
-                sr = fmaxf(sqrtf(fmaxf((float)(S3 / S2) - mean * mean, 0.f)), a.sigma_r_floor);
-            } else {
-                sr = fmaxf(sqrtf((float)(S1 / (S2 * (double)(P * P)))), a.sigma_r_floor);
-            }
-            if (tile == 0 && threadIdx.x == 0) *D.sigma_r = sr;
-        }
 
-        // patches overlapping the tile
-        int kxlo, kxhi, kylo, kyhi, tmp;
-        bool kxext, kyext, bext;
-        cover(x0, D.w, P, S, D.kxreg, D.npx, kxlo, tmp, bext);
-        cover(x1, D.w, P, S, D.kxreg, D.npx, tmp, kxhi, kxext);
-        cover(y0, D.h, P, S, D.kyreg, D.npy, kylo, tmp, bext);
-        cover(y1, D.h, P, S, D.kyreg, D.npy, tmp, kyhi, kyext);
-        const int nkxr = max(0, kxhi - kxlo + 1), nkyr = max(0, kyhi - kylo + 1);
-        const int nkx = nkxr + (kxext ? 1 : 0);
-        const int nky = nkyr + (kyext ? 1 : 0);
-        for (int i = threadIdx.x; i < nkx * nky; i += blockDim.x) {
-            const int ix = i % nkx, iy = i / nkx;
-            const int kx = ix < nkxr ? kxlo + ix : D.npx - 1;
-            const int ky = iy < nkyr ? kylo + iy : D.npy - 1;
-            const int ox = origin(kx, D.w, P, S, D.kxreg);
-            const int oy = origin(ky, D.h, P, S, D.kyreg);
-            const bool owner = ox >= x0 && ox < x0 + TW && oy >= y0 && oy < y0 + TH;
-            fz[i] = posterior_of(a, D, kx, ky, sr, owner);
+    const LevelDesc &D = a.descs[find_pair(a.descs, a.npairs, unit, W_FUSE)];
+    const int tile = unit - D.work_begin[W_FUSE];
+    const int tx = tile % D.tiles_x, ty = tile / D.tiles_x;
+    const int x0 = tx * TW, y0 = ty * TH;
+    const int x1 = min(x0 + TW, D.w) - 1, y1 = min(y0 + TH, D.h) - 1;
+    // sigma_r of the pair from the search's exact sums (text after Eq. 6)
+    float sr;
+    {
+        const double S1 = (double)__ldcg(D.acc) / (double)kSigmaFix1;
+        const double S2 = (double)__ldcg(D.acc + 1);
+        const double S3 = (double)__ldcg(D.acc + 2);
+        if (a.sigma_r_mode == BDIS_SIGMA_R_FIXED) {
+            sr = a.sigma_r_fixed;
+        } else if (S2 == 0.0) {
+            sr = a.sigma_r_floor;
+        } else if (a.sigma_r_mode == BDIS_SIGMA_R_LITERAL) {
+            const float mean = (float)(S1 / S2);
+            sr = fmaxf(sqrtf(fmaxf((float)(S3 / S2) - mean * mean, 0.f)), a.sigma_r_floor);
+        } else {
+            sr = fmaxf(sqrtf((float)(S1 / (S2 * (double)(P * P)))), a.sigma_r_floor);
         }
-        // covering patches (tile-local indices) and their weights per column / row
-        if (threadIdx.x < TW + TH) {
-            const bool col = threadIdx.x < TW;
-            const int c = col ? threadIdx.x : threadIdx.x - TW;
-            const int xy = (col ? x0 : y0) + c;
-            const int n = col ? D.w : D.h, kreg = col ? D.kxreg : D.kyreg, np = col ? D.npx : D.npy;
-            const int klo = col ? kxlo : kylo, nr = col ? nkxr : nkyr, nt = col ? nkx : nky;
-            int lo = 0, hi = -1;
-            bool ext = false;
-            if (xy < n) cover(xy, n, P, S, kreg, np, lo, hi, ext);
-            const int cnt = xy < n ? max(0, hi - lo + 1) + (ext ? 1 : 0) : 0;
-            float *mrow = col ? cxm[c] : cym[c];
-            for (int q = 0; q < cnt; ++q) {
-                const bool isx = lo + q > hi;  // the ragged extra patch comes last
-                const int k = isx ? np - 1 : lo + q;
-                const int o = origin(k, n, P, S, kreg);
-                mrow[q] = a.use_sgmm ? a.m[xy - o] : 1.f;
-            }
-            (col ? cxlo : cylo)[c] = lo - klo;  // first regular local index
-            (col ? cxn : cyn)[c] = cnt;
-            (col ? cxr : cyr)[c] = xy < n ? max(0, hi - lo + 1) : 0;  // regular entries
-            (void)nr;
-            (void)nt;
-        }
-        __syncthreads();
+        if (tile == 0 && threadIdx.x == 0) *D.sigma_r = sr;
+    }
 
-        // pass 1: per tile column x and patch row iy, sums over the covering columns
-        float4 *csum = fz + nkx * nky;  // [nky][TW] of (sum m rho d, sum m rho, sum m rho^2, sum m^2 rho^2 sig2)
-        for (int i = threadIdx.x; i < nky * TW; i += blockDim.x) {
-            const int iy = i / TW, c = i - iy * TW;
-            const int cnt = cxn[c], lo = cxlo[c], nreg = cxr[c];
-            float A = 0.f, Bw = 0.f, Cq = 0.f, V = 0.f;
-            for (int q = 0; q < cnt; ++q) {
-                const int lx = q < nreg ? lo + q : nkx - 1;
-                const float4 f = fz[iy * nkx + lx];
-                const float mr = cxm[c][q] * f.y;  // 0 for a rejected patch
-                A = fmaf(mr, f.x, A);
-                Bw += mr;
-                Cq = fmaf(mr, f.y, Cq);
-                V = fmaf(mr * mr, f.z, V);
-            }
-            csum[i] = make_float4(A, Bw, Cq, V);
+    // patches overlapping the tile
+    int kxlo, kxhi, kylo, kyhi, tmp;
+    bool kxext, kyext, bext;
+    cover(x0, D.w, P, S, D.kxreg, D.npx, kxlo, tmp, bext);
+    cover(x1, D.w, P, S, D.kxreg, D.npx, tmp, kxhi, kxext);
+    cover(y0, D.h, P, S, D.kyreg, D.npy, kylo, tmp, bext);
+    cover(y1, D.h, P, S, D.kyreg, D.npy, tmp, kyhi, kyext);
+    const int nkxr = max(0, kxhi - kxlo + 1), nkyr = max(0, kyhi - kylo + 1);
+    const int nkx = nkxr + (kxext ? 1 : 0);
+    const int nky = nkyr + (kyext ? 1 : 0);
+    for (int i = threadIdx.x; i < nkx * nky; i += blockDim.x) {
+        const int ix = i % nkx, iy = i / nkx;
+        const int kx = ix < nkxr ? kxlo + ix : D.npx - 1;
+        const int ky = iy < nkyr ? kylo + iy : D.npy - 1;
+        const int ox = origin(kx, D.w, P, S, D.kxreg);
+        const int oy = origin(ky, D.h, P, S, D.kyreg);
+        const bool owner = ox >= x0 && ox < x0 + TW && oy >= y0 && oy < y0 + TH;
+        fz[i] = posterior_of(a, D, kx, ky, sr, owner);
+    }
+    // covering patches (tile-local indices) and their weights per column / row
+    if (threadIdx.x < TW + TH) {
+        const bool col = threadIdx.x < TW;
+        const int c = col ? threadIdx.x : threadIdx.x - TW;
+        const int xy = (col ? x0 : y0) + c;
+        const int n = col ? D.w : D.h, kreg = col ? D.kxreg : D.kyreg, np = col ? D.npx : D.npy;
+        const int klo = col ? kxlo : kylo, nr = col ? nkxr : nkyr, nt = col ? nkx : nky;
+        int lo = 0, hi = -1;
+        bool ext = false;
+        if (xy < n) cover(xy, n, P, S, kreg, np, lo, hi, ext);
+        const int cnt = xy < n ? max(0, hi - lo + 1) + (ext ? 1 : 0) : 0;
+        float *mrow = col ? cxm[c] : cym[c];
+        for (int q = 0; q < cnt; ++q) {
+            const bool isx = lo + q > hi;  // the ragged extra patch comes last
+            const int k = isx ? np - 1 : lo + q;
+            const int o = origin(k, n, P, S, kreg);
+            mrow[q] = a.use_sgmm ? a.m[xy - o] : 1.f;
         }
-        __syncthreads();
+        (col ? cxlo : cylo)[c] = lo - klo;  // first regular local index
+        (col ? cxn : cyn)[c] = cnt;
+        (col ? cxr : cyr)[c] = xy < n ? max(0, hi - lo + 1) : 0;  // regular entries
+        (void)nr;
+        (void)nt;
+    }
+    __syncthreads();
 
-        // pass 2: per pixel, sums over the covering patch rows
-        for (int pix = threadIdx.x; pix < TW * TH; pix += blockDim.x) {
-            const int c = pix % TW, r = pix / TW;
-            const int x = x0 + c, y = y0 + r;
-            if (x > x1 || y > y1) continue;
-            const int cnt = cyn[r], lo = cylo[r], nreg = cyr[r];
-            float swd = 0.f, sw = 0.f, swr = 0.f, sw2 = 0.f;
-            for (int q = 0; q < cnt; ++q) {
-                const int ly = q < nreg ? lo + q : nky - 1;
-                const float4 cs = csum[ly * TW + c];
-                const float my = cym[r][q];
-                swd = fmaf(my, cs.x, swd);
-                sw = fmaf(my, cs.y, sw);
-                swr = fmaf(my, cs.z, swr);
-                sw2 = fmaf(my * my, cs.w, sw2);
+    // pass 1: per tile column x and patch row iy, sums over the covering columns
+    float4 *csum = fz + nkx * nky;  // [nky][TW] of (sum m rho d, sum m rho, sum m rho^2, sum m^2 rho^2 sig2)
+    for (int i = threadIdx.x; i < nky * TW; i += blockDim.x) {
+        const int iy = i / TW, c = i - iy * TW;
+        const int cnt = cxn[c], lo = cxlo[c], nreg = cxr[c];
+        float A = 0.f, Bw = 0.f, Cq = 0.f, V = 0.f;
+        for (int q = 0; q < cnt; ++q) {
+            const int lx = q < nreg ? lo + q : nkx - 1;
+            const float4 f = fz[iy * nkx + lx];
+            const float mr = cxm[c][q] * f.y;  // 0 for a rejected patch
+            A = fmaf(mr, f.x, A);
+            Bw += mr;
+            Cq = fmaf(mr, f.y, Cq);
+            V = fmaf(mr * mr, f.z, V);
+        }
+        csum[i] = make_float4(A, Bw, Cq, V);
+    }
+    __syncthreads();
+
+    // pass 2: per pixel, sums over the covering patch rows
+    for (int pix = threadIdx.x; pix < TW * TH; pix += blockDim.x) {
+        const int c = pix % TW, r = pix / TW;
+        const int x = x0 + c, y = y0 + r;
+        if (x > x1 || y > y1) continue;
+        const int cnt = cyn[r], lo = cylo[r], nreg = cyr[r];
+        float swd = 0.f, sw = 0.f, swr = 0.f, sw2 = 0.f;
+        for (int q = 0; q < cnt; ++q) {
+            const int ly = q < nreg ? lo + q : nky - 1;
+            const float4 cs = csum[ly * TW + c];
+            const float my = cym[r][q];
+            swd = fmaf(my, cs.x, swd);
+            sw = fmaf(my, cs.y, sw);
+            swr = fmaf(my, cs.z, swr);
+            sw2 = fmaf(my * my, cs.w, sw2);
+        }
+        const size_t idx = (size_t)y * D.w + x;
+        const bool any = sw > 0.f;
+        float Dv, Qv, Vv;
+        if (any) {
+            Dv = swd / sw;
+            Qv = swr / sw;
+            Vv = sw2 / (sw * sw);
+        } else {
+            Dv = D.Dc != nullptr ? 2.f * coarse_bilin(D.Dc, D.wc, D.hc, (float)x, (float)y) : 0.f;
+            Qv = 0.f;
+            Vv = 0.f;
+        }
+        if (a.level == 0) {
+            const bool ok = any && Qv >= a.pix_thresh;
+            D.valid[idx] = ok ? 1 : 0;
+            D.disp[idx] = ok ? Dv : __int_as_float(0x7fc00000);
+            if (D.var != nullptr && a.variance) D.var[idx] = ok ? Vv : __int_as_float(0x7fc00000);
+        } else {
+            D.D[idx] = Dv;
+            D.Q[idx] = Qv;
+        }
+    }
+    __syncthreads();
+    }
+
+__global__ void __launch_bounds__(256) k_fuse(LaunchArgs a) {
+    extern __shared__ float4 fz[];
+    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) fuse_unit(a, unit, fz);
+}
+
+// ---------------------------------------------------------------- persistent form
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).
+// Thread 0 of each block arrives on a counter; the last arrival resets it and
+// bumps the generation, the others wait for the generation to change.  Every
+// wait is bounded: past kBarrierSpinLimit polls the block records the timeout
+// and goes on, so the kernel always terminates.
+__device__ void grid_barrier(unsigned *bar, int *err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned it = 0;
+            while (*gen == g) {
+                if (++it > kBarrierSpinLimit) {
+                    atomicOr(err, 1);
+                    break;
+                }
+                __nanosleep(64);
             }
-            const size_t idx = (size_t)y * D.w + x;
-            const bool any = sw > 0.f;
-            float Dv, Qv, Vv;
-            if (any) {
-                Dv = swd / sw;
-                Qv = swr / sw;
-                Vv = sw2 / (sw * sw);
-            } else {
-                Dv = D.Dc != nullptr ? 2.f * coarse_bilin(D.Dc, D.wc, D.hc, (float)x, (float)y) : 0.f;
-                Qv = 0.f;
-                Vv = 0.f;
-            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// All stages of one call: the pyramid levels, then search and fuse per level
+// coarse to fine, each stage striding its units over the persistent grid.
+template <int P, typename TG>
+__global__ void __launch_bounds__(256) k_mega(MegaArgs m) {
+    extern __shared__ float smem[];
+    for (int s = 0; s < m.nstages; ++s) {
+        const LaunchArgs &a = m.stages[s];
+        const int total = a.total;
+        if (a.kind == 0) {
+            if (blockIdx.x == 0 && a.acc_zero != nullptr)
+                for (int i = threadIdx.x; i < a.acc_count; i += blockDim.x) a.acc_zero[i] = 0ull;
+            float(*Ls)[kPyrSW] = (float(*)[kPyrSW])smem;
+            float(*Rs)[kPyrSW] = Ls + kPyrSH;
             if (a.level == 0) {
-                const bool ok = any && Qv >= a.pix_thresh;
-                D.valid[idx] = ok ? 1 : 0;
-                D.disp[idx] = ok ? Dv : __int_as_float(0x7fc00000);
-                if (D.var != nullptr && a.variance) D.var[idx] = ok ? Vv : __int_as_float(0x7fc00000);
+                for (int u = blockIdx.x; u < total; u += gridDim.x) pyramid_unit<uint8_t, TG>(a, u, Ls, Rs);
             } else {
-                D.D[idx] = Dv;
-                D.Q[idx] = Qv;
+                for (int u = blockIdx.x; u < total; u += gridDim.x) pyramid_unit<TG, TG>(a, u, Ls, Rs);
             }
+        } else if (a.kind == 1) {
+            if (a.level == 0) {
+                for (int u = blockIdx.x; u < total; u += gridDim.x) search_unit<P, uint8_t, TG>(a, u, smem);
+            } else {
+                for (int u = blockIdx.x; u < total; u += gridDim.x) search_unit<P, TG, TG>(a, u, smem);
+            }
+        } else {
+            for (int u = blockIdx.x; u < total; u += gridDim.x) fuse_unit(a, u, (float4 *)smem);
         }
-        __syncthreads();
+        if (s + 1 < m.nstages) grid_barrier(m.bar, m.err);
+    }
+}
+
+const void *mega_kernel(int P, int st_type) {
+    const bool h = st_type == E_F16;
+    switch (P) {
+        case 6: return h ? (const void *)k_mega<6, __half> : (const void *)k_mega<6, float>;
+        case 8: return h ? (const void *)k_mega<8, __half> : (const void *)k_mega<8, float>;
+        case 10: return h ? (const void *)k_mega<10, __half> : (const void *)k_mega<10, float>;
+        case 12: return h ? (const void *)k_mega<12, __half> : (const void *)k_mega<12, float>;
+        case 16: return h ? (const void *)k_mega<16, __half> : (const void *)k_mega<16, float>;
+        default: return nullptr;
     }
 }
 
@@ -767,6 +865,33 @@ size_t fuse_smem(int P, int S, int tile_w, int tile_h) {
 }
 
 cudaError_t prepare_fuse(size_t smem_bytes) { return raise_smem_limit((const void *)k_fuse, smem_bytes); }
+
+bool mega_supported(int P) { return mega_kernel(P, E_F32) != nullptr; }
+
+int mega_grid(int P, int st_type, size_t smem) {
+    const void *f = mega_kernel(P, st_type);
+    if (f == nullptr || raise_smem_limit(f, smem) != cudaSuccess) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, 256, smem) != cudaSuccess) return 0;
+    return nb * num_sms();
+}
+
+cudaError_t launch_mega(const MegaArgs &m, int P, int st_type, int grid, size_t smem, cudaStream_t s) {
+    const void *f = mega_kernel(P, st_type);
+    if (f == nullptr || grid < 1) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void *args[] = {(void *)&m};
+    return cudaLaunchKernelExC(&cfg, f, args);
+}
 int search_group(int P) { return P <= 8 ? 8 : 16; }
 int search_chunk(int P, int passes) { return passes * (256 / search_group(P)); }
 

@@ -193,3 +193,36 @@ def test_stats_and_pitched_input(bd):
     assert s["patches"] == [4661, 1131, 266]
     assert s["valid_pixels"] == int(ok1.sum().item())
     assert all(sr >= 0.5 for sr in s["sigma_r"])
+
+
+@pytest.mark.parametrize("kw,size", [
+    (dict(patch=12, stride=6, levels=4, iters=8, variance=1), (640, 480)),
+    (dict(patch=8, stride=4, levels=3, iters=8, storage="f16"), (320, 240)),
+    (dict(patch=16, stride=8, levels=2, iters=6, variance=1), (200, 150)),
+])
+def test_persistent_form_equals_launch_sequence(bd, kw, size):
+    import torch
+    w, h = size
+    pair = synth.g2_pair(w, h, 9) if kw.get("variance") else synth.g1_pair(w, h, 9)
+    L = torch.from_numpy(pair.left).cuda()
+    R = torch.from_numpy(pair.right).cuda()
+    outs = []
+    for form in (1, 2):
+        m = bd.BDIS(**kw)
+        m.set_option(bd.B.OPT_FORM, form)
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            d, v, ok = m.match(L, R, stream=stream)
+            d2, v2, ok2 = m.match(L, R, stream=stream)   # a second call (graph / barrier reuse)
+        torch.cuda.synchronize()
+        st = m.stats()
+        assert st["persistent"] == (1 if form == 2 else 0)
+        assert st["barrier_timeouts"] == 0
+        assert torch.equal(torch.nan_to_num(d, nan=-1.0), torch.nan_to_num(d2, nan=-1.0))
+        outs.append((d, v, ok))
+        m.close()
+    (d1, v1, o1), (d2, v2, o2) = outs
+    assert torch.equal(o1, o2)
+    assert torch.equal(torch.nan_to_num(d1, nan=-1.0), torch.nan_to_num(d2, nan=-1.0))
+    if kw.get("variance"):
+        assert torch.equal(torch.nan_to_num(v1, nan=-1.0), torch.nan_to_num(v2, nan=-1.0))
