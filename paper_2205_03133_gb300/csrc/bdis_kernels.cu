@@ -47,13 +47,31 @@ __device__ __forceinline__ void pyramid_unit(const LaunchArgs &a, int unit, floa
     const TI *R = (const TI *)D.R;
     const bool next = D.Ln != nullptr;
     __syncthreads();
-    for (int i = threadIdx.x; i < kPyrSH * kPyrSW; i += blockDim.x) {
-        const int r = i / kPyrSW, c = i - r * kPyrSW;
-        // only indices within 2 of the image are ever used by a stencil
-        const int gy = refl(min(max(y0 + r, -2), h + 1), h);
-        const int gx = refl(min(max(x0 + c, -2), w + 1), w);
-        Ls[r][c] = ldf(L + (size_t)gy * pitch + gx);
-        if (next) Rs[r][c] = ldf(R + (size_t)gy * pitch + gx);
+    // all of a thread's loads are issued before its stores (memory-level parallelism);
+    // every launch of the pyramid stage uses 256 threads
+    constexpr int NEL = kPyrSH * kPyrSW;
+    constexpr int PER = (NEL + 255) / 256;
+    float vl[PER], vr[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = threadIdx.x + k * 256;
+        if (i < NEL) {
+            const int r = i / kPyrSW, c = i - r * kPyrSW;
+            // only indices within 2 of the image are ever used by a stencil
+            const int gy = refl(min(max(y0 + r, -2), h + 1), h);
+            const int gx = refl(min(max(x0 + c, -2), w + 1), w);
+            vl[k] = ldf(L + (size_t)gy * pitch + gx);
+            vr[k] = next ? ldf(R + (size_t)gy * pitch + gx) : 0.f;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = threadIdx.x + k * 256;
+        if (i < NEL) {
+            const int r = i / kPyrSW, c = i - r * kPyrSW;
+            Ls[r][c] = vl[k];
+            if (next) Rs[r][c] = vr[k];
+        }
     }
     __syncthreads();
     TO *G = (TO *)D.G;
@@ -203,15 +221,26 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
     const int xlo = cx0 - (int)ceilf(dhi) - margin;
     const int xhi = cx0 + cw - (int)floorf(dlo) + margin;
     const int wwin = min(xhi - xlo, cap);
-    for (int r = 0; r < P; ++r) {
-        const TI *src = R + (size_t)(oy + r) * D.pitch;
-        for (int c = tid; c < wwin; c += blockDim.x)
-            Rb[r * bp + c] = ldf(src + clampi(xlo + c, 0, w - 1));
-        const TI *lsrc = L + (size_t)(oy + r) * D.pitch + cx0;
-        const TG *gsrc = Gi + (size_t)(oy + r) * D.gpitch + cx0;
-        for (int c = tid; c < cw; c += blockDim.x) {
-            Lb[r * cp + c] = ldf(lsrc + c);
-            Gb[r * cp + c] = ldf(gsrc + c);
+    // staging: the P rows of a column are loaded together (memory-level parallelism)
+    for (int c = tid; c < wwin; c += blockDim.x) {
+        const int col = clampi(xlo + c, 0, w - 1);
+        float v[P];
+#pragma unroll
+        for (int r = 0; r < P; ++r) v[r] = ldf(R + (size_t)(oy + r) * D.pitch + col);
+#pragma unroll
+        for (int r = 0; r < P; ++r) Rb[r * bp + c] = v[r];
+    }
+    for (int c = tid; c < cw; c += blockDim.x) {
+        float vl[P], vg[P];
+#pragma unroll
+        for (int r = 0; r < P; ++r) {
+            vl[r] = ldf(L + (size_t)(oy + r) * D.pitch + cx0 + c);
+            vg[r] = ldf(Gi + (size_t)(oy + r) * D.gpitch + cx0 + c);
+        }
+#pragma unroll
+        for (int r = 0; r < P; ++r) {
+            Lb[r * cp + c] = vl[r];
+            Gb[r * cp + c] = vg[r];
         }
     }
     __syncthreads();
