@@ -184,6 +184,25 @@ def _stage_bytes(kernel, w, h, prm):
     return tot
 
 
+def search_flops(w, h, prm):
+    """Algorithmic FP32 operations of the patch search over all levels of one
+    pair: per patch iters*P^2*6 (two taps, interpolation and the two
+    accumulations of every GN step) + 5*P^2*5 (window samples, residual and
+    energy sums) + 60 (setup); the PDF fit (about 400 per kept patch) runs
+    in the fusion kernel and is not counted here."""
+    P, S, L, it = prm["patch"], prm["stride"], prm["levels"], prm["iters"]
+    per = it * P * P * 6 + 5 * P * P * 5 + 60
+    return per * sum(n for _, _, n in level_geometry(w, h, P, S, L))
+
+
+def alu_peak_tflops(sm_mhz=None):
+    """FP32 FMA peak: 152 SMs x 128 lanes x 2 flops x SM clock (the maximum
+    clock of MEASURED_PEAKS.json unless a measured median is given)."""
+    pk = measured_peaks() or {}
+    mhz = sm_mhz or pk.get("sm_max_mhz", 2070.0)
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -373,6 +392,8 @@ def main():
         k["share"] = round(k["ms_per_step"] / tot_k, 4)
         k["ms_per_step"] = round(k["ms_per_step"], 5)
         k["avg_launch_us"] = round(k["avg_launch_us"], 3)
+    st = m.stats(stream)
+    form = "persistent" if st["persistent"] else "launch sequence (CUDA graph, programmatic dependent launch)"
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
     peaks = measured_peaks()
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
@@ -384,6 +405,15 @@ def main():
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
                 "algorithmic_bytes_per_step": per_step_bytes,
                 "launches_per_step": kernels[dom]["launches_per_step"]}
+    roofline_alu = None
+    if "search" in kernels:
+        fl = search_flops(w, h, PARAMS)
+        ach = fl / (kernels["search"]["ms_per_step"] / 1e3) / 1e12
+        pk = alu_peak_tflops()
+        roofline_alu = {"kernel": "search", "bound": "alu", "achieved": round(ach, 4),
+                        "peak": round(pk, 2), "unit": "TFLOP/s", "frac": round(ach / pk, 5),
+                        "algorithmic_flops_per_step": fl,
+                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
 
     # ---- end to end through the host-buffer entry point (pinned buffers)
     hL = torch.from_numpy(pair.left).pin_memory()
@@ -421,9 +451,13 @@ def main():
     # ---- batched form: 64 uneven pairs, one launch per stage per level
     batched = None
     fwd_bwd = None
+    modes = None
+    depth_line = None
     if not args.no_batched:
         batched = bench_batched(bd, dev, stream, flush, rank, ws)
         fwd_bwd = bench_fwd_bwd(bd, dev, stream, flush, rank, ws)
+        modes = bench_modes(bd, dev, stream, flush, ws, Ld, Rd, out, w, h)
+        depth_line = bench_depth(bd, dev, stream, flush, ws)
 
     result = None
     if rank == 0:
@@ -447,13 +481,17 @@ def main():
                            l2="flushed between timed steps (256 MiB write, outside the events)",
                            graph="CUDA graph replay of the per-call launch sequence"),
             "gpu_launches": launches_per_step * args.steps,
+            "form": form,
             "kernels": kernels,
             "roofline": roofline,
+            "roofline_alu": roofline_alu,
             "e2e": e2e,
             "clocks": clock_info,
             "cpu_baseline": cpu,
             "batched": batched,
             "fwd_bwd": fwd_bwd,
+            "modes": modes,
+            "depth": depth_line,
             "paper_context": "BDIS(VAR) 0.072 s per 640x480 frame (4.27 Mpix/s) on one i5-9400 "
                              "core, finest scale 2^1 (Table VIII); 17 Hz claim (abstract)",
         }
@@ -592,13 +630,102 @@ def bench_batched(bd, dev, stream, flush, rank, ws, steps=10, warmup=3, compare_
     kern = {n: round(prof.ms[i] / 3, 4) for i, n in enumerate(bd.B.KERNEL_NAMES) if prof.launches[i]}
     m.close()
     mp.close()
+    roof = None
+    if "search" in kern:
+        fl = sum(search_flops(w, h, BATCH_PARAMS) for w, h in sizes)
+        by = sum(algorithmic_bytes("search", w, h, BATCH_PARAMS) for w, h in sizes)
+        t = kern["search"] / 1e3
+        pk = measured_peaks() or {}
+        hbm = pk.get("hbm_gbs", 6800.0)
+        roof = {"kernel": "search",
+                "alu": {"achieved": round(fl / t / 1e12, 3), "peak": round(alu_peak_tflops(), 2),
+                        "unit": "TFLOP/s", "frac": round(fl / t / 1e12 / alu_peak_tflops(), 4)},
+                "hbm": {"achieved": round(by / t / 1e9, 1), "peak": hbm, "unit": "GB/s",
+                        "frac": round(by / t / 1e9 / hbm, 4)},
+                "algorithmic_flops": fl, "algorithmic_bytes": by}
     return {"workload": "64 uneven pairs (24x640x480, 16x960x540, 16x1280x720, 8x1920x1080), "
                         "P8 S4 L3, 8 iters, fp16 pyramids",
             "value": round(ws * px / (t_b / 1e3) / 1e6, 2), "unit": UNIT,
             "ms_per_batch": round(t_b, 4),
             "plain_sequential_ms": round(t_p, 4),
             "plain_sequential_value": round(ws * px / (t_p / 1e3) / 1e6, 2),
-            "speedup_vs_plain": round(t_p / t_b, 3), "kernel_ms_per_batch": kern}
+            "speedup_vs_plain": round(t_p / t_b, 3), "kernel_ms_per_batch": kern,
+            "roofline": roof}
+
+
+MODES = {
+    # the paper's parameter set (Sec. IV-A): scales 2^5 .. 2^1, patch 10,
+    # overlap 0.55 (stride 4), 12 iterations, upsampled to full resolution
+    "paper_preset": dict(patch=10, stride=4, levels=6, iters=12, finest_level=1, variance=1),
+    "dis_weights": dict(PARAMS, weight_mode="dis"),
+    "fast_exp": dict(PARAMS, fast_exp=1),
+    "no_sgmm_no_c2f": dict(PARAMS, use_sgmm=0, use_c2f=0),
+    "sigma_r_fixed_8": dict(PARAMS, sigma_r_mode="fixed"),
+}
+
+
+def bench_modes(bd, dev, stream, flush, ws, Ld, Rd, out, w, h, steps=200, warmup=5):
+    """The plain 640x480 workload under the optional modes (same pair, same
+    outputs), device time per call with L2 flushed between calls."""
+    import torch
+    res = {}
+    for name, kw in MODES.items():
+        m = bd.BDIS(**kw)
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                flush.zero_()
+                m.match(Ld, Rd, out=out, stream=stream)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        with torch.cuda.stream(stream):
+            for k in range(steps):
+                flush.zero_()
+                ev[k][0].record(stream)
+                m.match(Ld, Rd, out=out, stream=stream)
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / steps, ws, dev)
+        st = m.stats(stream)
+        res[name] = {"params": {k: v for k, v in kw.items()}, "ms_per_call": round(ms, 5),
+                     "value": round(ws * w * h / (ms / 1e3) / 1e6, 2), "unit": UNIT,
+                     "valid_pixels": int(st["valid_pixels"])}
+        m.close()
+    return res
+
+
+def bench_depth(bd, dev, stream, flush, ws, frames=64, steps=20, warmup=3):
+    """Depth and depth variance (Eq. 13, Eq. 17) of 64 full-HD disparity and
+    variance maps: an HBM-bound elementwise kernel, 16 B per pixel."""
+    import torch
+    n = frames * 1920 * 1080
+    g = torch.Generator(device=dev).manual_seed(0)
+    d = torch.rand(n, device=dev, generator=g) * 100 + 1
+    v = torch.rand(n, device=dev, generator=g)
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            z, zv = bd.depth(d, v, fb=2.56, stream=stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            z, zv = bd.depth(d, v, fb=2.56, stream=stream)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / steps, ws, dev)
+    by = 16 * n
+    pk = measured_peaks() or {}
+    hbm = pk.get("hbm_gbs", 6800.0)
+    del d, v, z, zv
+    torch.cuda.empty_cache()
+    return {"workload": f"{frames} x 1920x1080 disparity + variance maps (f32)",
+            "ms": round(ms, 4), "value": round(ws * n / (ms / 1e3) / 1e6, 1), "unit": "Mpix/s",
+            "roofline": {"bound": "hbm", "achieved": round(by / (ms / 1e3) / 1e9, 1),
+                         "peak": hbm, "unit": "GB/s", "frac": round(by / (ms / 1e3) / 1e9 / hbm, 4),
+                         "algorithmic_bytes": by}}
 
 
 if __name__ == "__main__":

@@ -59,6 +59,15 @@ typedef enum {
     BDIS_SIGMA_R_FIXED = 2
 } bdis_sigma_r_mode;
 
+/* Fusion weights of the densification.
+ * BDIS: omega_k(x) = rho_k m[x - ox_k] m[y - oy_k], the sGMM kernel times the
+ *       propagated probability (Eq. 8, Eq. 12) -- the default;
+ * DIS:  omega_k(x) = 1 / max(1, r_k(x)^2), the inverse photometric residual
+ *       of Eq. 2, with r_k(x) = I_r(x - d_k) - I_l(x) - mu_k the residual of
+ *       patch k at pixel x after its mean offset mu_k (mean normalisation as
+ *       in the search).  Q and V use the same normalised weights. */
+typedef enum { BDIS_WEIGHT_BDIS = 0, BDIS_WEIGHT_DIS = 1 } bdis_weight_mode;
+
 typedef struct {
     int patch;            /* P: patch side (px), 4..16                       */
     int stride;           /* S: patch stride (px), 1..P                      */
@@ -80,6 +89,16 @@ typedef struct {
     float hess_eps;       /* patch rejected as flat if H < hess_eps * P^2    */
     int use_sgmm;         /* 0: equal pixel weights (ablation, Table VII)    */
     int use_c2f;          /* 0: no coarse-to-fine probability (ablation)     */
+    int weight_mode;      /* bdis_weight_mode of the fusion                  */
+    int finest_level;     /* finest processed level f, 0..L-1 (default 0).
+                             f > 0: levels < f are only pyramid steps; the
+                             level-f result is upsampled to full resolution:
+                             disp = 2^f bilinear(D_f), var = 4^f bilinear(V_f)
+                             at level-f coordinate (x + 0.5) / 2^f - 0.5,
+                             valid iff every level-f pixel with a non-zero
+                             bilinear weight is valid (Sec. IV-A: 2^1)      */
+    int fast_exp;         /* 1: Schraudolph's exponential in the window
+                             posterior (Sec. IV, technical details)         */
 } bdis_params;
 
 typedef struct bdis_handle bdis_handle;
@@ -243,15 +262,22 @@ typedef enum {
     /* Execution form: 0 (default) as chosen by the autotuner, 1 one launch per
      * stage, 2 persistent (every stage in one cooperative launch with grid
      * barriers; 8-bit inputs, patch sizes 6, 8, 10, 12, 16).  Same results. */
-    BDIS_OPT_FORM = 4
+    BDIS_OPT_FORM = 4,
+    /* 1 (default): launch each kernel of the launch sequence with
+     * programmatic stream serialisation, so that it is scheduled while its
+     * predecessor drains and starts reading once the predecessor has
+     * completed (hides the launch gap between dependent kernels); 0: plain
+     * stream order.  Same results. */
+    BDIS_OPT_PDL = 5
 } bdis_option;
 
 bdis_status bdis_set_option(bdis_handle *h, int option, int value);
 
 /* kernels: pyramid + gradient; patch search; fused sigma_r + posterior + densify;
- * the persistent form (all stages in one launch) */
+ * the persistent form (all stages in one launch); full-resolution upsampling
+ * of the finest processed level (finest_level > 0) */
 enum { BDIS_K_PYRAMID = 0, BDIS_K_SEARCH = 1, BDIS_K_FUSE = 2, BDIS_K_PERSISTENT = 3,
-       BDIS_K_COUNT = 4 };
+       BDIS_K_UPSAMPLE = 4, BDIS_K_COUNT = 5 };
 
 typedef struct {
     int launches[BDIS_K_COUNT];   /* launches per kernel since the last reset */
@@ -271,9 +297,12 @@ typedef struct {
                                       window offsets delta = {-h, +h, -2h, +2h}        */
     float cT;                      /* sum of centred gradient x template             */
     uint32_t flags;                /* rejection bits (0 = kept), see BDIS_F_*         */
-    int32_t nout;                  /* samples outside the image at the estimate      */
+    uint16_t nout;                 /* samples outside the image at the estimate      */
+    uint16_t pdf_flags;            /* PDF-fit exception bits, see BDIS_PDF_*          */
     float pi, rho, sig2;           /* window posterior, propagated probability, var  */
-    uint32_t pdf_flags;            /* PDF-fit exception bits, see BDIS_PDF_*          */
+    float mu;                      /* patch mean of I_r(x - d) - I_l(x) at the
+                                      estimate (the mean offset the normalised
+                                      residual removes)                          */
 } bdis_patch_record;
 
 enum {
@@ -290,7 +319,9 @@ typedef struct {
     int storage;              /* element type of left/right/grad (level 0: u8) */
     const void *left, *right, *grad;   /* device pointers (level 0: caller's)  */
     const bdis_patch_record *records;  /* npx*npy records, row-major           */
-    const float *D, *Q;       /* fused maps (w*h), NULL at level 0             */
+    const float *D, *Q;       /* fused maps (w*h), NULL at level 0; at the
+                                 finest processed level f > 0, D is NaN where
+                                 the level-f pixel is invalid                 */
     const float *sigma_r;     /* one float                                     */
 } bdis_level_view;
 
@@ -298,6 +329,18 @@ typedef struct {
  * Valid until the next call on the handle. */
 bdis_status bdis_level_view_get(const bdis_handle *h, int pair, int level,
                                 bdis_level_view *out);
+
+/* ---- depth (Eq. 13) and depth variance (Eq. 17) ---- */
+
+/* Elementwise on n pixels of device buffers, asynchronous on `stream`:
+ *   depth = fb / disp,   depth_var = fb^2 / disp^4 * var,
+ * fb = focal length (px) x baseline (any length unit; depth comes out in
+ * that unit).  A pixel whose disp is NaN or <= 0 gets NaN in both.  `var`
+ * and `depth_var` may be NULL (then no variance is written); n == 0 is a
+ * no-op.  BDIS_EINVAL for a null disp / depth with n > 0, n < 0, or a
+ * non-finite or non-positive fb. */
+bdis_status bdis_depth(const float *disp, const float *var, long long n, float fb, float *depth,
+                       float *depth_var, void *stream);
 
 /* cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, stream) + sync. */
 bdis_status bdis_copy(void *dst, const void *src, size_t bytes, void *stream);

@@ -28,6 +28,7 @@ _lib = None
 MAX_LEVELS = 8
 STORE = {"f64": 0, "f32": 1, "f16": 2}
 SIGMA_R = {"pooled": 0, "literal": 1, "fixed": 2}
+WEIGHT = {"bdis": 0, "dis": 1}
 
 F_FLAT, F_UNCONVERGED, F_MOVED, F_OUTSIDE, F_SADDLE, F_NONFINITE = (1 << i for i in range(6))
 PDF_NOT_PEAK, PDF_FAILED, PDF_RESIDUAL = (1 << i for i in range(3))
@@ -53,13 +54,14 @@ class Params(C.Structure):
         ("variance", C.c_int), ("pdf_iters", C.c_int), ("pdf_resid", C.c_double),
         ("storage", C.c_int), ("hess_eps", C.c_double),
         ("use_sgmm", C.c_int), ("use_c2f", C.c_int),
+        ("weight_mode", C.c_int), ("finest_level", C.c_int), ("fast_exp", C.c_int),
     ]
 
 
 PATCH_DTYPE = np.dtype([
     ("d", "f8"), ("dinit", "f8"), ("E", "f8", (5,)), ("H", "f8"), ("cT", "f8"),
     ("dlast", "f8"), ("nout", "i4"), ("flags", "u4"), ("pi", "f8"), ("rho", "f8"),
-    ("sig2", "f8"), ("prop", "f8"), ("pdf_flags", "u4"),
+    ("sig2", "f8"), ("prop", "f8"), ("pdf_flags", "u4"), ("mu", "f8"),
 ], align=True)
 
 
@@ -85,6 +87,12 @@ def lib():
         L.ob_origins.argtypes = [C.c_int, C.c_int, C.c_int, vp]
         L.ob_gamma_weight.restype = C.c_double
         L.ob_gamma_weight.argtypes = [C.c_int, C.c_int]
+        L.ob_gamma_weight_f.restype = C.c_double
+        L.ob_gamma_weight_f.argtypes = [C.c_int, C.c_int, C.c_int]
+        L.ob_exp_schraudolph.restype = C.c_double
+        L.ob_exp_schraudolph.argtypes = [C.c_double]
+        L.ob_upsample_output.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                         vp, vp, vp]
         L.ob_pyr_down.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int]
         L.ob_sobel_x.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int]
         L.ob_window_offsets.argtypes = [C.c_double, vp]
@@ -100,7 +108,7 @@ def lib():
                                    vp, C.c_int, C.c_int, vp, vp, C.c_int]
         L.ob_sgmm_table.argtypes = [C.c_int, C.c_double, vp]
         L.ob_densify.argtypes = [C.POINTER(Params), vp, vp, C.c_int, vp, C.c_int, C.c_int,
-                                 C.c_int, vp, C.c_int, C.c_int, vp, vp, vp, vp]
+                                 C.c_int, vp, vp, vp, C.c_int, C.c_int, vp, vp, vp, vp]
         L.ob_num_patches.argtypes = [C.POINTER(Params), C.c_int, C.c_int, C.c_int, vp, vp]
         L.ob_check.argtypes = [C.POINTER(Params), C.c_int, C.c_int]
         L.ob_match.argtypes = [C.POINTER(Params), vp, vp, C.c_int, C.c_int, vp, vp, vp,
@@ -119,11 +127,12 @@ def make_params(patch=8, stride=4, levels=3, iters=8, sigma_s=4.0, window_step=0
                 conv_eps=0.05, valid_gamma=0.75, pix_thresh=0.15, search_radius=0.0,
                 sigma_r_mode="pooled", sigma_r_floor=0.5, sigma_r_fixed=8.0, variance=0,
                 pdf_iters=10, pdf_resid=0.1, storage="f32", hess_eps=1e-4, use_sgmm=1,
-                use_c2f=1) -> Params:
+                use_c2f=1, weight_mode="bdis", finest_level=0, fast_exp=0) -> Params:
     return Params(patch, stride, levels, iters, sigma_s, window_step, conv_eps, valid_gamma,
                   pix_thresh, search_radius, SIGMA_R[sigma_r_mode], sigma_r_floor,
                   sigma_r_fixed, variance, pdf_iters, pdf_resid, STORE[storage], hess_eps,
-                  use_sgmm, use_c2f)
+                  use_sgmm, use_c2f, WEIGHT[weight_mode] if isinstance(weight_mode, str)
+                  else int(weight_mode), finest_level, fast_exp)
 
 
 def level_dim(n: int, l: int) -> int:
@@ -137,8 +146,24 @@ def origins(n: int, P: int, S: int) -> np.ndarray:
     return out[:k]
 
 
-def gamma_weight(n: int, levels: int) -> float:
-    return lib().ob_gamma_weight(n, levels)
+def gamma_weight(n: int, levels: int, finest: int = 0) -> float:
+    return lib().ob_gamma_weight_f(n, finest, levels)
+
+
+def exp_schraudolph(y: float) -> float:
+    return lib().ob_exp_schraudolph(float(y))
+
+
+def upsample_output(Df, Vf, okf, f: int, w: int, h: int):
+    """Full-resolution disp, var, valid from the level-f maps (f > 0)."""
+    Df = np.ascontiguousarray(Df, dtype=np.float64)
+    Vf = None if Vf is None else np.ascontiguousarray(Vf, dtype=np.float64)
+    okf = np.ascontiguousarray(okf, dtype=np.uint8)
+    hf, wf = Df.shape
+    disp = np.zeros((h, w)); var = np.zeros((h, w)); valid = np.zeros((h, w), dtype=np.uint8)
+    lib().ob_upsample_output(_ptr(Df), _ptr(Vf), _ptr(okf), wf, hf, f, w, h, _ptr(disp),
+                             _ptr(var), _ptr(valid))
+    return disp, var, valid.astype(bool)
 
 
 def round_f16(v: float) -> float:
@@ -231,9 +256,13 @@ def sgmm_table(P: int, sigma_s: float) -> np.ndarray:
     return M
 
 
-def densify(p: Params, rec: np.ndarray, w: int, h: int, Dc=None):
-    """Fuse a level's patch records (grid npy x npx) into D, Q, V, count."""
+def densify(p: Params, rec: np.ndarray, w: int, h: int, Dc=None, L=None, R=None):
+    """Fuse a level's patch records (grid npy x npx) into D, Q, V, count.
+    L, R (the level's images) are needed with the DIS weight mode."""
     rec = np.ascontiguousarray(rec)
+    if L is not None:
+        L = np.ascontiguousarray(L, dtype=np.float64)
+        R = np.ascontiguousarray(R, dtype=np.float64)
     ox = origins(w, p.patch, p.stride)
     oy = origins(h, p.patch, p.stride)
     assert rec.shape == (len(oy), len(ox))
@@ -245,7 +274,7 @@ def densify(p: Params, rec: np.ndarray, w: int, h: int, Dc=None):
     else:
         hc = wc = 0
     lib().ob_densify(C.byref(p), _ptr(rec), _ptr(ox), len(ox), _ptr(oy), len(oy), w, h,
-                     _ptr(Dc), wc, hc, _ptr(D), _ptr(Q), _ptr(V), _ptr(cnt))
+                     _ptr(L), _ptr(R), _ptr(Dc), wc, hc, _ptr(D), _ptr(Q), _ptr(V), _ptr(cnt))
     return D, Q, V, cnt
 
 

@@ -38,6 +38,9 @@
 /* storage emulation for the pyramid and gradient images */
 enum { OB_STORE_F64 = 0, OB_STORE_F32 = 1, OB_STORE_F16 = 2 };
 enum { OB_SIGMA_R_POOLED = 0, OB_SIGMA_R_LITERAL = 1, OB_SIGMA_R_FIXED = 2 };
+/* fusion weights: BDIS (Eq. 12, sGMM x probability) or DIS (Eq. 2, inverse
+ * photometric residual) */
+enum { OB_WEIGHT_BDIS = 0, OB_WEIGHT_DIS = 1 };
 
 /* patch rejection reasons (bit flags; a patch is valid iff flags == 0) */
 enum {
@@ -71,6 +74,9 @@ typedef struct {
     int storage;
     double hess_eps;       /* per-pixel Hessian threshold: H < hess_eps*P^2  */
     int use_sgmm, use_c2f; /* ablation switches (Table VII)                  */
+    int weight_mode;       /* OB_WEIGHT_BDIS | OB_WEIGHT_DIS                  */
+    int finest_level;      /* finest processed level f; f > 0 upsamples       */
+    int fast_exp;          /* 1: Schraudolph's exponential in the posterior   */
 } ob_params;
 
 typedef struct {
@@ -80,6 +86,7 @@ typedef struct {
     double pi, rho, sig2;
     double prop;           /* coarse probability inherited at the centre (Eq. 10) */
     uint32_t pdf_flags;
+    double mu;             /* patch mean of I_r(x - d) - T at the estimate    */
 } ob_patch;
 
 /* Per-level buffers the caller may ask for (any pointer may be NULL). */
@@ -158,12 +165,34 @@ int ob_origins(int n, int P, int S, int *out)
 }
 
 /* Gamma weight of level n (the formula following Eq. 11):
- * 2^n / sum_{m in levels} 2^m. */
-double ob_gamma_weight(int n, int levels)
+ * 2^n / sum_{m in N} 2^m, N the processed levels finest .. levels-1. */
+double ob_gamma_weight_f(int n, int finest, int levels)
 {
     double s = 0.0;
-    for (int m = 0; m < levels; ++m) s += ldexp(1.0, m);
+    for (int m = finest; m < levels; ++m) s += ldexp(1.0, m);
     return ldexp(1.0, n) / s;
+}
+
+double ob_gamma_weight(int n, int levels) { return ob_gamma_weight_f(n, 0, levels); }
+
+/* Schraudolph's exponential (N. Schraudolph, "A fast, compact approximation
+ * of the exponential function", Neural Computation 11(4), 1999), in the
+ * single-precision form: the integer i = A y + (B - C), A = 2^23 / ln 2,
+ * B = 127 * 2^23 (the exponent bias in place), C = 8 * 60801 (the published
+ * RMS-optimal correction of the double-precision form, moved to the 23-bit
+ * fraction), truncated, read as the bits of an IEEE-754 binary32 number.
+ * Relative error within about 4 %.  Arguments below -87 (where i would leave
+ * the normal range) give 0. */
+double ob_exp_schraudolph(double y)
+{
+    if (y < -87.0) return 0.0;
+    if (y > 88.0) y = 88.0;
+    const double A = 8388608.0 / log(2.0);
+    const double BC = 127.0 * 8388608.0 - 8.0 * 60801.0;
+    int32_t i = (int32_t)floor(A * y + BC);
+    float f;
+    memcpy(&f, &i, sizeof f);
+    return (double)f;
 }
 
 /* ------------------------------------------------------------------ */
@@ -335,6 +364,7 @@ void ob_search_patch(const ob_params *p, const double *L, const double *R,
         double E = 0.0;
         for (int i = 0; i < N; ++i) E += (a[i] - mean) * (a[i] - mean);
         out->E[k] = E;
+        if (k == 0) out->mu = mean;
     }
     int nout = 0;
     for (int r = 0; r < P; ++r)
@@ -475,7 +505,7 @@ void ob_posterior(const ob_params *p, int level, ob_patch *pt, int n, double sig
 {
     const double s = 5.0;
     const double scale = 2.0 * sigma_r * sigma_r * s * s;
-    const double wl = ob_gamma_weight(level, p->levels);
+    const double wl = ob_gamma_weight_f(level, p->finest_level, p->levels);
     const double tau0 = search_radius(p);
     double delta[5];
     ob_window_offsets(p->window_step, delta);
@@ -484,12 +514,16 @@ void ob_posterior(const ob_params *p, int level, ob_patch *pt, int n, double sig
         q->pi = q->rho = q->sig2 = q->prop = 0.0;
         q->pdf_flags = 0;
         if (q->flags != 0) continue;
-        double e[5], Z = 0.0;
+        double e[5], Z = 0.0, Zf = 0.0;
         for (int i = 0; i < 5; ++i) {
             e[i] = -(q->E[i] - q->E[0]) / scale; /* ln p_i - ln p_0 */
             Z += exp(e[i]);
+            Zf += ob_exp_schraudolph(e[i]);
         }
-        q->pi = 1.0 / Z;
+        /* pi = p_0 / sum_i p_i; with fast_exp every p_i (p_0 included) is
+         * Schraudolph's approximation.  The PDF fit below keeps the exact
+         * log-probabilities. */
+        q->pi = p->fast_exp ? ob_exp_schraudolph(0.0) / Zf : 1.0 / Z;
         if (p->use_c2f) {
             /* rho = Gamma_n pi + propagated probability of the coarser levels,
              * read from the fused coarse probability map at the patch centre
@@ -505,7 +539,7 @@ void ob_posterior(const ob_params *p, int level, ob_patch *pt, int n, double sig
         } else {
             q->rho = q->pi;
         }
-        if (level == 0 && p->variance) {
+        if (level == p->finest_level && p->variance) {
             double lnp[5], lnZ = log(Z);
             for (int i = 0; i < 5; ++i) lnp[i] = e[i] - lnZ;
             q->sig2 = ob_pdf_fit(lnp, delta, p->pdf_iters, p->pdf_resid, tau0,
@@ -535,14 +569,19 @@ void ob_sgmm_table(int P, double sigma_s, double *M)
 }
 
 /* Fuse the valid patches of one level into dense maps.  For pixel x with
- * covering valid patches Omega(x): omega_k = rho_k M[x - o_k],
+ * covering valid patches Omega(x): omega_k = rho_k M[x - o_k] (Eq. 12), or
+ * with weight_mode DIS the inverse photometric residual of Eq. 2,
+ * omega_k = 1 / max(1, r_k(x)^2) with r_k(x) = I_r(x - d_k) - I_l(x) - mu_k
+ * (mean-normalised like the search; the floor of 1 DN^2 avoids a division
+ * by zero at an exact match).  Then
  * D = sum omega_k d_k / sum omega_k, Q = sum omega_k rho_k / sum omega_k,
  * V = sum omega_k^2 sigma_k^2 / (sum omega_k)^2.  Pixels with no valid
  * covering patch take the upsampled coarser disparity (0 at the coarsest
- * level) and Q = 0, V = 0, and are marked invalid (cnt = 0). */
+ * level) and Q = 0, V = 0, and are marked invalid (cnt = 0).  L, R: the
+ * level's images (read only in DIS mode; may be NULL otherwise). */
 void ob_densify(const ob_params *p, const ob_patch *pt, const int *ox, int npx,
-                const int *oy, int npy, int w, int h, const double *Dc, int wc, int hc,
-                double *D, double *Q, double *V, int *cnt)
+                const int *oy, int npy, int w, int h, const double *L, const double *R,
+                const double *Dc, int wc, int hc, double *D, double *Q, double *V, int *cnt)
 {
     const int P = p->patch;
     double *M = (double *)malloc(sizeof(double) * P * P);
@@ -561,7 +600,14 @@ void ob_densify(const ob_params *p, const ob_patch *pt, const int *ox, int npx,
                     if (!(ox[kx] <= x && x < ox[kx] + P)) continue;
                     const ob_patch *q = &pt[ky * npx + kx];
                     if (q->flags != 0) continue;
-                    double om = q->rho * M[(y - oy[ky]) * P + (x - ox[kx])];
+                    double om;
+                    if (p->weight_mode == OB_WEIGHT_DIS) {
+                        double r = sample_row(R, w, y, (double)x - q->d) - L[(size_t)y * w + x] -
+                                   q->mu;
+                        om = 1.0 / (r * r > 1.0 ? r * r : 1.0);
+                    } else {
+                        om = q->rho * M[(y - oy[ky]) * P + (x - ox[kx])];
+                    }
                     sw += om;
                     swd += om * q->d;
                     swr += om * q->rho;
@@ -602,7 +648,7 @@ int ob_num_patches(const ob_params *p, int w, int h, int level, int *npx, int *n
 int ob_check(const ob_params *p, int w, int h)
 {
     if (p->patch < 2 || p->stride < 1 || p->levels < 1 || p->levels > OB_MAX_LEVELS ||
-        p->iters < 0)
+        p->iters < 0 || p->finest_level < 0 || p->finest_level >= p->levels)
         return 1;
     int wl = ob_level_dim(w, p->levels - 1), hl = ob_level_dim(h, p->levels - 1);
     if (wl < p->patch || hl < p->patch || wl < 3 || hl < 3) return 1;
@@ -627,6 +673,44 @@ void ob_search_level(const ob_params *p, const double *L, const double *R, const
         }
     free(ox);
     free(oy);
+}
+
+/* Full-resolution output from the finest processed level f > 0 (the paper
+ * stops at scale 2^1 and upsamples, Sec. IV-A).  For pixel x the level-f
+ * coordinate is X = (x + 0.5) / 2^f - 0.5, clamped to the map; disp =
+ * 2^f * bilinear(D_f), var = 4^f * bilinear(V_f) (a disparity scaled by s
+ * has s^2 times the variance).  The pixel is valid iff every level-f pixel
+ * with a non-zero bilinear weight is valid. */
+void ob_upsample_output(const double *Df, const double *Vf, const uint8_t *okf, int wf, int hf,
+                        int f, int w, int h, double *disp, double *var, uint8_t *valid)
+{
+    const double s = ldexp(1.0, f);
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            double X = (x + 0.5) / s - 0.5, Y = (y + 0.5) / s - 0.5;
+            if (X < 0.0) X = 0.0;
+            if (X > wf - 1.0) X = wf - 1.0;
+            if (Y < 0.0) Y = 0.0;
+            if (Y > hf - 1.0) Y = hf - 1.0;
+            int x0 = (int)floor(X), y0 = (int)floor(Y);
+            int x1 = x0 + 1 < wf ? x0 + 1 : wf - 1, y1 = y0 + 1 < hf ? y0 + 1 : hf - 1;
+            double fx = X - x0, fy = Y - y0;
+            int xs[4] = {x0, x1, x0, x1}, ys[4] = {y0, y0, y1, y1};
+            double wt[4] = {(1 - fx) * (1 - fy), fx * (1 - fy), (1 - fx) * fy, fx * fy};
+            int ok = 1;
+            double dv = 0.0, vv = 0.0;
+            for (int i = 0; i < 4; ++i) {
+                if (wt[i] == 0.0) continue;
+                size_t j = (size_t)ys[i] * wf + xs[i];
+                ok &= okf[j] != 0;
+                dv += wt[i] * Df[j];
+                if (Vf) vv += wt[i] * Vf[j];
+            }
+            size_t i = (size_t)y * w + x;
+            valid[i] = (uint8_t)ok;
+            disp[i] = ok ? s * dv : NAN;
+            if (var) var[i] = (ok && Vf) ? s * s * vv : NAN;
+        }
 }
 
 /* Full BDIS on one pair of level-0 images (values already in the storage
@@ -658,7 +742,8 @@ int ob_match(const ob_params *p, const double *L0, const double *R0, int w, int 
 
     double *Dprev = NULL, *Qprev = NULL;
     int wprev = 0, hprev = 0;
-    for (int l = NL - 1; l >= 0; --l) {
+    const int F = p->finest_level;
+    for (int l = NL - 1; l >= F; --l) {
         const int wl = W[l], hl = Hh[l];
         int *ox = (int *)malloc(sizeof(int) * (wl + 2));
         int *oy = (int *)malloc(sizeof(int) * (hl + 2));
@@ -672,9 +757,10 @@ int ob_match(const ob_params *p, const double *L0, const double *R0, int w, int 
         size_t n = (size_t)wl * hl;
         double *D = (double *)malloc(sizeof(double) * n);
         double *Q = (double *)malloc(sizeof(double) * n);
-        double *V = (l == 0) ? (double *)malloc(sizeof(double) * n) : NULL;
+        double *V = (l == F) ? (double *)malloc(sizeof(double) * n) : NULL;
         int *cnt = (int *)malloc(sizeof(int) * n);
-        ob_densify(p, pt, ox, npx, oy, npy, wl, hl, Dprev, wprev, hprev, D, Q, V, cnt);
+        ob_densify(p, pt, ox, npx, oy, npy, wl, hl, Lv[l], Rv[l], Dprev, wprev, hprev, D, Q, V,
+                   cnt);
         if (tr) {
             tr->sigma_r[l] = sr;
             if (tr->patches[l]) memcpy(tr->patches[l], pt, sizeof(ob_patch) * np);
@@ -693,6 +779,12 @@ int ob_match(const ob_params *p, const double *L0, const double *R0, int w, int 
                 disp[i] = ok ? D[i] : NAN;
                 if (var) var[i] = (ok && p->variance) ? V[i] : NAN;
             }
+        } else if (l == F) {
+            uint8_t *okf = (uint8_t *)malloc(n);
+            for (size_t i = 0; i < n; ++i) okf[i] = (uint8_t)(cnt[i] > 0 && Q[i] >= p->pix_thresh);
+            ob_upsample_output(D, p->variance ? V : NULL, okf, wl, hl, F, w, h, disp, var,
+                               valid);
+            free(okf);
         }
         free(Dprev);
         free(Qprev);
@@ -928,6 +1020,8 @@ double ob_diff_forward(const ob_params *p, const double *L, const double *R, int
                        const uint8_t *valid, int sr_const, double lambda,
                        const double *d_override, double *D_out, double *dk_out)
 {
+    /* the differentiable form covers the default fusion at full resolution */
+    if (p->weight_mode != OB_WEIGHT_BDIS || p->finest_level != 0 || p->fast_exp) return NAN;
     const int P = p->patch;
     int npx = ob_origins(w, P, p->stride, NULL), npy = ob_origins(h, P, p->stride, NULL);
     ob_dpatch *dp = (ob_dpatch *)calloc((size_t)npx * npy, sizeof(ob_dpatch));
@@ -955,6 +1049,8 @@ double ob_diff_grad(const ob_params *p, const double *L, const double *R, int w,
                     const uint8_t *valid, int sr_const, double lambda, double *gL, double *gR,
                     double *gdk, double *gD_out)
 {
+    /* the differentiable form covers the default fusion at full resolution */
+    if (p->weight_mode != OB_WEIGHT_BDIS || p->finest_level != 0 || p->fast_exp) return NAN;
     const int P = p->patch, N = P * P;
     int *ox = (int *)malloc(sizeof(int) * (w + 2)), *oy = (int *)malloc(sizeof(int) * (h + 2));
     int npx = ob_origins(w, P, p->stride, ox), npy = ob_origins(h, P, p->stride, oy);

@@ -17,10 +17,11 @@ import numpy as np
 from . import _binding as B
 from ._binding import BdisError
 
-__all__ = ["BDIS", "BdisError", "default_params", "B", "_grad_table"]
+__all__ = ["BDIS", "BdisError", "default_params", "B", "_grad_table", "depth"]
 
 _STORAGE = {"f32": B.STORE_F32, "f16": B.STORE_F16}
 _SIGMA_R = {"pooled": B.SIGMA_R_POOLED, "literal": B.SIGMA_R_LITERAL, "fixed": B.SIGMA_R_FIXED}
+_WEIGHT = {"bdis": B.WEIGHT_BDIS, "dis": B.WEIGHT_DIS}
 
 
 def default_params() -> B.bdis_params:
@@ -36,6 +37,8 @@ def _params(**kw) -> B.bdis_params:
             v = _STORAGE[v]
         if k == "sigma_r_mode" and isinstance(v, str):
             v = _SIGMA_R[v]
+        if k == "weight_mode" and isinstance(v, str):
+            v = _WEIGHT[v]
         if not hasattr(p, k):
             raise TypeError(f"unknown BDIS parameter {k!r}")
         setattr(p, k, v)
@@ -161,10 +164,14 @@ class BDIS:
             return a
 
         rec = np.dtype([("d", "f4"), ("dinit", "f4"), ("dlast", "f4"), ("H", "f4"),
-                        ("E", "f4", (5,)), ("cT", "f4"), ("flags", "u4"), ("nout", "i4"),
-                        ("pi", "f4"), ("rho", "f4"), ("sig2", "f4"), ("pdf_flags", "u4")])
+                        ("E", "f4", (5,)), ("cT", "f4"), ("flags", "u4"), ("nout", "u2"),
+                        ("pdf_flags", "u2"), ("pi", "f4"), ("rho", "f4"), ("sig2", "f4"),
+                        ("mu", "f4")])
         assert rec.itemsize == C.sizeof(B.bdis_patch_record)
-        out["patches"] = cp(v.records, rec, (v.npy, v.npx))
+        if not v.records:  # below the finest processed level: no search there
+            out["patches"] = None
+        else:
+            out["patches"] = cp(v.records, rec, (v.npy, v.npx))
         sr = cp(v.sigma_r, np.float32, (1,))
         out["sigma_r"] = float(sr[0])
         if level > 0:
@@ -175,7 +182,8 @@ class BDIS:
             for key, ptr in (("L", v.left), ("R", v.right)):
                 out[key] = cp(ptr, dt, (v.h, pitch))[:, :v.w].astype(np.float64)
         gdt = np.float16 if self.params.storage == B.STORE_F16 else np.float32
-        out["G"] = cp(v.grad, gdt, (v.h, v.grad_pitch))[:, :v.w].astype(np.float64)
+        out["G"] = (cp(v.grad, gdt, (v.h, v.grad_pitch))[:, :v.w].astype(np.float64)
+                    if v.grad else None)
         return out
 
 
@@ -310,3 +318,26 @@ class _Lazy:
 
 _Disparity = _Lazy()
 __all__ += ["disparity"]
+
+
+# ---------------------------------------------------------------- depth
+
+def depth(disp, var=None, fb: float = 1.0, stream=None):
+    """Depth fb / disp (Eq. 13) and, given the disparity variance, the depth
+    variance fb^2 / disp^4 var (Eq. 17) of device tensors, computed by the
+    library's elementwise kernel.  fb = focal length (px) x baseline."""
+    import torch
+    disp = disp.contiguous()
+    assert disp.is_cuda and disp.dtype == torch.float32
+    z = torch.empty_like(disp)
+    zv = None
+    if var is not None:
+        var = var.contiguous()
+        assert var.shape == disp.shape and var.dtype == torch.float32
+        zv = torch.empty_like(disp)
+    B.check(B.lib().bdis_depth(C.c_void_p(disp.data_ptr()),
+                               C.c_void_p(var.data_ptr()) if var is not None else None,
+                               disp.numel(), C.c_float(fb), C.c_void_p(z.data_ptr()),
+                               C.c_void_p(zv.data_ptr()) if zv is not None else None,
+                               _stream_handle(stream)))
+    return z, zv

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libbdis.so")
 BDIS_OK, BDIS_EINVAL, BDIS_ENOMEM, BDIS_ECUDA, BDIS_EUNSUPPORTED = range(5)
 STORE_F32, STORE_F16 = 0, 1
 SIGMA_R_POOLED, SIGMA_R_LITERAL, SIGMA_R_FIXED = 0, 1, 2
+WEIGHT_BDIS, WEIGHT_DIS = 0, 1
 
 F_FLAT, F_UNCONVERGED, F_MOVED, F_OUTSIDE, F_SADDLE, F_NONFINITE = (1 << i for i in range(6))
 PDF_NOT_PEAK, PDF_FAILED, PDF_RESIDUAL = (1 << i for i in range(3))
@@ -29,7 +30,8 @@ class bdis_params(C.Structure):
         ("sigma_r_mode", C.c_int), ("sigma_r_floor", C.c_float), ("sigma_r_fixed", C.c_float),
         ("variance", C.c_int), ("pdf_iters", C.c_int), ("pdf_resid", C.c_float),
         ("storage", C.c_int), ("hess_eps", C.c_float), ("use_sgmm", C.c_int),
-        ("use_c2f", C.c_int),
+        ("use_c2f", C.c_int), ("weight_mode", C.c_int), ("finest_level", C.c_int),
+        ("fast_exp", C.c_int),
     ]
 
 
@@ -51,8 +53,9 @@ class bdis_stats(C.Structure):
 class bdis_patch_record(C.Structure):
     _fields_ = [
         ("d", C.c_float), ("dinit", C.c_float), ("dlast", C.c_float), ("H", C.c_float),
-        ("E", C.c_float * 5), ("cT", C.c_float), ("flags", C.c_uint32), ("nout", C.c_int32),
-        ("pi", C.c_float), ("rho", C.c_float), ("sig2", C.c_float), ("pdf_flags", C.c_uint32),
+        ("E", C.c_float * 5), ("cT", C.c_float), ("flags", C.c_uint32), ("nout", C.c_uint16),
+        ("pdf_flags", C.c_uint16), ("pi", C.c_float), ("rho", C.c_float), ("sig2", C.c_float),
+        ("mu", C.c_float),
     ]
 
 
@@ -78,11 +81,11 @@ class bdis_grad(C.Structure):
 
 
 class bdis_profile(C.Structure):
-    _fields_ = [("launches", C.c_int * 4), ("ms", C.c_double * 4)]
+    _fields_ = [("launches", C.c_int * 5), ("ms", C.c_double * 5)]
 
 
-OPT_GRAPH, OPT_PROFILE, OPT_AUTOTUNE, OPT_FORM = 1, 2, 3, 4
-KERNEL_NAMES = ["pyramid", "search", "fuse", "persistent"]
+OPT_GRAPH, OPT_PROFILE, OPT_AUTOTUNE, OPT_FORM, OPT_PDL = 1, 2, 3, 4, 5
+KERNEL_NAMES = ["pyramid", "search", "fuse", "persistent", "upsample"]
 
 
 # (name, restype, argtypes) of every exported function of include/bdis.h
@@ -109,6 +112,7 @@ EXPORTS = [
     ("bdis_backward", C.c_int, [_h, C.POINTER(bdis_grad), _vp]),
     ("bdis_match_noalloc", C.c_int, [C.POINTER(bdis_params), _vp, _vp, C.c_int, C.c_int, C.c_int,
                                      _vp, _vp, _vp, _vp]),
+    ("bdis_depth", C.c_int, [_vp, _vp, C.c_longlong, C.c_float, _vp, _vp, _vp]),
 ]
 
 _lib = None

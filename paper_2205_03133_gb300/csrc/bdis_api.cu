@@ -52,6 +52,7 @@ struct bdis_handle {
     int *err_flag = nullptr;  // timeout flag of the persistent form
     bool last_persistent = false;
     int form = 0;             // BDIS_OPT_FORM
+    bool use_pdl = true;      // BDIS_OPT_PDL
     // per-kernel event timing
     bool profile = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -113,6 +114,9 @@ std::string check_params(const bdis_params &p) {
     if (!finite_nonneg(p.hess_eps)) return "hess_eps must be >= 0";
     if (p.use_sgmm != 0 && p.use_sgmm != 1) return "use_sgmm must be 0 or 1";
     if (p.use_c2f != 0 && p.use_c2f != 1) return "use_c2f must be 0 or 1";
+    if (p.weight_mode != BDIS_WEIGHT_BDIS && p.weight_mode != BDIS_WEIGHT_DIS) return "bad weight_mode";
+    if (p.finest_level < 0 || p.finest_level >= p.levels) return "finest_level must be in [0, levels-1]";
+    if (p.fast_exp != 0 && p.fast_exp != 1) return "fast_exp must be 0 or 1";
     return "";
 }
 
@@ -157,9 +161,13 @@ LaunchArgs base_args(const bdis_params &p, int level, const LevelDesc *descs, in
     a.tau = tau_at(p);
     a.tau0 = tau_at(p);
     a.hess_eps = p.hess_eps;
+    // Gamma weight over the processed levels finest .. L-1 (Eq. 11)
     double s = 0.0;
-    for (int m = 0; m < p.levels; ++m) s += std::ldexp(1.0, m);
+    for (int m = p.finest_level; m < p.levels; ++m) s += std::ldexp(1.0, m);
     a.gamma_w = (float)(std::ldexp(1.0, level) / s);
+    a.finest = p.finest_level;
+    a.weight_mode = p.weight_mode;
+    a.fast_exp = p.fast_exp;
     a.sigma_r_mode = p.sigma_r_mode;
     a.sigma_r_floor = p.sigma_r_floor;
     a.sigma_r_fixed = p.sigma_r_fixed;
@@ -183,7 +191,7 @@ struct Plan {
     int wmax[kMaxLevels] = {0};
     int units[kMaxLevels][W_COUNT] = {{0}};
     // arena offsets, index level * n + pair
-    std::vector<size_t> oG, oL, oR, oD, oQ, oRec, oFuse, oSr;
+    std::vector<size_t> oG, oL, oR, oD, oQ, oV, oRec, oFuse, oSr;
 };
 
 struct Bump {
@@ -203,8 +211,9 @@ void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, const Leve
     const size_t esz = p.storage == BDIS_STORE_F16 ? 2 : 4;
     const size_t cnt = (size_t)NL * n;
     pl.descs.assign(cnt, LevelDesc{});
-    for (auto *v : {&pl.oG, &pl.oL, &pl.oR, &pl.oD, &pl.oQ, &pl.oRec, &pl.oFuse, &pl.oSr})
+    for (auto *v : {&pl.oG, &pl.oL, &pl.oR, &pl.oD, &pl.oQ, &pl.oV, &pl.oRec, &pl.oFuse, &pl.oSr})
         v->assign(cnt, 0);
+    const int F = p.finest_level;
     Bump b;
     pl.off_desc = b.take(sizeof(LevelDesc) * cnt);
     pl.off_stages = b.take(sizeof(LaunchArgs) * 3 * NL);
@@ -213,7 +222,7 @@ void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, const Leve
     pl.off_bar = b.take(4 * sizeof(unsigned));
     for (int l = 0; l < NL; ++l) {
         const int chunk = search_chunk(P, cfg[l].passes);
-        int begin[W_COUNT] = {0, 0, 0};
+        int begin[W_COUNT] = {0, 0, 0, 0};
         pl.wmax[l] = 0;
         for (int i = 0; i < n; ++i) {
             const size_t k = (size_t)l * n + i;
@@ -225,10 +234,13 @@ void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, const Leve
             d.npy = num_origins(d.h, P, S, &d.kyreg);
             d.nchunks = (d.npx + chunk - 1) / chunk;
             d.tiles_x = (d.w + cfg[l].tile_w - 1) / cfg[l].tile_w;
+            const bool searched = l >= F;
             const int units[W_COUNT] = {
                 ((d.w + 63) / 64) * ((d.h + 31) / 32),             // pyramid: 64 x 32 tiles
-                d.npy * d.nchunks,                                // search: chunks of a patch row
-                d.tiles_x * ((d.h + cfg[l].tile_h - 1) / cfg[l].tile_h),  // fuse: pixel tiles
+                searched ? d.npy * d.nchunks : 0,                 // search: chunks of a patch row
+                searched ? d.tiles_x * ((d.h + cfg[l].tile_h - 1) / cfg[l].tile_h) : 0,  // fuse tiles
+                (l == 0 && F > 0)
+                    ? (int)(((size_t)d.w * d.h + kUpUnitPixels - 1) / kUpUnitPixels) : 0,  // upsample
             };
             for (int q = 0; q < W_COUNT; ++q) {
                 d.work_begin[q] = begin[q];
@@ -236,7 +248,8 @@ void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, const Leve
             }
             const size_t gp = align_up((size_t)d.w * esz, 128) / esz;
             d.gpitch = (int)gp;
-            pl.oG[k] = b.take(gp * esz * d.h);
+            if (searched) pl.oG[k] = b.take(gp * esz * d.h);
+            if (l == F && F > 0 && p.variance) pl.oV[k] = b.take(sizeof(float) * (size_t)d.w * d.h);
             if (l == 0) {
                 d.pitch = pairs[i].pitch;
             } else {
@@ -246,9 +259,11 @@ void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, const Leve
                 pl.oD[k] = b.take(sizeof(float) * (size_t)d.w * d.h);
                 pl.oQ[k] = b.take(sizeof(float) * (size_t)d.w * d.h);
             }
-            const size_t np = (size_t)d.npx * d.npy;
-            pl.oRec[k] = b.take(sizeof(bdis_patch_record) * np);
-            pl.oFuse[k] = b.take(sizeof(float4) * np);
+            const size_t np = searched ? (size_t)d.npx * d.npy : 0;
+            if (searched) {
+                pl.oRec[k] = b.take(sizeof(bdis_patch_record) * np);
+                pl.oFuse[k] = b.take(sizeof(float4) * np);
+            }
             pl.oSr[k] = b.take(sizeof(float));
         }
         for (int q = 0; q < W_COUNT; ++q) pl.units[l][q] = begin[q];
@@ -258,12 +273,13 @@ void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, const Leve
 
 // Phase 2: pointers, once the arena base is known.
 void plan_pointers(const bdis_params &p, int n, const bdis_pair *pairs, char *base, Plan &pl) {
-    const int NL = p.levels;
+    const int NL = p.levels, F = p.finest_level;
     for (int l = 0; l < NL; ++l)
         for (int i = 0; i < n; ++i) {
             const size_t k = (size_t)l * n + i;
             LevelDesc &d = pl.descs[k];
-            d.G = base + pl.oG[k];
+            const bool searched = l >= F;
+            d.G = searched ? base + pl.oG[k] : nullptr;
             if (l == 0) {
                 d.L = pairs[i].left;
                 d.R = pairs[i].right;
@@ -279,10 +295,22 @@ void plan_pointers(const bdis_params &p, int n, const bdis_pair *pairs, char *ba
                 d.disp = d.var = nullptr;
                 d.valid = nullptr;
             }
-            d.rec = (bdis_patch_record *)(base + pl.oRec[k]);
-            d.fuse = (float4 *)(base + pl.oFuse[k]);
+            if (l == F && F > 0) d.var = p.variance ? (float *)(base + pl.oV[k]) : nullptr;
+            d.rec = searched ? (bdis_patch_record *)(base + pl.oRec[k]) : nullptr;
+            d.fuse = searched ? (float4 *)(base + pl.oFuse[k]) : nullptr;
             d.sigma_r = (float *)(base + pl.oSr[k]);
             d.acc = (unsigned long long *)(base + pl.off_acc) + 3 * k;
+            d.Df = d.Vf = nullptr;
+            d.wf = d.hf = 0;
+        }
+    if (F > 0)
+        for (int i = 0; i < n; ++i) {
+            LevelDesc &d0 = pl.descs[(size_t)i];
+            const LevelDesc &df = pl.descs[(size_t)F * n + i];
+            d0.Df = df.D;
+            d0.Vf = df.var;
+            d0.wf = df.w;
+            d0.hf = df.h;
         }
     for (int l = 0; l < NL; ++l)
         for (int i = 0; i < n; ++i) {
@@ -410,8 +438,10 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
         stages.push_back(a);
         stage_itype.push_back(l == 0 ? in_type : st_type);
     }
-    for (int l = NL - 1; l >= 0; --l) {
+    const int F = p.finest_level;
+    for (int l = NL - 1; l >= F; --l) {
         LaunchArgs a = base_args(p, l, d_descs + (size_t)l * n, n);
+        a.img_type = l == 0 ? in_type : st_type;
         a.chunk = search_chunk(p.patch, cfg[l].passes);
         a.tile_w = cfg[l].tile_w;
         a.tile_h = cfg[l].tile_h;
@@ -427,6 +457,14 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
         stages.push_back(a);
         stage_itype.push_back(l == 0 ? in_type : st_type);
     }
+    if (F > 0) {
+        LaunchArgs a = base_args(p, 0, d_descs, n);
+        a.kind = 3;
+        a.total = pl.units[0][W_UP];
+        stages.push_back(a);
+        stage_itype.push_back(in_type);
+    }
+    for (auto &a : stages) a.pdl = h->use_pdl ? 1 : 0;
     // upload descriptors (and the stage list) unless identical to the last upload
     const size_t dbytes = sizeof(LevelDesc) * pl.descs.size();
     const size_t sbytes = sizeof(LaunchArgs) * stages.size();
@@ -434,7 +472,9 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
     std::vector<char> host((size_t)blob, 0);
     std::memcpy(host.data(), pl.descs.data(), dbytes);
     std::memcpy(host.data() + (pl.off_stages - pl.off_desc), stages.data(), sbytes);
-    const size_t tbytes = dbytes;
+    // graph key: descriptors and stage arguments (launch parameters are baked
+    // into a captured graph)
+    const std::vector<char> key = host;
     const bool same = h->last_upload.size() == host.size() &&
                       std::memcmp(h->last_upload.data(), host.data(), host.size()) == 0;
     if (!same) {
@@ -510,9 +550,12 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
                 const int grid = std::max(1, std::min(a.total, sm_count() * occ));
                 e = timed(BDIS_K_SEARCH, [&] { return launch_search(a, itype, st_type, sm, grid, st); });
                 if (e != cudaSuccess) return cuda_fail(h, e, "search launch");
-            } else {
+            } else if (a.kind == 2) {
                 e = timed(BDIS_K_FUSE, [&] { return launch_fuse(a, fsm[a.level], st); });
                 if (e != cudaSuccess) return cuda_fail(h, e, "fuse launch");
+            } else {
+                e = timed(BDIS_K_UPSAMPLE, [&] { return launch_upsample(a, st); });
+                if (e != cudaSuccess) return cuda_fail(h, e, "upsample launch");
             }
         }
         return BDIS_OK;
@@ -527,9 +570,7 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
             can_graph = false;
         cudaGetLastError();
     }
-    const bool graph_hit = can_graph && h->graph_exec != nullptr &&
-                           h->graph_descs.size() == tbytes &&
-                           std::memcmp(h->graph_descs.data(), pl.descs.data(), tbytes) == 0;
+    const bool graph_hit = can_graph && h->graph_exec != nullptr && h->graph_descs == key;
     if (graph_hit) {
         cudaError_t e = cudaGraphLaunch(h->graph_exec, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
@@ -559,8 +600,7 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
                 h->graph_exec = nullptr;
                 return cuda_fail(h, e2, "cudaGraphInstantiate");
             }
-            h->graph_descs.assign((const char *)pl.descs.data(),
-                                  (const char *)pl.descs.data() + tbytes);
+            h->graph_descs = key;
             e2 = cudaGraphLaunch(h->graph_exec, st);
             if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaGraphLaunch");
         }
@@ -599,7 +639,9 @@ bdis_status autotune(bdis_handle *h, int n, const bdis_pair *pairs, int in_type,
         const size_t m0 = h->ev_marks.size();
         s = run_cfg(h, n, pairs, in_type, st, cfg.data(), false, true);
         if (s != BDIS_OK) return s;
-        // marks in launch order: NL pyramids, then (search, fuse) for l = NL-1 .. 0
+        // marks in launch order: NL pyramids, then (search, fuse) for l = NL-1 .. F,
+        // then the upsampling when F > 0
+        const int F = h->p.finest_level;
         for (size_t m = m0; m < h->ev_marks.size(); ++m) {
             float ms = 0.f;
             const size_t ev = h->ev_marks[m].second;
@@ -607,14 +649,14 @@ bdis_status autotune(bdis_handle *h, int n, const bdis_pair *pairs, int in_type,
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, h->ev_pool[ev], h->ev_pool[ev + 1]);
             if (e != cudaSuccess) return cuda_fail(h, e, "autotune events");
             const int idx = (int)(m - m0);
-            if (idx < NL) continue;
+            if (idx < NL || idx - NL >= 2 * (NL - F)) continue;
             const int l = NL - 1 - (idx - NL) / 2;
             if ((idx - NL) % 2 == 0) tsearch[c][l] = ms; else tfuse[c][l] = ms;
         }
         h->ev_marks.resize(m0);
     }
     best.assign((size_t)NL, kDefaultCfg);
-    for (int l = 0; l < NL; ++l) {
+    for (int l = h->p.finest_level; l < NL; ++l) {
         int bs = 0, bf = 0;
         for (int c = 1; c < 3; ++c) {
             if (tsearch[c][l] < tsearch[bs][l]) bs = c;
@@ -720,6 +762,9 @@ void bdis_default_params(bdis_params *p) {
     p->hess_eps = 1e-4f;
     p->use_sgmm = 1;
     p->use_c2f = 1;
+    p->weight_mode = BDIS_WEIGHT_BDIS;
+    p->finest_level = 0;
+    p->fast_exp = 0;
 }
 
 bdis_status bdis_create(const bdis_params *p, bdis_handle **out) {
@@ -769,6 +814,10 @@ bdis_status bdis_set_option(bdis_handle *h, int option, int value) {
     if (option == BDIS_OPT_FORM) {
         if (value < 0 || value > 2) return fail(h, BDIS_EINVAL, "form must be 0, 1 or 2");
         h->form = value;
+        return BDIS_OK;
+    }
+    if (option == BDIS_OPT_PDL) {
+        h->use_pdl = value != 0;
         return BDIS_OK;
     }
     return fail(h, BDIS_EINVAL, "unknown option");
@@ -903,6 +952,7 @@ bdis_status bdis_get_stats(bdis_handle *h, bdis_stats *out, void *stream) {
     for (int l = 0; l < h->levels; ++l) {
         for (int i = 0; i < h->npairs; ++i) {
             const LevelDesc &d = h->descs[(size_t)l * h->npairs + i];
+            if (d.rec == nullptr) continue;  // below the finest processed level
             const size_t np = (size_t)d.npx * d.npy;
             recs.resize(np);
             e = cudaMemcpy(recs.data(), d.rec, sizeof(bdis_patch_record) * np, cudaMemcpyDeviceToHost);
@@ -939,6 +989,16 @@ bdis_status bdis_copy(void *dst, const void *src, size_t bytes, void *stream) {
     return BDIS_OK;
 }
 
+bdis_status bdis_depth(const float *disp, const float *var, long long n, float fb, float *depth,
+                       float *depth_var, void *stream) {
+    if (n < 0 || !(std::isfinite(fb) && fb > 0.f)) return BDIS_EINVAL;
+    if (n == 0) return BDIS_OK;
+    if (!disp || !depth) return BDIS_EINVAL;
+    if ((var == nullptr) != (depth_var == nullptr)) return BDIS_EINVAL;
+    return launch_depth(disp, var, n, fb, depth, depth_var, (cudaStream_t)stream) == cudaSuccess
+               ? BDIS_OK : BDIS_ECUDA;
+}
+
 bdis_status bdis_match_batched_f32(bdis_handle *h, int n, const bdis_pair_f32 *pairs,
                                    void *stream) {
     if (!h) return BDIS_EINVAL;
@@ -971,6 +1031,10 @@ bdis_status grad_setup(bdis_handle *h, const bdis_grad *g, bool need_loss, cudaS
     if (h->npairs < 1 || h->in_type != E_F32)
         return fail(h, BDIS_EINVAL, "no float-image forward to differentiate (call bdis_match_f32)");
     const bdis_params &p = h->p;
+    if (p.finest_level != 0 || p.weight_mode != BDIS_WEIGHT_BDIS || p.fast_exp != 0)
+        return fail(h, BDIS_EUNSUPPORTED,
+                    "the adjoint covers the default fusion at full resolution "
+                    "(finest_level 0, BDIS weights, exact exponential)");
     const int n = h->npairs;
     for (int i = 0; i < n; ++i) {
         if (!g[i].g_disp || !g[i].g_left || !g[i].g_right)

@@ -17,6 +17,17 @@ __device__ __forceinline__ void stf(__half *p, float v) { *p = __float2half_rn(v
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialisation may start while its predecessor on the stream still runs;
+// pdl_wait() returns once the predecessor has completed and its memory is
+// visible (at once when there is no programmatic predecessor), so it comes
+// before the first global-memory access.  pdl_release() lets the next
+// kernel of the stream be scheduled early (it still waits in pdl_wait()).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // reflect about the edge pixel without repeating it (-1 -> 1, n -> n-2); n >= 3
 __device__ __forceinline__ int refl(int i, int n) {
     i = i < 0 ? -i : i;

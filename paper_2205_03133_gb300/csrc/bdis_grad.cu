@@ -102,7 +102,7 @@ __device__ float weight_sum(const GradDesc &g, const GradArgs &a, int x, int y) 
             const int kx = (kxlo + ix <= kxhi) ? kxlo + ix : g.npx - 1;
             const int ox = origin(kx, g.w, P, S, g.kxreg);
             const float4 f = __ldg(g.fuse + (size_t)ky * g.npx + kx);
-            if (f.w == 0.f) continue;
+            if (!(f.y > 0.f)) continue;  // rejected patch (rho = 0)
             sw += f.y * (my * (a.use_sgmm ? a.m[x - ox] : 1.f));
         }
     }

@@ -19,7 +19,9 @@ constexpr int kWindow = 5;  // samples of the small window P' (Sec. III-B, s = 5
 
 // Work spaces of the per-level kernels.  Each (pair, level) owns the
 // half-open unit range [work_begin[k], work_begin[k] + units) of kernel k.
-enum WorkKind { W_PYR = 0, W_SEARCH = 1, W_FUSE = 2, W_COUNT = 3 };
+enum WorkKind { W_PYR = 0, W_SEARCH = 1, W_FUSE = 2, W_UP = 3, W_COUNT = 4 };
+// Pixels per unit of the full-resolution upsampling (256 threads x 4).
+constexpr int kUpUnitPixels = 1024;
 
 // Largest pixel tile of the fused posterior / densify kernel.
 constexpr int kFuseTileWMax = 64;
@@ -47,10 +49,13 @@ struct alignas(16) LevelDesc {
     void *Ln, *Rn;            // next coarser level to build (nullptr at the coarsest)
     float *D, *Q;             // fused disparity / probability maps (levels >= 1)
     const float *Dc, *Qc;     // coarser fused maps (nullptr at the coarsest level)
-    float *disp, *var;        // finest-level outputs (var may be nullptr)
+    float *disp, *var;        // level-0 outputs (var may be nullptr); at the finest
+                              // processed level f > 0, var is its V map
     uint8_t *valid;
+    const float *Df, *Vf;     // level 0 with f > 0: the level-f maps to upsample
+    int wf, hf;               // their size
     bdis_patch_record *rec;   // npx * npy records of this pair at this level
-    float4 *fuse;             // (d, rho, sig2, kept) per patch for the fusion gather
+    float4 *fuse;             // (d, rho, sig2, mu) per patch for the fusion gather (rho = 0: rejected)
     float *sigma_r;           // one float
     unsigned long long *acc;  // sigma_r sums of kept patches: E(0) * 2^16, count, E(0)^2
     int w, h, pitch;          // level size, row pitch (elements) of L and R
@@ -88,7 +93,13 @@ struct LaunchArgs {
     float m[kMaxPatch];       // 1D sGMM factors m[a] (Eq. 8 is separable)
     unsigned long long *acc_zero;  // finest pyramid launch: accumulators to clear
     int acc_count;
-    int kind;                 // stage of the persistent form: 0 pyramid, 1 search, 2 fuse
+    int kind;                 // stage of the persistent form: 0 pyramid, 1 search, 2 fuse,
+                              // 3 upsample
+    int finest;               // finest processed level f
+    int weight_mode;          // bdis_weight_mode
+    int fast_exp;             // Schraudolph exponential in the posterior
+    int img_type;             // ElemType of this level's L, R (read by the DIS fusion)
+    int pdl;                  // launch with programmatic stream serialisation
 };
 
 // Persistent form: every stage of a call in one cooperative launch, with a
@@ -147,6 +158,9 @@ cudaError_t launch_pyramid(const LaunchArgs &a, int in_type, int out_type, cudaS
 cudaError_t launch_search(const LaunchArgs &a, int in_type, int g_type, size_t smem, int grid,
                           cudaStream_t s);
 cudaError_t launch_fuse(const LaunchArgs &a, size_t smem, cudaStream_t s);
+cudaError_t launch_upsample(const LaunchArgs &a, cudaStream_t s);
+cudaError_t launch_depth(const float *disp, const float *var, long long n, float fb, float *depth,
+                         float *depth_var, cudaStream_t s);
 // Shared-memory layout of the search (band pitch and capacity, chunk pitch, bytes).
 void search_layout(int P, int S, float tau, float window_step, int passes, int &band_pitch,
                    int &band_cap, int &chunk_pitch, size_t &bytes);

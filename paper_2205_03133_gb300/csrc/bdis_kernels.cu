@@ -15,7 +15,9 @@
 //               coarse-to-fine rho (Eq. 10-11) and PDF fit (Eq. 14-16) of the
 //               patches overlapping the tile, then the sGMM fusion gather
 //               (Eq. 8-9, Eq. 12) and pixel variance (Eq. 17)
+#include <algorithm>
 #include <cfloat>
+#include <cstring>
 #include <cmath>
 
 #include "bdis_device.cuh"
@@ -74,8 +76,8 @@ __device__ __forceinline__ void pyramid_unit(const LaunchArgs &a, int unit, floa
         }
     }
     __syncthreads();
-    TO *G = (TO *)D.G;
-    for (int i = threadIdx.x; i < kPyrTW * kPyrTH; i += blockDim.x) {
+    TO *G = (TO *)D.G;  // nullptr below the finest processed level
+    for (int i = threadIdx.x; G != nullptr && i < kPyrTW * kPyrTH; i += blockDim.x) {
         const int ly = i / kPyrTW, lx = i - ly * kPyrTW;
         const int x = x0 + 2 + lx, y = y0 + 2 + ly;
         if (x >= w || y >= h) continue;
@@ -114,11 +116,13 @@ template <typename TI, typename TO>
 __global__ void __launch_bounds__(256) k_pyramid(LaunchArgs a) {
     __shared__ float Ls[kPyrSH][kPyrSW];
     __shared__ float Rs[kPyrSH][kPyrSW];
+    pdl_wait();
     // the finest pyramid launch runs before every search: it clears the
     // sigma_r accumulators of all levels and pairs
     if (blockIdx.x == 0 && a.acc_zero != nullptr)
         for (int i = threadIdx.x; i < a.acc_count; i += blockDim.x) a.acc_zero[i] = 0ull;
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) pyramid_unit<TI, TO>(a, unit, Ls, Rs);
+    pdl_release();
 }
 
 // ---------------------------------------------------------------- patch search
@@ -401,11 +405,12 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
             for (int k = 0; k < 5; ++k) rec.E[k] = E[k];
             rec.cT = cT;
             rec.flags = f;
-            rec.nout = nout_all;
+            rec.nout = (uint16_t)nout_all;
+            rec.pdf_flags = 0;
             rec.pi = 0.f;
             rec.rho = 0.f;
             rec.sig2 = 0.f;
-            rec.pdf_flags = 0u;
+            rec.mu = mean0;
             D.rec[(size_t)py * D.npx + kx] = rec;
             const bool kept = f == 0u;
             pe[3 * kk] = kept ? E[0] : 0.f;
@@ -441,7 +446,9 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
 template <int P, typename TI, typename TG>
 __global__ void __launch_bounds__(256) k_search(LaunchArgs a) {
     extern __shared__ float smem[];
+    pdl_wait();
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) search_unit<P, TI, TG>(a, unit, smem);
+    pdl_release();
 }
 
 // ---------------------------------------------------------------- posterior, fusion
@@ -517,6 +524,26 @@ __device__ float pdf_fit(const float lnp[5], const float dlt[5], int iters, floa
     return s * s;
 }
 
+// A pixel of an image whose element type is known only at run time.
+__device__ __forceinline__ float ld_typed(const void *p, size_t i, int t) {
+    if (t == E_U8) return (float)__ldg((const uint8_t *)p + i);
+    if (t == E_F16) return __half2float(__ldg((const __half *)p + i));
+    return __ldg((const float *)p + i);
+}
+
+// Schraudolph's exponential (Neural Computation 11(4), 1999) in single
+// precision: the bits of the binary32 result are the integer
+// A y + (B - C), A = 2^23 / ln 2, B = 127 * 2^23, C = 8 * 60801 (the paper's
+// RMS-optimal correction moved to the 23-bit fraction), truncated.  Within
+// about 4 % of exp(y); 0 below y = -87.
+__device__ __forceinline__ float exp_schraudolph(float y) {
+    if (y < -87.f) return 0.f;
+    y = fminf(y, 88.f);
+    const float A = 12102203.161561485f;        // 2^23 / ln 2
+    const float BC = 1065353216.f - 486408.f;   // 127 * 2^23 - 8 * 60801
+    return __int_as_float((int)floorf(fmaf(A, y, BC)));
+}
+
 // One thread per patch of a tile's patch set: pi_k = p_0 / sum_i p_i with
 // p_i = exp(-E_i/(2 sigma_r^2 s^2)), rho_k = Gamma_n pi_k + Q^(n+1)(centre),
 // and at the finest level with variance on the PDF fit.
@@ -528,16 +555,17 @@ __device__ float4 posterior_of(const LaunchArgs &a, const LevelDesc &D, int kx, 
     // the same (persistent) launch
     const float4 r0 = __ldcg((const float4 *)rec);       // d, dinit, dlast, H
     const float4 r1 = __ldcg((const float4 *)rec + 1);   // E0, dE1, dE2, dE3
-    const float4 r2 = __ldcg((const float4 *)rec + 2);   // dE4, cT, flags, nout
+    const float4 r2 = __ldcg((const float4 *)rec + 2);   // dE4, cT, flags, nout | pdf_flags
     const uint32_t flags = __float_as_uint(r2.z);
     if (flags != 0u) {
         if (write) {
             rec->pi = rec->rho = rec->sig2 = 0.f;
-            rec->pdf_flags = 0u;
+            rec->pdf_flags = 0;
             D.fuse[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         return make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    const float mu = __ldcg(&rec->mu);
     const float h = a.window_step;
     const float dlt[5] = {0.f, -h, h, -2.f * h, 2.f * h};
     const float scale = 2.f * sr * sr * (float)(kWindow * kWindow);
@@ -550,7 +578,16 @@ __device__ float4 posterior_of(const LaunchArgs &a, const LevelDesc &D, int kx, 
         e[i] = -dE[i] / scale;
         Z += expf(e[i]);
     }
-    const float pi = 1.f / Z;
+    // pi = p_0 / sum_i p_i; with fast_exp every p_i (p_0 included) is
+    // Schraudolph's approximation; the PDF fit keeps the exact log-probabilities
+    float pi = 1.f / Z;
+    if (a.fast_exp) {
+        const float p0 = exp_schraudolph(0.f);
+        float Zf = p0;
+#pragma unroll
+        for (int i = 1; i < 5; ++i) Zf += exp_schraudolph(e[i]);
+        pi = p0 / Zf;
+    }
     float rho;
     if (a.use_c2f) {
         float prop = 0.f;
@@ -565,19 +602,20 @@ __device__ float4 posterior_of(const LaunchArgs &a, const LevelDesc &D, int kx, 
     }
     float sig2 = 0.f;
     uint32_t pf = 0u;
-    if (a.level == 0 && a.variance) {
+    if (a.level == a.finest && a.variance) {
         const float lnZ = logf(Z);
         float lnp[5];
 #pragma unroll
         for (int i = 0; i < 5; ++i) lnp[i] = e[i] - lnZ;
         sig2 = pdf_fit(lnp, dlt, a.pdf_iters, a.pdf_resid, a.tau0, pf);
     }
-    const float4 fz = make_float4(r0.x, rho, sig2, 1.f);
+    // .w: the mean offset, read by the DIS-weighted fusion
+    const float4 fz = make_float4(r0.x, rho, sig2, mu);
     if (write) {
         rec->pi = pi;
         rec->rho = rho;
         rec->sig2 = sig2;
-        rec->pdf_flags = pf;
+        rec->pdf_flags = (uint16_t)pf;
         D.fuse[k] = fz;
     }
     return fz;
@@ -680,6 +718,77 @@ __device__ __forceinline__ void fuse_unit(const LaunchArgs &a, int unit, float4 
     }
     __syncthreads();
 
+    // one fused pixel: D = sum omega d / sum omega, Q = sum omega rho / sum omega,
+    // V = sum omega^2 sig2 / (sum omega)^2
+    auto emit = [&](int x, int y, float swd, float sw, float swr, float sw2) {
+        const size_t idx = (size_t)y * D.w + x;
+        const bool any = sw > 0.f;
+        float Dv, Qv, Vv;
+        if (any) {
+            Dv = swd / sw;
+            Qv = swr / sw;
+            Vv = sw2 / (sw * sw);
+        } else {
+            Dv = D.Dc != nullptr ? 2.f * coarse_bilin(D.Dc, D.wc, D.hc, (float)x, (float)y) : 0.f;
+            Qv = 0.f;
+            Vv = 0.f;
+        }
+        const float qnan = __int_as_float(0x7fc00000);
+        if (a.level == a.finest) {
+            const bool ok = any && Qv >= a.pix_thresh;
+            if (a.level == 0) {
+                D.valid[idx] = ok ? 1 : 0;
+                D.disp[idx] = ok ? Dv : qnan;
+                if (D.var != nullptr && a.variance) D.var[idx] = ok ? Vv : qnan;
+            } else {
+                // level-f maps for the full-resolution upsampling (NaN = invalid)
+                D.D[idx] = ok ? Dv : qnan;
+                if (D.var != nullptr && a.variance) D.var[idx] = Vv;
+            }
+        } else {
+            D.D[idx] = Dv;
+            D.Q[idx] = Qv;
+        }
+    };
+
+    if (a.weight_mode == BDIS_WEIGHT_DIS) {
+        // Eq. 2 weights depend on the pixel: direct gather over the covering
+        // patches, omega = 1 / max(1, (I_r(x - d) - I_l(x) - mu)^2)
+        for (int pix = threadIdx.x; pix < TW * TH; pix += blockDim.x) {
+            const int c = pix % TW, r = pix / TW;
+            const int x = x0 + c, y = y0 + r;
+            if (x > x1 || y > y1) continue;
+            const size_t row = (size_t)y * D.pitch;
+            const float Il = ld_typed(D.L, row + x, a.img_type);
+            const int cntx = cxn[c], lox = cxlo[c], nrx = cxr[c];
+            const int cnty = cyn[r], loy = cylo[r], nry = cyr[r];
+            float swd = 0.f, sw = 0.f, swr = 0.f, sw2 = 0.f;
+            for (int qy = 0; qy < cnty; ++qy) {
+                const int ly = qy < nry ? loy + qy : nky - 1;
+                for (int qx = 0; qx < cntx; ++qx) {
+                    const int lx = qx < nrx ? lox + qx : nkx - 1;
+                    const float4 f = fz[ly * nkx + lx];
+                    if (!(f.y > 0.f)) continue;  // rejected patch
+                    const float X = fminf(fmaxf((float)x - f.x, 0.f), (float)(D.w - 1));
+                    const int xa = (int)floorf(X);
+                    const int xb = min(xa + 1, D.w - 1);
+                    const float t = X - (float)xa;
+                    const float ra = ld_typed(D.R, row + xa, a.img_type);
+                    const float rb = ld_typed(D.R, row + xb, a.img_type);
+                    const float res = fmaf(t, rb - ra, ra) - Il - f.w;
+                    const float om = 1.f / fmaxf(res * res, 1.f);
+                    swd = fmaf(om, f.x, swd);
+                    sw += om;
+                    swr = fmaf(om, f.y, swr);
+                    sw2 = fmaf(om * om, f.z, sw2);
+                }
+            }
+            emit(x, y, swd, sw, swr, sw2);
+        }
+        __syncthreads();
+        return;
+    }
+
     // pass 1: per tile column x and patch row iy, sums over the covering columns
     float4 *csum = fz + nkx * nky;  // [nky][TW] of (sum m rho d, sum m rho, sum m rho^2, sum m^2 rho^2 sig2)
     for (int i = threadIdx.x; i < nky * TW; i += blockDim.x) {
@@ -715,34 +824,80 @@ __device__ __forceinline__ void fuse_unit(const LaunchArgs &a, int unit, float4 
             swr = fmaf(my, cs.z, swr);
             sw2 = fmaf(my * my, cs.w, sw2);
         }
-        const size_t idx = (size_t)y * D.w + x;
-        const bool any = sw > 0.f;
-        float Dv, Qv, Vv;
-        if (any) {
-            Dv = swd / sw;
-            Qv = swr / sw;
-            Vv = sw2 / (sw * sw);
-        } else {
-            Dv = D.Dc != nullptr ? 2.f * coarse_bilin(D.Dc, D.wc, D.hc, (float)x, (float)y) : 0.f;
-            Qv = 0.f;
-            Vv = 0.f;
-        }
-        if (a.level == 0) {
-            const bool ok = any && Qv >= a.pix_thresh;
-            D.valid[idx] = ok ? 1 : 0;
-            D.disp[idx] = ok ? Dv : __int_as_float(0x7fc00000);
-            if (D.var != nullptr && a.variance) D.var[idx] = ok ? Vv : __int_as_float(0x7fc00000);
-        } else {
-            D.D[idx] = Dv;
-            D.Q[idx] = Qv;
-        }
+        emit(x, y, swd, sw, swr, sw2);
     }
     __syncthreads();
     }
 
+// Full-resolution output from the finest processed level f > 0: a unit is
+// kUpUnitPixels consecutive level-0 pixels of one pair.  Level-f coordinate
+// X = (x + 0.5) / 2^f - 0.5 (clamped), disp = 2^f bilinear(D_f),
+// var = 4^f bilinear(V_f); valid iff every level-f pixel with a non-zero
+// bilinear weight is valid (not NaN in D_f).
+__device__ __forceinline__ void upsample_unit(const LaunchArgs &a, int unit) {
+    const LevelDesc &D = a.descs[find_pair(a.descs, a.npairs, unit, W_UP)];
+    const int u = unit - D.work_begin[W_UP];
+    const float sc = (float)(1 << a.finest), inv = 1.f / sc;  // exact (power of two)
+    const long long npix = (long long)D.w * D.h;
+    const float qnan = __int_as_float(0x7fc00000);
+    for (int i = threadIdx.x; i < kUpUnitPixels; i += blockDim.x) {
+        const long long pix = (long long)u * kUpUnitPixels + i;
+        if (pix >= npix) break;
+        const int y = (int)(pix / D.w), x = (int)(pix - (long long)y * D.w);
+        const float X = fminf(fmaxf(((float)x + 0.5f) * inv - 0.5f, 0.f), (float)(D.wf - 1));
+        const float Y = fminf(fmaxf(((float)y + 0.5f) * inv - 0.5f, 0.f), (float)(D.hf - 1));
+        const int xa = (int)floorf(X), ya = (int)floorf(Y);
+        const int xb = min(xa + 1, D.wf - 1), yb = min(ya + 1, D.hf - 1);
+        const float fx = X - (float)xa, fy = Y - (float)ya;
+        const int xs[4] = {xa, xb, xa, xb}, ys[4] = {ya, ya, yb, yb};
+        const float wt[4] = {(1.f - fx) * (1.f - fy), fx * (1.f - fy), (1.f - fx) * fy, fx * fy};
+        bool ok = true;
+        float dv = 0.f, vv = 0.f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (wt[k] == 0.f) continue;
+            const size_t j = (size_t)ys[k] * D.wf + xs[k];
+            const float dk = __ldcg(D.Df + j);
+            ok = ok && !isnan(dk);
+            dv = fmaf(wt[k], dk, dv);
+            if (D.Vf != nullptr) vv = fmaf(wt[k], __ldcg(D.Vf + j), vv);
+        }
+        D.valid[pix] = ok ? 1 : 0;
+        D.disp[pix] = ok ? sc * dv : qnan;
+        if (D.var != nullptr && a.variance) D.var[pix] = (ok && D.Vf != nullptr) ? sc * sc * vv : qnan;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_upsample(LaunchArgs a) {
+    pdl_wait();
+    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) upsample_unit(a, unit);
+    pdl_release();
+}
+
+// Depth (Eq. 13) and its variance (the depth factor of Eq. 17), elementwise.
+__global__ void __launch_bounds__(256) k_depth(const float *__restrict__ disp,
+                                               const float *__restrict__ var, long long n, float fb,
+                                               float *__restrict__ depth,
+                                               float *__restrict__ depth_var) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const float qnan = __int_as_float(0x7fc00000);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float d = __ldg(disp + i);
+        const bool ok = d > 0.f;  // false for NaN
+        const float z = fb / d;
+        depth[i] = ok ? z : qnan;
+        if (depth_var != nullptr) {
+            const float zd = z / d;  // fb / d^2
+            depth_var[i] = ok ? zd * zd * __ldg(var + i) : qnan;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_fuse(LaunchArgs a) {
     extern __shared__ float4 fz[];
+    pdl_wait();
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) fuse_unit(a, unit, fz);
+    pdl_release();
 }
 
 // ---------------------------------------------------------------- persistent form
@@ -802,8 +957,10 @@ __global__ void __launch_bounds__(256) k_mega(MegaArgs m) {
             } else {
                 for (int u = blockIdx.x; u < total; u += gridDim.x) search_unit<P, TG, TG>(a, u, smem);
             }
-        } else {
+        } else if (a.kind == 2) {
             for (int u = blockIdx.x; u < total; u += gridDim.x) fuse_unit(a, u, (float4 *)smem);
+        } else {
+            for (int u = blockIdx.x; u < total; u += gridDim.x) upsample_unit(a, u);
         }
         if (s + 1 < m.nstages) grid_barrier(m.bar, m.err);
     }
@@ -955,29 +1112,59 @@ int search_occupancy(int P, int in_type, int g_type, size_t smem_bytes) {
     return nb > 0 ? nb : 1;
 }
 
+namespace {
+// One 256-thread launch of a LaunchArgs kernel; with a.pdl the launch allows
+// programmatic stream serialisation (the kernel waits in pdl_wait()).
+cudaError_t launch_args_kernel(const void *f, const LaunchArgs &a, int grid, size_t smem,
+                               cudaStream_t s) {
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = a.pdl ? 1 : 0;
+    void *args[] = {(void *)&a};
+    return cudaLaunchKernelExC(&cfg, f, args);
+}
+}  // namespace
+
 cudaError_t launch_pyramid(const LaunchArgs &a, int in_type, int out_type, cudaStream_t s) {
-    const int grid = grid_for(a.total, 8);
+    const void *f = nullptr;
     if (out_type == E_F32) {
-        if (in_type == E_U8) k_pyramid<uint8_t, float><<<grid, 256, 0, s>>>(a);
-        else k_pyramid<float, float><<<grid, 256, 0, s>>>(a);
+        f = in_type == E_U8 ? (const void *)k_pyramid<uint8_t, float> : (const void *)k_pyramid<float, float>;
     } else {
-        if (in_type == E_U8) k_pyramid<uint8_t, __half><<<grid, 256, 0, s>>>(a);
-        else if (in_type == E_F32) k_pyramid<float, __half><<<grid, 256, 0, s>>>(a);
-        else k_pyramid<__half, __half><<<grid, 256, 0, s>>>(a);
+        f = in_type == E_U8    ? (const void *)k_pyramid<uint8_t, __half>
+            : in_type == E_F32 ? (const void *)k_pyramid<float, __half>
+                               : (const void *)k_pyramid<__half, __half>;
     }
-    return cudaGetLastError();
+    return launch_args_kernel(f, a, grid_for(a.total, 8), 0, s);
 }
 
 cudaError_t launch_search(const LaunchArgs &a, int in_type, int g_type, size_t smem, int grid,
                           cudaStream_t s) {
     const void *f = search_kernel(a.P, in_type, g_type);
     if (f == nullptr) return cudaErrorInvalidValue;
-    void *args[] = {(void *)&a};
-    return cudaLaunchKernel(f, dim3(grid), dim3(256), args, smem, s);
+    return launch_args_kernel(f, a, grid, smem, s);
 }
 
 cudaError_t launch_fuse(const LaunchArgs &a, size_t smem, cudaStream_t s) {
-    k_fuse<<<grid_for(a.total, 8), 256, smem, s>>>(a);
+    return launch_args_kernel((const void *)k_fuse, a, grid_for(a.total, 8), smem, s);
+}
+
+cudaError_t launch_upsample(const LaunchArgs &a, cudaStream_t s) {
+    return launch_args_kernel((const void *)k_upsample, a, grid_for(a.total, 8), 0, s);
+}
+
+cudaError_t launch_depth(const float *disp, const float *var, long long n, float fb, float *depth,
+                         float *depth_var, cudaStream_t s) {
+    const long long blocks = (n + 255) / 256;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(blocks, (long long)num_sms() * 8));
+    k_depth<<<grid, 256, 0, s>>>(disp, var, n, fb, depth, depth_var);
     return cudaGetLastError();
 }
 

@@ -80,6 +80,9 @@ bool na_params_ok(const bdis_params &p) {
     if (p.storage != BDIS_STORE_F32 && p.storage != BDIS_STORE_F16) return false;
     if (!(fin(p.hess_eps) && p.hess_eps >= 0.f)) return false;
     if ((p.use_sgmm != 0 && p.use_sgmm != 1) || (p.use_c2f != 0 && p.use_c2f != 1)) return false;
+    if (p.weight_mode != BDIS_WEIGHT_BDIS && p.weight_mode != BDIS_WEIGHT_DIS) return false;
+    if (p.finest_level < 0 || p.finest_level >= p.levels || (p.fast_exp != 0 && p.fast_exp != 1))
+        return false;
     return true;
 }
 
@@ -113,6 +116,8 @@ extern "C" bdis_status bdis_match_noalloc(const bdis_params *pp, const uint8_t *
     if (w < 1 || hgt < 1 || w > 32768 || hgt > 32768 || pitch < w) return BDIS_EINVAL;
     const int NL = p.levels, P = p.patch, S = p.stride;
     if (na_level_dim(w, NL - 1) < P || na_level_dim(hgt, NL - 1) < P) return BDIS_EINVAL;
+    // full resolution only: the upsampled form (finest_level > 0) needs bdis_match
+    if (p.finest_level != 0) return BDIS_EUNSUPPORTED;
 
     // ---- layout inside the scratch array (no heap use)
     DescTable tab;
@@ -244,6 +249,10 @@ extern "C" bdis_status bdis_match_noalloc(const bdis_params *pp, const uint8_t *
     a.pdf_resid = p.pdf_resid;
     a.use_c2f = p.use_c2f;
     a.use_sgmm = p.use_sgmm;
+    a.weight_mode = p.weight_mode;
+    a.fast_exp = p.fast_exp;
+    a.finest = 0;
+    a.pdl = 1;  // each launch may start while its predecessor drains
     a.chunk = chunk;
     a.tile_w = cfg.tile_w;
     a.tile_h = cfg.tile_h;
@@ -274,6 +283,7 @@ extern "C" bdis_status bdis_match_noalloc(const bdis_params *pp, const uint8_t *
         a.chunk_pitch = chunk_pitch;
         a.total = units[l][W_SEARCH];
         const int itype = l == 0 ? E_U8 : st_type;
+        a.img_type = itype;
         int occ = search_occupancy(P, itype, st_type, smem);
         if (occ < 1) occ = 1;
         const int grid = a.total < sms * occ ? a.total : sms * occ;

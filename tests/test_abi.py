@@ -75,3 +75,27 @@ def test_host_side_argument_checks(lib):
     # level views before any call
     v = B.bdis_level_view()
     assert lib.bdis_level_view_get(m._h, 0, 0, C.byref(v)) == B.BDIS_EINVAL
+
+
+def test_mode_parameter_checks(lib):
+    import paper_2205_03133_gb300 as bd
+    for bad in (dict(weight_mode=2), dict(finest_level=3), dict(finest_level=-1), dict(fast_exp=2)):
+        with pytest.raises(bd.BdisError):
+            bd.BDIS(levels=3, **bad)
+    m = bd.BDIS(levels=6, patch=10, stride=4, finest_level=1, weight_mode="dis", fast_exp=1)
+    p = bd.B.bdis_params()
+    assert lib.bdis_get_params(m._h, C.byref(p)) == 0
+    assert (p.finest_level, p.weight_mode, p.fast_exp) == (1, 1, 1)
+    d = bd.default_params()
+    assert (d.finest_level, d.weight_mode, d.fast_exp) == (0, 0, 0)
+
+
+def test_depth_argument_checks(lib):
+    from paper_2205_03133_gb300 import _binding as B
+    # rejected before any CUDA call
+    assert lib.bdis_depth(16, None, 10, C.c_float(0.0), 16, None, None) == B.BDIS_EINVAL
+    assert lib.bdis_depth(16, None, 10, C.c_float(float("nan")), 16, None, None) == B.BDIS_EINVAL
+    assert lib.bdis_depth(16, None, -1, C.c_float(1.0), 16, None, None) == B.BDIS_EINVAL
+    assert lib.bdis_depth(None, None, 10, C.c_float(1.0), 16, None, None) == B.BDIS_EINVAL
+    assert lib.bdis_depth(16, 16, 10, C.c_float(1.0), 16, None, None) == B.BDIS_EINVAL
+    assert lib.bdis_depth(None, None, 0, C.c_float(1.0), None, None, None) == B.BDIS_OK
