@@ -444,7 +444,7 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
     }
 
 template <int P, typename TI, typename TG>
-__global__ void __launch_bounds__(256) k_search(LaunchArgs a) {
+__global__ void __launch_bounds__(256, (P <= 8 ? 4 : P <= 12 ? 3 : 2)) k_search(LaunchArgs a) {
     extern __shared__ float smem[];
     pdl_wait();
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) search_unit<P, TI, TG>(a, unit, smem);
@@ -875,21 +875,41 @@ __global__ void __launch_bounds__(256) k_upsample(LaunchArgs a) {
 }
 
 // Depth (Eq. 13) and its variance (the depth factor of Eq. 17), elementwise.
+__device__ __forceinline__ void depth_px(float d, float v, float fb, float &z, float &zv) {
+    const bool ok = d > 0.f;  // false for NaN
+    const float q = fb / d;
+    const float qd = q / d;   // fb / d^2
+    z = ok ? q : __int_as_float(0x7fc00000);
+    zv = ok ? qd * qd * v : __int_as_float(0x7fc00000);
+}
+
+// 16-byte vectors when every pointer allows it (the common case), scalars
+// for the tail; grid-strided so each thread keeps several loads in flight.
 __global__ void __launch_bounds__(256) k_depth(const float *__restrict__ disp,
                                                const float *__restrict__ var, long long n, float fb,
                                                float *__restrict__ depth,
                                                float *__restrict__ depth_var) {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    const float qnan = __int_as_float(0x7fc00000);
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float d = __ldg(disp + i);
-        const bool ok = d > 0.f;  // false for NaN
-        const float z = fb / d;
-        depth[i] = ok ? z : qnan;
-        if (depth_var != nullptr) {
-            const float zd = z / d;  // fb / d^2
-            depth_var[i] = ok ? zd * zd * __ldg(var + i) : qnan;
-        }
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool hv = depth_var != nullptr;
+    const uintptr_t al = (uintptr_t)disp | (uintptr_t)depth | (uintptr_t)var | (uintptr_t)depth_var;
+    const long long n4 = (al & 15u) == 0 ? n / 4 : 0;
+    for (long long i = tid; i < n4; i += stride) {
+        const float4 d = __ldg((const float4 *)disp + i);
+        const float4 v = hv ? __ldg((const float4 *)var + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 z, zv;
+        depth_px(d.x, v.x, fb, z.x, zv.x);
+        depth_px(d.y, v.y, fb, z.y, zv.y);
+        depth_px(d.z, v.z, fb, z.z, zv.z);
+        depth_px(d.w, v.w, fb, z.w, zv.w);
+        __stcs((float4 *)depth + i, z);
+        if (hv) __stcs((float4 *)depth_var + i, zv);
+    }
+    for (long long i = 4 * n4 + tid; i < n; i += stride) {
+        float z, zv;
+        depth_px(__ldg(disp + i), hv ? __ldg(var + i) : 0.f, fb, z, zv);
+        depth[i] = z;
+        if (hv) depth_var[i] = zv;
     }
 }
 
@@ -1162,7 +1182,7 @@ cudaError_t launch_upsample(const LaunchArgs &a, cudaStream_t s) {
 
 cudaError_t launch_depth(const float *disp, const float *var, long long n, float fb, float *depth,
                          float *depth_var, cudaStream_t s) {
-    const long long blocks = (n + 255) / 256;
+    const long long blocks = (n / 4 + 255) / 256 + 1;
     const int grid = (int)std::max<long long>(1, std::min<long long>(blocks, (long long)num_sms() * 8));
     k_depth<<<grid, 256, 0, s>>>(disp, var, n, fb, depth, depth_var);
     return cudaGetLastError();
