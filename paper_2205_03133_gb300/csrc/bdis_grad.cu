@@ -289,11 +289,31 @@ __global__ void __launch_bounds__(256) k_bwd_sigma(GradArgs a) {
 
 // A group of G lanes per kept patch, lane = patch row (as in the search).
 // Window energies and the implicit-function rule through F_k.
+// Right-image values one lane stages for its patch row: the columns
+// lo .. lo + P + kSegExtra - 1 (lo = leftmost tap of the window), clamped to
+// the image like every sample.
+constexpr int kSegExtra = 6;
+template <int P>
+__host__ __device__ constexpr int seg_stride() { return (P + kSegExtra) | 1; }  // odd: distinct banks
+
+// Per-row tap of the staged segment at column j + S (S = offset of the
+// window sample's integer part from lo): value and right-sided slope, equal
+// to tap_row() on the image (a clamped tap reads equal neighbours: slope 0).
+__device__ __forceinline__ void seg_tap(const float *seg, int k, float t, float &v, float &slope) {
+    const float a = seg[k], b = seg[k + 1];
+    slope = b - a;
+    v = fmaf(t, slope, a);
+}
+
 template <int P>
 __global__ void __launch_bounds__(256) k_bwd_patch(GradArgs a) {
     constexpr int G = P <= 8 ? 8 : 16;
     constexpr int N = P * P;
+    constexpr int SEGN = P + kSegExtra;
     constexpr float invN = 1.f / (float)N;
+    extern __shared__ float bsm[];
+    float *seg = bsm + (size_t)threadIdx.x * 2 * seg_stride<P>();  // lane-private
+    float *acc = seg + seg_stride<P>();
     const int tid = threadIdx.x;
     const int gl = tid & (G - 1);
     const int grp = tid / G;
@@ -324,13 +344,48 @@ __global__ void __launch_bounds__(256) k_bwd_patch(GradArgs a) {
 #pragma unroll
         for (int j = 0; j < P; ++j) gt[j] = row_on ? gt[j] - gbar : 0.f;
         const float d = rc.d;
+        // every sample of the row at offset delta_i is split_shift(d + delta_i):
+        // taps ox + j + off_i and the next column, weights (1 - t_i), t_i
+        int offs[5], sh[5];
+        float ts[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) split_shift(d + dl[i], offs[i], ts[i]);
+        int omin = offs[0], omax = offs[0];
+#pragma unroll
+        for (int i = 1; i < 5; ++i) {
+            omin = min(omin, offs[i]);
+            omax = max(omax, offs[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 5; ++i) sh[i] = offs[i] - omin;
+        const int lo = ox + omin;
+        // taps reach column j + sh_i + 1 <= P + (omax - omin); a wider
+        // window (window_step > 1.25) takes the per-tap path below
+        const bool staged = omax - omin <= kSegExtra - 1;
+        if (staged && row_on) {
+#pragma unroll
+            for (int q = 0; q < SEGN; ++q) {
+                seg[q] = __ldg(Rrow + clampi(lo + q, 0, g.w - 1));
+                acc[q] = 0.f;
+            }
+        }
+        auto tap = [&](int i, int j, float &v, float &slope) {
+            if (staged) {
+                seg_tap(seg, j + sh[i], ts[i], v, slope);
+            } else {
+                const Tap q = tap_row(Rrow, g.w, ox + j + offs[i], ts[i]);
+                v = q.v;
+                slope = q.slope;
+            }
+        };
         // residual at d, and dF/dd
         float sres = 0.f, fd = 0.f;
 #pragma unroll
         for (int j = 0; j < P; ++j) {
-            const Tap q = tap_at(Rrow, g.w, ox + j, d);
-            sres += row_on ? q.v - T[j] : 0.f;
-            fd -= gt[j] * q.slope;
+            float v, sl;
+            tap(0, j, v, sl);
+            sres += row_on ? v - T[j] : 0.f;
+            fd -= gt[j] * sl;
         }
         const float mres = group_sum<G>(sres) * invN;
         const float Fd = group_sum<G>(fd);
@@ -341,20 +396,22 @@ __global__ void __launch_bounds__(256) k_bwd_patch(GradArgs a) {
             float sa = 0.f;
 #pragma unroll
             for (int j = 0; j < P; ++j) {
-                const Tap q = tap_at(Rrow, g.w, ox + j, d + dl[i]);
-                sa += row_on ? q.v - T[j] : 0.f;
+                float v, sl;
+                tap(i, j, v, sl);
+                sa += row_on ? v - T[j] : 0.f;
             }
             abar[i] = group_sum<G>(sa) * invN;
         }
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
-            float s = 0.f;
+            float sd = 0.f;
 #pragma unroll
             for (int j = 0; j < P; ++j) {
-                const Tap q = tap_at(Rrow, g.w, ox + j, d + dl[i]);
-                s += row_on ? 2.f * (q.v - T[j] - abar[i]) * (-q.slope) : 0.f;
+                float v, sl;
+                tap(i, j, v, sl);
+                sd += row_on ? 2.f * (v - T[j] - abar[i]) * (-sl) : 0.f;
             }
-            dEdd[i] = group_sum<G>(s);
+            dEdd[i] = group_sum<G>(sd);
         }
         // dL/dE_i from dL/dpi_k and sigma_r
         const float sr = __ldg(g.sigma_r);
@@ -377,29 +434,59 @@ __global__ void __launch_bounds__(256) k_bwd_patch(GradArgs a) {
         float gdt = g.gd[kk];
 #pragma unroll
         for (int i = 0; i < 5; ++i) gdt = fmaf(gE[i], dEdd[i], gdt);
-        const float v = -gdt / Fd;
+        const float vF = -gdt / Fd;
         if (active_patch && gl == 0 && g.gPatch) g.gPatch[kk] = gdt;
         if (!(active_patch && row_on)) continue;
-        // scatter: window energies, the solve F, the gradient image
+        // scatter: window energies and the solve F into the right image (the
+        // adjoint of each tap), the template into the left image, the solve
+        // into the gradient image
         float *gRrow = g.gR + (size_t)row * g.w;
         float *gLrow = g.gL + (size_t)row * g.w + ox;
         float *gGrow = g.gG + (size_t)row * g.w + ox;
+        if (staged) {
+            // per-row sums over the staged columns, then one atomic per column
 #pragma unroll
-        for (int j = 0; j < P; ++j) {
-            float tsum = 0.f;
+            for (int j = 0; j < P; ++j) {
+                float tsum = 0.f;
 #pragma unroll
-            for (int i = 0; i < 5; ++i) {
-                const Tap q = tap_at(Rrow, g.w, ox + j, d + dl[i]);
-                const float c = gE[i] * 2.f * (q.v - T[j] - abar[i]);
-                atomicAdd(gRrow + q.x0, c * (1.f - q.t));
-                atomicAdd(gRrow + q.x1, c * q.t);
-                tsum += c;
+                for (int i = 0; i < 5; ++i) {
+                    float v, sl;
+                    seg_tap(seg, j + sh[i], ts[i], v, sl);
+                    const float c = gE[i] * 2.f * (v - T[j] - abar[i]);
+                    acc[j + sh[i]] = fmaf(c, 1.f - ts[i], acc[j + sh[i]]);
+                    acc[j + sh[i] + 1] = fmaf(c, ts[i], acc[j + sh[i] + 1]);
+                    tsum += c;
+                }
+                float v0, sl0;
+                seg_tap(seg, j + sh[0], ts[0], v0, sl0);
+                const float cF = vF * gt[j];
+                acc[j + sh[0]] = fmaf(cF, 1.f - ts[0], acc[j + sh[0]]);
+                acc[j + sh[0] + 1] = fmaf(cF, ts[0], acc[j + sh[0] + 1]);
+                atomicAdd(gLrow + j, -tsum - cF);
+                atomicAdd(gGrow + j, vF * ((v0 - T[j]) - mres));
             }
-            const Tap q = tap_at(Rrow, g.w, ox + j, d);
-            atomicAdd(gRrow + q.x0, v * gt[j] * (1.f - q.t));
-            atomicAdd(gRrow + q.x1, v * gt[j] * q.t);
-            atomicAdd(gLrow + j, -tsum - v * gt[j]);
-            atomicAdd(gGrow + j, v * ((q.v - T[j]) - mres));
+            // a clamped tap's weight lands on the edge column, as in tap_row()
+#pragma unroll
+            for (int q = 0; q < SEGN; ++q)
+                if (acc[q] != 0.f) atomicAdd(gRrow + clampi(lo + q, 0, g.w - 1), acc[q]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                float tsum = 0.f;
+#pragma unroll
+                for (int i = 0; i < 5; ++i) {
+                    const Tap q = tap_at(Rrow, g.w, ox + j, d + dl[i]);
+                    const float c = gE[i] * 2.f * (q.v - T[j] - abar[i]);
+                    atomicAdd(gRrow + q.x0, c * (1.f - q.t));
+                    atomicAdd(gRrow + q.x1, c * q.t);
+                    tsum += c;
+                }
+                const Tap q = tap_at(Rrow, g.w, ox + j, d);
+                atomicAdd(gRrow + q.x0, vF * gt[j] * (1.f - q.t));
+                atomicAdd(gRrow + q.x1, vF * gt[j] * q.t);
+                atomicAdd(gLrow + j, -tsum - vF * gt[j]);
+                atomicAdd(gGrow + j, vF * ((q.v - T[j]) - mres));
+            }
         }
     }
 }
@@ -463,25 +550,36 @@ cudaError_t launch_bwd_dens(const GradArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int P>
+cudaError_t launch_bwd_patch_p(const GradArgs &a, int grid, cudaStream_t s) {
+    const size_t smem = sizeof(float) * 256 * 2 * seg_stride<P>();
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_bwd_patch<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_bwd_patch<P><<<grid, 256, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bwd_patch(const GradArgs &a, cudaStream_t s) {
     const int grid = ggrid(a.total);
     switch (a.P) {
-        case 4: k_bwd_patch<4><<<grid, 256, 0, s>>>(a); break;
-        case 5: k_bwd_patch<5><<<grid, 256, 0, s>>>(a); break;
-        case 6: k_bwd_patch<6><<<grid, 256, 0, s>>>(a); break;
-        case 7: k_bwd_patch<7><<<grid, 256, 0, s>>>(a); break;
-        case 8: k_bwd_patch<8><<<grid, 256, 0, s>>>(a); break;
-        case 9: k_bwd_patch<9><<<grid, 256, 0, s>>>(a); break;
-        case 10: k_bwd_patch<10><<<grid, 256, 0, s>>>(a); break;
-        case 11: k_bwd_patch<11><<<grid, 256, 0, s>>>(a); break;
-        case 12: k_bwd_patch<12><<<grid, 256, 0, s>>>(a); break;
-        case 13: k_bwd_patch<13><<<grid, 256, 0, s>>>(a); break;
-        case 14: k_bwd_patch<14><<<grid, 256, 0, s>>>(a); break;
-        case 15: k_bwd_patch<15><<<grid, 256, 0, s>>>(a); break;
-        case 16: k_bwd_patch<16><<<grid, 256, 0, s>>>(a); break;
+        case 4: return launch_bwd_patch_p<4>(a, grid, s);
+        case 5: return launch_bwd_patch_p<5>(a, grid, s);
+        case 6: return launch_bwd_patch_p<6>(a, grid, s);
+        case 7: return launch_bwd_patch_p<7>(a, grid, s);
+        case 8: return launch_bwd_patch_p<8>(a, grid, s);
+        case 9: return launch_bwd_patch_p<9>(a, grid, s);
+        case 10: return launch_bwd_patch_p<10>(a, grid, s);
+        case 11: return launch_bwd_patch_p<11>(a, grid, s);
+        case 12: return launch_bwd_patch_p<12>(a, grid, s);
+        case 13: return launch_bwd_patch_p<13>(a, grid, s);
+        case 14: return launch_bwd_patch_p<14>(a, grid, s);
+        case 15: return launch_bwd_patch_p<15>(a, grid, s);
+        case 16: return launch_bwd_patch_p<16>(a, grid, s);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_bwd_sobel(const GradArgs &a, cudaStream_t s) {
