@@ -16,6 +16,7 @@
 //               patches overlapping the tile, then the sGMM fusion gather
 //               (Eq. 8-9, Eq. 12) and pixel variance (Eq. 17)
 #include <algorithm>
+#include <climits>
 #include <cfloat>
 #include <cstring>
 #include <cmath>
@@ -287,35 +288,47 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
         const float dinit = dsh[kl];
         const float dlim = (float)w + 2.f * (float)P;
 
-        // right-image samples of this lane's row at x - d = base + j (+ t):
-        // the P + 1 values base .. base + P
-        auto load_row = [&](int base, float (&v)[P + 1]) {
+        // right-image values of this lane's row at columns base .. base + NV - 1
+        // (staged band, else the image with the same clamping)
+        auto load_vals = [&](int base, auto &v) {
+            constexpr int NV = sizeof(v) / sizeof(float);
             const int o = base - xlo;
-            if (o >= 0 && o + P < wwin) {
+            if (o >= 0 && o + NV <= wwin) {
                 const float *p = Rs + o;
 #pragma unroll
-                for (int j = 0; j <= P; ++j) v[j] = p[j];
+                for (int j = 0; j < NV; ++j) v[j] = p[j];
             } else {
 #pragma unroll
-                for (int j = 0; j <= P; ++j) v[j] = ldf(Rg + clampi(base + j, 0, w - 1));
+                for (int j = 0; j < NV; ++j) v[j] = ldf(Rg + clampi(base + j, 0, w - 1));
             }
         };
 
-        // Gauss-Newton: d <- d + (sum gt_i s_i - cT) / H, s_i = I_r(x_i - d)
+        // Gauss-Newton: d <- d + (sum gt_i s_i - cT) / H, s_i = I_r(x_i - d).
+        // With x - d = base + j + t the sum is A + t (B - A), A and B the
+        // correlations of gt with the row at integer offsets base and base + 1;
+        // they change only when d crosses an integer, so the warp recomputes
+        // them only when one of its patches did.
         float d = dinit, dlast = 0.f;
+        int offc = INT_MIN;
+        float At = 0.f, Bt = 0.f;
         for (int it = 0; it < a.iters; ++it) {
             int off;
             float t;
             split_shift(d, off, t);
-            float v[P + 1];
-            load_row(ox + off, v);
-            float A = 0.f, B = 0.f;
+            if (__any_sync(0xffffffffu, off != offc)) {
+                float v[P + 1];
+                load_vals(ox + off, v);
+                float A = 0.f, B = 0.f;
 #pragma unroll
-            for (int j = 0; j < P; ++j) {
-                A = fmaf(gt[j], v[j], A);
-                B = fmaf(gt[j], v[j + 1], B);
+                for (int j = 0; j < P; ++j) {
+                    A = fmaf(gt[j], v[j], A);
+                    B = fmaf(gt[j], v[j + 1], B);
+                }
+                At = group_sum<G>(A);
+                Bt = group_sum<G>(B);
+                offc = off;
             }
-            const float s = group_sum<G>(fmaf(t, B - A, A));
+            const float s = fmaf(t, Bt - At, At);
             if (!flat) {
                 const float delta = (s - cT) * invH;
                 d = fminf(fmaxf(d + delta, -dlim), dlim);
@@ -332,17 +345,33 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
         float t0;
         split_shift(d, off0, t0);
         const int base0 = ox + off0;
-        float s0[P];
+        // samples of the window offsets {-h, +h, -2h, +2h}: sw[k][j]
+        // (general h: one split per offset; h = 1/2: the +-2h samples are the
+        // centre samples one column over and -h is +h one column over, so two
+        // interpolated rows cover all five)
+        float su[4], suu[4], suc[4];
         float sa = 0.f;
+        const bool half = h == 0.5f;
+        // S0: columns -1 .. P at d (the centre samples are S0[1 .. P]);
+        // Sp (h = 1/2 only): columns 0 .. P at d + 1/2
+        float S0[P + 2], Sp[P + 1];
         {
-            float v[P + 1];
-            load_row(base0, v);
+            float v0[P + 3];
+            load_vals(base0 - 1, v0);
 #pragma unroll
-            for (int j = 0; j < P; ++j) {
-                s0[j] = fmaf(t0, v[j + 1] - v[j], v[j]);
-                sa += row_on ? s0[j] - T[j] : 0.f;
-            }
+            for (int j = 0; j < P + 2; ++j) S0[j] = fmaf(t0, v0[j + 1] - v0[j], v0[j]);
         }
+        if (half) {
+            int offp;
+            float tp;
+            split_shift(d + 0.5f, offp, tp);
+            float vp[P + 2];
+            load_vals(ox + offp, vp);
+#pragma unroll
+            for (int j = 0; j < P + 1; ++j) Sp[j] = fmaf(tp, vp[j + 1] - vp[j], vp[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < P; ++j) sa += row_on ? S0[j + 1] - T[j] : 0.f;
         // samples outside [0, w-1]: every row shares base0 and t0, so per
         // row j < -base0 on the left and base0 + j >= w - 1 (t0 > 0) or
         // >= w (t0 = 0) on the right
@@ -353,21 +382,34 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
         float e0 = 0.f;
 #pragma unroll
         for (int j = 0; j < P; ++j) {
-            T[j] = row_on ? (s0[j] - T[j]) - mean0 : 0.f;  // now the centred residual
+            T[j] = row_on ? (S0[j + 1] - T[j]) - mean0 : 0.f;  // now the centred residual
             e0 = fmaf(T[j], T[j], e0);
         }
-        float su[4], suu[4], suc[4];
+        // window energies.  E(0) in two passes; for the four offsets the
+        // differences dE_k = E(delta_k) - E(0) directly from the sample
+        // differences u_j = s_kj - s_0j (the template cancels):
+        //   dE_k = sum u^2 - (sum u)^2 / N + 2 sum u (a_0j - mean a_0),
+        // which keeps full relative precision when dE_k << E(0).
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            int off;
-            float t;
-            split_shift(d + dl[k], off, t);
-            float v[P + 1];
-            load_row(ox + off, v);
+            float sk[P];
+            if (half) {
+#pragma unroll
+                for (int j = 0; j < P; ++j)
+                    sk[j] = k == 0 ? Sp[j + 1] : k == 1 ? Sp[j] : k == 2 ? S0[j + 2] : S0[j];
+            } else {
+                int off;
+                float t;
+                split_shift(d + dl[k], off, t);
+                float v[P + 1];
+                load_vals(ox + off, v);
+#pragma unroll
+                for (int j = 0; j < P; ++j) sk[j] = fmaf(t, v[j + 1] - v[j], v[j]);
+            }
             float p1 = 0.f, p2 = 0.f, p3 = 0.f;
 #pragma unroll
             for (int j = 0; j < P; ++j) {
-                const float uj = row_on ? fmaf(t, v[j + 1] - v[j], v[j]) - s0[j] : 0.f;
+                const float uj = row_on ? sk[j] - S0[j + 1] : 0.f;
                 p1 += uj;
                 p2 = fmaf(uj, uj, p2);
                 p3 = fmaf(uj, T[j], p3);
@@ -444,7 +486,7 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
     }
 
 template <int P, typename TI, typename TG>
-__global__ void __launch_bounds__(256, (P <= 8 ? 4 : P <= 12 ? 3 : 2)) k_search(LaunchArgs a) {
+__global__ void __launch_bounds__(256, (P <= 8 ? 3 : 2)) k_search(LaunchArgs a) {
     extern __shared__ float smem[];
     pdl_wait();
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) search_unit<P, TI, TG>(a, unit, smem);
