@@ -696,9 +696,11 @@ __device__ __forceinline__ void fuse_unit(const LaunchArgs &a, int unit, float4 
     const int tx = tile % D.tiles_x, ty = tile / D.tiles_x;
     const int x0 = tx * TW, y0 = ty * TH;
     const int x1 = min(x0 + TW, D.w) - 1, y1 = min(y0 + TH, D.h) - 1;
-    // sigma_r of the pair from the search's exact sums (text after Eq. 6)
-    float sr;
-    {
+    // sigma_r of the pair from the search's exact sums (text after Eq. 6),
+    // by one thread (FP64 conversions), broadcast through shared memory
+    __shared__ float sr_sh;
+    if (threadIdx.x == 0) {
+        float sr;
         const double S1 = (double)__ldcg(D.acc) / (double)kSigmaFix1;
         const double S2 = (double)__ldcg(D.acc + 1);
         const double S3 = (double)__ldcg(D.acc + 2);
@@ -712,8 +714,11 @@ __device__ __forceinline__ void fuse_unit(const LaunchArgs &a, int unit, float4 
         } else {
             sr = fmaxf(sqrtf((float)(S1 / (S2 * (double)(P * P)))), a.sigma_r_floor);
         }
-        if (tile == 0 && threadIdx.x == 0) *D.sigma_r = sr;
+        if (tile == 0) *D.sigma_r = sr;
+        sr_sh = sr;
     }
+    __syncthreads();
+    const float sr = sr_sh;
 
     // patches overlapping the tile
     int kxlo, kxhi, kylo, kyhi, tmp;
@@ -767,9 +772,10 @@ __device__ __forceinline__ void fuse_unit(const LaunchArgs &a, int unit, float4 
         const bool any = sw > 0.f;
         float Dv, Qv, Vv;
         if (any) {
-            Dv = swd / sw;
-            Qv = swr / sw;
-            Vv = sw2 / (sw * sw);
+            const float inv = 1.f / sw;
+            Dv = swd * inv;
+            Qv = swr * inv;
+            Vv = sw2 * inv * inv;
         } else {
             Dv = D.Dc != nullptr ? 2.f * coarse_bilin(D.Dc, D.wc, D.hc, (float)x, (float)y) : 0.f;
             Qv = 0.f;
