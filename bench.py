@@ -349,7 +349,7 @@ def main():
         flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
         stream = torch.cuda.Stream(device=dev)
         res = bench_batched(bd, dev, stream, flush, rank, ws, steps=args.steps,
-                            warmup=args.warmup, compare_plain=False)
+                            warmup=args.warmup, compare_plain=False, form=args.form)
         if rank == 0:
             print(json.dumps({"metric": METRIC, "batched": res}))
         return 0
@@ -483,7 +483,7 @@ def main():
     modes = None
     depth_line = None
     if not args.no_batched:
-        batched = bench_batched(bd, dev, stream, flush, rank, ws)
+        batched = bench_batched(bd, dev, stream, flush, rank, ws, form=args.form)
         fwd_bwd = bench_fwd_bwd(bd, dev, stream, flush, rank, ws)
         modes = bench_modes(bd, dev, stream, flush, ws, Ld, Rd, out, w, h)
         depth_line = bench_depth(bd, dev, stream, flush, ws)
@@ -597,7 +597,8 @@ def bench_fwd_bwd(bd, dev, stream, flush, rank, ws, steps=10, warmup=3):
             "fwd_only_ms": round(t_f, 4), "mean_loss": round(loss, 5)}
 
 
-def bench_batched(bd, dev, stream, flush, rank, ws, steps=10, warmup=3, compare_plain=True):
+def bench_batched(bd, dev, stream, flush, rank, ws, steps=10, warmup=3, compare_plain=True,
+                  form="auto"):
     """64 pairs of uneven sizes (24x640x480, 16x960x540, 16x1280x720,
     8x1920x1080; G1 generator, seeds 64*rank + i) in one batched call per
     step, against 64 sequential plain calls."""
@@ -615,6 +616,8 @@ def bench_batched(bd, dev, stream, flush, rank, ws, steps=10, warmup=3, compare_
     px = sum(w * h for w, h in sizes)
     m = bd.BDIS(**BATCH_PARAMS)
     mp = bd.BDIS(**BATCH_PARAMS)
+    if form != "auto":
+        m.set_option(bd.B.OPT_FORM, {"launches": 1, "persistent": 2}[form])
 
     def run(fn, n):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
