@@ -482,10 +482,12 @@ def main():
     fwd_bwd = None
     modes = None
     depth_line = None
+    coverage = None
     if not args.no_batched:
         batched = bench_batched(bd, dev, stream, flush, rank, ws, form=args.form)
         fwd_bwd = bench_fwd_bwd(bd, dev, stream, flush, rank, ws)
         modes = bench_modes(bd, dev, stream, flush, ws, Ld, Rd, out, w, h)
+        coverage = variance_coverage_experiment(bd, dev, stream)
         depth_line = bench_depth(bd, dev, stream, flush, ws)
 
     result = None
@@ -520,6 +522,7 @@ def main():
             "batched": batched,
             "fwd_bwd": fwd_bwd,
             "modes": modes,
+            "variance_coverage": coverage,
             "depth": depth_line,
             "paper_context": "BDIS(VAR) 0.072 s per 640x480 frame (4.27 Mpix/s) on one i5-9400 "
                              "core, finest scale 2^1 (Table VIII); 17 Hz claim (abstract)",
@@ -722,6 +725,43 @@ def bench_modes(bd, dev, stream, flush, ws, Ld, Rd, out, w, h, steps=200, warmup
         res[name] = {"params": {k: v for k, v in kw.items()}, "ms_per_call": round(ms, 5),
                      "value": round(ws * w * h / (ms / 1e3) / 1e6, 2), "unit": UNIT,
                      "valid_pixels": int(st["valid_pixels"])}
+        m.close()
+    return res
+
+
+def variance_coverage(disp, var, valid, gt, z=1.96):
+    """Fraction of valid pixels whose error is within z standard deviations
+    of the estimated variance (the synthetic analogue of Table VI)."""
+    import numpy as np
+    v = valid.astype(bool) & np.isfinite(var) & (var > 0)
+    e = np.abs(disp[v].astype(np.float64) - gt[v])
+    return {"valid_frac": round(float(valid.astype(bool).mean()), 4),
+            "coverage": round(float((e <= z * np.sqrt(var[v])).mean()), 4) if v.any() else None,
+            "mean_abs_err_px": round(float(e.mean()), 4) if v.any() else None,
+            "median_abs_err_px": round(float(np.median(e)), 4) if v.any() else None,
+            "median_sigma_px": round(float(np.median(np.sqrt(var[v]))), 4) if v.any() else None}
+
+
+def variance_coverage_experiment(bd, dev, stream):
+    """|e| <= 1.96 sigma on seeded G1 / G2 pairs with known ground truth, for
+    the bench parameters and for the paper's parameter set (Sec. IV-A)."""
+    import torch
+
+    import synth
+    res = {}
+    cases = {
+        "g1_640x480": (synth.g1_pair(640, 480, 0), dict(PARAMS)),
+        "g2_640x480": (synth.g2_pair(640, 480, 0), dict(PARAMS)),
+        "g1_640x480_paper_preset": (synth.g1_pair(640, 480, 0), dict(MODES["paper_preset"])),
+        "g2_640x480_paper_preset": (synth.g2_pair(640, 480, 0), dict(MODES["paper_preset"])),
+    }
+    for name, (pr, kw) in cases.items():
+        kw["variance"] = 1
+        m = bd.BDIS(**kw)
+        d, v, ok = m.match(torch.from_numpy(pr.left).to(dev), torch.from_numpy(pr.right).to(dev),
+                           stream=stream)
+        torch.cuda.synchronize()
+        res[name] = variance_coverage(d.cpu().numpy(), v.cpu().numpy(), ok.cpu().numpy(), pr.gt_left())
         m.close()
     return res
 

@@ -191,7 +191,7 @@ struct Plan {
     int wmax[kMaxLevels] = {0};
     int units[kMaxLevels][W_COUNT] = {{0}};
     // arena offsets, index level * n + pair
-    std::vector<size_t> oG, oL, oR, oD, oQ, oV, oRec, oFuse, oSr;
+    std::vector<size_t> oG, oL, oR, oD, oQ, oV, oW, oRec, oFuse, oSr;
 };
 
 struct Bump {
@@ -206,12 +206,12 @@ struct Bump {
 
 // Phase 1: geometry, work ranges and arena offsets.
 void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, const LevelCfg *cfg,
-                 Plan &pl) {
+                 Plan &pl, bool wsum) {
     const int NL = p.levels, P = p.patch, S = p.stride;
     const size_t esz = p.storage == BDIS_STORE_F16 ? 2 : 4;
     const size_t cnt = (size_t)NL * n;
     pl.descs.assign(cnt, LevelDesc{});
-    for (auto *v : {&pl.oG, &pl.oL, &pl.oR, &pl.oD, &pl.oQ, &pl.oV, &pl.oRec, &pl.oFuse, &pl.oSr})
+    for (auto *v : {&pl.oG, &pl.oL, &pl.oR, &pl.oD, &pl.oQ, &pl.oV, &pl.oW, &pl.oRec, &pl.oFuse, &pl.oSr})
         v->assign(cnt, 0);
     const int F = p.finest_level;
     Bump b;
@@ -252,6 +252,7 @@ void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, const Leve
             if (l == F && F > 0 && p.variance) pl.oV[k] = b.take(sizeof(float) * (size_t)d.w * d.h);
             if (l == 0) {
                 d.pitch = pairs[i].pitch;
+                if (wsum && F == 0) pl.oW[k] = b.take(sizeof(float) * (size_t)d.w * d.h);
             } else {
                 d.pitch = (int)gp;
                 pl.oL[k] = b.take(gp * esz * d.h);
@@ -272,7 +273,8 @@ void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, const Leve
 }
 
 // Phase 2: pointers, once the arena base is known.
-void plan_pointers(const bdis_params &p, int n, const bdis_pair *pairs, char *base, Plan &pl) {
+void plan_pointers(const bdis_params &p, int n, const bdis_pair *pairs, char *base, Plan &pl,
+                   bool wsum) {
     const int NL = p.levels, F = p.finest_level;
     for (int l = 0; l < NL; ++l)
         for (int i = 0; i < n; ++i) {
@@ -302,6 +304,7 @@ void plan_pointers(const bdis_params &p, int n, const bdis_pair *pairs, char *ba
             d.acc = (unsigned long long *)(base + pl.off_acc) + 3 * k;
             d.Df = d.Vf = nullptr;
             d.wf = d.hf = 0;
+            d.wsum = (l == 0 && wsum && F == 0) ? (float *)(base + pl.oW[k]) : nullptr;
         }
     if (F > 0)
         for (int i = 0; i < n; ++i) {
@@ -401,7 +404,8 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
     const bdis_params &p = h->p;
     const int NL = p.levels;
     Plan pl;
-    plan_layout(p, n, pairs, cfg, pl);
+    const bool wsum = in_type == E_F32;  // the differentiable form keeps the weight sums
+    plan_layout(p, n, pairs, cfg, pl, wsum);
     int bpitch[kMaxLevels], bcap[kMaxLevels], cpitch[kMaxLevels];
     size_t ssm[kMaxLevels], fsm[kMaxLevels], smax = 0, fmax = 0;
     for (int l = 0; l < NL; ++l) {
@@ -415,7 +419,7 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
         return fail(h, BDIS_EUNSUPPORTED, "search radius too large for the shared-memory band");
     bdis_status s = ensure_arena(h, pl.bytes);
     if (s != BDIS_OK) return s;
-    plan_pointers(p, n, pairs, h->arena, pl);
+    plan_pointers(p, n, pairs, h->arena, pl, wsum);
     {
         // limits are only raised, so other handles' settings stay valid
         cudaError_t e = prepare_search(p.patch, smax);
@@ -887,7 +891,7 @@ bdis_status bdis_match_host(bdis_handle *h, const uint8_t *left, const uint8_t *
     // device staging for the inputs and outputs, after the pipeline's arena
     Plan pl;
     std::vector<LevelCfg> dcfg((size_t)h->p.levels, LevelCfg{2, 32, 16});
-    plan_layout(h->p, 1, &q, dcfg.data(), pl);
+    plan_layout(h->p, 1, &q, dcfg.data(), pl, false);
     const size_t img = align_up((size_t)w * hgt, 256);
     const size_t fo = align_up(sizeof(float) * (size_t)w * hgt, 256);
     const size_t extra = 2 * img + 2 * fo + img;
@@ -1046,7 +1050,7 @@ bdis_status grad_setup(bdis_handle *h, const bdis_grad *g, bool need_loss, cudaS
     const size_t off_desc = b.take(sizeof(GradDesc) * n);
     std::vector<size_t> oDw(n), oG(n), od(n), opi(n), osp(n), oce(n), olp(n);
     const int ngrp = 256 / search_group(p.patch);
-    int begin[G_COUNT] = {0, 0, 0};
+    int begin[G_COUNT] = {0, 0};
     for (int i = 0; i < n; ++i) {
         const LevelDesc &d = h->descs[(size_t)i];  // level 0
         GradDesc &q = gd[i];
@@ -1060,8 +1064,7 @@ bdis_status grad_setup(bdis_handle *h, const bdis_grad *g, bool need_loss, cudaS
         q.kxreg = d.kxreg;
         q.kyreg = d.kyreg;
         const size_t px = (size_t)d.w * d.h, np = (size_t)d.npx * d.npy;
-        const int units[G_COUNT] = {(int)((px + 255) / 256), (int)((np + 255) / 256),
-                                    (int)((np + ngrp - 1) / ngrp)};
+        const int units[G_COUNT] = {(int)((px + 255) / 256), (int)((np + ngrp - 1) / ngrp)};
         for (int k = 0; k < G_COUNT; ++k) {
             q.work_begin[k] = begin[k];
             begin[k] += units[k];
@@ -1069,7 +1072,7 @@ bdis_status grad_setup(bdis_handle *h, const bdis_grad *g, bool need_loss, cudaS
         oDw[i] = b.take(sizeof(float) * px);
         od[i] = b.take(sizeof(float) * np);
         opi[i] = b.take(sizeof(float) * np);
-        osp[i] = b.take(sizeof(float) * 2 * ((np + 255) / 256));
+        osp[i] = b.take(sizeof(float) * 2 * ((np + ngrp - 1) / ngrp));
         oce[i] = b.take(sizeof(float));
         olp[i] = b.take(sizeof(float) * ((px + 255) / 256));
     }
@@ -1102,6 +1105,7 @@ bdis_status grad_setup(bdis_handle *h, const bdis_grad *g, bool need_loss, cudaS
         q.R = (const float *)d.R;
         q.G = d.G;
         q.disp = d.disp;
+        q.wsum = d.wsum;
         q.valid = d.valid;
         q.rec = d.rec;
         q.fuse = d.fuse;
@@ -1187,7 +1191,7 @@ bdis_status bdis_backward(bdis_handle *h, const bdis_grad *g, void *stream) {
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
     a.total = tot[G_PIX];
     if ((e = launch_bwd_pix(a, st)) != cudaSuccess) return cuda_fail(h, e, "backward launch");
-    a.total = tot[G_PATCH];
+    a.total = tot[G_GROUP];
     if ((e = launch_bwd_dens(a, st)) != cudaSuccess) return cuda_fail(h, e, "backward launch");
     a.total = tot[G_GROUP];
     if ((e = launch_bwd_patch(a, st)) != cudaSuccess) return cuda_fail(h, e, "backward launch");

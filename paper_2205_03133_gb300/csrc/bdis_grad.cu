@@ -82,33 +82,6 @@ __device__ __forceinline__ float ldg_grad(const GradDesc &g, int row, int col) {
                             : __ldg((const float *)g.G + i);
 }
 
-// Sum of the sGMM weights over the kept patches covering pixel (x, y).
-__device__ float weight_sum(const GradDesc &g, const GradArgs &a, int x, int y) {
-    const int P = a.P, S = a.S;
-    const int kxlo = x - P + 1 > 0 ? (x - P + 1 + S - 1) / S : 0;
-    const int kxhi = min(g.kxreg - 1, x / S);
-    const bool kxext = g.npx > g.kxreg && x >= g.w - P;
-    const int kylo = y - P + 1 > 0 ? (y - P + 1 + S - 1) / S : 0;
-    const int kyhi = min(g.kyreg - 1, y / S);
-    const bool kyext = g.npy > g.kyreg && y >= g.h - P;
-    const int nky = kyhi - kylo + 1 + (kyext ? 1 : 0);
-    const int nkx = kxhi - kxlo + 1 + (kxext ? 1 : 0);
-    float sw = 0.f;
-    for (int iy = 0; iy < nky; ++iy) {
-        const int ky = (kylo + iy <= kyhi) ? kylo + iy : g.npy - 1;
-        const int oy = origin(ky, g.h, P, S, g.kyreg);
-        const float my = a.use_sgmm ? a.m[y - oy] : 1.f;
-        for (int ix = 0; ix < nkx; ++ix) {
-            const int kx = (kxlo + ix <= kxhi) ? kxlo + ix : g.npx - 1;
-            const int ox = origin(kx, g.w, P, S, g.kxreg);
-            const float4 f = __ldg(g.fuse + (size_t)ky * g.npx + kx);
-            if (!(f.y > 0.f)) continue;  // rejected patch (rho = 0)
-            sw += f.y * (my * (a.use_sgmm ? a.m[x - ox] : 1.f));
-        }
-    }
-    return sw;
-}
-
 __device__ __forceinline__ float block_sum256(float v, float *red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -188,7 +161,8 @@ __global__ void __launch_bounds__(256) k_loss_reduce(GradArgs a) {
 
 // ---------------------------------------------------------------- fusion adjoint
 
-// Per pixel: dL/dD / sum omega (0 at invalid pixels).
+// Per pixel: dL/dD / sum omega (0 at invalid pixels), the weight sum saved
+// by the forward's fusion.
 __global__ void __launch_bounds__(256) k_bwd_pix(GradArgs a) {
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) {
         const GradDesc &g = a.descs[find_pair_g(a.descs, a.npairs, unit, G_PIX)];
@@ -196,7 +170,7 @@ __global__ void __launch_bounds__(256) k_bwd_pix(GradArgs a) {
         if (idx >= g.w * g.h) continue;
         float v = 0.f;
         if (g.valid[idx]) {
-            const float sw = weight_sum(g, a, idx % g.w, idx / g.w);
+            const float sw = __ldg(g.wsum + idx);
             v = sw > 0.f ? g.gDisp[idx] / sw : 0.f;
         }
         g.gDw[idx] = v;
@@ -204,60 +178,76 @@ __global__ void __launch_bounds__(256) k_bwd_pix(GradArgs a) {
 }
 
 // Per kept patch: dL/dd_k = sum_x gDw rho_k M, dL/drho_k = sum_x gDw M (d_k - D),
-// dL/dpi_k, and the patch's share of dL/dsigma_r (block partials).
+// dL/dpi_k, and the patch's share of dL/dsigma_r (block partials).  A group
+// of lanes per patch, lane = patch row, so the pixel reads are row segments.
+template <int G>
+__device__ __forceinline__ void bwd_dens_unit(const GradArgs &a, int unit, float *red) {
+    const int P = a.P, S = a.S;
+    const int pi = find_pair_g(a.descs, a.npairs, unit, G_GROUP);
+    const GradDesc &g = a.descs[pi];
+    const int local = unit - g.work_begin[G_GROUP];
+    const int ngrp = blockDim.x / G;
+    const int gl = threadIdx.x & (G - 1);
+    const int k = local * ngrp + (int)threadIdx.x / G;
+    const int np = g.npx * g.npy;
+    const int kk = min(k, np - 1);
+    const bdis_patch_record &rc = g.rec[kk];
+    const bool kept = k < np && rc.flags == 0u;
+    float gd = 0.f, grho = 0.f;
+    if (kept && gl < P) {
+        const int ox = origin(kk % g.npx, g.w, P, S, g.kxreg);
+        const int oy = origin(kk / g.npx, g.h, P, S, g.kyreg);
+        const float my = a.use_sgmm ? a.m[gl] : 1.f;
+        const size_t row = (size_t)(oy + gl) * g.w + ox;
+        for (int c = 0; c < P; ++c) {
+            const float w = __ldg(g.gDw + row + c);
+            if (w == 0.f) continue;
+            const float M = my * (a.use_sgmm ? a.m[c] : 1.f);
+            gd = fmaf(w * rc.rho, M, gd);
+            grho = fmaf(w * M, rc.d - __ldg(g.disp + row + c), grho);
+        }
+    }
+    gd = group_sum<G>(gd);
+    grho = group_sum<G>(grho);
+    float gsr = 0.f, cnt = 0.f;
+    if (gl == 0 && k < np) {
+        float gpi = 0.f;
+        if (kept) {
+            gpi = a.use_c2f ? a.gamma_w * grho : grho;
+            // dpi/dsigma_r = (2 pi / sigma_r) sum_i pi_i e_i
+            const float sr = __ldg(g.sigma_r);
+            const float S2 = 2.f * sr * sr * (float)(kWindow * kWindow);
+            float e[5], Z = 1.f;
+            e[0] = 0.f;
+#pragma unroll
+            for (int i = 1; i < 5; ++i) {
+                e[i] = -rc.E[i] / S2;
+                Z += expf(e[i]);
+            }
+            float se = 0.f;
+#pragma unroll
+            for (int i = 1; i < 5; ++i) se += expf(e[i]) / Z * e[i];
+            gsr = gpi * (2.f * rc.pi / sr) * se;
+            cnt = 1.f;
+        } else {
+            gd = 0.f;
+        }
+        g.gd[k] = gd;
+        g.gpi[k] = gpi;
+    }
+    const float s1 = block_sum256(gsr, red);
+    const float s2 = block_sum256(cnt, red);
+    if (threadIdx.x == 0) {
+        g.sig_part[2 * local] = s1;
+        g.sig_part[2 * local + 1] = s2;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_bwd_dens(GradArgs a) {
     __shared__ float red[32];
-    const int P = a.P, S = a.S;
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) {
-        const int pi = find_pair_g(a.descs, a.npairs, unit, G_PATCH);
-        const GradDesc &g = a.descs[pi];
-        const int local = unit - g.work_begin[G_PATCH];
-        const int k = local * blockDim.x + threadIdx.x;
-        float gsr = 0.f, cnt = 0.f;
-        if (k < g.npx * g.npy) {
-            const bdis_patch_record &rc = g.rec[k];
-            float gd = 0.f, gpi = 0.f;
-            if (rc.flags == 0u) {
-                const int ox = origin(k % g.npx, g.w, P, S, g.kxreg);
-                const int oy = origin(k / g.npx, g.h, P, S, g.kyreg);
-                float grho = 0.f;
-                for (int r = 0; r < P; ++r) {
-                    const float my = a.use_sgmm ? a.m[r] : 1.f;
-                    for (int c = 0; c < P; ++c) {
-                        const size_t i = (size_t)(oy + r) * g.w + ox + c;
-                        const float w = __ldg(g.gDw + i);
-                        if (w == 0.f) continue;
-                        const float M = my * (a.use_sgmm ? a.m[c] : 1.f);
-                        gd = fmaf(w * rc.rho, M, gd);
-                        grho = fmaf(w * M, rc.d - __ldg(g.disp + i), grho);
-                    }
-                }
-                gpi = a.use_c2f ? a.gamma_w * grho : grho;
-                // dpi/dsigma_r = (2 pi / sigma_r) sum_i pi_i e_i
-                const float sr = __ldg(g.sigma_r);
-                const float S2 = 2.f * sr * sr * (float)(kWindow * kWindow);
-                float e[5], Z = 1.f;
-                e[0] = 0.f;
-#pragma unroll
-                for (int i = 1; i < 5; ++i) {
-                    e[i] = -rc.E[i] / S2;
-                    Z += expf(e[i]);
-                }
-                float se = 0.f;
-#pragma unroll
-                for (int i = 1; i < 5; ++i) se += expf(e[i]) / Z * e[i];
-                gsr = gpi * (2.f * rc.pi / sr) * se;
-                cnt = 1.f;
-            }
-            g.gd[k] = gd;
-            g.gpi[k] = gpi;
-        }
-        const float s1 = block_sum256(gsr, red);
-        const float s2 = block_sum256(cnt, red);
-        if (threadIdx.x == 0) {
-            g.sig_part[2 * local] = s1;
-            g.sig_part[2 * local + 1] = s2;
-        }
+        if (a.P <= 8) bwd_dens_unit<8>(a, unit, red);
+        else bwd_dens_unit<16>(a, unit, red);
     }
 }
 
@@ -267,7 +257,8 @@ __global__ void __launch_bounds__(256) k_bwd_sigma(GradArgs a) {
     __shared__ float red[32];
     for (int pair = blockIdx.x; pair < a.npairs; pair += gridDim.x) {
         const GradDesc &g = a.descs[pair];
-        const int n = (g.npx * g.npy + 255) / 256;
+        const int ngrp = 256 / (a.P <= 8 ? 8 : 16);
+        const int n = (g.npx * g.npy + ngrp - 1) / ngrp;
         float s = 0.f, c = 0.f;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             s += g.sig_part[2 * i];

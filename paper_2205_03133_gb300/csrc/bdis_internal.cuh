@@ -54,6 +54,8 @@ struct alignas(16) LevelDesc {
     uint8_t *valid;
     const float *Df, *Vf;     // level 0 with f > 0: the level-f maps to upsample
     int wf, hf;               // their size
+    float *wsum;              // level 0 of a float-image forward: sum of the fusion
+                              // weights per pixel (read by the adjoint), else nullptr
     bdis_patch_record *rec;   // npx * npy records of this pair at this level
     float4 *fuse;             // (d, rho, sig2, mu) per patch for the fusion gather (rho = 0: rejected)
     float *sigma_r;           // one float
@@ -117,7 +119,9 @@ constexpr unsigned kBarrierSpinLimit = 1u << 22;
 
 // ---- differentiable finest level (bdis_grad.cu)
 
-enum GradWork { G_PIX = 0, G_PATCH = 1, G_GROUP = 2, G_COUNT = 3 };
+// G_PIX: 256 pixels per unit; G_GROUP: one lane group per patch, 256 / group
+// patches per unit (the fusion and patch adjoints)
+enum GradWork { G_PIX = 0, G_GROUP = 1, G_COUNT = 2 };
 
 // One pair of the backward pass.  Images are the level-0 float images of the
 // forward; gradients are dense w*h arrays.
@@ -125,6 +129,7 @@ struct alignas(16) GradDesc {
     const float *L, *R;            // level-0 images, `pitch` elements per row
     const void *G;                 // level-0 x-gradient (storage type)
     const float *disp;             // forward disparity (valid pixels)
+    const float *wsum;             // forward fusion-weight sums per pixel
     const uint8_t *valid;
     const bdis_patch_record *rec;  // level-0 records
     const float4 *fuse;            // level-0 fusion records

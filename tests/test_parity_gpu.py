@@ -353,3 +353,28 @@ def test_launch_options_do_not_change_results(bd, kw):
                 for a, b in zip(ref, got):
                     assert torch.equal(a, b), (graph, pdl)
             m.close()
+
+
+def _coverage(disp, var, valid, gt, z=1.96):
+    v = valid.astype(bool) & np.isfinite(var) & (var > 0)
+    e = np.abs(disp[v].astype(np.float64) - gt[v])
+    return float((e <= z * np.sqrt(var[v])).mean()), int(v.sum())
+
+
+@pytest.mark.parametrize("gen,kw", [
+    ("g1", dict(patch=8, stride=4, levels=3, iters=8, variance=1)),
+    ("g2", dict(patch=12, stride=6, levels=3, iters=8, variance=1)),
+    ("g1", dict(patch=10, stride=4, levels=4, iters=12, variance=1, finest_level=1)),
+])
+def test_variance_coverage_matches_oracle(bd, gen, kw):
+    """The synthetic coverage experiment (|e| <= 1.96 sigma against the known
+    ground truth) gives the same fraction from the GPU outputs as from the oracle's."""
+    pr = synth.g1_pair(320, 240, 0) if gen == "g1" else synth.g2_pair(320, 240, 5)
+    g = _run(bd, kw, pr.left, pr.right, views=False)
+    o = oracle.match(oracle_params(g["params"]), pr.left, pr.right)
+    gt = pr.gt_left()
+    cg, ng = _coverage(g["disp"], g["var"], g["valid"], gt)
+    co, no = _coverage(o["disp"], o["var"], o["valid"], gt)
+    assert abs(ng - no) <= max(2, 0.001 * no)
+    assert abs(cg - co) <= 1e-3, (cg, co)
+    assert 0.5 < co <= 1.0
