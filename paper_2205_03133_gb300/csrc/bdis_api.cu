@@ -1048,7 +1048,7 @@ bdis_status grad_setup(bdis_handle *h, const bdis_grad *g, bool need_loss, cudaS
     gd.assign((size_t)n, GradDesc{});
     Bump b;
     const size_t off_desc = b.take(sizeof(GradDesc) * n);
-    std::vector<size_t> oDw(n), oG(n), od(n), opi(n), osp(n), oce(n), olp(n);
+    std::vector<size_t> oDw(n), oG(n), od(n), opi(n), osp(n), oce(n), olp(n), ocp(n);
     const int ngrp = 256 / search_group(p.patch);
     int begin[G_COUNT] = {0, 0};
     for (int i = 0; i < n; ++i) {
@@ -1075,6 +1075,7 @@ bdis_status grad_setup(bdis_handle *h, const bdis_grad *g, bool need_loss, cudaS
         osp[i] = b.take(sizeof(float) * 2 * ((np + ngrp - 1) / ngrp));
         oce[i] = b.take(sizeof(float));
         olp[i] = b.take(sizeof(float) * ((px + 255) / 256));
+        ocp[i] = b.take(sizeof(float) * np * 2 * p.patch * p.patch);
     }
     // the gradient images of all pairs are contiguous (one memset)
     gG_off = b.take(0);
@@ -1122,6 +1123,7 @@ bdis_status grad_setup(bdis_handle *h, const bdis_grad *g, bool need_loss, cudaS
         q.sig_part = (float *)(base + osp[i]);
         q.coefE0 = (float *)(base + oce[i]);
         q.loss_part = (float *)(base + olp[i]);
+        q.cpatch = (float *)(base + ocp[i]);
     }
     const size_t tbytes = sizeof(GradDesc) * n;
     bdis_status s = ensure_pinned(h, std::max(tbytes, h->last_upload.size()));
@@ -1187,8 +1189,9 @@ bdis_status bdis_backward(bdis_handle *h, const bdis_grad *g, void *stream) {
     int tot[G_COUNT];
     bdis_status s = grad_setup(h, g, false, st, a, gd, goff, gbytes, tot);
     if (s != BDIS_OK) return s;
-    cudaError_t e = cudaMemsetAsync(h->garena + goff, 0, gbytes, st);  // gradient images
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
+    (void)goff;  // the gradient-image scratch is written in full by k_bwd_gather
+    (void)gbytes;
+    cudaError_t e;
     a.total = tot[G_PIX];
     if ((e = launch_bwd_pix(a, st)) != cudaSuccess) return cuda_fail(h, e, "backward launch");
     a.total = tot[G_GROUP];
@@ -1196,6 +1199,7 @@ bdis_status bdis_backward(bdis_handle *h, const bdis_grad *g, void *stream) {
     a.total = tot[G_GROUP];
     if ((e = launch_bwd_patch(a, st)) != cudaSuccess) return cuda_fail(h, e, "backward launch");
     a.total = tot[G_PIX];
+    if ((e = launch_bwd_gather(a, st)) != cudaSuccess) return cuda_fail(h, e, "backward launch");
     if ((e = launch_bwd_sobel(a, st)) != cudaSuccess) return cuda_fail(h, e, "backward launch");
     return BDIS_OK;
 }

@@ -296,6 +296,146 @@ __device__ __forceinline__ void seg_tap(const float *seg, int k, float t, float 
     v = fmaf(t, slope, a);
 }
 
+// dL/dE_i of a kept patch from dL/dpi_k (through the window posterior) and
+// the sigma_r coefficient of E(0).
+__device__ __forceinline__ void grad_energies(const GradDesc &g, const bdis_patch_record &rc,
+                                              int kk, float gE[5]) {
+    const float sr = __ldg(g.sigma_r);
+    const float S2 = 2.f * sr * sr * (float)(kWindow * kWindow);
+    float pik[5], Z = 1.f;
+    pik[0] = 1.f;
+#pragma unroll
+    for (int i = 1; i < 5; ++i) {
+        pik[i] = expf(-rc.E[i] / S2);
+        Z += pik[i];
+    }
+    const float gpi = g.gpi[kk];
+    gE[0] = __ldg(g.coefE0);
+#pragma unroll
+    for (int i = 1; i < 5; ++i) {
+        gE[i] = gpi * rc.pi * (pik[i] / Z) / S2;
+        gE[0] -= gE[i];
+    }
+}
+
+// Window step 1/2: the samples of the row at d + delta for delta in
+// {0, -1/2, +1/2, -1, +1} come from two clamped value rows, v0 (columns
+// base0 - 1 .. base0 + P + 1, phase t0 of d) and vp (columns basep ..
+// basep + P + 1, phase tp of d + 1/2): d -+ 1 is the d row one column over
+// and d - 1/2 is the d + 1/2 row one column over.  Every tap, slope and tap
+// adjoint then has a compile-time register index.
+template <int P, int G>
+__device__ __forceinline__ void patch_adjoint_half(const GradDesc &g, const bdis_patch_record &rc,
+                                                   int k, int kk, bool active_patch, int gl,
+                                                   bool row_on, int ox, int row,
+                                                   const float *Rrow, const float (&T)[P],
+                                                   const float (&gt)[P]) {
+    constexpr float invN = 1.f / (float)(P * P);
+    const float d = rc.d;
+    int off0, offp;
+    float t0, tp;
+    split_shift(d, off0, t0);
+    split_shift(d + 0.5f, offp, tp);
+    const int b0 = ox + off0 - 1, bp = ox + offp;
+    float v0[P + 3], vp[P + 2];
+#pragma unroll
+    for (int q = 0; q < P + 3; ++q) v0[q] = __ldg(Rrow + clampi(b0 + q, 0, g.w - 1));
+#pragma unroll
+    for (int q = 0; q < P + 2; ++q) vp[q] = __ldg(Rrow + clampi(bp + q, 0, g.w - 1));
+    // tap (value, slope) of offset i at pixel j: row, first index, phase
+    auto tap = [&](int i, int j, float &v, float &sl) {
+        const float *r = (i == 1 || i == 2) ? vp : v0;
+        const int q = i == 0 ? j + 1 : i == 1 ? j + 1 : i == 2 ? j : i == 3 ? j + 2 : j;
+        const float t = (i == 1 || i == 2) ? tp : t0;
+        sl = r[q + 1] - r[q];
+        v = fmaf(t, sl, r[q]);
+    };
+    float sres = 0.f, fd = 0.f;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        float v, sl;
+        tap(0, j, v, sl);
+        sres += row_on ? v - T[j] : 0.f;
+        fd -= gt[j] * sl;
+    }
+    const float mres = group_sum<G>(sres) * invN;
+    const float Fd = group_sum<G>(fd);
+    float abar[5], dEdd[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        float sa = 0.f;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            float v, sl;
+            tap(i, j, v, sl);
+            sa += row_on ? v - T[j] : 0.f;
+        }
+        abar[i] = group_sum<G>(sa) * invN;
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        float sd = 0.f;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            float v, sl;
+            tap(i, j, v, sl);
+            sd += row_on ? 2.f * (v - T[j] - abar[i]) * (-sl) : 0.f;
+        }
+        dEdd[i] = group_sum<G>(sd);
+    }
+    float gE[5];
+    grad_energies(g, rc, kk, gE);
+    float gdt = g.gd[kk];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) gdt = fmaf(gE[i], dEdd[i], gdt);
+    const float vF = -gdt / Fd;
+    if (active_patch && gl == 0 && g.gPatch) g.gPatch[kk] = gdt;
+    const int P2 = P * P;
+    float *cLrow = g.cpatch + ((size_t)kk * 2 * P + (row_on ? gl : 0)) * P;
+    float *cGrow = cLrow + P2;
+    if (k < g.npx * g.npy && row_on && !active_patch) {
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            cLrow[j] = 0.f;
+            cGrow[j] = 0.f;
+        }
+    }
+    if (!(active_patch && row_on)) return;
+    float a0[P + 3], ap[P + 3];
+#pragma unroll
+    for (int q = 0; q < P + 3; ++q) a0[q] = ap[q] = 0.f;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        float tsum = 0.f, v00 = 0.f;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            float v, sl;
+            tap(i, j, v, sl);
+            if (i == 0) v00 = v;
+            const float c = gE[i] * 2.f * (v - T[j] - abar[i]);
+            tsum += c;
+            const int q = i == 0 ? j + 1 : i == 1 ? j + 1 : i == 2 ? j : i == 3 ? j + 2 : j;
+            const float t = (i == 1 || i == 2) ? tp : t0;
+            float *acc = (i == 1 || i == 2) ? ap : a0;
+            acc[q] = fmaf(c, 1.f - t, acc[q]);
+            acc[q + 1] = fmaf(c, t, acc[q + 1]);
+        }
+        const float cF = vF * gt[j];
+        a0[j + 1] = fmaf(cF, 1.f - t0, a0[j + 1]);
+        a0[j + 2] = fmaf(cF, t0, a0[j + 2]);
+        cLrow[j] = -tsum - cF;
+        cGrow[j] = vF * ((v00 - T[j]) - mres);
+    }
+    // a clamped column's weight lands on the edge column, as in tap_row()
+    float *gRrow = g.gR + (size_t)row * g.w;
+#pragma unroll
+    for (int q = 0; q < P + 3; ++q)
+        if (a0[q] != 0.f) atomicAdd(gRrow + clampi(b0 + q, 0, g.w - 1), a0[q]);
+#pragma unroll
+    for (int q = 0; q < P + 2; ++q)
+        if (ap[q] != 0.f) atomicAdd(gRrow + clampi(bp + q, 0, g.w - 1), ap[q]);
+}
+
 template <int P>
 __global__ void __launch_bounds__(256) k_bwd_patch(GradArgs a) {
     constexpr int G = P <= 8 ? 8 : 16;
@@ -334,6 +474,10 @@ __global__ void __launch_bounds__(256) k_bwd_patch(GradArgs a) {
         const float gbar = group_sum<G>(gs) * invN;
 #pragma unroll
         for (int j = 0; j < P; ++j) gt[j] = row_on ? gt[j] - gbar : 0.f;
+        if (h == 0.5f) {
+            patch_adjoint_half<P, G>(g, rc, k, kk, active_patch, gl, row_on, ox, row, Rrow, T, gt);
+            continue;
+        }
         const float d = rc.d;
         // every sample of the row at offset delta_i is split_shift(d + delta_i):
         // taps ox + j + off_i and the next column, weights (1 - t_i), t_i
@@ -427,13 +571,22 @@ __global__ void __launch_bounds__(256) k_bwd_patch(GradArgs a) {
         for (int i = 0; i < 5; ++i) gdt = fmaf(gE[i], dEdd[i], gdt);
         const float vF = -gdt / Fd;
         if (active_patch && gl == 0 && g.gPatch) g.gPatch[kk] = gdt;
+        // this row's template and gradient-image terms (gathered per pixel
+        // by k_bwd_gather); a rejected patch contributes zeros
+        float *cLrow = g.cpatch + ((size_t)kk * 2 * P + (row_on ? gl : 0)) * P;
+        float *cGrow = cLrow + P * P;
+        if (k < g.npx * g.npy && row_on && !active_patch) {
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                cLrow[j] = 0.f;
+                cGrow[j] = 0.f;
+            }
+        }
         if (!(active_patch && row_on)) continue;
         // scatter: window energies and the solve F into the right image (the
         // adjoint of each tap), the template into the left image, the solve
         // into the gradient image
         float *gRrow = g.gR + (size_t)row * g.w;
-        float *gLrow = g.gL + (size_t)row * g.w + ox;
-        float *gGrow = g.gG + (size_t)row * g.w + ox;
         if (staged) {
             // per-row sums over the staged columns, then one atomic per column
 #pragma unroll
@@ -453,8 +606,8 @@ __global__ void __launch_bounds__(256) k_bwd_patch(GradArgs a) {
                 const float cF = vF * gt[j];
                 acc[j + sh[0]] = fmaf(cF, 1.f - ts[0], acc[j + sh[0]]);
                 acc[j + sh[0] + 1] = fmaf(cF, ts[0], acc[j + sh[0] + 1]);
-                atomicAdd(gLrow + j, -tsum - cF);
-                atomicAdd(gGrow + j, vF * ((v0 - T[j]) - mres));
+                cLrow[j] = -tsum - cF;
+                cGrow[j] = vF * ((v0 - T[j]) - mres);
             }
             // a clamped tap's weight lands on the edge column, as in tap_row()
 #pragma unroll
@@ -475,14 +628,49 @@ __global__ void __launch_bounds__(256) k_bwd_patch(GradArgs a) {
                 const Tap q = tap_at(Rrow, g.w, ox + j, d);
                 atomicAdd(gRrow + q.x0, vF * gt[j] * (1.f - q.t));
                 atomicAdd(gRrow + q.x1, vF * gt[j] * q.t);
-                atomicAdd(gLrow + j, -tsum - vF * gt[j]);
-                atomicAdd(gGrow + j, vF * ((q.v - T[j]) - mres));
+                cLrow[j] = -tsum - vF * gt[j];
+                cGrow[j] = vF * ((q.v - T[j]) - mres);
             }
         }
     }
 }
 
 // dL/dg -> dL/dI_l through Sobel-x/8 (reflect-101), scattered.
+// Per pixel: the template and gradient-image terms of the covering patches
+// (no atomics): gG = sum of the gradient-image terms, gL += sum of the
+// template terms.
+__global__ void __launch_bounds__(256) k_bwd_gather(GradArgs a) {
+    const int P = a.P, S = a.S;
+    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) {
+        const GradDesc &g = a.descs[find_pair_g(a.descs, a.npairs, unit, G_PIX)];
+        const int idx = (unit - g.work_begin[G_PIX]) * blockDim.x + threadIdx.x;
+        if (idx >= g.w * g.h) continue;
+        const int x = idx % g.w, y = idx / g.w;
+        const int kxlo = x - P + 1 > 0 ? (x - P + 1 + S - 1) / S : 0;
+        const int kxhi = min(g.kxreg - 1, x / S);
+        const bool kxext = g.npx > g.kxreg && x >= g.w - P;
+        const int kylo = y - P + 1 > 0 ? (y - P + 1 + S - 1) / S : 0;
+        const int kyhi = min(g.kyreg - 1, y / S);
+        const bool kyext = g.npy > g.kyreg && y >= g.h - P;
+        const int nkx = kxhi - kxlo + 1 + (kxext ? 1 : 0);
+        const int nky = kyhi - kylo + 1 + (kyext ? 1 : 0);
+        float sL = 0.f, sG = 0.f;
+        for (int iy = 0; iy < nky; ++iy) {
+            const int ky = (kylo + iy <= kyhi) ? kylo + iy : g.npy - 1;
+            const int r = y - origin(ky, g.h, P, S, g.kyreg);
+            for (int ix = 0; ix < nkx; ++ix) {
+                const int kx = (kxlo + ix <= kxhi) ? kxlo + ix : g.npx - 1;
+                const int c = x - origin(kx, g.w, P, S, g.kxreg);
+                const float *cp = g.cpatch + ((size_t)(ky * g.npx + kx) * 2 * P + r) * P + c;
+                sL += __ldg(cp);
+                sG += __ldg(cp + P * P);
+            }
+        }
+        g.gG[idx] = sG;
+        g.gL[idx] += sL;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_bwd_sobel(GradArgs a) {
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) {
         const GradDesc &g = a.descs[find_pair_g(a.descs, a.npairs, unit, G_PIX)];
@@ -571,6 +759,11 @@ cudaError_t launch_bwd_patch(const GradArgs &a, cudaStream_t s) {
         case 16: return launch_bwd_patch_p<16>(a, grid, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_bwd_gather(const GradArgs &a, cudaStream_t s) {
+    k_bwd_gather<<<ggrid(a.total), 256, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_bwd_sobel(const GradArgs &a, cudaStream_t s) {

@@ -136,6 +136,7 @@ struct alignas(16) GradDesc {
     const float *sigma_r;
     float *gDisp, *gL, *gR, *gPatch, *loss;        // caller buffers
     float *gDw, *gG, *gd, *gpi, *sig_part, *coefE0, *loss_part;  // scratch
+    float *cpatch;                 // per patch: P x P template and gradient-image terms
     int w, h, pitch, gpitch, gtype;
     int npx, npy, kxreg, kyreg;
     int work_begin[G_COUNT];
@@ -156,6 +157,7 @@ cudaError_t launch_loss(const GradArgs &a, cudaStream_t s);        // + per-pair
 cudaError_t launch_bwd_pix(const GradArgs &a, cudaStream_t s);
 cudaError_t launch_bwd_dens(const GradArgs &a, cudaStream_t s);    // + sigma_r adjoint
 cudaError_t launch_bwd_patch(const GradArgs &a, cudaStream_t s);
+cudaError_t launch_bwd_gather(const GradArgs &a, cudaStream_t s);
 cudaError_t launch_bwd_sobel(const GradArgs &a, cudaStream_t s);
 
 // Kernel launchers (bdis_kernels.cu).  Each returns cudaGetLastError().

@@ -61,6 +61,8 @@ def _close(a, b, frac=1.0):
     dict(patch=8, stride=4, levels=3, iters=50),
     dict(patch=8, stride=4, levels=3, iters=50, sigma_r_mode="fixed"),
     dict(patch=12, stride=4, levels=2, iters=50, use_sgmm=0),
+    # a window step other than 1/2 takes the general (per-offset split) adjoint
+    dict(patch=8, stride=4, levels=2, iters=50, window_step=0.4),
 ])
 def test_adjoint_matches_oracle_small(bd, kw):
     pr = synth.g1_pair(64, 48, 3, d0=1.0, d1=3.0, amp=1.0, as_float=True)
