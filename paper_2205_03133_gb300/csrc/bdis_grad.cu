@@ -180,9 +180,10 @@ __global__ void __launch_bounds__(256) k_bwd_pix(GradArgs a) {
 // Per kept patch: dL/dd_k = sum_x gDw rho_k M, dL/drho_k = sum_x gDw M (d_k - D),
 // dL/dpi_k, and the patch's share of dL/dsigma_r (block partials).  A group
 // of lanes per patch, lane = patch row, so the pixel reads are row segments.
-template <int G>
+template <int P>
 __device__ __forceinline__ void bwd_dens_unit(const GradArgs &a, int unit, float *red) {
-    const int P = a.P, S = a.S;
+    constexpr int G = P <= 8 ? 8 : 16;
+    const int S = a.S;
     const int pi = find_pair_g(a.descs, a.npairs, unit, G_GROUP);
     const GradDesc &g = a.descs[pi];
     const int local = unit - g.work_begin[G_GROUP];
@@ -199,12 +200,18 @@ __device__ __forceinline__ void bwd_dens_unit(const GradArgs &a, int unit, float
         const int oy = origin(kk / g.npx, g.h, P, S, g.kyreg);
         const float my = a.use_sgmm ? a.m[gl] : 1.f;
         const size_t row = (size_t)(oy + gl) * g.w + ox;
+        float wv[P], dv[P];
+#pragma unroll
+        for (int c = 0; c < P; ++c) {  // all loads first
+            wv[c] = __ldg(g.gDw + row + c);
+            dv[c] = __ldg(g.disp + row + c);
+        }
+#pragma unroll
         for (int c = 0; c < P; ++c) {
-            const float w = __ldg(g.gDw + row + c);
-            if (w == 0.f) continue;
+            if (wv[c] == 0.f) continue;  // invalid pixel (disp may be NaN)
             const float M = my * (a.use_sgmm ? a.m[c] : 1.f);
-            gd = fmaf(w * rc.rho, M, gd);
-            grho = fmaf(w * M, rc.d - __ldg(g.disp + row + c), grho);
+            gd = fmaf(wv[c] * rc.rho, M, gd);
+            grho = fmaf(wv[c] * M, rc.d - dv[c], grho);
         }
     }
     gd = group_sum<G>(gd);
@@ -243,12 +250,10 @@ __device__ __forceinline__ void bwd_dens_unit(const GradArgs &a, int unit, float
     }
 }
 
+template <int P>
 __global__ void __launch_bounds__(256) k_bwd_dens(GradArgs a) {
     __shared__ float red[32];
-    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) {
-        if (a.P <= 8) bwd_dens_unit<8>(a, unit, red);
-        else bwd_dens_unit<16>(a, unit, red);
-    }
+    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) bwd_dens_unit<P>(a, unit, red);
 }
 
 // One block per pair: dL/dsigma_r -> the coefficient added to every kept
@@ -350,17 +355,9 @@ __device__ __forceinline__ void patch_adjoint_half(const GradDesc &g, const bdis
         sl = r[q + 1] - r[q];
         v = fmaf(t, sl, r[q]);
     };
-    float sres = 0.f, fd = 0.f;
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-        float v, sl;
-        tap(0, j, v, sl);
-        sres += row_on ? v - T[j] : 0.f;
-        fd -= gt[j] * sl;
-    }
-    const float mres = group_sum<G>(sres) * invN;
-    const float Fd = group_sum<G>(fd);
-    float abar[5], dEdd[5];
+    // means of the window residuals (the centre one is the residual mean of
+    // the solve) and dF/dd
+    float abar[5], dEdd[5], fd = 0.f;
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
         float sa = 0.f;
@@ -369,9 +366,12 @@ __device__ __forceinline__ void patch_adjoint_half(const GradDesc &g, const bdis
             float v, sl;
             tap(i, j, v, sl);
             sa += row_on ? v - T[j] : 0.f;
+            if (i == 0) fd -= gt[j] * sl;
         }
         abar[i] = group_sum<G>(sa) * invN;
     }
+    const float mres = abar[0];
+    const float Fd = group_sum<G>(fd);
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
         float sd = 0.f;
@@ -722,7 +722,23 @@ cudaError_t launch_bwd_pix(const GradArgs &a, cudaStream_t s) {
 }
 
 cudaError_t launch_bwd_dens(const GradArgs &a, cudaStream_t s) {
-    k_bwd_dens<<<ggrid(a.total), 256, 0, s>>>(a);
+    const int grid = ggrid(a.total);
+    switch (a.P) {
+        case 4: k_bwd_dens<4><<<grid, 256, 0, s>>>(a); break;
+        case 5: k_bwd_dens<5><<<grid, 256, 0, s>>>(a); break;
+        case 6: k_bwd_dens<6><<<grid, 256, 0, s>>>(a); break;
+        case 7: k_bwd_dens<7><<<grid, 256, 0, s>>>(a); break;
+        case 8: k_bwd_dens<8><<<grid, 256, 0, s>>>(a); break;
+        case 9: k_bwd_dens<9><<<grid, 256, 0, s>>>(a); break;
+        case 10: k_bwd_dens<10><<<grid, 256, 0, s>>>(a); break;
+        case 11: k_bwd_dens<11><<<grid, 256, 0, s>>>(a); break;
+        case 12: k_bwd_dens<12><<<grid, 256, 0, s>>>(a); break;
+        case 13: k_bwd_dens<13><<<grid, 256, 0, s>>>(a); break;
+        case 14: k_bwd_dens<14><<<grid, 256, 0, s>>>(a); break;
+        case 15: k_bwd_dens<15><<<grid, 256, 0, s>>>(a); break;
+        case 16: k_bwd_dens<16><<<grid, 256, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_bwd_sigma<<<ggrid(a.npairs), 256, 0, s>>>(a);
