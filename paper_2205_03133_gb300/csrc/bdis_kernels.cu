@@ -206,6 +206,20 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
     const TG *Gi = (const TG *)D.G;
 
     __syncthreads();  // the previous unit's readers are done with smem
+    // the left-image and gradient bands do not depend on the estimates: the
+    // first column's loads are issued before the initial estimates are read.
+    // Only where the register budget has room (P > 8 runs 2 blocks per SM;
+    // the 3-block instances would spill).
+    constexpr bool kEarlyLG = P > 8;
+    float vl0[P], vg0[P];
+    const bool col0 = kEarlyLG && tid < cw;
+    if (col0) {
+#pragma unroll
+        for (int r = 0; r < P; ++r) {
+            vl0[r] = ldf(L + (size_t)(oy + r) * D.pitch + cx0 + tid);
+            vg0[r] = ldf(Gi + (size_t)(oy + r) * D.gpitch + cx0 + tid);
+        }
+    }
     // initial estimates of the chunk (coarser fused map at the centre)
     float dlo = FLT_MAX, dhi = -FLT_MAX;
     for (int t = tid; t < nk; t += blockDim.x) {
@@ -218,6 +232,13 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
         dsh[t] = di;
         dlo = fminf(dlo, di);
         dhi = fmaxf(dhi, di);
+    }
+    if (col0) {
+#pragma unroll
+        for (int r = 0; r < P; ++r) {
+            Lb[r * cp + tid] = vl0[r];
+            Gb[r * cp + tid] = vg0[r];
+        }
     }
     block_minmax(dlo, dhi, red);
     // column window of the right band
@@ -235,7 +256,7 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
 #pragma unroll
         for (int r = 0; r < P; ++r) Rb[r * bp + c] = v[r];
     }
-    for (int c = tid; c < cw; c += blockDim.x) {
+    for (int c = kEarlyLG ? tid + blockDim.x : tid; c < cw; c += blockDim.x) {
         float vl[P], vg[P];
 #pragma unroll
         for (int r = 0; r < P; ++r) {
@@ -589,15 +610,37 @@ __device__ __forceinline__ float exp_schraudolph(float y) {
 // One thread per patch of a tile's patch set: pi_k = p_0 / sum_i p_i with
 // p_i = exp(-E_i/(2 sigma_r^2 s^2)), rho_k = Gamma_n pi_k + Q^(n+1)(centre),
 // and at the finest level with variance on the PDF fit.
-__device__ float4 posterior_of(const LaunchArgs &a, const LevelDesc &D, int kx, int ky, float sr,
-                               bool write) {
-    const int k = ky * D.npx + kx;
-    bdis_patch_record *rec = D.rec + k;
+// The memory inputs of one patch's posterior (loaded before sigma_r is
+// known, so the loads overlap its reduction).
+struct PostIn {
+    float4 r0, r1, r2;  // d, dinit, dlast, H | E0, dE1, dE2, dE3 | dE4, cT, flags, nout + pdf_flags
+    float mu, prop;     // mean offset; coarse probability at the centre (Eq. 10)
+};
+
+__device__ __forceinline__ PostIn posterior_load(const LaunchArgs &a, const LevelDesc &D, int kx,
+                                                 int ky) {
+    const bdis_patch_record *rec = D.rec + ky * D.npx + kx;
     // L2 loads: the record was written by another block, possibly earlier in
     // the same (persistent) launch
-    const float4 r0 = __ldcg((const float4 *)rec);       // d, dinit, dlast, H
-    const float4 r1 = __ldcg((const float4 *)rec + 1);   // E0, dE1, dE2, dE3
-    const float4 r2 = __ldcg((const float4 *)rec + 2);   // dE4, cT, flags, nout | pdf_flags
+    PostIn in;
+    in.r0 = __ldcg((const float4 *)rec);
+    in.r1 = __ldcg((const float4 *)rec + 1);
+    in.r2 = __ldcg((const float4 *)rec + 2);
+    in.mu = __ldcg(&rec->mu);
+    in.prop = 0.f;
+    if (a.use_c2f && D.Qc != nullptr) {
+        const float cx = (float)origin(kx, D.w, a.P, a.S, D.kxreg) + 0.5f * (float)(a.P - 1);
+        const float cy = (float)origin(ky, D.h, a.P, a.S, D.kyreg) + 0.5f * (float)(a.P - 1);
+        in.prop = coarse_bilin(D.Qc, D.wc, D.hc, cx, cy);
+    }
+    return in;
+}
+
+__device__ float4 posterior_of(const LaunchArgs &a, const LevelDesc &D, int kx, int ky,
+                               const PostIn &in, float sr, bool write) {
+    const int k = ky * D.npx + kx;
+    bdis_patch_record *rec = D.rec + k;
+    const float4 r0 = in.r0, r1 = in.r1, r2 = in.r2;
     const uint32_t flags = __float_as_uint(r2.z);
     if (flags != 0u) {
         if (write) {
@@ -607,7 +650,7 @@ __device__ float4 posterior_of(const LaunchArgs &a, const LevelDesc &D, int kx, 
         }
         return make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    const float mu = __ldcg(&rec->mu);
+    const float mu = in.mu;
     const float h = a.window_step;
     const float dlt[5] = {0.f, -h, h, -2.f * h, 2.f * h};
     const float scale = 2.f * sr * sr * (float)(kWindow * kWindow);
@@ -632,13 +675,7 @@ __device__ float4 posterior_of(const LaunchArgs &a, const LevelDesc &D, int kx, 
     }
     float rho;
     if (a.use_c2f) {
-        float prop = 0.f;
-        if (D.Qc != nullptr) {
-            const float cx = (float)origin(kx, D.w, a.P, a.S, D.kxreg) + 0.5f * (float)(a.P - 1);
-            const float cy = (float)origin(ky, D.h, a.P, a.S, D.kyreg) + 0.5f * (float)(a.P - 1);
-            prop = coarse_bilin(D.Qc, D.wc, D.hc, cx, cy);
-        }
-        rho = a.gamma_w * pi + prop;
+        rho = a.gamma_w * pi + in.prop;
     } else {
         rho = pi;
     }
@@ -696,6 +733,28 @@ __device__ __forceinline__ void fuse_unit(const LaunchArgs &a, int unit, float4 
     const int tx = tile % D.tiles_x, ty = tile / D.tiles_x;
     const int x0 = tx * TW, y0 = ty * TH;
     const int x1 = min(x0 + TW, D.w) - 1, y1 = min(y0 + TH, D.h) - 1;
+    // patches overlapping the tile
+    int kxlo, kxhi, kylo, kyhi, tmp;
+    bool kxext, kyext, bext;
+    cover(x0, D.w, P, S, D.kxreg, D.npx, kxlo, tmp, bext);
+    cover(x1, D.w, P, S, D.kxreg, D.npx, tmp, kxhi, kxext);
+    cover(y0, D.h, P, S, D.kyreg, D.npy, kylo, tmp, bext);
+    cover(y1, D.h, P, S, D.kyreg, D.npy, tmp, kyhi, kyext);
+    const int nkxr = max(0, kxhi - kxlo + 1), nkyr = max(0, kyhi - kylo + 1);
+    const int nkx = nkxr + (kxext ? 1 : 0);
+    const int nky = nkyr + (kyext ? 1 : 0);
+    // the first patch's posterior inputs are loaded before sigma_r is known
+    auto patch_of = [&](int i, int &kx, int &ky) {
+        const int ix = i % nkx, iy = i / nkx;
+        kx = ix < nkxr ? kxlo + ix : D.npx - 1;
+        ky = iy < nkyr ? kylo + iy : D.npy - 1;
+    };
+    PostIn pre;
+    if ((int)threadIdx.x < nkx * nky) {
+        int kx, ky;
+        patch_of(threadIdx.x, kx, ky);
+        pre = posterior_load(a, D, kx, ky);
+    }
     // sigma_r of the pair from the search's exact sums (text after Eq. 6),
     // by one thread (FP64 conversions), broadcast through shared memory
     __shared__ float sr_sh;
@@ -720,24 +779,14 @@ __device__ __forceinline__ void fuse_unit(const LaunchArgs &a, int unit, float4 
     __syncthreads();
     const float sr = sr_sh;
 
-    // patches overlapping the tile
-    int kxlo, kxhi, kylo, kyhi, tmp;
-    bool kxext, kyext, bext;
-    cover(x0, D.w, P, S, D.kxreg, D.npx, kxlo, tmp, bext);
-    cover(x1, D.w, P, S, D.kxreg, D.npx, tmp, kxhi, kxext);
-    cover(y0, D.h, P, S, D.kyreg, D.npy, kylo, tmp, bext);
-    cover(y1, D.h, P, S, D.kyreg, D.npy, tmp, kyhi, kyext);
-    const int nkxr = max(0, kxhi - kxlo + 1), nkyr = max(0, kyhi - kylo + 1);
-    const int nkx = nkxr + (kxext ? 1 : 0);
-    const int nky = nkyr + (kyext ? 1 : 0);
     for (int i = threadIdx.x; i < nkx * nky; i += blockDim.x) {
-        const int ix = i % nkx, iy = i / nkx;
-        const int kx = ix < nkxr ? kxlo + ix : D.npx - 1;
-        const int ky = iy < nkyr ? kylo + iy : D.npy - 1;
+        int kx, ky;
+        patch_of(i, kx, ky);
         const int ox = origin(kx, D.w, P, S, D.kxreg);
         const int oy = origin(ky, D.h, P, S, D.kyreg);
         const bool owner = ox >= x0 && ox < x0 + TW && oy >= y0 && oy < y0 + TH;
-        fz[i] = posterior_of(a, D, kx, ky, sr, owner);
+        const PostIn in = i == (int)threadIdx.x ? pre : posterior_load(a, D, kx, ky);
+        fz[i] = posterior_of(a, D, kx, ky, in, sr, owner);
     }
     // covering patches (tile-local indices) and their weights per column / row
     if (threadIdx.x < TW + TH) {
