@@ -366,7 +366,7 @@ def main():
     m = bd.BDIS(**PARAMS)
     if args.form != "auto":
         m.set_option(B.OPT_FORM, {"launches": 1, "persistent": 2}[args.form])
-    launches_per_step = 3 * PARAMS["levels"]
+    launches_per_step = None  # counted by the profiling pass below
 
     def step():
         m.match(Ld, Rd, out=out, stream=stream)
@@ -416,6 +416,7 @@ def main():
             kernels[name] = {"launches_per_step": prof.launches[i] // n_prof,
                              "ms_per_step": prof.ms[i] / n_prof,
                              "avg_launch_us": prof.ms[i] / prof.launches[i] * 1e3}
+    launches_per_step = sum(k["launches_per_step"] for k in kernels.values())
     tot_k = sum(k["ms_per_step"] for k in kernels.values())
     for k in kernels.values():
         k["share"] = round(k["ms_per_step"] / tot_k, 4)

@@ -268,7 +268,12 @@ typedef enum {
      * predecessor drains and starts reading once the predecessor has
      * completed (hides the launch gap between dependent kernels); 0: plain
      * stream order.  Same results. */
-    BDIS_OPT_PDL = 5
+    BDIS_OPT_PDL = 5,
+    /* Pyramid launches: 0 (default) two steps per launch (level l -> l+1 ->
+     * l+2, recomputing a 2-pixel halo of level l+1) when the call has at most
+     * 2^21 level-0 pixels, else one step per launch; 1 always one step;
+     * 2 always two steps where two coarser levels remain.  Same results. */
+    BDIS_OPT_PYRAMID_STEPS = 6
 } bdis_option;
 
 bdis_status bdis_set_option(bdis_handle *h, int option, int value);

@@ -53,6 +53,7 @@ struct bdis_handle {
     bool last_persistent = false;
     int form = 0;             // BDIS_OPT_FORM
     bool use_pdl = true;      // BDIS_OPT_PDL
+    int pyr_steps = 0;        // BDIS_OPT_PYRAMID_STEPS
     // per-kernel event timing
     bool profile = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -431,9 +432,18 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
     // stage list: the pyramid levels, then (search, fuse) per level coarse to fine
     std::vector<LaunchArgs> stages;
     std::vector<int> stage_itype;
-    for (int l = 0; l < NL; ++l) {
+    // pyramid stages: two steps per launch (level l -> l+1 -> l+2) while two
+    // coarser levels remain, then single steps (the coarsest builds only its
+    // gradient).  Two steps save launches but recompute a halo: worth it while
+    // the launch latency dominates, i.e. for calls of up to 2^21 level-0 pixels.
+    size_t px0 = 0;
+    for (int i = 0; i < n; ++i) px0 += (size_t)pairs[i].w * pairs[i].h;
+    const bool two_steps = h->pyr_steps == 2 || (h->pyr_steps == 0 && px0 <= ((size_t)1 << 21));
+    for (int l = 0; l < NL;) {
         LaunchArgs a = base_args(p, l, d_descs + (size_t)l * n, n);
-        a.kind = 0;
+        const bool two = two_steps && l + 2 <= NL - 1;
+        a.kind = two ? 4 : 0;
+        a.descs2 = two ? d_descs + (size_t)(l + 1) * n : nullptr;
         a.total = pl.units[l][W_PYR];
         if (l == 0) {
             a.acc_zero = (unsigned long long *)(h->arena + pl.off_acc);
@@ -441,6 +451,7 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
         }
         stages.push_back(a);
         stage_itype.push_back(l == 0 ? in_type : st_type);
+        l += two ? 2 : 1;
     }
     const int F = p.finest_level;
     for (int l = NL - 1; l >= F; --l) {
@@ -520,7 +531,7 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
 
     if (mega) {
         // persistent form: one cooperative launch runs every stage
-        const size_t msm = std::max(kPyrSmemBytes, std::max(smax, fmax));
+        const size_t msm = std::max(kPyr2SmemBytes, std::max(smax, fmax));
         const int grid = mega_grid(p.patch, st_type, msm);
         if (grid < 1) return fail(h, BDIS_EUNSUPPORTED, "persistent form unavailable");
         MegaArgs m;
@@ -545,8 +556,11 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
         for (size_t k = 0; k < stages.size(); ++k) {
             const LaunchArgs &a = stages[k];
             const int itype = stage_itype[k];
-            if (a.kind == 0) {
-                e = timed(BDIS_K_PYRAMID, [&] { return launch_pyramid(a, itype, st_type, st); });
+            if (a.kind == 0 || a.kind == 4) {
+                e = timed(BDIS_K_PYRAMID, [&] {
+                    return a.kind == 4 ? launch_pyramid2(a, itype, st_type, st)
+                                       : launch_pyramid(a, itype, st_type, st);
+                });
                 if (e != cudaSuccess) return cuda_fail(h, e, "pyramid launch");
             } else if (a.kind == 1) {
                 const size_t sm = ssm[a.level];
@@ -643,19 +657,17 @@ bdis_status autotune(bdis_handle *h, int n, const bdis_pair *pairs, int in_type,
         const size_t m0 = h->ev_marks.size();
         s = run_cfg(h, n, pairs, in_type, st, cfg.data(), false, true);
         if (s != BDIS_OK) return s;
-        // marks in launch order: NL pyramids, then (search, fuse) for l = NL-1 .. F,
-        // then the upsampling when F > 0
-        const int F = h->p.finest_level;
+        // search and fuse marks come coarsest level first
+        int ns = 0, nf = 0;
         for (size_t m = m0; m < h->ev_marks.size(); ++m) {
             float ms = 0.f;
             const size_t ev = h->ev_marks[m].second;
             cudaError_t e = cudaEventSynchronize(h->ev_pool[ev + 1]);
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, h->ev_pool[ev], h->ev_pool[ev + 1]);
             if (e != cudaSuccess) return cuda_fail(h, e, "autotune events");
-            const int idx = (int)(m - m0);
-            if (idx < NL || idx - NL >= 2 * (NL - F)) continue;
-            const int l = NL - 1 - (idx - NL) / 2;
-            if ((idx - NL) % 2 == 0) tsearch[c][l] = ms; else tfuse[c][l] = ms;
+            const int kid = h->ev_marks[m].first;
+            if (kid == BDIS_K_SEARCH) tsearch[c][NL - 1 - ns++] = ms;
+            else if (kid == BDIS_K_FUSE) tfuse[c][NL - 1 - nf++] = ms;
         }
         h->ev_marks.resize(m0);
     }
@@ -822,6 +834,11 @@ bdis_status bdis_set_option(bdis_handle *h, int option, int value) {
     }
     if (option == BDIS_OPT_PDL) {
         h->use_pdl = value != 0;
+        return BDIS_OK;
+    }
+    if (option == BDIS_OPT_PYRAMID_STEPS) {
+        if (value < 0 || value > 2) return fail(h, BDIS_EINVAL, "pyramid steps must be 0, 1 or 2");
+        h->pyr_steps = value;
         return BDIS_OK;
     }
     return fail(h, BDIS_EINVAL, "unknown option");

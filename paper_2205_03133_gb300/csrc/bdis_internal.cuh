@@ -73,6 +73,7 @@ struct alignas(16) LevelDesc {
 // Per-launch arguments (passed by value).
 struct LaunchArgs {
     const LevelDesc *descs;   // the npairs descriptors of this level
+    const LevelDesc *descs2;  // two-step pyramid stage: the descriptors of the next level
     int npairs;
     int total;                // total work units of this launch
     int level, levels;
@@ -96,7 +97,7 @@ struct LaunchArgs {
     unsigned long long *acc_zero;  // finest pyramid launch: accumulators to clear
     int acc_count;
     int kind;                 // stage of the persistent form: 0 pyramid, 1 search, 2 fuse,
-                              // 3 upsample
+                              // 3 upsample, 4 two-step pyramid
     int finest;               // finest processed level f
     int weight_mode;          // bdis_weight_mode
     int fast_exp;             // Schraudolph exponential in the posterior
@@ -162,6 +163,8 @@ cudaError_t launch_bwd_sobel(const GradArgs &a, cudaStream_t s);
 
 // Kernel launchers (bdis_kernels.cu).  Each returns cudaGetLastError().
 cudaError_t launch_pyramid(const LaunchArgs &a, int in_type, int out_type, cudaStream_t s);
+// Two pyramid steps (level l -> l+1 -> l+2, with both gradients) per launch.
+cudaError_t launch_pyramid2(const LaunchArgs &a, int in_type, int out_type, cudaStream_t s);
 cudaError_t launch_search(const LaunchArgs &a, int in_type, int g_type, size_t smem, int grid,
                           cudaStream_t s);
 cudaError_t launch_fuse(const LaunchArgs &a, size_t smem, cudaStream_t s);
@@ -179,6 +182,7 @@ bool mega_supported(int P);
 int mega_grid(int P, int st_type, size_t smem);
 cudaError_t launch_mega(const MegaArgs &m, int P, int st_type, int grid, size_t smem, cudaStream_t s);
 constexpr size_t kPyrSmemBytes = sizeof(float) * 2 * 36 * 68;
+constexpr size_t kPyr2SmemBytes = sizeof(float) * (2 * 44 * 76 + 2 * 20 * 36 + 2 * 44 * 36);
 // Raise (never lower) the dynamic shared-memory limit of every search instance.
 cudaError_t prepare_search(int P, size_t smem_bytes);
 // Number of resident search blocks per SM for (P, image type, gradient type, smem).

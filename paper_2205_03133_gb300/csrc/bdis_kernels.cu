@@ -113,6 +113,166 @@ __device__ __forceinline__ void pyramid_unit(const LaunchArgs &a, int unit, floa
     }
     }
 
+// Two pyramid steps in one unit: a 64x32 tile of level l gives its Sobel-x,
+// the 32x16 tile of level l+1 with its Sobel-x, and the 16x8 tile of level
+// l+2.  The level-(l+1) values the second step reads (the tile plus a
+// 2-pixel halo) are computed here from a 76x44 level-l region and rounded to
+// the storage type exactly as when they are read back from memory; a halo
+// pixel outside level l+1 takes the value of its reflect-101 image pixel.
+constexpr int kPyr2SW = kPyrTW + 12, kPyr2SH = kPyrTH + 12;    // level l: +-6
+constexpr int kPyr2MW = kPyrTW / 2 + 4, kPyr2MH = kPyrTH / 2 + 4;  // level l+1: +-2
+// level l region (L, R), level l+1 region (L, R), horizontal blur rows (L, R)
+constexpr size_t kPyr2SmemFloats = 2 * (size_t)kPyr2SW * kPyr2SH + 2 * (size_t)kPyr2MW * kPyr2MH +
+                                   2 * (size_t)kPyr2SH * kPyr2MW;
+static_assert(kPyr2SmemFloats * sizeof(float) == kPyr2SmemBytes, "two-step pyramid shared memory");
+
+template <typename TO>
+__device__ __forceinline__ float round_to(float v) {
+    if constexpr (sizeof(TO) == 2) return __half2float(__float2half_rn(v));
+    return v;
+}
+
+template <typename TI, typename TO>
+__device__ __forceinline__ void pyramid2_unit(const LaunchArgs &a, int unit, float *sm) {
+    float(*Ls)[kPyr2SW] = (float(*)[kPyr2SW])sm;
+    float(*Rs)[kPyr2SW] = Ls + kPyr2SH;
+    float(*Lm)[kPyr2MW] = (float(*)[kPyr2MW])(sm + 2 * kPyr2SW * kPyr2SH);
+    float(*Rm)[kPyr2MW] = Lm + kPyr2MH;
+    float(*Lh)[kPyr2MW] = Rm + kPyr2MH;   // horizontal blur of every level-l row
+    float(*Rh)[kPyr2MW] = Lh + kPyr2SH;
+    const int pi = find_pair(a.descs, a.npairs, unit, W_PYR);
+    const LevelDesc &D = a.descs[pi];     // level l
+    const LevelDesc &E = a.descs2[pi];    // level l+1 (its Ln, Rn: level l+2)
+    const int tile = unit - D.work_begin[W_PYR];
+    const int ntx = (D.w + kPyrTW - 1) / kPyrTW;
+    const int tx = tile % ntx, ty = tile / ntx;
+    const int x0 = tx * kPyrTW - 6, y0 = ty * kPyrTH - 6;  // level-l region origin
+    const int X0 = tx * (kPyrTW / 2) - 2, Y0 = ty * (kPyrTH / 2) - 2;  // level-(l+1) region origin
+    const int w = D.w, h = D.h, pitch = D.pitch;
+    const int w1 = E.w, h1 = E.h;
+    const TI *L = (const TI *)D.L;
+    const TI *R = (const TI *)D.R;
+    __syncthreads();
+    constexpr int NEL = kPyr2SH * kPyr2SW;
+    constexpr int PER = (NEL + 255) / 256;
+    float vl[PER], vr[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = threadIdx.x + k * 256;
+        if (i < NEL) {
+            const int r = i / kPyr2SW, c = i - r * kPyr2SW;
+            const int gy = refl(min(max(y0 + r, -2), h + 1), h);
+            const int gx = refl(min(max(x0 + c, -2), w + 1), w);
+            vl[k] = ldf(L + (size_t)gy * pitch + gx);
+            vr[k] = ldf(R + (size_t)gy * pitch + gx);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = threadIdx.x + k * 256;
+        if (i < NEL) {
+            const int r = i / kPyr2SW, c = i - r * kPyr2SW;
+            Ls[r][c] = vl[k];
+            Rs[r][c] = vr[k];
+        }
+    }
+    __syncthreads();
+    // Sobel-x/8 of level l over the 64x32 tile
+    TO *G = (TO *)D.G;
+    for (int i = threadIdx.x; G != nullptr && i < kPyrTW * kPyrTH; i += blockDim.x) {
+        const int ly = i / kPyrTW, lx = i - ly * kPyrTW;
+        const int x = x0 + 6 + lx, y = y0 + 6 + ly;
+        if (x >= w || y >= h) continue;
+        const int cx = lx + 6, cy = ly + 6;
+        const float acc = (Ls[cy - 1][cx + 1] - Ls[cy - 1][cx - 1]) +
+                          2.f * (Ls[cy][cx + 1] - Ls[cy][cx - 1]) +
+                          (Ls[cy + 1][cx + 1] - Ls[cy + 1][cx - 1]);
+        stf(G + (size_t)y * D.gpitch + x, acc * 0.125f);
+    }
+    // level l+1 over the tile and its 2-pixel halo (halo pixels take their
+    // reflect-101 image pixel): horizontal pass at the needed even columns,
+    // then vertical pass; the same multiply-add order as the one-step kernel
+    const float k5[5] = {1.f, 4.f, 6.f, 4.f, 1.f};
+    for (int i = threadIdx.x; i < kPyr2SH * kPyr2MW; i += blockDim.x) {
+        const int r = i / kPyr2MW, mx = i - r * kPyr2MW;
+        const int Xr = refl(min(max(X0 + mx, -2), w1 + 1), w1);
+        const int cx = 2 * Xr - x0;
+        float sl = 0.f, sr = 0.f;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            sl += k5[q] * Ls[r][cx + q - 2];
+            sr += k5[q] * Rs[r][cx + q - 2];
+        }
+        Lh[r][mx] = sl;
+        Rh[r][mx] = sr;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kPyr2MW * kPyr2MH; i += blockDim.x) {
+        const int my = i / kPyr2MW, mx = i - my * kPyr2MW;
+        const int X = X0 + mx, Y = Y0 + my;
+        const int Yr = refl(min(max(Y, -2), h1 + 1), h1);
+        const int cy = 2 * Yr - y0;
+        float accL = 0.f, accR = 0.f;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            accL += k5[j] * Lh[cy + j - 2][mx];
+            accR += k5[j] * Rh[cy + j - 2][mx];
+        }
+        const float vL = accL * (1.f / 256.f), vR = accR * (1.f / 256.f);
+        Lm[my][mx] = round_to<TO>(vL);
+        Rm[my][mx] = round_to<TO>(vR);
+        const bool own = mx >= 2 && mx < 2 + kPyrTW / 2 && my >= 2 && my < 2 + kPyrTH / 2;
+        if (own && X < w1 && Y < h1) {
+            stf((TO *)D.Ln + (size_t)Y * D.pitchn + X, vL);
+            stf((TO *)D.Rn + (size_t)Y * D.pitchn + X, vR);
+        }
+    }
+    __syncthreads();
+    // Sobel-x/8 of level l+1 over its 32x16 tile
+    TO *G1 = (TO *)E.G;
+    for (int i = threadIdx.x; G1 != nullptr && i < (kPyrTW / 2) * (kPyrTH / 2); i += blockDim.x) {
+        const int ly = i / (kPyrTW / 2), lx = i - ly * (kPyrTW / 2);
+        const int X = X0 + 2 + lx, Y = Y0 + 2 + ly;
+        if (X >= w1 || Y >= h1) continue;
+        const int cx = lx + 2, cy = ly + 2;
+        const float acc = (Lm[cy - 1][cx + 1] - Lm[cy - 1][cx - 1]) +
+                          2.f * (Lm[cy][cx + 1] - Lm[cy][cx - 1]) +
+                          (Lm[cy + 1][cx + 1] - Lm[cy + 1][cx - 1]);
+        stf(G1 + (size_t)Y * E.gpitch + X, acc * 0.125f);
+    }
+    // level l+2 over its 16x8 tile
+    for (int i = threadIdx.x; i < (kPyrTW / 4) * (kPyrTH / 4); i += blockDim.x) {
+        const int oy = i / (kPyrTW / 4), ox = i - oy * (kPyrTW / 4);
+        const int X = tx * (kPyrTW / 4) + ox, Y = ty * (kPyrTH / 4) + oy;
+        if (X >= E.wn || Y >= E.hn) continue;
+        const int cx = 2 * ox + 2, cy = 2 * oy + 2;
+        float accL = 0.f, accR = 0.f;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            float sl = 0.f, sr = 0.f;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                sl += k5[q] * Lm[cy + j - 2][cx + q - 2];
+                sr += k5[q] * Rm[cy + j - 2][cx + q - 2];
+            }
+            accL += k5[j] * sl;
+            accR += k5[j] * sr;
+        }
+        stf((TO *)E.Ln + (size_t)Y * E.pitchn + X, accL * (1.f / 256.f));
+        stf((TO *)E.Rn + (size_t)Y * E.pitchn + X, accR * (1.f / 256.f));
+    }
+}
+
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(256) k_pyramid2(LaunchArgs a) {
+    __shared__ float sm[kPyr2SmemFloats];
+    pdl_wait();
+    if (blockIdx.x == 0 && a.acc_zero != nullptr)
+        for (int i = threadIdx.x; i < a.acc_count; i += blockDim.x) a.acc_zero[i] = 0ull;
+    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) pyramid2_unit<TI, TO>(a, unit, sm);
+    pdl_release();
+}
+
 template <typename TI, typename TO>
 __global__ void __launch_bounds__(256) k_pyramid(LaunchArgs a) {
     __shared__ float Ls[kPyrSH][kPyrSW];
@@ -1069,6 +1229,14 @@ __global__ void __launch_bounds__(256) k_mega(MegaArgs m) {
             } else {
                 for (int u = blockIdx.x; u < total; u += gridDim.x) pyramid_unit<TG, TG>(a, u, Ls, Rs);
             }
+        } else if (a.kind == 4) {
+            if (blockIdx.x == 0 && a.acc_zero != nullptr)
+                for (int i = threadIdx.x; i < a.acc_count; i += blockDim.x) a.acc_zero[i] = 0ull;
+            if (a.level == 0) {
+                for (int u = blockIdx.x; u < total; u += gridDim.x) pyramid2_unit<uint8_t, TG>(a, u, smem);
+            } else {
+                for (int u = blockIdx.x; u < total; u += gridDim.x) pyramid2_unit<TG, TG>(a, u, smem);
+            }
         } else if (a.kind == 1) {
             if (a.level == 0) {
                 for (int u = blockIdx.x; u < total; u += gridDim.x) search_unit<P, uint8_t, TG>(a, u, smem);
@@ -1199,9 +1367,9 @@ cudaError_t launch_mega(const MegaArgs &m, int P, int st_type, int grid, size_t 
 int search_group(int P) { return P <= 8 ? 8 : 16; }
 int search_chunk(int P, int passes) { return passes * (256 / search_group(P)); }
 
-// Raises (never lowers) a kernel's dynamic shared-memory limit to `bytes`.
+// Raises (never lowers) a kernel's dynamic shared-memory limit to `bytes`
+// (the default limit is 48 KB less the kernel's static shared memory).
 cudaError_t raise_smem_limit(const void *f, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
     cudaFuncAttributes at;
     cudaError_t e = cudaFuncGetAttributes(&at, f);
     if (e != cudaSuccess) return e;
@@ -1259,6 +1427,18 @@ cudaError_t launch_pyramid(const LaunchArgs &a, int in_type, int out_type, cudaS
         f = in_type == E_U8    ? (const void *)k_pyramid<uint8_t, __half>
             : in_type == E_F32 ? (const void *)k_pyramid<float, __half>
                                : (const void *)k_pyramid<__half, __half>;
+    }
+    return launch_args_kernel(f, a, grid_for(a.total, 8), 0, s);
+}
+
+cudaError_t launch_pyramid2(const LaunchArgs &a, int in_type, int out_type, cudaStream_t s) {
+    const void *f = nullptr;
+    if (out_type == E_F32) {
+        f = in_type == E_U8 ? (const void *)k_pyramid2<uint8_t, float> : (const void *)k_pyramid2<float, float>;
+    } else {
+        f = in_type == E_U8    ? (const void *)k_pyramid2<uint8_t, __half>
+            : in_type == E_F32 ? (const void *)k_pyramid2<float, __half>
+                               : (const void *)k_pyramid2<__half, __half>;
     }
     return launch_args_kernel(f, a, grid_for(a.total, 8), 0, s);
 }

@@ -328,31 +328,32 @@ def test_noalloc_rejects_finest_level(bd):
     dict(patch=10, stride=4, levels=6, iters=12, finest_level=1, variance=1),
 ])
 def test_launch_options_do_not_change_results(bd, kw):
-    """Programmatic dependent launch and graph replay change only how the
-    launch sequence is issued: outputs are bitwise equal with every combination."""
+    """Programmatic dependent launch, graph replay and one or two pyramid
+    steps per launch change only how the work is issued: outputs are bitwise
+    equal with every combination."""
     import torch
     pair = synth.g2_pair(640, 480, 11)
     L = torch.from_numpy(pair.left).cuda()
     R = torch.from_numpy(pair.right).cuda()
     ref = None
-    for graph in (0, 1):
-        for pdl in (0, 1):
-            m = bd.BDIS(**kw)
-            m.set_option(bd.B.OPT_FORM, 1)
-            m.set_option(bd.B.OPT_GRAPH, graph)
-            m.set_option(bd.B.OPT_PDL, pdl)
-            stream = torch.cuda.Stream()
-            with torch.cuda.stream(stream):
-                for _ in range(3):   # capture, then replays
-                    d, v, ok = m.match(L, R, stream=stream)
-            torch.cuda.synchronize()
-            got = (torch.nan_to_num(d, nan=-1.0), torch.nan_to_num(v, nan=-1.0), ok)
-            if ref is None:
-                ref = got
-            else:
-                for a, b in zip(ref, got):
-                    assert torch.equal(a, b), (graph, pdl)
-            m.close()
+    for graph, pdl, steps in ((0, 0, 1), (0, 1, 2), (1, 0, 2), (1, 1, 1), (1, 1, 2)):
+        m = bd.BDIS(**kw)
+        m.set_option(bd.B.OPT_FORM, 1)
+        m.set_option(bd.B.OPT_GRAPH, graph)
+        m.set_option(bd.B.OPT_PDL, pdl)
+        m.set_option(bd.B.OPT_PYRAMID_STEPS, steps)
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            for _ in range(3):   # capture, then replays
+                d, v, ok = m.match(L, R, stream=stream)
+        torch.cuda.synchronize()
+        got = (torch.nan_to_num(d, nan=-1.0), torch.nan_to_num(v, nan=-1.0), ok)
+        if ref is None:
+            ref = got
+        else:
+            for a, b in zip(ref, got):
+                assert torch.equal(a, b), (graph, pdl, steps)
+        m.close()
 
 
 def _coverage(disp, var, valid, gt, z=1.96):
