@@ -99,3 +99,21 @@ def test_depth_argument_checks(lib):
     assert lib.bdis_depth(None, None, 10, C.c_float(1.0), 16, None, None) == B.BDIS_EINVAL
     assert lib.bdis_depth(16, 16, 10, C.c_float(1.0), 16, None, None) == B.BDIS_EINVAL
     assert lib.bdis_depth(None, None, 0, C.c_float(1.0), None, None, None) == B.BDIS_OK
+
+
+def test_empty_and_oversize_inputs_rejected(lib):
+    import paper_2205_03133_gb300 as bd
+    B = bd.B
+    m = bd.BDIS(patch=8, stride=4, levels=2)
+    for (w, h, pitch) in ((0, 48, 64), (64, 0, 64), (-5, 48, 64), (40000, 48, 40000),
+                          (64, 40000, 64), (64, 48, 0)):
+        st = lib.bdis_match(m._h, 16, 16, w, h, pitch, 16, None, 16, None)
+        assert st == B.BDIS_EINVAL, (w, h, pitch)
+    # an empty batch
+    assert lib.bdis_match_batched(m._h, 0, None, None) == B.BDIS_EINVAL
+    pairs = (B.bdis_pair * 1)()
+    assert lib.bdis_match_batched(m._h, 0, pairs, None) == B.BDIS_EINVAL
+    assert lib.bdis_match_batched(m._h, -1, pairs, None) == B.BDIS_EINVAL
+    # the extreme patch geometries are accepted
+    for kw in (dict(patch=4, stride=1), dict(patch=16, stride=16), dict(patch=16, stride=1)):
+        bd.BDIS(levels=1, **kw).close()

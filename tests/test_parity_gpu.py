@@ -103,6 +103,8 @@ def test_pyramid_and_gradient_f16(bd):
     (160, 120, dict(patch=8, stride=4, levels=3, iters=8, use_sgmm=0, use_c2f=0)),
     (160, 120, dict(patch=8, stride=4, levels=1, iters=8, variance=1)),
     (160, 120, dict(patch=8, stride=4, levels=2, iters=0)),
+    (64, 48, dict(patch=4, stride=1, levels=2, iters=8)),          # smallest patch, densest grid
+    (96, 80, dict(patch=16, stride=1, levels=1, iters=6, variance=1)),  # 256 patches per pixel
 ])
 def test_ragged_and_parameter_cases(bd, w, h, kw):
     pair = synth.g1_pair(w, h, w * 7 + h)
@@ -379,3 +381,12 @@ def test_variance_coverage_matches_oracle(bd, gen, kw):
     assert abs(ng - no) <= max(2, 0.001 * no)
     assert abs(cg - co) <= 1e-3, (cg, co)
     assert 0.5 < co <= 1.0
+
+
+def test_largest_workload_4k_f16(bd):
+    """3840x2160 (HD generator, disparities to 160 px), 12x12 patches at stride
+    4, 6 levels, variance, FP16 pyramids: the largest single pair tested."""
+    pair = synth.g1_pair(3840, 2160, 2, d0=10.0, d1=140.0, amp=20.0, sigma=240.0)
+    m = {}
+    _check_pair(bd, dict(patch=12, stride=4, levels=6, iters=8, variance=1, storage="f16"), pair, m)
+    print("3840x2160 f16", m)
