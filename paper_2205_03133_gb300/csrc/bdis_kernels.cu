@@ -879,10 +879,11 @@ __device__ __forceinline__ void cover(int x, int n, int P, int S, int kreg, int 
 // The weight is separable, so the gather runs in two passes: per tile column
 // and covering patch row, sums over the covering patch columns; then per
 // pixel, sums over the covering patch rows.
+template <int TW, int TH>
 __device__ __forceinline__ void fuse_unit(const LaunchArgs &a, int unit, float4 *fz) {
-    // fz: nkx * nky posteriors, then nky * TW column sums (dynamic shared memory)
-
-    const int TW = a.tile_w, TH = a.tile_h;
+    // fz: nkx * nky posteriors, then nky * TW column sums (dynamic shared memory).
+    // The tile size is a compile-time constant (32x16 or 64x32), so the pixel
+    // index arithmetic is shifts and masks.
     __shared__ int cxlo[kFuseTileWMax], cxn[kFuseTileWMax], cxr[kFuseTileWMax];
     __shared__ int cylo[kFuseTileHMax], cyn[kFuseTileHMax], cyr[kFuseTileHMax];
     __shared__ float cxm[kFuseTileWMax][kMaxPatch + 2], cym[kFuseTileHMax][kMaxPatch + 2];
@@ -1171,10 +1172,11 @@ __global__ void __launch_bounds__(256) k_depth(const float *__restrict__ disp,
     }
 }
 
+template <int TW, int TH>
 __global__ void __launch_bounds__(256) k_fuse(LaunchArgs a) {
     extern __shared__ float4 fz[];
     pdl_wait();
-    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) fuse_unit(a, unit, fz);
+    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) fuse_unit<TW, TH>(a, unit, fz);
     pdl_release();
 }
 
@@ -1244,7 +1246,11 @@ __global__ void __launch_bounds__(256) k_mega(MegaArgs m) {
                 for (int u = blockIdx.x; u < total; u += gridDim.x) search_unit<P, TG, TG>(a, u, smem);
             }
         } else if (a.kind == 2) {
-            for (int u = blockIdx.x; u < total; u += gridDim.x) fuse_unit(a, u, (float4 *)smem);
+            if (a.tile_w == 64) {
+                for (int u = blockIdx.x; u < total; u += gridDim.x) fuse_unit<64, 32>(a, u, (float4 *)smem);
+            } else {
+                for (int u = blockIdx.x; u < total; u += gridDim.x) fuse_unit<32, 16>(a, u, (float4 *)smem);
+            }
         } else {
             for (int u = blockIdx.x; u < total; u += gridDim.x) upsample_unit(a, u);
         }
@@ -1336,7 +1342,10 @@ size_t fuse_smem(int P, int S, int tile_w, int tile_h) {
     return sizeof(float4) * ((size_t)nkx * nky + (size_t)nky * tile_w);
 }
 
-cudaError_t prepare_fuse(size_t smem_bytes) { return raise_smem_limit((const void *)k_fuse, smem_bytes); }
+cudaError_t prepare_fuse(size_t smem_bytes) {
+    const cudaError_t e = raise_smem_limit((const void *)k_fuse<32, 16>, smem_bytes);
+    return e != cudaSuccess ? e : raise_smem_limit((const void *)k_fuse<64, 32>, smem_bytes);
+}
 
 bool mega_supported(int P) { return mega_kernel(P, E_F32) != nullptr; }
 
@@ -1451,7 +1460,8 @@ cudaError_t launch_search(const LaunchArgs &a, int in_type, int g_type, size_t s
 }
 
 cudaError_t launch_fuse(const LaunchArgs &a, size_t smem, cudaStream_t s) {
-    return launch_args_kernel((const void *)k_fuse, a, grid_for(a.total, 8), smem, s);
+    const void *f = a.tile_w == 64 ? (const void *)k_fuse<64, 32> : (const void *)k_fuse<32, 16>;
+    return launch_args_kernel(f, a, grid_for(a.total, 8), smem, s);
 }
 
 cudaError_t launch_upsample(const LaunchArgs &a, cudaStream_t s) {
