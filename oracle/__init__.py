@@ -373,3 +373,70 @@ def diff_grad(p: Params, left, right, st: dict, lam: float = 0.1):
                           _ptr(st["prop"]), _ptr(st["valid"]), st["sr_const"], lam, _ptr(gL), _ptr(gR),
                           _ptr(gdk), _ptr(gD))
     return loss, gL, gR, gdk, gD
+
+
+# ---------------------------------------------------------------- differentiable form, all levels
+
+class MState(C.Structure):
+    _fields_ = [("kept", C.c_void_p * MAX_LEVELS), ("dinit", C.c_void_p * MAX_LEVELS),
+                ("sr_const", C.c_int * MAX_LEVELS), ("valid", C.c_void_p)]
+
+
+def frozen_state_ml(p: Params, out: dict) -> dict:
+    """Per-level discrete state of a traced forward: kept patches, their
+    Gauss-Newton starting values, sigma_r at its floor; level-0 valid pixels."""
+    st = {"kept": [], "dinit": [], "sr_const": [],
+          "valid": np.ascontiguousarray(out["valid"].astype(np.uint8))}
+    for lv in out["levels"][:p.levels]:
+        rec = lv["patches"]
+        st["kept"].append(np.ascontiguousarray((rec["flags"] == 0).astype(np.uint8).ravel()))
+        st["dinit"].append(np.ascontiguousarray(rec["dinit"].ravel()))
+        st["sr_const"].append(int(lv["sigma_r"] <= p.sigma_r_floor))
+    return st
+
+
+def _mstate(st: dict) -> MState:
+    m = MState()
+    for n, (k, d) in enumerate(zip(st["kept"], st["dinit"])):
+        m.kept[n] = k.ctypes.data
+        m.dinit[n] = d.ctypes.data
+        m.sr_const[n] = st["sr_const"][n]
+    m.valid = st["valid"].ctypes.data
+    return m
+
+
+def mdiff_forward(p: Params, left, right, st: dict, lam: float = 0.1, d_override=None):
+    """Frozen-state forward through every level: returns (loss, D, d_k of level 0)."""
+    L = lib()
+    vp = C.c_void_p
+    L.ob_mdiff_forward.restype = C.c_double
+    L.ob_mdiff_forward.argtypes = [C.POINTER(Params), vp, vp, C.c_int, C.c_int, C.POINTER(MState),
+                                   C.c_double, vp, vp, vp]
+    Lf = np.ascontiguousarray(left, dtype=np.float64)
+    Rf = np.ascontiguousarray(right, dtype=np.float64)
+    h, w = Lf.shape
+    D = np.zeros((h, w))
+    dk = np.zeros(st["kept"][0].size)
+    do = None if d_override is None else np.ascontiguousarray(d_override, dtype=np.float64)
+    ms = _mstate(st)
+    loss = L.ob_mdiff_forward(C.byref(p), _ptr(Lf), _ptr(Rf), w, h, C.byref(ms), lam, _ptr(do),
+                              _ptr(D), _ptr(dk))
+    return loss, D, dk
+
+
+def mdiff_grad(p: Params, left, right, st: dict, lam: float = 0.1):
+    """Analytic gradient through every level: (loss, dL/dI_l, dL/dI_r, dL/dd_k level 0)."""
+    L = lib()
+    vp = C.c_void_p
+    L.ob_mdiff_grad.restype = C.c_double
+    L.ob_mdiff_grad.argtypes = [C.POINTER(Params), vp, vp, C.c_int, C.c_int, C.POINTER(MState),
+                                C.c_double, vp, vp, vp]
+    Lf = np.ascontiguousarray(left, dtype=np.float64)
+    Rf = np.ascontiguousarray(right, dtype=np.float64)
+    h, w = Lf.shape
+    gL = np.zeros((h, w)); gR = np.zeros((h, w))
+    gdk = np.zeros(st["kept"][0].size)
+    ms = _mstate(st)
+    loss = L.ob_mdiff_grad(C.byref(p), _ptr(Lf), _ptr(Rf), w, h, C.byref(ms), lam, _ptr(gL),
+                           _ptr(gR), _ptr(gdk))
+    return loss, gL, gR, gdk

@@ -1229,3 +1229,472 @@ double ob_diff_grad(const ob_params *p, const double *L, const double *R, int w,
     free(oy);
     return loss;
 }
+
+/* ------------------------------------------------------------------ */
+/* differentiable form through every level                              */
+/* ------------------------------------------------------------------ */
+
+/* The coarse levels reach the loss only through the propagated probability
+ * (Eq. 10): rho_k^(n) = Gamma_n pi_k^(n) + Q^(n+1)(c_k), with
+ * Q^(n+1) = sum omega rho / sum omega the fused probability of the coarser
+ * level.  The coarse disparity maps only initialise the finer searches, and a
+ * converged patch solve F_k(d) = 0 does not depend on its initial value, so
+ * they carry no gradient.  The frozen state is per level: kept patches, the
+ * Gauss-Newton starting values, whether sigma_r sat at its floor; plus the
+ * valid pixels of level 0.  The pyramid is FP64 (no storage rounding). */
+typedef struct {
+    const uint8_t *kept[OB_MAX_LEVELS];
+    const double *dinit[OB_MAX_LEVELS];
+    int sr_const[OB_MAX_LEVELS];
+    const uint8_t *valid;
+} ob_mstate;
+
+typedef struct {
+    int w, h, npx, npy;
+    int *ox, *oy;
+    double *L, *R, *G, *W, *Q, *D;
+    ob_dpatch *dp;
+    double sr;
+} ob_mlevel;
+
+/* bilinear taps of the coarse map at fine position (x, y), as coarse_lookup */
+static void coarse_taps(int wc, int hc, double x, double y, int ix[4], int iy[4], double wt[4])
+{
+    double X = (x + 0.5) / 2.0 - 0.5, Y = (y + 0.5) / 2.0 - 0.5;
+    if (X < 0.0) X = 0.0;
+    if (X > wc - 1.0) X = wc - 1.0;
+    if (Y < 0.0) Y = 0.0;
+    if (Y > hc - 1.0) Y = hc - 1.0;
+    int x0 = (int)floor(X), y0 = (int)floor(Y);
+    int x1 = x0 + 1 < wc ? x0 + 1 : wc - 1, y1 = y0 + 1 < hc ? y0 + 1 : hc - 1;
+    double fx = X - x0, fy = Y - y0;
+    ix[0] = x0; iy[0] = y0; wt[0] = (1.0 - fx) * (1.0 - fy);
+    ix[1] = x1; iy[1] = y0; wt[1] = fx * (1.0 - fy);
+    ix[2] = x0; iy[2] = y1; wt[2] = (1.0 - fx) * fy;
+    ix[3] = x1; iy[3] = y1; wt[3] = fx * fy;
+}
+
+static void mlevels_free(ob_mlevel *lv, int NL)
+{
+    for (int n = 0; n < NL; ++n) {
+        free(lv[n].ox); free(lv[n].oy);
+        free(lv[n].L); free(lv[n].R); free(lv[n].G);
+        free(lv[n].W); free(lv[n].Q); free(lv[n].D);
+        free(lv[n].dp);
+    }
+}
+
+/* One level of the frozen forward: patch solves, window energies, sigma_r,
+ * posterior, rho with the coarser Q, and the fused W, Q (and D at level 0). */
+static void mdiff_level(const ob_params *p, const ob_mstate *st, ob_mlevel *lv, int n, int NL,
+                        const double *d_override)
+{
+    ob_mlevel *v = &lv[n];
+    const int P = p->patch, N = P * P, w = v->w, h = v->h, npx = v->npx, npy = v->npy;
+    const uint8_t *kept = st->kept[n];
+    double delta[5];
+    ob_window_offsets(p->window_step, delta);
+    double *T = (double *)malloc(sizeof(double) * N), *gt = (double *)malloc(sizeof(double) * N);
+    double sumE0 = 0.0;
+    int nk = 0;
+    for (int k = 0; k < npx * npy; ++k) {
+        if (!kept[k]) continue;
+        const int x0 = v->ox[k % npx], y0 = v->oy[k / npx];
+        double gbar = 0.0;
+        for (int r = 0; r < P; ++r)
+            for (int c = 0; c < P; ++c) {
+                T[r * P + c] = v->L[(size_t)(y0 + r) * w + x0 + c];
+                gt[r * P + c] = v->G[(size_t)(y0 + r) * w + x0 + c];
+                gbar += gt[r * P + c];
+            }
+        gbar /= N;
+        double H = 0.0, cT = 0.0;
+        for (int i = 0; i < N; ++i) {
+            gt[i] -= gbar;
+            H += gt[i] * gt[i];
+            cT += gt[i] * T[i];
+        }
+        double d = st->dinit[n][k];
+        if (d_override) {
+            d = d_override[k];
+        } else {
+            const double dlim = (double)w + 2.0 * P;
+            for (int it = 0; it < p->iters; ++it) {
+                double acc = 0.0;
+                for (int r = 0; r < P; ++r)
+                    for (int c = 0; c < P; ++c)
+                        acc += gt[r * P + c] * sample_row(v->R, w, y0 + r, (double)(x0 + c) - d);
+                d += (acc - cT) / H;
+                if (d > dlim) d = dlim;
+                if (d < -dlim) d = -dlim;
+            }
+        }
+        ob_dpatch *q = &v->dp[k];
+        q->d = d;
+        double Fd = 0.0;
+        for (int r = 0; r < P; ++r)
+            for (int c = 0; c < P; ++c)
+                Fd -= gt[r * P + c] * slope_row(v->R, w, y0 + r, (double)(x0 + c) - d);
+        q->Fd = Fd;
+        for (int i = 0; i < 5; ++i) {
+            double mean = 0.0, E = 0.0;
+            for (int r = 0; r < P; ++r)
+                for (int c = 0; c < P; ++c)
+                    mean += sample_row(v->R, w, y0 + r, (double)(x0 + c) - d - delta[i]) - T[r * P + c];
+            mean /= N;
+            for (int r = 0; r < P; ++r)
+                for (int c = 0; c < P; ++c) {
+                    double a = sample_row(v->R, w, y0 + r, (double)(x0 + c) - d - delta[i]) -
+                               T[r * P + c] - mean;
+                    E += a * a;
+                }
+            q->E[i] = E;
+        }
+        sumE0 += q->E[0];
+        ++nk;
+    }
+    if (st->sr_const[n] || p->sigma_r_mode == OB_SIGMA_R_FIXED || nk == 0)
+        v->sr = p->sigma_r_mode == OB_SIGMA_R_FIXED ? p->sigma_r_fixed : p->sigma_r_floor;
+    else
+        v->sr = sqrt(sumE0 / ((double)nk * P * P));
+    const double S2 = 2.0 * v->sr * v->sr * 25.0;
+    const double gw = ob_gamma_weight(n, NL);
+    for (int k = 0; k < npx * npy; ++k) {
+        if (!kept[k]) continue;
+        ob_dpatch *q = &v->dp[k];
+        double Z = 0.0;
+        for (int i = 0; i < 5; ++i) {
+            q->e[i] = -(q->E[i] - q->E[0]) / S2;
+            Z += exp(q->e[i]);
+        }
+        for (int i = 0; i < 5; ++i) q->pik[i] = exp(q->e[i]) / Z;
+        q->pi = 1.0 / Z;
+        double prop = 0.0;
+        if (p->use_c2f && n + 1 < NL) {
+            const double cx = v->ox[k % npx] + (P - 1) / 2.0, cy = v->oy[k / npx] + (P - 1) / 2.0;
+            prop = coarse_lookup(lv[n + 1].Q, lv[n + 1].w, lv[n + 1].h, cx, cy);
+        }
+        q->rho = p->use_c2f ? gw * q->pi + prop : q->pi;
+    }
+    double *M = (double *)malloc(sizeof(double) * N);
+    if (p->use_sgmm) ob_sgmm_table(P, p->sigma_s, M);
+    else for (int i = 0; i < N; ++i) M[i] = 1.0;
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            double sw = 0.0, swd = 0.0, swr = 0.0;
+            for (int ky = 0; ky < npy; ++ky) {
+                if (!(v->oy[ky] <= y && y < v->oy[ky] + P)) continue;
+                for (int kx = 0; kx < npx; ++kx) {
+                    if (!(v->ox[kx] <= x && x < v->ox[kx] + P)) continue;
+                    int k = ky * npx + kx;
+                    if (!kept[k]) continue;
+                    double om = v->dp[k].rho * M[(y - v->oy[ky]) * P + (x - v->ox[kx])];
+                    sw += om;
+                    swd += om * v->dp[k].d;
+                    swr += om * v->dp[k].rho;
+                }
+            }
+            size_t i = (size_t)y * w + x;
+            v->W[i] = sw;
+            v->Q[i] = sw > 0.0 ? swr / sw : 0.0;
+            if (v->D) v->D[i] = sw > 0.0 ? swd / sw : 0.0;
+        }
+    free(M);
+    free(T);
+    free(gt);
+}
+
+/* Builds the levels (FP64 pyramid, gradients, patch grids) and runs the
+ * frozen forward coarse to fine; returns the loss. */
+static double mdiff_forward(const ob_params *p, const double *L0, const double *R0, int w, int h,
+                            const ob_mstate *st, double lambda, const double *d_override0,
+                            ob_mlevel *lv)
+{
+    const int NL = p->levels, P = p->patch;
+    memset(lv, 0, sizeof(ob_mlevel) * NL);
+    for (int n = 0; n < NL; ++n) {
+        ob_mlevel *v = &lv[n];
+        v->w = ob_level_dim(w, n);
+        v->h = ob_level_dim(h, n);
+        size_t px = (size_t)v->w * v->h;
+        v->L = (double *)malloc(sizeof(double) * px);
+        v->R = (double *)malloc(sizeof(double) * px);
+        v->G = (double *)malloc(sizeof(double) * px);
+        v->W = (double *)malloc(sizeof(double) * px);
+        v->Q = (double *)malloc(sizeof(double) * px);
+        v->D = n == 0 ? (double *)malloc(sizeof(double) * px) : NULL;
+        v->ox = (int *)malloc(sizeof(int) * (v->w + 2));
+        v->oy = (int *)malloc(sizeof(int) * (v->h + 2));
+        v->npx = ob_origins(v->w, P, p->stride, v->ox);
+        v->npy = ob_origins(v->h, P, p->stride, v->oy);
+        v->dp = (ob_dpatch *)calloc((size_t)v->npx * v->npy, sizeof(ob_dpatch));
+        if (n == 0) {
+            memcpy(v->L, L0, sizeof(double) * px);
+            memcpy(v->R, R0, sizeof(double) * px);
+        } else {
+            ob_pyr_down(lv[n - 1].L, lv[n - 1].w, lv[n - 1].h, v->L, OB_STORE_F64);
+            ob_pyr_down(lv[n - 1].R, lv[n - 1].w, lv[n - 1].h, v->R, OB_STORE_F64);
+        }
+        ob_sobel_x(v->L, v->w, v->h, v->G, OB_STORE_F64);
+    }
+    for (int n = NL - 1; n >= 0; --n) mdiff_level(p, st, lv, n, NL, n == 0 ? d_override0 : NULL);
+    const ob_mlevel *v = &lv[0];
+    double loss = 0.0;
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            size_t i = (size_t)y * w + x;
+            if (!st->valid[i]) continue;
+            loss += fabs(sample_row(v->R, w, y, x - v->D[i]) - v->L[i]);
+            if (x + 1 < w && st->valid[i + 1]) loss += lambda * fabs(v->D[i] - v->D[i + 1]);
+            if (y + 1 < h && st->valid[i + w]) loss += lambda * fabs(v->D[i] - v->D[i + w]);
+        }
+    return loss / ((double)w * h);
+}
+
+double ob_mdiff_forward(const ob_params *p, const double *L, const double *R, int w, int h,
+                        const ob_mstate *st, double lambda, const double *d_override,
+                        double *D_out, double *dk_out)
+{
+    if (p->weight_mode != OB_WEIGHT_BDIS || p->finest_level != 0 || p->fast_exp) return NAN;
+    ob_mlevel lv[OB_MAX_LEVELS];
+    const double loss = mdiff_forward(p, L, R, w, h, st, lambda, d_override, lv);
+    if (D_out) memcpy(D_out, lv[0].D, sizeof(double) * w * h);
+    if (dk_out)
+        for (int k = 0; k < lv[0].npx * lv[0].npy; ++k) dk_out[k] = lv[0].dp[k].d;
+    mlevels_free(lv, p->levels);
+    return loss;
+}
+
+/* Analytic gradient of ob_mdiff_forward with respect to both level-0 images
+ * (and the level-0 patch disparities, images held fixed).  Reverse order:
+ * the loss and the level-0 fusion; then per level, finest first, the Q-map
+ * fusion adjoint (n >= 1), the posterior, sigma_r, the window energies and
+ * the implicit-function adjoint of each solve into that level's images, the
+ * Sobel transpose, and the bilinear transpose of rho's coarse term into the
+ * next level's Q map; finally the pyramid transpose, coarsest first. */
+double ob_mdiff_grad(const ob_params *p, const double *L, const double *R, int w, int h,
+                     const ob_mstate *st, double lambda, double *gL_out, double *gR_out,
+                     double *gdk_out)
+{
+    if (p->weight_mode != OB_WEIGHT_BDIS || p->finest_level != 0 || p->fast_exp) return NAN;
+    const int NL = p->levels, P = p->patch, N = P * P;
+    ob_mlevel lv[OB_MAX_LEVELS];
+    const double loss = mdiff_forward(p, L, R, w, h, st, lambda, NULL, lv);
+    double *gLv[OB_MAX_LEVELS], *gRv[OB_MAX_LEVELS], *gQv[OB_MAX_LEVELS];
+    for (int n = 0; n < NL; ++n) {
+        size_t px = (size_t)lv[n].w * lv[n].h;
+        gLv[n] = (double *)calloc(px, sizeof(double));
+        gRv[n] = (double *)calloc(px, sizeof(double));
+        gQv[n] = (double *)calloc(px, sizeof(double));
+    }
+    double *M = (double *)malloc(sizeof(double) * N);
+    if (p->use_sgmm) ob_sgmm_table(P, p->sigma_s, M);
+    else for (int i = 0; i < N; ++i) M[i] = 1.0;
+    double delta[5];
+    ob_window_offsets(p->window_step, delta);
+    const double inv = 1.0 / ((double)w * h);
+
+    /* 1. loss -> D and the direct image terms (level 0) */
+    double *gD = (double *)calloc((size_t)w * h, sizeof(double));
+    {
+        const ob_mlevel *v = &lv[0];
+        for (int y = 0; y < h; ++y)
+            for (int x = 0; x < w; ++x) {
+                size_t i = (size_t)y * w + x;
+                if (!st->valid[i]) continue;
+                double X = x - v->D[i];
+                double r = sample_row(v->R, w, y, X) - v->L[i];
+                double s = sgn(r) * inv;
+                gD[i] += -s * slope_row(v->R, w, y, X);
+                int a0, a1;
+                double t;
+                taps_row(w, X, &a0, &a1, &t);
+                gRv[0][(size_t)y * w + a0] += s * (1.0 - t);
+                gRv[0][(size_t)y * w + a1] += s * t;
+                gLv[0][i] += -s;
+                if (x + 1 < w && st->valid[i + 1]) {
+                    double q = lambda * inv * sgn_tie(v->D[i] - v->D[i + 1], v->D[i], v->D[i + 1]);
+                    gD[i] += q;
+                    gD[i + 1] -= q;
+                }
+                if (y + 1 < h && st->valid[i + w]) {
+                    double q = lambda * inv * sgn_tie(v->D[i] - v->D[i + w], v->D[i], v->D[i + w]);
+                    gD[i] += q;
+                    gD[i + w] -= q;
+                }
+            }
+    }
+
+    double *T = (double *)malloc(sizeof(double) * N), *gt = (double *)malloc(sizeof(double) * N);
+    double *a = (double *)malloc(sizeof(double) * N);
+    for (int n = 0; n < NL; ++n) {
+        ob_mlevel *v = &lv[n];
+        const int lw = v->w, lh = v->h, npx = v->npx, npy = v->npy, np = npx * npy;
+        const uint8_t *kept = st->kept[n];
+        double *gd = (double *)calloc((size_t)np, sizeof(double));
+        double *grho = (double *)calloc((size_t)np, sizeof(double));
+        double *gG = (double *)calloc((size_t)lw * lh, sizeof(double));
+        /* 2. fusion adjoint: D (level 0, Eq. 12) and Q (levels >= 1) */
+        for (int k = 0; k < np; ++k) {
+            if (!kept[k]) continue;
+            const int x0 = v->ox[k % npx], y0 = v->oy[k / npx];
+            const ob_dpatch *q = &v->dp[k];
+            for (int r = 0; r < P; ++r)
+                for (int c = 0; c < P; ++c) {
+                    size_t i = (size_t)(y0 + r) * lw + x0 + c;
+                    if (v->W[i] <= 0.0) continue;
+                    double m = M[r * P + c];
+                    if (n == 0 && st->valid[i]) {
+                        gd[k] += gD[i] * q->rho * m / v->W[i];
+                        grho[k] += gD[i] * m * (q->d - v->D[i]) / v->W[i];
+                    }
+                    /* Q = sum rho^2 M / sum rho M: dQ/drho_k = M (2 rho_k - Q) / W */
+                    if (n > 0) grho[k] += gQv[n][i] * m * (2.0 * q->rho - v->Q[i]) / v->W[i];
+                }
+        }
+        /* 3. rho = Gamma_n pi + Q^(n+1)(centre): pi, and the coarser Q map */
+        const double gw = ob_gamma_weight(n, NL);
+        double *gpi = (double *)calloc((size_t)np, sizeof(double));
+        for (int k = 0; k < np; ++k) {
+            if (!kept[k]) continue;
+            gpi[k] = p->use_c2f ? gw * grho[k] : grho[k];
+            if (p->use_c2f && n + 1 < NL && grho[k] != 0.0) {
+                const double cx = v->ox[k % npx] + (P - 1) / 2.0, cy = v->oy[k / npx] + (P - 1) / 2.0;
+                int ix[4], iy[4];
+                double wt[4];
+                coarse_taps(lv[n + 1].w, lv[n + 1].h, cx, cy, ix, iy, wt);
+                for (int j = 0; j < 4; ++j)
+                    gQv[n + 1][(size_t)iy[j] * lv[n + 1].w + ix[j]] += grho[k] * wt[j];
+            }
+        }
+        /* 4. posterior (Eq. 5-6) -> window energies and sigma_r */
+        const double sr = v->sr, S2 = 2.0 * sr * sr * 25.0;
+        int nk = 0;
+        double gsr = 0.0;
+        double *gE = (double *)calloc((size_t)np * 5, sizeof(double));
+        for (int k = 0; k < np; ++k) {
+            if (!kept[k]) continue;
+            ++nk;
+            const ob_dpatch *q = &v->dp[k];
+            for (int i = 1; i < 5; ++i) {
+                double g = gpi[k] * q->pi * q->pik[i] / S2;
+                gE[k * 5 + i] += g;
+                gE[k * 5 + 0] -= g;
+                gsr += gpi[k] * (-q->pi * q->pik[i]) * (-2.0 * q->e[i] / sr);
+            }
+        }
+        const int sr_free = !(st->sr_const[n] || p->sigma_r_mode == OB_SIGMA_R_FIXED) && nk > 0;
+        if (sr_free)
+            for (int k = 0; k < np; ++k)
+                if (kept[k]) gE[k * 5 + 0] += gsr / (2.0 * sr * (double)nk * P * P);
+        /* 5. window energies and the patch solve -> this level's images */
+        for (int k = 0; k < np; ++k) {
+            if (!kept[k]) continue;
+            const int x0 = v->ox[k % npx], y0 = v->oy[k / npx];
+            const double d = v->dp[k].d;
+            double gbar = 0.0;
+            for (int r = 0; r < P; ++r)
+                for (int c = 0; c < P; ++c) {
+                    T[r * P + c] = v->L[(size_t)(y0 + r) * lw + x0 + c];
+                    gt[r * P + c] = v->G[(size_t)(y0 + r) * lw + x0 + c];
+                    gbar += gt[r * P + c];
+                }
+            gbar /= N;
+            for (int i = 0; i < N; ++i) gt[i] -= gbar;
+            double gdt = gd[k];
+            for (int i = 0; i < 5; ++i) {
+                const double ge = gE[k * 5 + i];
+                double mean = 0.0;
+                for (int r = 0; r < P; ++r)
+                    for (int c = 0; c < P; ++c) {
+                        a[r * P + c] = sample_row(v->R, lw, y0 + r, (double)(x0 + c) - d - delta[i]) -
+                                       T[r * P + c];
+                        mean += a[r * P + c];
+                    }
+                mean /= N;
+                for (int r = 0; r < P; ++r)
+                    for (int c = 0; c < P; ++c) {
+                        double X = (double)(x0 + c) - d - delta[i];
+                        double dE_da = 2.0 * (a[r * P + c] - mean);
+                        gdt += ge * dE_da * (-slope_row(v->R, lw, y0 + r, X));
+                        int a0, a1;
+                        double t;
+                        taps_row(lw, X, &a0, &a1, &t);
+                        gRv[n][(size_t)(y0 + r) * lw + a0] += ge * dE_da * (1.0 - t);
+                        gRv[n][(size_t)(y0 + r) * lw + a1] += ge * dE_da * t;
+                        gLv[n][(size_t)(y0 + r) * lw + x0 + c] += -ge * dE_da;
+                    }
+            }
+            if (n == 0 && gdk_out) gdk_out[k] = gdt;
+            const double vF = -gdt / v->dp[k].Fd;
+            double mres = 0.0;
+            for (int r = 0; r < P; ++r)
+                for (int c = 0; c < P; ++c)
+                    mres += sample_row(v->R, lw, y0 + r, (double)(x0 + c) - d) - T[r * P + c];
+            mres /= N;
+            for (int r = 0; r < P; ++r)
+                for (int c = 0; c < P; ++c) {
+                    double X = (double)(x0 + c) - d;
+                    int a0, a1;
+                    double t;
+                    taps_row(lw, X, &a0, &a1, &t);
+                    gRv[n][(size_t)(y0 + r) * lw + a0] += vF * gt[r * P + c] * (1.0 - t);
+                    gRv[n][(size_t)(y0 + r) * lw + a1] += vF * gt[r * P + c] * t;
+                    gLv[n][(size_t)(y0 + r) * lw + x0 + c] += -vF * gt[r * P + c];
+                    double res = sample_row(v->R, lw, y0 + r, X) - T[r * P + c];
+                    gG[(size_t)(y0 + r) * lw + x0 + c] += vF * (res - mres);
+                }
+        }
+        if (n == 0 && gdk_out)
+            for (int k = 0; k < np; ++k)
+                if (!kept[k]) gdk_out[k] = 0.0;
+        /* 6. Sobel-x/8 transpose -> this level's left image */
+        static const double wr[3] = {1.0, 2.0, 1.0};
+        for (int y = 0; y < lh; ++y)
+            for (int x = 0; x < lw; ++x) {
+                double g = gG[(size_t)y * lw + x];
+                if (g == 0.0) continue;
+                for (int j = -1; j <= 1; ++j) {
+                    int yy = reflect101(y + j, lh);
+                    gLv[n][(size_t)yy * lw + reflect101(x + 1, lw)] += g * wr[j + 1] / 8.0;
+                    gLv[n][(size_t)yy * lw + reflect101(x - 1, lw)] -= g * wr[j + 1] / 8.0;
+                }
+            }
+        free(gd);
+        free(grho);
+        free(gpi);
+        free(gE);
+        free(gG);
+    }
+    /* 7. pyramid transpose, coarsest first: the blur-and-decimate of level
+     * n - 1 gives level n, so its gradient flows back to level n - 1 */
+    static const double k5[5] = {1.0 / 16, 4.0 / 16, 6.0 / 16, 4.0 / 16, 1.0 / 16};
+    for (int n = NL - 1; n >= 1; --n) {
+        const int w1 = lv[n].w, h1 = lv[n].h, w0 = lv[n - 1].w, h0 = lv[n - 1].h;
+        for (int Y = 0; Y < h1; ++Y)
+            for (int X = 0; X < w1; ++X) {
+                const double gl = gLv[n][(size_t)Y * w1 + X], gr = gRv[n][(size_t)Y * w1 + X];
+                if (gl == 0.0 && gr == 0.0) continue;
+                for (int j = -2; j <= 2; ++j)
+                    for (int i = -2; i <= 2; ++i) {
+                        size_t o = (size_t)reflect101(2 * Y + j, h0) * w0 + reflect101(2 * X + i, w0);
+                        gLv[n - 1][o] += k5[j + 2] * k5[i + 2] * gl;
+                        gRv[n - 1][o] += k5[j + 2] * k5[i + 2] * gr;
+                    }
+            }
+    }
+    memcpy(gL_out, gLv[0], sizeof(double) * w * h);
+    memcpy(gR_out, gRv[0], sizeof(double) * w * h);
+    for (int n = 0; n < NL; ++n) {
+        free(gLv[n]);
+        free(gRv[n]);
+        free(gQv[n]);
+    }
+    free(gD);
+    free(M);
+    free(T);
+    free(gt);
+    free(a);
+    mlevels_free(lv, NL);
+    return loss;
+}
