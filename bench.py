@@ -592,13 +592,22 @@ def bench_fwd_bwd(bd, dev, stream, flush, rank, ws, steps=10, warmup=3):
     t_fb = max_over_ranks(run(fwd_bwd, steps), ws, dev)
     t_f = max_over_ranks(run(fwd, steps), ws, dev)
     loss = float(torch.stack([b["loss"] for b in bufs]).mean().item())
+    # the adjoint through every level (coarse levels through Eq. 10, pyramid)
+    B.check(B.lib().bdis_set_option(m._h, B.OPT_ADJOINT_LEVELS, 1), m._h)
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            fwd_bwd()
+    torch.cuda.synchronize()
+    t_fb_all = max_over_ranks(run(fwd_bwd, steps), ws, dev)
     m.close()
     px = n * w * h
     return {"workload": "16 float pairs 640x480 (G1), P8 S4 L3, 8 iters, loss = L1 reprojection "
                         "+ 0.1 smoothness; grads w.r.t. both images and patch disparities",
             "value": round(ws * px / (t_fb / 1e3) / 1e6, 2), "unit": UNIT,
             "ms_per_step": round(t_fb, 4), "fwd_only_value": round(ws * px / (t_f / 1e3) / 1e6, 2),
-            "fwd_only_ms": round(t_f, 4), "mean_loss": round(loss, 5)}
+            "fwd_only_ms": round(t_f, 4), "mean_loss": round(loss, 5),
+            "all_levels_value": round(ws * px / (t_fb_all / 1e3) / 1e6, 2),
+            "all_levels_ms_per_step": round(t_fb_all, 4)}
 
 
 def bench_batched(bd, dev, stream, flush, rank, ws, steps=10, warmup=3, compare_plain=True,

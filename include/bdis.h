@@ -273,7 +273,15 @@ typedef enum {
      * l+2, recomputing a 2-pixel halo of level l+1) when the call has at most
      * 2^21 level-0 pixels, else one step per launch; 1 always one step;
      * 2 always two steps where two coarser levels remain.  Same results. */
-    BDIS_OPT_PYRAMID_STEPS = 6
+    BDIS_OPT_PYRAMID_STEPS = 6,
+    /* Extent of bdis_backward: 0 (default) the finest level, with the coarser
+     * levels' state frozen (their propagated probability enters as a
+     * constant); 1 through every level: the coarse levels reach the loss
+     * through rho = Gamma_n pi + Q^(n+1)(centre) (Eq. 10), so their window
+     * posteriors, sigma_r, patch solves, gradients and the pyramid are
+     * differentiated too (FP32 pyramids only).  The coarse disparity maps
+     * only initialise the finer searches and carry no gradient. */
+    BDIS_OPT_ADJOINT_LEVELS = 7
 } bdis_option;
 
 bdis_status bdis_set_option(bdis_handle *h, int option, int value);

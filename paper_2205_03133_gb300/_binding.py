@@ -84,7 +84,8 @@ class bdis_profile(C.Structure):
     _fields_ = [("launches", C.c_int * 5), ("ms", C.c_double * 5)]
 
 
-OPT_GRAPH, OPT_PROFILE, OPT_AUTOTUNE, OPT_FORM, OPT_PDL, OPT_PYRAMID_STEPS = 1, 2, 3, 4, 5, 6
+OPT_GRAPH, OPT_PROFILE, OPT_AUTOTUNE, OPT_FORM, OPT_PDL, OPT_PYRAMID_STEPS, OPT_ADJOINT_LEVELS = (
+    1, 2, 3, 4, 5, 6, 7)
 KERNEL_NAMES = ["pyramid", "search", "fuse", "persistent", "upsample"]
 
 

@@ -54,6 +54,7 @@ struct bdis_handle {
     int form = 0;             // BDIS_OPT_FORM
     bool use_pdl = true;      // BDIS_OPT_PDL
     int pyr_steps = 0;        // BDIS_OPT_PYRAMID_STEPS
+    bool adjoint_levels = false;  // BDIS_OPT_ADJOINT_LEVELS
     // per-kernel event timing
     bool profile = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -253,7 +254,7 @@ void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, const Leve
             if (l == F && F > 0 && p.variance) pl.oV[k] = b.take(sizeof(float) * (size_t)d.w * d.h);
             if (l == 0) {
                 d.pitch = pairs[i].pitch;
-                if (wsum && F == 0) pl.oW[k] = b.take(sizeof(float) * (size_t)d.w * d.h);
+
             } else {
                 d.pitch = (int)gp;
                 pl.oL[k] = b.take(gp * esz * d.h);
@@ -261,6 +262,7 @@ void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, const Leve
                 pl.oD[k] = b.take(sizeof(float) * (size_t)d.w * d.h);
                 pl.oQ[k] = b.take(sizeof(float) * (size_t)d.w * d.h);
             }
+            if (wsum && F == 0) pl.oW[k] = b.take(sizeof(float) * (size_t)d.w * d.h);
             const size_t np = searched ? (size_t)d.npx * d.npy : 0;
             if (searched) {
                 pl.oRec[k] = b.take(sizeof(bdis_patch_record) * np);
@@ -305,7 +307,7 @@ void plan_pointers(const bdis_params &p, int n, const bdis_pair *pairs, char *ba
             d.acc = (unsigned long long *)(base + pl.off_acc) + 3 * k;
             d.Df = d.Vf = nullptr;
             d.wf = d.hf = 0;
-            d.wsum = (l == 0 && wsum && F == 0) ? (float *)(base + pl.oW[k]) : nullptr;
+            d.wsum = (wsum && F == 0) ? (float *)(base + pl.oW[k]) : nullptr;
         }
     if (F > 0)
         for (int i = 0; i < n; ++i) {
@@ -836,6 +838,10 @@ bdis_status bdis_set_option(bdis_handle *h, int option, int value) {
         h->use_pdl = value != 0;
         return BDIS_OK;
     }
+    if (option == BDIS_OPT_ADJOINT_LEVELS) {
+        h->adjoint_levels = value != 0;
+        return BDIS_OK;
+    }
     if (option == BDIS_OPT_PYRAMID_STEPS) {
         if (value < 0 || value > 2) return fail(h, BDIS_EINVAL, "pyramid steps must be 0, 1 or 2");
         h->pyr_steps = value;
@@ -1044,10 +1050,18 @@ bdis_status bdis_match_f32(bdis_handle *h, const float *left, const float *right
 
 namespace {
 
-// Builds and uploads the per-pair descriptors of the backward pass.
+// Backward plan: per-level launch arguments and work totals.
+struct GradPlan {
+    int nlev = 1;
+    GradArgs a[kMaxLevels];
+    int tot[kMaxLevels][G_COUNT];
+    size_t zero_off = 0, zero_bytes = 0;  // gradient buffers of levels >= 1 (zeroed per call)
+};
+
+// Builds and uploads the (level, pair) descriptors of the backward pass for
+// levels 0 .. nlev-1.
 bdis_status grad_setup(bdis_handle *h, const bdis_grad *g, bool need_loss, cudaStream_t st,
-                       GradArgs &a, std::vector<GradDesc> &gd, size_t &gG_off, size_t &gG_bytes,
-                       int totals[G_COUNT]) {
+                       int nlev, GradPlan &gp) {
     if (!g) return fail(h, BDIS_EINVAL, "null gradient table");
     if (h->npairs < 1 || h->in_type != E_F32)
         return fail(h, BDIS_EINVAL, "no float-image forward to differentiate (call bdis_match_f32)");
@@ -1056,48 +1070,65 @@ bdis_status grad_setup(bdis_handle *h, const bdis_grad *g, bool need_loss, cudaS
         return fail(h, BDIS_EUNSUPPORTED,
                     "the adjoint covers the default fusion at full resolution "
                     "(finest_level 0, BDIS weights, exact exponential)");
+    if (nlev > 1 && p.storage != BDIS_STORE_F32)
+        return fail(h, BDIS_EUNSUPPORTED, "the adjoint through every level needs FP32 pyramids");
     const int n = h->npairs;
     for (int i = 0; i < n; ++i) {
         if (!g[i].g_disp || !g[i].g_left || !g[i].g_right)
             return fail(h, BDIS_EINVAL, "null gradient buffer");
         if (need_loss && !g[i].loss) return fail(h, BDIS_EINVAL, "null loss pointer");
     }
-    gd.assign((size_t)n, GradDesc{});
+    gp.nlev = nlev;
+    const size_t cnt = (size_t)nlev * n;
+    std::vector<GradDesc> gd(cnt, GradDesc{});
     Bump b;
-    const size_t off_desc = b.take(sizeof(GradDesc) * n);
-    std::vector<size_t> oDw(n), oG(n), od(n), opi(n), osp(n), oce(n), olp(n), ocp(n);
+    const size_t off_desc = b.take(sizeof(GradDesc) * cnt);
+    std::vector<size_t> oDw(cnt), oG(cnt), od(cnt), opi(cnt), osp(cnt), oce(cnt), olp(cnt), ocp(cnt);
+    std::vector<size_t> oL(cnt), oR(cnt), oQ(cnt);
     const int ngrp = 256 / search_group(p.patch);
-    int begin[G_COUNT] = {0, 0};
-    for (int i = 0; i < n; ++i) {
-        const LevelDesc &d = h->descs[(size_t)i];  // level 0
-        GradDesc &q = gd[i];
-        q.w = d.w;
-        q.h = d.h;
-        q.pitch = d.pitch;
-        q.gpitch = d.gpitch;
-        q.gtype = p.storage == BDIS_STORE_F16 ? E_F16 : E_F32;
-        q.npx = d.npx;
-        q.npy = d.npy;
-        q.kxreg = d.kxreg;
-        q.kyreg = d.kyreg;
-        const size_t px = (size_t)d.w * d.h, np = (size_t)d.npx * d.npy;
-        const int units[G_COUNT] = {(int)((px + 255) / 256), (int)((np + ngrp - 1) / ngrp)};
-        for (int k = 0; k < G_COUNT; ++k) {
-            q.work_begin[k] = begin[k];
-            begin[k] += units[k];
+    for (int l = 0; l < nlev; ++l) {
+        int begin[G_COUNT] = {0, 0};
+        for (int i = 0; i < n; ++i) {
+            const size_t k = (size_t)l * n + i;
+            const LevelDesc &d = h->descs[k];
+            GradDesc &q = gd[k];
+            q.w = d.w;
+            q.h = d.h;
+            q.pitch = d.pitch;
+            q.gpitch = d.gpitch;
+            q.gtype = p.storage == BDIS_STORE_F16 ? E_F16 : E_F32;
+            q.npx = d.npx;
+            q.npy = d.npy;
+            q.kxreg = d.kxreg;
+            q.kyreg = d.kyreg;
+            const size_t px = (size_t)d.w * d.h, np = (size_t)d.npx * d.npy;
+            const int units[G_COUNT] = {(int)((px + 255) / 256), (int)((np + ngrp - 1) / ngrp)};
+            for (int u = 0; u < G_COUNT; ++u) {
+                q.work_begin[u] = begin[u];
+                begin[u] += units[u];
+            }
+            oDw[k] = b.take(sizeof(float) * px);
+            od[k] = b.take(sizeof(float) * np);
+            opi[k] = b.take(sizeof(float) * np);
+            osp[k] = b.take(sizeof(float) * 2 * ((np + ngrp - 1) / ngrp));
+            oce[k] = b.take(sizeof(float));
+            olp[k] = b.take(sizeof(float) * ((px + 255) / 256));
+            ocp[k] = b.take(sizeof(float) * np * 2 * p.patch * p.patch);
+            oG[k] = b.take(sizeof(float) * px);
         }
-        oDw[i] = b.take(sizeof(float) * px);
-        od[i] = b.take(sizeof(float) * np);
-        opi[i] = b.take(sizeof(float) * np);
-        osp[i] = b.take(sizeof(float) * 2 * ((np + ngrp - 1) / ngrp));
-        oce[i] = b.take(sizeof(float));
-        olp[i] = b.take(sizeof(float) * ((px + 255) / 256));
-        ocp[i] = b.take(sizeof(float) * np * 2 * p.patch * p.patch);
+        for (int u = 0; u < G_COUNT; ++u) gp.tot[l][u] = begin[u];
     }
-    // the gradient images of all pairs are contiguous (one memset)
-    gG_off = b.take(0);
-    for (int i = 0; i < n; ++i) oG[i] = b.take(sizeof(float) * (size_t)gd[i].w * gd[i].h);
-    gG_bytes = b.off - gG_off;
+    // image and probability gradients of the coarser levels: one zeroed block
+    gp.zero_off = b.take(0);
+    for (int l = 1; l < nlev; ++l)
+        for (int i = 0; i < n; ++i) {
+            const size_t k = (size_t)l * n + i;
+            const size_t px = (size_t)gd[k].w * gd[k].h;
+            oL[k] = b.take(sizeof(float) * px);
+            oR[k] = b.take(sizeof(float) * px);
+            oQ[k] = b.take(sizeof(float) * px);
+        }
+    gp.zero_bytes = b.off - gp.zero_off;
     const size_t bytes = align_up(b.off, 256);
     if (bytes > h->garena_cap) {
         if (h->garena) {
@@ -1116,33 +1147,59 @@ bdis_status grad_setup(bdis_handle *h, const bdis_grad *g, bool need_loss, cudaS
         h->garena_cap = cap;
     }
     char *base = h->garena;
-    for (int i = 0; i < n; ++i) {
-        const LevelDesc &d = h->descs[(size_t)i];
-        GradDesc &q = gd[i];
-        q.L = (const float *)d.L;
-        q.R = (const float *)d.R;
-        q.G = d.G;
-        q.disp = d.disp;
-        q.wsum = d.wsum;
-        q.valid = d.valid;
-        q.rec = d.rec;
-        q.fuse = d.fuse;
-        q.sigma_r = d.sigma_r;
-        q.gDisp = g[i].g_disp;
-        q.gL = g[i].g_left;
-        q.gR = g[i].g_right;
-        q.gPatch = g[i].g_patch_disp;
-        q.loss = g[i].loss;
-        q.gDw = (float *)(base + oDw[i]);
-        q.gG = (float *)(base + oG[i]);
-        q.gd = (float *)(base + od[i]);
-        q.gpi = (float *)(base + opi[i]);
-        q.sig_part = (float *)(base + osp[i]);
-        q.coefE0 = (float *)(base + oce[i]);
-        q.loss_part = (float *)(base + olp[i]);
-        q.cpatch = (float *)(base + ocp[i]);
-    }
-    const size_t tbytes = sizeof(GradDesc) * n;
+    for (int l = 0; l < nlev; ++l)
+        for (int i = 0; i < n; ++i) {
+            const size_t k = (size_t)l * n + i;
+            const LevelDesc &d = h->descs[k];
+            GradDesc &q = gd[k];
+            q.L = (const float *)d.L;
+            q.R = (const float *)d.R;
+            q.G = d.G;
+            q.disp = d.disp;
+            q.wsum = d.wsum;
+            q.valid = d.valid;
+            q.rec = d.rec;
+            q.fuse = d.fuse;
+            q.sigma_r = d.sigma_r;
+            q.Q = l > 0 ? d.Q : nullptr;
+            if (l == 0) {
+                q.gDisp = g[i].g_disp;
+                q.gL = g[i].g_left;
+                q.gR = g[i].g_right;
+                q.gPatch = g[i].g_patch_disp;
+                q.loss = g[i].loss;
+                q.gQ = nullptr;
+            } else {
+                q.gDisp = nullptr;
+                q.gL = (float *)(base + oL[k]);
+                q.gR = (float *)(base + oR[k]);
+                q.gPatch = nullptr;
+                q.loss = nullptr;
+                q.gQ = (float *)(base + oQ[k]);
+            }
+            q.gDw = (float *)(base + oDw[k]);
+            q.gG = (float *)(base + oG[k]);
+            q.gd = (float *)(base + od[k]);
+            q.gpi = (float *)(base + opi[k]);
+            q.sig_part = (float *)(base + osp[k]);
+            q.coefE0 = (float *)(base + oce[k]);
+            q.loss_part = (float *)(base + olp[k]);
+            q.cpatch = (float *)(base + ocp[k]);
+            if (l + 1 < nlev) {
+                const size_t kc = (size_t)(l + 1) * n + i;
+                q.gQn = (float *)(base + oQ[kc]);
+                q.gLc = (const float *)(base + oL[kc]);
+                q.gRc = (const float *)(base + oR[kc]);
+                q.wn = gd[kc].w;
+                q.hn = gd[kc].h;
+            } else {
+                q.gQn = nullptr;
+                q.gLc = q.gRc = nullptr;
+                q.wn = q.hn = 0;
+            }
+            if (q.wsum == nullptr) return fail(h, BDIS_EINVAL, "forward kept no fusion weights");
+        }
+    const size_t tbytes = sizeof(GradDesc) * cnt;
     bdis_status s = ensure_pinned(h, std::max(tbytes, h->last_upload.size()));
     if (s != BDIS_OK) return s;
     cudaError_t e = cudaEventSynchronize(h->upload_done);
@@ -1153,22 +1210,24 @@ bdis_status grad_setup(bdis_handle *h, const bdis_grad *g, bool need_loss, cudaS
     if (e != cudaSuccess) return cuda_fail(h, e, "gradient descriptor upload");
     e = cudaEventRecord(h->upload_done, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
-    std::memset(&a, 0, sizeof(a));
-    a.descs = d_desc;
-    a.npairs = n;
-    a.P = p.patch;
-    a.S = p.stride;
-    a.window_step = p.window_step;
     double gsum = 0.0;
     for (int m = 0; m < p.levels; ++m) gsum += std::ldexp(1.0, m);
-    a.gamma_w = (float)(1.0 / gsum);
-    a.sigma_r_mode = p.sigma_r_mode;
-    a.sigma_r_floor = p.sigma_r_floor;
-    a.use_sgmm = p.use_sgmm;
-    a.use_c2f = p.use_c2f;
-    fill_sgmm(p, a.m);
-    for (int k = 0; k < G_COUNT; ++k) totals[k] = begin[k];
-    a.total = begin[G_PIX];
+    for (int l = 0; l < nlev; ++l) {
+        GradArgs &a = gp.a[l];
+        std::memset(&a, 0, sizeof(a));
+        a.descs = d_desc + (size_t)l * n;
+        a.npairs = n;
+        a.level = l;
+        a.P = p.patch;
+        a.S = p.stride;
+        a.window_step = p.window_step;
+        a.gamma_w = (float)(std::ldexp(1.0, l) / gsum);
+        a.sigma_r_mode = p.sigma_r_mode;
+        a.sigma_r_floor = p.sigma_r_floor;
+        a.use_sgmm = p.use_sgmm;
+        a.use_c2f = p.use_c2f;
+        fill_sgmm(p, a.m);
+    }
     return BDIS_OK;
 }
 
@@ -1178,18 +1237,17 @@ bdis_status bdis_loss(bdis_handle *h, float lambda, const bdis_grad *g, void *st
     if (!h) return BDIS_EINVAL;
     if (!std::isfinite(lambda) || lambda < 0.f) return fail(h, BDIS_EINVAL, "lambda must be >= 0");
     cudaStream_t st = (cudaStream_t)stream;
-    GradArgs a;
-    std::vector<GradDesc> gd;
-    size_t goff, gbytes;
-    int tot[G_COUNT];
-    bdis_status s = grad_setup(h, g, true, st, a, gd, goff, gbytes, tot);
+    GradPlan gp;
+    bdis_status s = grad_setup(h, g, true, st, 1, gp);
     if (s != BDIS_OK) return s;
+    GradArgs a = gp.a[0];
     a.lambda = lambda;
-    for (size_t i = 0; i < gd.size(); ++i) {
-        cudaError_t e = cudaMemsetAsync(gd[i].gR, 0, sizeof(float) * (size_t)gd[i].w * gd[i].h, st);
+    for (int i = 0; i < h->npairs; ++i) {
+        const LevelDesc &d = h->descs[(size_t)i];
+        cudaError_t e = cudaMemsetAsync(g[i].g_right, 0, sizeof(float) * (size_t)d.w * d.h, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
     }
-    a.total = tot[G_PIX];
+    a.total = gp.tot[0][G_PIX];
     cudaError_t e = launch_loss(a, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "loss launch");
     return BDIS_OK;
@@ -1200,24 +1258,33 @@ bdis_status bdis_backward(bdis_handle *h, const bdis_grad *g, void *stream) {
     if (h->p.sigma_r_mode == BDIS_SIGMA_R_LITERAL)
         return fail(h, BDIS_EUNSUPPORTED, "no adjoint for the LITERAL sigma_r reading");
     cudaStream_t st = (cudaStream_t)stream;
-    GradArgs a;
-    std::vector<GradDesc> gd;
-    size_t goff, gbytes;
-    int tot[G_COUNT];
-    bdis_status s = grad_setup(h, g, false, st, a, gd, goff, gbytes, tot);
+    const int nlev = h->adjoint_levels ? h->levels : 1;
+    GradPlan gp;
+    bdis_status s = grad_setup(h, g, false, st, nlev, gp);
     if (s != BDIS_OK) return s;
-    (void)goff;  // the gradient-image scratch is written in full by k_bwd_gather
-    (void)gbytes;
     cudaError_t e;
-    a.total = tot[G_PIX];
-    if ((e = launch_bwd_pix(a, st)) != cudaSuccess) return cuda_fail(h, e, "backward launch");
-    a.total = tot[G_GROUP];
-    if ((e = launch_bwd_dens(a, st)) != cudaSuccess) return cuda_fail(h, e, "backward launch");
-    a.total = tot[G_GROUP];
-    if ((e = launch_bwd_patch(a, st)) != cudaSuccess) return cuda_fail(h, e, "backward launch");
-    a.total = tot[G_PIX];
-    if ((e = launch_bwd_gather(a, st)) != cudaSuccess) return cuda_fail(h, e, "backward launch");
-    if ((e = launch_bwd_sobel(a, st)) != cudaSuccess) return cuda_fail(h, e, "backward launch");
+    if (gp.zero_bytes > 0) {
+        e = cudaMemsetAsync(h->garena + gp.zero_off, 0, gp.zero_bytes, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
+    }
+    // finest level first: each level's fusion adjoint feeds the next level's dL/dQ
+    for (int l = 0; l < nlev; ++l) {
+        GradArgs a = gp.a[l];
+        a.total = gp.tot[l][G_PIX];
+        if ((e = launch_bwd_pix(a, st)) != cudaSuccess) return cuda_fail(h, e, "backward launch");
+        a.total = gp.tot[l][G_GROUP];
+        if ((e = launch_bwd_dens(a, st)) != cudaSuccess) return cuda_fail(h, e, "backward launch");
+        if ((e = launch_bwd_patch(a, st)) != cudaSuccess) return cuda_fail(h, e, "backward launch");
+        a.total = gp.tot[l][G_PIX];
+        if ((e = launch_bwd_gather(a, st)) != cudaSuccess) return cuda_fail(h, e, "backward launch");
+        if ((e = launch_bwd_sobel(a, st)) != cudaSuccess) return cuda_fail(h, e, "backward launch");
+    }
+    // pyramid transpose, coarsest first
+    for (int l = nlev - 2; l >= 0; --l) {
+        GradArgs a = gp.a[l];
+        a.total = gp.tot[l][G_PIX];
+        if ((e = launch_bwd_pyr(a, st)) != cudaSuccess) return cuda_fail(h, e, "backward launch");
+    }
     return BDIS_OK;
 }
 

@@ -161,25 +161,31 @@ __global__ void __launch_bounds__(256) k_loss_reduce(GradArgs a) {
 
 // ---------------------------------------------------------------- fusion adjoint
 
-// Per pixel: dL/dD / sum omega (0 at invalid pixels), the weight sum saved
-// by the forward's fusion.
+// Per pixel, divided by the weight sum saved by the forward's fusion:
+// level 0 dL/dD (0 at invalid pixels), coarser levels dL/dQ.
 __global__ void __launch_bounds__(256) k_bwd_pix(GradArgs a) {
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) {
         const GradDesc &g = a.descs[find_pair_g(a.descs, a.npairs, unit, G_PIX)];
         const int idx = (unit - g.work_begin[G_PIX]) * blockDim.x + threadIdx.x;
         if (idx >= g.w * g.h) continue;
+        const float sw = __ldg(g.wsum + idx);
         float v = 0.f;
-        if (g.valid[idx]) {
-            const float sw = __ldg(g.wsum + idx);
-            v = sw > 0.f ? g.gDisp[idx] / sw : 0.f;
+        if (a.level == 0) {
+            if (g.valid[idx]) v = sw > 0.f ? g.gDisp[idx] / sw : 0.f;
+        } else {
+            v = sw > 0.f ? g.gQ[idx] / sw : 0.f;
         }
         g.gDw[idx] = v;
     }
 }
 
-// Per kept patch: dL/dd_k = sum_x gDw rho_k M, dL/drho_k = sum_x gDw M (d_k - D),
-// dL/dpi_k, and the patch's share of dL/dsigma_r (block partials).  A group
-// of lanes per patch, lane = patch row, so the pixel reads are row segments.
+// Per kept patch: dL/dd_k = sum_x gDw rho_k M, dL/drho_k = sum_x gDw M (d_k - D)
+// at level 0 (D = sum omega d / sum omega, Eq. 12); at coarser levels, from the
+// fused probability Q = sum omega rho / sum omega, dL/drho_k = sum_x gQw M (2 rho_k
+// - Q).  Then dL/dpi_k = Gamma_n dL/drho_k, the bilinear transpose of rho's
+// coarse term (Eq. 10) into the next level's dL/dQ, and the patch's share of
+// dL/dsigma_r (block partials).  A group of lanes per patch, lane = patch row,
+// so the pixel reads are row segments.
 template <int P>
 __device__ __forceinline__ void bwd_dens_unit(const GradArgs &a, int unit, float *red) {
     constexpr int G = P <= 8 ? 8 : 16;
@@ -200,18 +206,24 @@ __device__ __forceinline__ void bwd_dens_unit(const GradArgs &a, int unit, float
         const int oy = origin(kk / g.npx, g.h, P, S, g.kyreg);
         const float my = a.use_sgmm ? a.m[gl] : 1.f;
         const size_t row = (size_t)(oy + gl) * g.w + ox;
+        const bool fine = a.level == 0;
+        const float *mp = fine ? g.disp : g.Q;
         float wv[P], dv[P];
 #pragma unroll
         for (int c = 0; c < P; ++c) {  // all loads first
             wv[c] = __ldg(g.gDw + row + c);
-            dv[c] = __ldg(g.disp + row + c);
+            dv[c] = __ldg(mp + row + c);
         }
 #pragma unroll
         for (int c = 0; c < P; ++c) {
             if (wv[c] == 0.f) continue;  // invalid pixel (disp may be NaN)
             const float M = my * (a.use_sgmm ? a.m[c] : 1.f);
-            gd = fmaf(wv[c] * rc.rho, M, gd);
-            grho = fmaf(wv[c] * M, rc.d - dv[c], grho);
+            if (fine) {
+                gd = fmaf(wv[c] * rc.rho, M, gd);
+                grho = fmaf(wv[c] * M, rc.d - dv[c], grho);
+            } else {
+                grho = fmaf(wv[c] * M, 2.f * rc.rho - dv[c], grho);
+            }
         }
     }
     gd = group_sum<G>(gd);
@@ -221,6 +233,21 @@ __device__ __forceinline__ void bwd_dens_unit(const GradArgs &a, int unit, float
         float gpi = 0.f;
         if (kept) {
             gpi = a.use_c2f ? a.gamma_w * grho : grho;
+            // rho_k = Gamma_n pi_k + Q^(n+1)(centre): bilinear transpose
+            if (a.use_c2f && g.gQn != nullptr && grho != 0.f) {
+                const float cx = (float)origin(kk % g.npx, g.w, P, S, g.kxreg) + 0.5f * (float)(P - 1);
+                const float cy = (float)origin(kk / g.npx, g.h, P, S, g.kyreg) + 0.5f * (float)(P - 1);
+                float X = (cx + 0.5f) * 0.5f - 0.5f, Y = (cy + 0.5f) * 0.5f - 0.5f;
+                X = fminf(fmaxf(X, 0.f), (float)(g.wn - 1));
+                Y = fminf(fmaxf(Y, 0.f), (float)(g.hn - 1));
+                const int x0 = (int)floorf(X), y0 = (int)floorf(Y);
+                const int x1 = min(x0 + 1, g.wn - 1), y1 = min(y0 + 1, g.hn - 1);
+                const float fx = X - (float)x0, fy = Y - (float)y0;
+                atomicAdd(g.gQn + (size_t)y0 * g.wn + x0, grho * (1.f - fx) * (1.f - fy));
+                atomicAdd(g.gQn + (size_t)y0 * g.wn + x1, grho * fx * (1.f - fy));
+                atomicAdd(g.gQn + (size_t)y1 * g.wn + x0, grho * (1.f - fx) * fy);
+                atomicAdd(g.gQn + (size_t)y1 * g.wn + x1, grho * fx * fy);
+            }
             // dpi/dsigma_r = (2 pi / sigma_r) sum_i pi_i e_i
             const float sr = __ldg(g.sigma_r);
             const float S2 = 2.f * sr * sr * (float)(kWindow * kWindow);
@@ -671,6 +698,65 @@ __global__ void __launch_bounds__(256) k_bwd_gather(GradArgs a) {
     }
 }
 
+// Sources of fine index x in the blur-and-decimate of a row of n pixels into
+// nc coarse ones (coarse X reads fine refl(2X + i), i = -2..2, weight
+// k[i + 2]): up to 3 (coarse index, weight) pairs.  Away from the borders
+// they follow from the parity of x; near a border the reflected taps are
+// enumerated.
+__device__ __forceinline__ int pyr_sources(int x, int n, int nc, int (&X)[4], float (&wt)[4]) {
+    if (x >= 3 && x <= n - 4) {
+        if ((x & 1) == 0) {
+            X[0] = x / 2 - 1; wt[0] = 1.f / 16;
+            X[1] = x / 2;     wt[1] = 6.f / 16;
+            X[2] = x / 2 + 1; wt[2] = 1.f / 16;
+            return 3;
+        }
+        X[0] = (x - 1) / 2; wt[0] = 4.f / 16;
+        X[1] = (x + 1) / 2; wt[1] = 4.f / 16;
+        return 2;
+    }
+    const float k5[5] = {1.f / 16, 4.f / 16, 6.f / 16, 4.f / 16, 1.f / 16};
+    int cnt = 0;
+    const int lo = max(0, x / 2 - 2), hi = min(nc - 1, x / 2 + 2);
+    for (int c = lo; c <= hi; ++c) {
+        float s = 0.f;
+#pragma unroll
+        for (int i = -2; i <= 2; ++i)
+            if (refl(2 * c + i, n) == x) s += k5[i + 2];
+        if (s != 0.f && cnt < 4) {
+            X[cnt] = c;
+            wt[cnt] = s;
+            ++cnt;
+        }
+    }
+    return cnt;
+}
+
+// Pyramid transpose (a gather, no atomics): the image gradients of level n+1
+// flow back to level n through the blur-and-decimate that made level n+1.
+__global__ void __launch_bounds__(256) k_bwd_pyr(GradArgs a) {
+    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) {
+        const GradDesc &g = a.descs[find_pair_g(a.descs, a.npairs, unit, G_PIX)];
+        const int idx = (unit - g.work_begin[G_PIX]) * blockDim.x + threadIdx.x;
+        if (idx >= g.w * g.h || g.gLc == nullptr) continue;
+        const int x = idx % g.w, y = idx / g.w;
+        int Xs[4], Ys[4];
+        float wx[4], wy[4];
+        const int nx = pyr_sources(x, g.w, g.wn, Xs, wx);
+        const int ny = pyr_sources(y, g.h, g.hn, Ys, wy);
+        float sL = 0.f, sR = 0.f;
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const size_t o = (size_t)Ys[j] * g.wn + Xs[i];
+                const float wgt = wy[j] * wx[i];
+                sL = fmaf(wgt, __ldg(g.gLc + o), sL);
+                sR = fmaf(wgt, __ldg(g.gRc + o), sR);
+            }
+        g.gL[idx] += sL;
+        g.gR[idx] += sR;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_bwd_sobel(GradArgs a) {
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) {
         const GradDesc &g = a.descs[find_pair_g(a.descs, a.npairs, unit, G_PIX)];
@@ -775,6 +861,11 @@ cudaError_t launch_bwd_patch(const GradArgs &a, cudaStream_t s) {
         case 16: return launch_bwd_patch_p<16>(a, grid, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_bwd_pyr(const GradArgs &a, cudaStream_t s) {
+    k_bwd_pyr<<<ggrid(a.total), 256, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_bwd_gather(const GradArgs &a, cudaStream_t s) {

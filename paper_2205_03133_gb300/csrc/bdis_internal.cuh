@@ -54,8 +54,8 @@ struct alignas(16) LevelDesc {
     uint8_t *valid;
     const float *Df, *Vf;     // level 0 with f > 0: the level-f maps to upsample
     int wf, hf;               // their size
-    float *wsum;              // level 0 of a float-image forward: sum of the fusion
-                              // weights per pixel (read by the adjoint), else nullptr
+    float *wsum;              // float-image forward: sum of the fusion weights per
+                              // pixel of every level (read by the adjoint), else nullptr
     bdis_patch_record *rec;   // npx * npy records of this pair at this level
     float4 *fuse;             // (d, rho, sig2, mu) per patch for the fusion gather (rho = 0: rejected)
     float *sigma_r;           // one float
@@ -124,8 +124,8 @@ constexpr unsigned kBarrierSpinLimit = 1u << 22;
 // patches per unit (the fusion and patch adjoints)
 enum GradWork { G_PIX = 0, G_GROUP = 1, G_COUNT = 2 };
 
-// One pair of the backward pass.  Images are the level-0 float images of the
-// forward; gradients are dense w*h arrays.
+// One (pair, level) of the backward pass.  Images are the float images of the
+// forward at that level; gradients are dense w*h arrays of the level.
 struct alignas(16) GradDesc {
     const float *L, *R;            // level-0 images, `pitch` elements per row
     const void *G;                 // level-0 x-gradient (storage type)
@@ -138,14 +138,21 @@ struct alignas(16) GradDesc {
     float *gDisp, *gL, *gR, *gPatch, *loss;        // caller buffers
     float *gDw, *gG, *gd, *gpi, *sig_part, *coefE0, *loss_part;  // scratch
     float *cpatch;                 // per patch: P x P template and gradient-image terms
+    // levels >= 1 (the adjoint through every level)
+    const float *Q;                // the level's fused probability map (forward)
+    float *gQ;                     // dL/dQ of this level (zeroed, accumulated by level - 1)
+    float *gQn;                    // dL/dQ of the next coarser level, or nullptr
+    const float *gLc, *gRc;        // image gradients of the next coarser level, or nullptr
+    int wn, hn;                    // next coarser level size
     int w, h, pitch, gpitch, gtype;
     int npx, npy, kxreg, kyreg;
     int work_begin[G_COUNT];
 };
 
 struct GradArgs {
-    const GradDesc *descs;
+    const GradDesc *descs;         // the npairs descriptors of this level
     int npairs, total;
+    int level;
     int P, S;
     float window_step, lambda, gamma_w;
     int sigma_r_mode;
@@ -160,6 +167,7 @@ cudaError_t launch_bwd_dens(const GradArgs &a, cudaStream_t s);    // + sigma_r 
 cudaError_t launch_bwd_patch(const GradArgs &a, cudaStream_t s);
 cudaError_t launch_bwd_gather(const GradArgs &a, cudaStream_t s);
 cudaError_t launch_bwd_sobel(const GradArgs &a, cudaStream_t s);
+cudaError_t launch_bwd_pyr(const GradArgs &a, cudaStream_t s);   // pyramid transpose into this level
 
 // Kernel launchers (bdis_kernels.cu).  Each returns cudaGetLastError().
 cudaError_t launch_pyramid(const LaunchArgs &a, int in_type, int out_type, cudaStream_t s);

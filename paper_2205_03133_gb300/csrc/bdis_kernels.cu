@@ -992,10 +992,10 @@ __device__ __forceinline__ void fuse_unit(const LaunchArgs &a, int unit, float4 
             Vv = 0.f;
         }
         const float qnan = __int_as_float(0x7fc00000);
+        if (D.wsum != nullptr) D.wsum[idx] = sw;
         if (a.level == a.finest) {
             const bool ok = any && Qv >= a.pix_thresh;
             if (a.level == 0) {
-                if (D.wsum != nullptr) D.wsum[idx] = sw;
                 D.valid[idx] = ok ? 1 : 0;
                 D.disp[idx] = ok ? Dv : qnan;
                 if (D.var != nullptr && a.variance) D.var[idx] = ok ? Vv : qnan;

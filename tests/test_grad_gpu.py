@@ -142,3 +142,68 @@ def test_autograd_function(bd):
     assert torch.allclose(L.grad, gl, rtol=1e-4, atol=1e-6 * gl.abs().max().item())
     assert torch.allclose(R.grad, gr, rtol=1e-4, atol=1e-6 * gr.abs().max().item())
     assert L.grad.abs().sum() > 0 and R.grad.abs().sum() > 0
+
+
+# ---------------------------------------------------------------- through every level
+
+def _gpu_ml(bd, kw, L32, R32, lam=0.1):
+    import torch
+    m = bd.BDIS(**kw)
+    m.set_option(bd.B.OPT_ADJOINT_LEVELS, 1)
+    Lt = torch.from_numpy(L32).cuda()
+    Rt = torch.from_numpy(R32).cuda()
+    (d, v, ok), = m.match_f32([Lt], [Rt])
+    g, = m.loss_and_grad(lam)
+    torch.cuda.synchronize()
+    recs = [m.level_view(0, l)["patches"] for l in range(m.params.levels)]
+    out = {k: t.cpu().numpy() for k, t in g.items()}
+    out.update(valid=ok.cpu().numpy().astype(bool), recs=recs, params=m.params)
+    m.close()
+    return out
+
+
+@pytest.mark.parametrize("kw", [
+    dict(patch=8, stride=4, levels=2, iters=50),
+    dict(patch=8, stride=4, levels=3, iters=50),
+    dict(patch=8, stride=4, levels=3, iters=50, sigma_r_mode="fixed"),
+])
+def test_adjoint_through_levels_matches_oracle_small(bd, kw):
+    pr = synth.g1_pair(64, 48, 3, d0=1.0, d1=3.0, amp=1.0, as_float=True)
+    L32, R32 = pr.left.astype(np.float32), pr.right.astype(np.float32)
+    L, R = L32.astype(np.float64), R32.astype(np.float64)
+    g = _gpu_ml(bd, kw, L32, R32)
+    op = oracle_params(g["params"])
+    o = oracle.match(op, L, R, trace=True)
+    st = oracle.frozen_state_ml(op, o)
+    # same discrete state on both sides, every level
+    assert np.array_equal(g["valid"], o["valid"])
+    for l in range(op.levels):
+        assert np.array_equal(g["recs"][l]["flags"].ravel() == 0, st["kept"][l].astype(bool)), l
+    loss, gL, gR, gdk = oracle.mdiff_grad(op, L, R, st)
+    assert abs(float(g["loss"][0]) - loss) <= 1e-5 * loss
+    for key, ref in (("g_left", gL), ("g_right", gR)):
+        good, info = _close(g[key], ref)
+        assert good, (key, info)
+    kept = st["kept"][0].astype(bool)
+    good, info = _close(g["g_patch_disp"].ravel()[kept], gdk[kept])
+    assert good, ("g_patch_disp", info)
+
+
+def test_adjoint_through_levels_640x480(bd):
+    pr = synth.g1_pair(640, 480, 0)
+    L32, R32 = pr.left.astype(np.float32), pr.right.astype(np.float32)
+    kw = dict(patch=8, stride=4, levels=3, iters=8)
+    g = _gpu_ml(bd, kw, L32, R32)
+    op = oracle_params(g["params"])
+    L, R = L32.astype(np.float64), R32.astype(np.float64)
+    o = oracle.match(op, L, R, trace=True)
+    st = oracle.frozen_state_ml(op, o)
+    flips = sum(int(((g["recs"][l]["flags"].ravel() == 0) != st["kept"][l].astype(bool)).sum())
+                for l in range(op.levels))
+    assert flips <= max(2, int(0.001 * st["kept"][0].size))
+    loss, gL, gR, gdk = oracle.mdiff_grad(op, L, R, st)
+    assert abs(float(g["loss"][0]) - loss) <= 1e-4 * loss
+    for key, ref in (("g_left", gL), ("g_right", gR)):
+        good, info = _close(g[key], ref, frac=0.999)
+        print(key, info, "flips", flips)
+        assert good, (key, info)
