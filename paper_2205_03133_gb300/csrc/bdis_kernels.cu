@@ -38,7 +38,8 @@ constexpr int kPyrSW = kPyrTW + 4, kPyrSH = kPyrTH + 4;
 
 template <typename TI, typename TO>
 __device__ __forceinline__ void pyramid_unit(const LaunchArgs &a, int unit, float (*Ls)[kPyrSW],
-                                             float (*Rs)[kPyrSW]) {
+                                             float (*Rs)[kPyrSW], float (*Lh)[kPyrTW / 2],
+                                             float (*Rh)[kPyrTW / 2]) {
 
     const LevelDesc &D = a.descs[find_pair(a.descs, a.npairs, unit, W_PYR)];
     const int tile = unit - D.work_begin[W_PYR];
@@ -89,23 +90,32 @@ __device__ __forceinline__ void pyramid_unit(const LaunchArgs &a, int unit, floa
         stf(G + (size_t)y * D.gpitch + x, acc * 0.125f);
     }
     if (next) {
+        // separable blur: horizontal at the even columns of every staged row,
+        // then vertical at the even rows (the multiply-add order of the 2D sum)
         const float k[5] = {1.f, 4.f, 6.f, 4.f, 1.f};
+        for (int i = threadIdx.x; i < kPyrSH * (kPyrTW / 2); i += blockDim.x) {
+            const int r = i / (kPyrTW / 2), ox = i - r * (kPyrTW / 2);
+            const int cx = 2 * ox + 2;
+            float sl = 0.f, sr = 0.f;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                sl += k[q] * Ls[r][cx + q - 2];
+                sr += k[q] * Rs[r][cx + q - 2];
+            }
+            Lh[r][ox] = sl;
+            Rh[r][ox] = sr;
+        }
+        __syncthreads();
         for (int i = threadIdx.x; i < (kPyrTW / 2) * (kPyrTH / 2); i += blockDim.x) {
             const int oy = i / (kPyrTW / 2), ox = i - oy * (kPyrTW / 2);
             const int X = tx * (kPyrTW / 2) + ox, Y = ty * (kPyrTH / 2) + oy;
             if (X >= D.wn || Y >= D.hn) continue;
-            const int cx = 2 * ox + 2, cy = 2 * oy + 2;
+            const int cy = 2 * oy + 2;
             float accL = 0.f, accR = 0.f;
 #pragma unroll
             for (int j = 0; j < 5; ++j) {
-                float sl = 0.f, sr = 0.f;
-#pragma unroll
-                for (int q = 0; q < 5; ++q) {
-                    sl += k[q] * Ls[cy + j - 2][cx + q - 2];
-                    sr += k[q] * Rs[cy + j - 2][cx + q - 2];
-                }
-                accL += k[j] * sl;
-                accR += k[j] * sr;
+                accL += k[j] * Lh[cy + j - 2][ox];
+                accR += k[j] * Rh[cy + j - 2][ox];
             }
             stf((TO *)D.Ln + (size_t)Y * D.pitchn + X, accL * (1.f / 256.f));
             stf((TO *)D.Rn + (size_t)Y * D.pitchn + X, accR * (1.f / 256.f));
@@ -277,12 +287,15 @@ template <typename TI, typename TO>
 __global__ void __launch_bounds__(256) k_pyramid(LaunchArgs a) {
     __shared__ float Ls[kPyrSH][kPyrSW];
     __shared__ float Rs[kPyrSH][kPyrSW];
+    __shared__ float Lh[kPyrSH][kPyrTW / 2];
+    __shared__ float Rh[kPyrSH][kPyrTW / 2];
     pdl_wait();
     // the finest pyramid launch runs before every search: it clears the
     // sigma_r accumulators of all levels and pairs
     if (blockIdx.x == 0 && a.acc_zero != nullptr)
         for (int i = threadIdx.x; i < a.acc_count; i += blockDim.x) a.acc_zero[i] = 0ull;
-    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) pyramid_unit<TI, TO>(a, unit, Ls, Rs);
+    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x)
+        pyramid_unit<TI, TO>(a, unit, Ls, Rs, Lh, Rh);
     pdl_release();
 }
 
@@ -1226,10 +1239,13 @@ __global__ void __launch_bounds__(256) k_mega(MegaArgs m) {
                 for (int i = threadIdx.x; i < a.acc_count; i += blockDim.x) a.acc_zero[i] = 0ull;
             float(*Ls)[kPyrSW] = (float(*)[kPyrSW])smem;
             float(*Rs)[kPyrSW] = Ls + kPyrSH;
+            float(*Lh)[kPyrTW / 2] = (float(*)[kPyrTW / 2])(smem + 2 * kPyrSH * kPyrSW);
+            float(*Rh)[kPyrTW / 2] = Lh + kPyrSH;
             if (a.level == 0) {
-                for (int u = blockIdx.x; u < total; u += gridDim.x) pyramid_unit<uint8_t, TG>(a, u, Ls, Rs);
+                for (int u = blockIdx.x; u < total; u += gridDim.x)
+                    pyramid_unit<uint8_t, TG>(a, u, Ls, Rs, Lh, Rh);
             } else {
-                for (int u = blockIdx.x; u < total; u += gridDim.x) pyramid_unit<TG, TG>(a, u, Ls, Rs);
+                for (int u = blockIdx.x; u < total; u += gridDim.x) pyramid_unit<TG, TG>(a, u, Ls, Rs, Lh, Rh);
             }
         } else if (a.kind == 4) {
             if (blockIdx.x == 0 && a.acc_zero != nullptr)
