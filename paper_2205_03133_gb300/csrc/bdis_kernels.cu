@@ -446,6 +446,9 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
 
     const int passes = a.chunk / (8 * GPW);
     for (int pass = 0; pass < passes; ++pass) {
+        // pass p holds the chunk slots [p * 8 * GPW, (p + 1) * 8 * GPW): none
+        // is a patch once they start past the chunk's last one (block-uniform)
+        if (pass * 8 * GPW >= nk) break;
         const int uu = pass * 8 + warp;
         const int kk = (uu / sp) * (sp * GPW) + (uu % sp) + sp * q;  // patch slot in chunk
         const bool active = kk < nk;
