@@ -473,9 +473,30 @@ def main():
             ev2[k][1].record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev2), ws, dev)
+    # the same with staging copies through device memory (cudaMemcpyAsync)
+    B.check(B.lib().bdis_set_option(m._h, B.OPT_HOST_MAPPED, 0), m._h)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            flush.zero_()
+            hstep()
+    torch.cuda.synchronize()
+    ev3 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(e2e_steps)]
+    with torch.cuda.stream(stream):
+        for k in range(e2e_steps):
+            flush.zero_()
+            ev3[k][0].record(stream)
+            hstep()
+            ev3[k][1].record(stream)
+    torch.cuda.synchronize()
+    B.check(B.lib().bdis_set_option(m._h, B.OPT_HOST_MAPPED, 1), m._h)
+    staged_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev3), ws, dev)
     e2e = {"value": round(ws * w * h * e2e_steps / (e2e_ms / 1e3) / 1e6, 3), "unit": UNIT,
            "h2d_bytes_per_step": 2 * w * h, "d2h_bytes_per_step": (4 + 4 + 1) * w * h,
-           "steps": e2e_steps, "api": "bdis_match_host (pinned host buffers)"}
+           "steps": e2e_steps,
+           "api": "bdis_match_host with pinned host buffers, read and written in place by the "
+                  "kernels over the host link (no staging copies)",
+           "staged_copies_value": round(ws * w * h * e2e_steps / (staged_ms / 1e3) / 1e6, 3)}
     clock_info = clocks.stop()
 
     # ---- batched form: 64 uneven pairs, one launch per stage per level

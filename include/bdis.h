@@ -146,10 +146,11 @@ bdis_status bdis_match(bdis_handle *h, const uint8_t *left, const uint8_t *right
                        int hgt, int pitch, float *disp, float *var, uint8_t *valid,
                        void *stream);
 
-/* Same computation with HOST buffers: the inputs are copied to the device,
- * the pipeline runs, and the outputs are copied back, all on `stream`; the
- * call returns after the stream has finished (host outputs are ready).
- * Pinned (page-locked) host memory gives the fastest copies. */
+/* Same computation with HOST buffers, on `stream`; the call returns after
+ * the stream has finished (host outputs are ready).  Page-locked buffers the
+ * device can address are read and written in place by the kernels
+ * (BDIS_OPT_HOST_MAPPED); other host memory goes through staging copies
+ * (inputs copied to the device, outputs copied back). */
 bdis_status bdis_match_host(bdis_handle *h, const uint8_t *left, const uint8_t *right, int w,
                             int hgt, int pitch, float *disp, float *var, uint8_t *valid,
                             void *stream);
@@ -281,7 +282,13 @@ typedef enum {
      * posteriors, sigma_r, patch solves, gradients and the pyramid are
      * differentiated too (FP32 pyramids only).  The coarse disparity maps
      * only initialise the finer searches and carry no gradient. */
-    BDIS_OPT_ADJOINT_LEVELS = 7
+    BDIS_OPT_ADJOINT_LEVELS = 7,
+    /* bdis_match_host: 1 (default) when every buffer is page-locked host
+     * memory the device can address (cudaMallocHost, cudaHostRegister), the
+     * kernels read the inputs and write the outputs in place over the
+     * host-device link; 0, or any other buffer: staging copies through device
+     * memory.  Same results. */
+    BDIS_OPT_HOST_MAPPED = 8
 } bdis_option;
 
 bdis_status bdis_set_option(bdis_handle *h, int option, int value);

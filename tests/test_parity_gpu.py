@@ -178,6 +178,33 @@ def test_host_api_equals_device_api(bd):
     assert np.array_equal(np.nan_to_num(hv, nan=-1), np.nan_to_num(v.cpu().numpy(), nan=-1))
 
 
+@pytest.mark.parametrize("mapped", [1, 0])
+def test_pinned_host_buffers_equal_device_api(bd, mapped):
+    """Page-locked host buffers: read and written in place by the kernels
+    (mapped) or through staging copies; bitwise equal to the device API."""
+    import ctypes as C
+    import torch
+    pair = synth.config_pair("plain_640x480_var")
+    h, w = pair.left.shape
+    m = bd.BDIS(patch=12, stride=6, levels=4, iters=8, variance=1)
+    m.set_option(bd.B.OPT_HOST_MAPPED, mapped)
+    d, v, ok = m.match(torch.from_numpy(pair.left).cuda(), torch.from_numpy(pair.right).cuda())
+    torch.cuda.synchronize()
+    hL = torch.from_numpy(pair.left).pin_memory()
+    hR = torch.from_numpy(pair.right).pin_memory()
+    hD = torch.full((h, w), 7.0).pin_memory()
+    hV = torch.full((h, w), 7.0).pin_memory()
+    hM = torch.full((h, w), 7, dtype=torch.uint8).pin_memory()
+    stream = torch.cuda.Stream()
+    for _ in range(2):   # first call tunes, second replays
+        m.match_host_ptr(hL.data_ptr(), hR.data_ptr(), w, h, hD.data_ptr(), hV.data_ptr(),
+                         hM.data_ptr(), C.c_void_p(stream.cuda_stream))
+    assert torch.equal(hM, ok.cpu())
+    assert torch.equal(torch.nan_to_num(hD, nan=-1.0), torch.nan_to_num(d.cpu(), nan=-1.0))
+    assert torch.equal(torch.nan_to_num(hV, nan=-1.0), torch.nan_to_num(v.cpu(), nan=-1.0))
+    m.close()
+
+
 def test_stats_and_pitched_input(bd):
     import torch
     pair = synth.config_pair("plain_320x240")
