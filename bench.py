@@ -322,8 +322,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--only", default="all", choices=["all", "batched"],
-                    help="batched: only the 64-pair batched form (used for profiling)")
+    ap.add_argument("--only", default="all", choices=["all", "batched", "fwdbwd"],
+                    help="batched / fwdbwd: only the 64-pair batched form / the differentiable "
+                         "form (used for profiling)")
     ap.add_argument("--form", default="auto", choices=["auto", "launches", "persistent"],
                     help="execution form of the plain workload (auto: the autotuner's choice)")
     args = ap.parse_args()
@@ -352,6 +353,13 @@ def main():
                             warmup=args.warmup, compare_plain=False, form=args.form)
         if rank == 0:
             print(json.dumps({"metric": METRIC, "batched": res}))
+        return 0
+    if args.only == "fwdbwd":
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+        stream = torch.cuda.Stream(device=dev)
+        res = bench_fwd_bwd(bd, dev, stream, flush, rank, ws, steps=args.steps, warmup=args.warmup)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "fwd_bwd": res}))
         return 0
 
     pair = synth.config_pair("plain_640x480_var", seed=rank_seed(rank))
