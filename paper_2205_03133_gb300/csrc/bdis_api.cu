@@ -739,9 +739,14 @@ int option_bits(const bdis_handle *h) {
 bdis_status run(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, cudaStream_t st) {
     // the same call as the last one, which replayed or captured a graph: replay it
     bdis_handle::Repeat &r = h->repeat;
-    if (h->repeat_ok && h->graph_exec != nullptr && r.in_type == in_type && r.st == st &&
-        r.arena == h->arena && r.opts == option_bits(h) && (int)r.pairs.size() == n &&
-        std::memcmp(r.pairs.data(), pairs, sizeof(bdis_pair) * n) == 0) {
+    auto same_pair = [](const bdis_pair &x, const bdis_pair &y) {  // field by field (no padding)
+        return x.left == y.left && x.right == y.right && x.w == y.w && x.h == y.h && x.pitch == y.pitch &&
+               x.disp == y.disp && x.var == y.var && x.valid == y.valid;
+    };
+    bool same = h->repeat_ok && h->graph_exec != nullptr && r.in_type == in_type && r.st == st &&
+                r.arena == h->arena && r.opts == option_bits(h) && (int)r.pairs.size() == n;
+    for (int i = 0; i < n && same; ++i) same = same_pair(r.pairs[i], pairs[i]);
+    if (same) {
         cudaError_t e = cudaGraphLaunch(h->graph_exec, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
         return BDIS_OK;
