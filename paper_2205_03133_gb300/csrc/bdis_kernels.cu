@@ -812,7 +812,7 @@ __device__ __forceinline__ PostIn posterior_load(const LaunchArgs &a, const Leve
     return in;
 }
 
-__device__ float4 posterior_of(const LaunchArgs &a, const LevelDesc &D, int kx, int ky,
+__device__ __forceinline__ float4 posterior_of(const LaunchArgs &a, const LevelDesc &D, int kx, int ky,
                                const PostIn &in, float sr, bool write) {
     const int k = ky * D.npx + kx;
     bdis_patch_record *rec = D.rec + k;
@@ -905,7 +905,9 @@ __device__ __forceinline__ void fuse_unit(const LaunchArgs &a, int unit, float4 
     __shared__ float cxm[kFuseTileWMax][kMaxPatch + 2], cym[kFuseTileHMax][kMaxPatch + 2];
     const int P = a.P, S = a.S;
 
-    const LevelDesc &D = a.descs[find_pair(a.descs, a.npairs, unit, W_FUSE)];
+    // the descriptor is copied to registers: the pixel stores could alias it
+    // as far as the compiler knows, which would reload its fields per pixel
+    const LevelDesc D = a.descs[find_pair(a.descs, a.npairs, unit, W_FUSE)];
     const int tile = unit - D.work_begin[W_FUSE];
     const int tx = tile % D.tiles_x, ty = tile / D.tiles_x;
     const int x0 = tx * TW, y0 = ty * TH;
@@ -1110,7 +1112,7 @@ __device__ __forceinline__ void fuse_unit(const LaunchArgs &a, int unit, float4 
 // var = 4^f bilinear(V_f); valid iff every level-f pixel with a non-zero
 // bilinear weight is valid (not NaN in D_f).
 __device__ __forceinline__ void upsample_unit(const LaunchArgs &a, int unit) {
-    const LevelDesc &D = a.descs[find_pair(a.descs, a.npairs, unit, W_UP)];
+    const LevelDesc D = a.descs[find_pair(a.descs, a.npairs, unit, W_UP)];  // in registers (see fuse_unit)
     const int u = unit - D.work_begin[W_UP];
     const float sc = (float)(1 << a.finest), inv = 1.f / sc;  // exact (power of two)
     const long long npix = (long long)D.w * D.h;
