@@ -17,6 +17,39 @@ __device__ __forceinline__ void stf(__half *p, float v) { *p = __float2half_rn(v
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
+// Four consecutive elements as floats; p aligned to four elements.
+__device__ __forceinline__ float4 ld4f(const uint8_t *p) {
+    const uchar4 u = __ldg((const uchar4 *)p);
+    return make_float4((float)u.x, (float)u.y, (float)u.z, (float)u.w);
+}
+__device__ __forceinline__ float4 ld4f(const float *p) { return __ldg((const float4 *)p); }
+__device__ __forceinline__ float4 ld4f(const __half *p) {
+    const uint2 u = __ldg((const uint2 *)p);
+    const float2 a = __half22float2(*(const __half2 *)&u.x);
+    const float2 b = __half22float2(*(const __half2 *)&u.y);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Eight consecutive values stored as floats or halves (rounded to nearest);
+// p aligned to 16 bytes.
+__device__ __forceinline__ void st8(float *p, const float *v) {
+    ((float4 *)p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    ((float4 *)p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+__device__ __forceinline__ void st8(__half *p, const float *v) {
+    const __half2 h0 = __floats2half2_rn(v[0], v[1]), h1 = __floats2half2_rn(v[2], v[3]);
+    const __half2 h2 = __floats2half2_rn(v[4], v[5]), h3 = __floats2half2_rn(v[6], v[7]);
+    uint4 u;
+    u.x = *(const unsigned *)&h0;
+    u.y = *(const unsigned *)&h1;
+    u.z = *(const unsigned *)&h2;
+    u.w = *(const unsigned *)&h3;
+    *(uint4 *)p = u;
+}
+// Two consecutive values; p aligned to two elements.
+__device__ __forceinline__ void st2(float *p, float a, float b) { *(float2 *)p = make_float2(a, b); }
+__device__ __forceinline__ void st2(__half *p, float a, float b) { *(__half2 *)p = __floats2half2_rn(a, b); }
+
 // Programmatic dependent launch.  A kernel launched with programmatic stream
 // serialisation may start while its predecessor on the stream still runs;
 // pdl_wait() returns once the predecessor has completed and its memory is

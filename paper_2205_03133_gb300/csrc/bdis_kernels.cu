@@ -29,96 +29,189 @@ namespace {
 // ---------------------------------------------------------------- pyramid
 
 // A block owns a 64 x 32 pixel tile of level l and the 32 x 16 tile of
-// level l+1 under it.  It stages the 68 x 36 region of L (and R when a
-// coarser level is built) with reflect-101 indices applied once, then writes
-// Sobel-x/8 of L for the 64 x 32 pixels and the [1 4 6 4 1]/16 blur of L and
-// R at the even pixels (2X, 2Y).
+// level l+1 under it.  It stages the 72 x 36 region of L (and R when a
+// coarser level is built) that starts 4 columns and 2 rows before the tile,
+// with reflect-101 indices applied once, then writes Sobel-x/8 of L for the
+// 64 x 32 pixels and the [1 4 6 4 1]/16 blur of L and R at the even pixels
+// (2X, 2Y).  A region inside the image with rows aligned to four elements is
+// staged with four-element loads; a thread computes eight Sobel outputs of a
+// row, four horizontally blurred columns and two blurred pixels from 16-byte
+// shared-memory reads, and stores them as vectors where the row allows.
 constexpr int kPyrTW = 64, kPyrTH = 32;
-constexpr int kPyrSW = kPyrTW + 4, kPyrSH = kPyrTH + 4;
+constexpr int kPyrSW = kPyrTW + 8, kPyrSH = kPyrTH + 4;
+constexpr int kPyrOX = 4;  // staged column of the tile's first pixel
 
 template <typename TI, typename TO>
 __device__ __forceinline__ void pyramid_unit(const LaunchArgs &a, int unit, float (*Ls)[kPyrSW],
                                              float (*Rs)[kPyrSW], float (*Lh)[kPyrTW / 2],
                                              float (*Rh)[kPyrTW / 2]) {
-
+    static_assert(kPyrTW * kPyrTH == 8 * 256 && (kPyrTW / 2) * (kPyrTH / 2) == 2 * 256,
+                  "one Sobel segment and one blurred pair per thread");
     const LevelDesc &D = a.descs[find_pair(a.descs, a.npairs, unit, W_PYR)];
     const int tile = unit - D.work_begin[W_PYR];
     const int ntx = (D.w + kPyrTW - 1) / kPyrTW;
     const int tx = tile % ntx, ty = tile / ntx;
-    const int x0 = tx * kPyrTW - 2, y0 = ty * kPyrTH - 2;  // region origin
+    const int xs = tx * kPyrTW - kPyrOX, y0 = ty * kPyrTH - 2;  // region origin
     const int w = D.w, h = D.h, pitch = D.pitch;
     const TI *L = (const TI *)D.L;
     const TI *R = (const TI *)D.R;
     const bool next = D.Ln != nullptr;
+    const int tid = threadIdx.x;
+    const bool vec_in = xs >= 0 && xs + kPyrSW <= w && y0 >= 0 && y0 + kPyrSH <= h && pitch % 4 == 0 &&
+                        ((uintptr_t)L | (next ? (uintptr_t)R : (uintptr_t)0)) % (4 * sizeof(TI)) == 0;
     __syncthreads();
     // all of a thread's loads are issued before its stores (memory-level parallelism);
     // every launch of the pyramid stage uses 256 threads
-    constexpr int NEL = kPyrSH * kPyrSW;
-    constexpr int PER = (NEL + 255) / 256;
-    float vl[PER], vr[PER];
+    if (vec_in) {
+        constexpr int NV = kPyrSH * (kPyrSW / 4);
+        constexpr int PER = (NV + 255) / 256;
+        float4 vl[PER], vr[PER];
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int i = threadIdx.x + k * 256;
-        if (i < NEL) {
-            const int r = i / kPyrSW, c = i - r * kPyrSW;
-            // only indices within 2 of the image are ever used by a stencil
-            const int gy = refl(min(max(y0 + r, -2), h + 1), h);
-            const int gx = refl(min(max(x0 + c, -2), w + 1), w);
-            vl[k] = ldf(L + (size_t)gy * pitch + gx);
-            vr[k] = next ? ldf(R + (size_t)gy * pitch + gx) : 0.f;
+        for (int k = 0; k < PER; ++k) {
+            const int i = tid + k * 256;
+            if (i < NV) {
+                const int r = i / (kPyrSW / 4), c = 4 * (i - r * (kPyrSW / 4));
+                const size_t o = (size_t)(y0 + r) * pitch + xs + c;
+                vl[k] = ld4f(L + o);
+                vr[k] = next ? ld4f(R + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         }
-    }
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int i = threadIdx.x + k * 256;
-        if (i < NEL) {
-            const int r = i / kPyrSW, c = i - r * kPyrSW;
-            Ls[r][c] = vl[k];
-            if (next) Rs[r][c] = vr[k];
+        for (int k = 0; k < PER; ++k) {
+            const int i = tid + k * 256;
+            if (i < NV) {
+                const int r = i / (kPyrSW / 4), c = 4 * (i - r * (kPyrSW / 4));
+                *(float4 *)&Ls[r][c] = vl[k];
+                if (next) *(float4 *)&Rs[r][c] = vr[k];
+            }
+        }
+    } else {
+        // image borders or unaligned rows: element loads with reflected
+        // indices, in two batches of loads in flight
+        constexpr int NEL = kPyrSH * kPyrSW;
+        constexpr int PER = (NEL + 511) / 512;
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+            float vl[PER], vr[PER];
+#pragma unroll
+            for (int k = 0; k < PER; ++k) {
+                const int i = tid + (half * PER + k) * 256;
+                if (i < NEL) {
+                    const int r = i / kPyrSW, c = i - r * kPyrSW;
+                    // only indices within 2 of the image are ever used by a stencil
+                    const int gy = refl(min(max(y0 + r, -2), h + 1), h);
+                    const int gx = refl(min(max(xs + c, -2), w + 1), w);
+                    vl[k] = ldf(L + (size_t)gy * pitch + gx);
+                    vr[k] = next ? ldf(R + (size_t)gy * pitch + gx) : 0.f;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < PER; ++k) {
+                const int i = tid + (half * PER + k) * 256;
+                if (i < NEL) {
+                    const int r = i / kPyrSW, c = i - r * kPyrSW;
+                    Ls[r][c] = vl[k];
+                    if (next) Rs[r][c] = vr[k];
+                }
+            }
         }
     }
     __syncthreads();
     TO *G = (TO *)D.G;  // nullptr below the finest processed level
-    for (int i = threadIdx.x; G != nullptr && i < kPyrTW * kPyrTH; i += blockDim.x) {
-        const int ly = i / kPyrTW, lx = i - ly * kPyrTW;
-        const int x = x0 + 2 + lx, y = y0 + 2 + ly;
-        if (x >= w || y >= h) continue;
-        const int cx = lx + 2, cy = ly + 2;
-        const float acc = (Ls[cy - 1][cx + 1] - Ls[cy - 1][cx - 1]) +
-                          2.f * (Ls[cy][cx + 1] - Ls[cy][cx - 1]) +
-                          (Ls[cy + 1][cx + 1] - Ls[cy + 1][cx - 1]);
-        stf(G + (size_t)y * D.gpitch + x, acc * 0.125f);
+    if (G != nullptr) {
+        // pixels lx0 .. lx0 + 7 of row ly: staged columns lx0 + 3 .. lx0 + 12
+        // of rows ly + 1 .. ly + 3
+        const int ly = tid >> 3, lx0 = (tid & 7) * 8;
+        const int x = tx * kPyrTW + lx0, y = ty * kPyrTH + ly;
+        if (x < w && y < h) {
+            float u[3][10];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const float *row = Ls[ly + 1 + q] + lx0;
+                const float4 c0 = *(const float4 *)row, c1 = *(const float4 *)(row + 4);
+                const float4 c2 = *(const float4 *)(row + 8);
+                u[q][0] = c0.w;
+                u[q][1] = c1.x; u[q][2] = c1.y; u[q][3] = c1.z; u[q][4] = c1.w;
+                u[q][5] = c2.x; u[q][6] = c2.y; u[q][7] = c2.z; u[q][8] = c2.w;
+                u[q][9] = row[12];
+            }
+            float g[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float acc = (u[0][j + 2] - u[0][j]) + 2.f * (u[1][j + 2] - u[1][j]) +
+                                  (u[2][j + 2] - u[2][j]);
+                g[j] = acc * 0.125f;
+            }
+            TO *gp = G + (size_t)y * D.gpitch + x;
+            if (x + 8 <= w && (((uintptr_t)gp) & 15u) == 0) {
+                st8(gp, g);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (x + j < w) stf(gp + j, g[j]);
+            }
+        }
     }
     if (next) {
-        // separable blur: horizontal at the even columns of every staged row,
-        // then vertical at the even rows (the multiply-add order of the 2D sum)
+        // separable blur: horizontal at the even columns of every staged row
+        // (outputs q .. q + 3 read staged columns 2q .. 2q + 15), then
+        // vertical at the even rows (the multiply-add order of the 2D sum)
         const float k[5] = {1.f, 4.f, 6.f, 4.f, 1.f};
-        for (int i = threadIdx.x; i < kPyrSH * (kPyrTW / 2); i += blockDim.x) {
-            const int r = i / (kPyrTW / 2), ox = i - r * (kPyrTW / 2);
-            const int cx = 2 * ox + 2;
-            float sl = 0.f, sr = 0.f;
+        auto hblur = [&](const float *src, float *dst) {
+            float v[16];
 #pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                sl += k[q] * Ls[r][cx + q - 2];
-                sr += k[q] * Rs[r][cx + q - 2];
+            for (int c = 0; c < 4; ++c) {
+                const float4 a4 = *(const float4 *)(src + 4 * c);
+                v[4 * c] = a4.x;
+                v[4 * c + 1] = a4.y;
+                v[4 * c + 2] = a4.z;
+                v[4 * c + 3] = a4.w;
             }
-            Lh[r][ox] = sl;
-            Rh[r][ox] = sr;
+            float o[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                o[j] = 0.f;
+#pragma unroll
+                for (int t = 0; t < 5; ++t) o[j] += k[t] * v[2 * j + 2 + t];
+            }
+            *(float4 *)dst = make_float4(o[0], o[1], o[2], o[3]);
+        };
+        for (int i = tid; i < kPyrSH * (kPyrTW / 8); i += blockDim.x) {
+            const int r = i / (kPyrTW / 8), q = 4 * (i - r * (kPyrTW / 8));
+            hblur(&Ls[r][2 * q], &Lh[r][q]);
+            hblur(&Rs[r][2 * q], &Rh[r][q]);
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < (kPyrTW / 2) * (kPyrTH / 2); i += blockDim.x) {
-            const int oy = i / (kPyrTW / 2), ox = i - oy * (kPyrTW / 2);
+        {
+            const int oy = tid >> 4, ox = (tid & 15) * 2;
             const int X = tx * (kPyrTW / 2) + ox, Y = ty * (kPyrTH / 2) + oy;
-            if (X >= D.wn || Y >= D.hn) continue;
-            const int cy = 2 * oy + 2;
-            float accL = 0.f, accR = 0.f;
+            if (X < D.wn && Y < D.hn) {
+                const int cy = 2 * oy + 2;
+                float aL0 = 0.f, aL1 = 0.f, aR0 = 0.f, aR1 = 0.f;
 #pragma unroll
-            for (int j = 0; j < 5; ++j) {
-                accL += k[j] * Lh[cy + j - 2][ox];
-                accR += k[j] * Rh[cy + j - 2][ox];
+                for (int j = 0; j < 5; ++j) {
+                    const float2 l2 = *(const float2 *)&Lh[cy + j - 2][ox];
+                    const float2 r2 = *(const float2 *)&Rh[cy + j - 2][ox];
+                    aL0 += k[j] * l2.x;
+                    aL1 += k[j] * l2.y;
+                    aR0 += k[j] * r2.x;
+                    aR1 += k[j] * r2.y;
+                }
+                TO *lp = (TO *)D.Ln + (size_t)Y * D.pitchn + X;
+                TO *rp = (TO *)D.Rn + (size_t)Y * D.pitchn + X;
+                const float s = 1.f / 256.f;
+                if (X + 1 < D.wn && ((((uintptr_t)lp) | ((uintptr_t)rp)) & (2 * sizeof(TO) - 1)) == 0) {
+                    st2(lp, aL0 * s, aL1 * s);
+                    st2(rp, aR0 * s, aR1 * s);
+                } else {
+                    stf(lp, aL0 * s);
+                    stf(rp, aR0 * s);
+                    if (X + 1 < D.wn) {
+                        stf(lp + 1, aL1 * s);
+                        stf(rp + 1, aR1 * s);
+                    }
+                }
             }
-            stf((TO *)D.Ln + (size_t)Y * D.pitchn + X, accL * (1.f / 256.f));
-            stf((TO *)D.Rn + (size_t)Y * D.pitchn + X, accR * (1.f / 256.f));
         }
     }
     }
@@ -284,11 +377,11 @@ __global__ void __launch_bounds__(256) k_pyramid2(LaunchArgs a) {
 }
 
 template <typename TI, typename TO>
-__global__ void __launch_bounds__(256) k_pyramid(LaunchArgs a) {
-    __shared__ float Ls[kPyrSH][kPyrSW];
-    __shared__ float Rs[kPyrSH][kPyrSW];
-    __shared__ float Lh[kPyrSH][kPyrTW / 2];
-    __shared__ float Rh[kPyrSH][kPyrTW / 2];
+__global__ void __launch_bounds__(256, 4) k_pyramid(LaunchArgs a) {
+    __shared__ __align__(16) float Ls[kPyrSH][kPyrSW];
+    __shared__ __align__(16) float Rs[kPyrSH][kPyrSW];
+    __shared__ __align__(16) float Lh[kPyrSH][kPyrTW / 2];
+    __shared__ __align__(16) float Rh[kPyrSH][kPyrTW / 2];
     pdl_wait();
     // the finest pyramid launch runs before every search: it clears the
     // sigma_r accumulators of all levels and pairs
@@ -1235,7 +1328,7 @@ __device__ void grid_barrier(unsigned *bar, int *err) {
 // coarse to fine, each stage striding its units over the persistent grid.
 template <int P, typename TG>
 __global__ void __launch_bounds__(256) k_mega(MegaArgs m) {
-    extern __shared__ float smem[];
+    extern __shared__ __align__(16) float smem[];
     for (int s = 0; s < m.nstages; ++s) {
         const LaunchArgs &a = m.stages[s];
         const int total = a.total;
