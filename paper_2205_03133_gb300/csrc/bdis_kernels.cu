@@ -40,11 +40,18 @@ namespace {
 constexpr int kPyrTW = 64, kPyrTH = 32;
 constexpr int kPyrSW = kPyrTW + 8, kPyrSH = kPyrTH + 4;
 constexpr int kPyrOX = 4;  // staged column of the tile's first pixel
+// Row pitches (floats) of the staged region and of the horizontal blur:
+// 76 = 12 and 36 = 4 modulo 32 banks, so eight consecutive rows at the same
+// column fall in distinct 4-bank groups (16-byte reads and writes by a
+// quarter warp without conflicts).
+constexpr int kPyrSP = kPyrSW + 4, kPyrHP = kPyrTW / 2 + 4;
+static_assert(kPyrSmemBytes == sizeof(float) * (2 * kPyrSH * kPyrSP + 2 * kPyrSH * kPyrHP),
+              "one-step pyramid shared memory");
 
 template <typename TI, typename TO>
-__device__ __forceinline__ void pyramid_unit(const LaunchArgs &a, int unit, float (*Ls)[kPyrSW],
-                                             float (*Rs)[kPyrSW], float (*Lh)[kPyrTW / 2],
-                                             float (*Rh)[kPyrTW / 2]) {
+__device__ __forceinline__ void pyramid_unit(const LaunchArgs &a, int unit, float (*Ls)[kPyrSP],
+                                             float (*Rs)[kPyrSP], float (*Lh)[kPyrHP],
+                                             float (*Rh)[kPyrHP]) {
     static_assert(kPyrTW * kPyrTH == 8 * 256 && (kPyrTW / 2) * (kPyrTH / 2) == 2 * 256,
                   "one Sobel segment and one blurred pair per thread");
     const LevelDesc &D = a.descs[find_pair(a.descs, a.npairs, unit, W_PYR)];
@@ -120,8 +127,11 @@ __device__ __forceinline__ void pyramid_unit(const LaunchArgs &a, int unit, floa
     TO *G = (TO *)D.G;  // nullptr below the finest processed level
     if (G != nullptr) {
         // pixels lx0 .. lx0 + 7 of row ly: staged columns lx0 + 3 .. lx0 + 12
-        // of rows ly + 1 .. ly + 3
-        const int ly = tid >> 3, lx0 = (tid & 7) * 8;
+        // of rows ly + 1 .. ly + 3.  A quarter warp takes eight rows of one
+        // segment (conflict-free shared reads); a warp, eight rows of four
+        // segments (whole 32-byte sectors of G)
+        const int lane = tid & 31, wp = tid >> 5;
+        const int ly = (wp & 3) * 8 + (lane & 7), lx0 = ((wp >> 2) * 4 + (lane >> 3)) * 8;
         const int x = tx * kPyrTW + lx0, y = ty * kPyrTH + ly;
         if (x < w && y < h) {
             float u[3][10];
@@ -176,8 +186,9 @@ __device__ __forceinline__ void pyramid_unit(const LaunchArgs &a, int unit, floa
             }
             *(float4 *)dst = make_float4(o[0], o[1], o[2], o[3]);
         };
+        // consecutive threads take consecutive rows of one column quad
         for (int i = tid; i < kPyrSH * (kPyrTW / 8); i += blockDim.x) {
-            const int r = i / (kPyrTW / 8), q = 4 * (i - r * (kPyrTW / 8));
+            const int qd = i / kPyrSH, r = i - qd * kPyrSH, q = 4 * qd;
             hblur(&Ls[r][2 * q], &Lh[r][q]);
             hblur(&Rs[r][2 * q], &Rh[r][q]);
         }
@@ -378,10 +389,10 @@ __global__ void __launch_bounds__(256) k_pyramid2(LaunchArgs a) {
 
 template <typename TI, typename TO>
 __global__ void __launch_bounds__(256, 4) k_pyramid(LaunchArgs a) {
-    __shared__ __align__(16) float Ls[kPyrSH][kPyrSW];
-    __shared__ __align__(16) float Rs[kPyrSH][kPyrSW];
-    __shared__ __align__(16) float Lh[kPyrSH][kPyrTW / 2];
-    __shared__ __align__(16) float Rh[kPyrSH][kPyrTW / 2];
+    __shared__ __align__(16) float Ls[kPyrSH][kPyrSP];
+    __shared__ __align__(16) float Rs[kPyrSH][kPyrSP];
+    __shared__ __align__(16) float Lh[kPyrSH][kPyrHP];
+    __shared__ __align__(16) float Rh[kPyrSH][kPyrHP];
     pdl_wait();
     // the finest pyramid launch runs before every search: it clears the
     // sigma_r accumulators of all levels and pairs
@@ -922,14 +933,15 @@ __device__ __forceinline__ float4 posterior_of(const LaunchArgs &a, const LevelD
     const float mu = in.mu;
     const float h = a.window_step;
     const float dlt[5] = {0.f, -h, h, -2.f * h, 2.f * h};
-    const float scale = 2.f * sr * sr * (float)(kWindow * kWindow);
+    // 1 / (2 sigma_r^2 s^2): one division, the same for every patch of the pair
+    const float iscale = 1.f / (2.f * sr * sr * (float)(kWindow * kWindow));
     // ln p_i - ln p_0 = -(E_i - E_0) / (2 sigma_r^2 s^2); the record holds E_i - E_0
     const float dE[5] = {0.f, r1.y, r1.z, r1.w, r2.x};
     float e[5], Z = 1.f;
     e[0] = 0.f;
 #pragma unroll
     for (int i = 1; i < 5; ++i) {
-        e[i] = -dE[i] / scale;
+        e[i] = -dE[i] * iscale;
         Z += expf(e[i]);
     }
     // pi = p_0 / sum_i p_i; with fast_exp every p_i (p_0 included) is
@@ -1335,10 +1347,10 @@ __global__ void __launch_bounds__(256) k_mega(MegaArgs m) {
         if (a.kind == 0) {
             if (blockIdx.x == 0 && a.acc_zero != nullptr)
                 for (int i = threadIdx.x; i < a.acc_count; i += blockDim.x) a.acc_zero[i] = 0ull;
-            float(*Ls)[kPyrSW] = (float(*)[kPyrSW])smem;
-            float(*Rs)[kPyrSW] = Ls + kPyrSH;
-            float(*Lh)[kPyrTW / 2] = (float(*)[kPyrTW / 2])(smem + 2 * kPyrSH * kPyrSW);
-            float(*Rh)[kPyrTW / 2] = Lh + kPyrSH;
+            float(*Ls)[kPyrSP] = (float(*)[kPyrSP])smem;
+            float(*Rs)[kPyrSP] = Ls + kPyrSH;
+            float(*Lh)[kPyrHP] = (float(*)[kPyrHP])(smem + 2 * kPyrSH * kPyrSP);
+            float(*Rh)[kPyrHP] = Lh + kPyrSH;
             if (a.level == 0) {
                 for (int u = blockIdx.x; u < total; u += gridDim.x)
                     pyramid_unit<uint8_t, TG>(a, u, Ls, Rs, Lh, Rh);
