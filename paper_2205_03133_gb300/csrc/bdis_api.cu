@@ -445,16 +445,18 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
     // stage list: the pyramid levels, then (search, fuse) per level coarse to fine
     std::vector<LaunchArgs> stages;
     std::vector<int> stage_itype;
-    // pyramid stages: two steps per launch (level l -> l+1 -> l+2) while two
-    // coarser levels remain, then single steps (the coarsest builds only its
-    // gradient).  Two steps save launches but recompute a halo: worth it while
-    // the launch latency dominates, i.e. for calls of up to 2^21 level-0 pixels.
+    // pyramid stages: two steps per launch (level l -> l+1 -> l+2, with the
+    // gradients of l and l+1; when l+1 is the coarsest level the launch ends
+    // with its gradient) while a coarser level remains, then a single step
+    // (the coarsest alone builds only its gradient).  Two steps save launches
+    // but recompute a halo: worth it while the launch latency dominates, i.e.
+    // for calls of up to 2^21 level-0 pixels.
     size_t px0 = 0;
     for (int i = 0; i < n; ++i) px0 += (size_t)pairs[i].w * pairs[i].h;
     const bool two_steps = h->pyr_steps == 2 || (h->pyr_steps == 0 && px0 <= ((size_t)1 << 21));
     for (int l = 0; l < NL;) {
         LaunchArgs a = base_args(p, l, d_descs + (size_t)l * n, n);
-        const bool two = two_steps && l + 2 <= NL - 1;
+        const bool two = two_steps && l + 1 <= NL - 1;
         a.kind = two ? 4 : 0;
         a.descs2 = two ? d_descs + (size_t)(l + 1) * n : nullptr;
         a.total = pl.units[l][W_PYR];
