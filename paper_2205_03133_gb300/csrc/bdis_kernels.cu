@@ -1072,10 +1072,12 @@ __device__ __forceinline__ void fuse_unit(const LaunchArgs &a, int unit, float4 
         const PostIn in = i == (int)threadIdx.x ? pre : posterior_load(a, D, kx, ky);
         fz[i] = posterior_of(a, D, kx, ky, in, sr, owner);
     }
-    // covering patches (tile-local indices) and their weights per column / row
-    if (threadIdx.x < TW + TH) {
-        const bool col = threadIdx.x < TW;
-        const int c = col ? threadIdx.x : threadIdx.x - TW;
+    // covering patches (tile-local indices) and their weights per column / row,
+    // by the block's last two warps (the posteriors start at thread 0, so the
+    // two run side by side)
+    for (int ci = (int)threadIdx.x - ((int)blockDim.x - 64); ci >= 0 && ci < TW + TH; ci += 64) {
+        const bool col = ci < TW;
+        const int c = col ? ci : ci - TW;
         const int xy = (col ? x0 : y0) + c;
         const int n = col ? D.w : D.h, kreg = col ? D.kxreg : D.kyreg, np = col ? D.npx : D.npy;
         const int klo = col ? kxlo : kylo, nr = col ? nkxr : nkyr, nt = col ? nkx : nky;
