@@ -377,11 +377,20 @@ def test_launch_options_do_not_change_results(bd, kw):
                 d, v, ok = m.match(L, R, stream=stream)
         torch.cuda.synchronize()
         got = (torch.nan_to_num(d, nan=-1.0), torch.nan_to_num(v, nan=-1.0), ok)
+        # every level's images and gradient as well (the two-step pyramid
+        # computes the next level and its gradient from a recomputed halo)
+        views = [m.level_view(0, l) for l in range(kw["levels"])]
+        imgs = [np.nan_to_num(vw[key], nan=-1.0) for vw in views for key in ("L", "R", "G")
+                if vw.get(key) is not None]
         if ref is None:
             ref = got
+            ref_imgs = imgs
         else:
             for a, b in zip(ref, got):
                 assert torch.equal(a, b), (graph, pdl, steps)
+            assert len(imgs) == len(ref_imgs)
+            for a, b in zip(ref_imgs, imgs):
+                assert np.array_equal(a, b), (graph, pdl, steps)
         m.close()
 
 
