@@ -203,12 +203,26 @@ def alu_peak_tflops(sm_mhz=None):
     return 152 * 128 * 2 * mhz * 1e6 / 1e12
 
 
-def kernel_source_digest():
+KERNEL_SOURCES = ("bdis_kernels.cu", "bdis_device.cuh", "bdis_internal.cuh")
+
+
+def code_digest(texts):
+    """Digest of CUDA sources without their comments and blank lines (what
+    the compiler sees), so that a comment edit keeps a capture valid."""
     import hashlib
+    import re
     h = hashlib.sha256()
-    for f in ("bdis_kernels.cu", "bdis_device.cuh", "bdis_internal.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2205_03133_gb300", "csrc", f), "rb").read())
+    for t in texts:
+        t = re.sub(r"/\*.*?\*/", "", t, flags=re.S)
+        t = re.sub(r"//[^\n]*", "", t)
+        lines = [ln.rstrip() for ln in t.splitlines()]
+        h.update("\n".join(ln for ln in lines if ln.strip()).encode())
     return h.hexdigest()[:16]
+
+
+def kernel_source_digest():
+    return code_digest(open(os.path.join(ROOT, "paper_2205_03133_gb300", "csrc", f)).read()
+                       for f in KERNEL_SOURCES)
 
 
 def recorded_traffic(kernel):

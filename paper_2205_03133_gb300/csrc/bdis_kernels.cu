@@ -3,18 +3,24 @@
 // Every kernel processes one pyramid level of a whole batch of pairs: work
 // units are flattened over the pairs through LevelDesc::work_begin, and each
 // block strides over the units (grid sized to the SM count), so the plain
-// single-pair call and the batched call run the same code.  Two launches per
-// level after the pyramid:
-//   k_pyramid   image pyramid + Sobel-x/8 of the left image (Sec. III-A),
-//               tiles staged in shared memory
+// single-pair call and the batched call run the same code.
+//   k_pyramid   one pyramid step (64x32 tiles staged in shared memory): the
+//               [1 4 6 4 1]/16 blur and decimation of L and R and Sobel-x/8 of
+//               the left image (Sec. III-A)
+//   k_pyramid2  two steps per launch (level l -> l+1 -> l+2 with the gradients
+//               of l and l+1), the level-(l+1) halo recomputed in the block
 //   k_search    inverse-compositional GN per patch (Eq. 1), window energies,
 //               rejection flags (Sec. III-B, Sec. IV technical details), and the
 //               sums of the dynamic sigma_r (text after Eq. 6), accumulated in
 //               exact 64-bit fixed point
-//   k_fuse      per 32x16 pixel tile: window posterior (Eq. 5-6),
+//   k_fuse      per 32x16 or 64x32 pixel tile: window posterior (Eq. 5-6),
 //               coarse-to-fine rho (Eq. 10-11) and PDF fit (Eq. 14-16) of the
 //               patches overlapping the tile, then the sGMM fusion gather
 //               (Eq. 8-9, Eq. 12) and pixel variance (Eq. 17)
+//   k_upsample  full-resolution output from a finest processed level f > 0
+//   k_depth     depth and its variance (Eq. 13, Eq. 17)
+//   k_mega      every stage of a call in one cooperative launch, with a
+//               bounded grid barrier between dependent stages
 #include <algorithm>
 #include <climits>
 #include <cfloat>
