@@ -670,8 +670,13 @@ bdis_status autotune(bdis_handle *h, int n, const bdis_pair *pairs, int in_type,
     std::vector<LevelCfg> cfg((size_t)NL, kDefaultCfg);
     bdis_status s = run_cfg(h, n, pairs, in_type, st, cfg.data(), false, false);  // warm-up
     if (s != BDIS_OK) return s;
-    double tsearch[3][kMaxLevels] = {{0}}, tfuse[3][kMaxLevels] = {{0}};
-    for (int c = 0; c < 3; ++c) {
+    // every candidate is timed twice (interleaved) and keeps its faster run,
+    // so that one noisy timing does not decide a level's configuration
+    double tsearch[3][kMaxLevels], tfuse[3][kMaxLevels];
+    for (int c = 0; c < 3; ++c)
+        for (int l = 0; l < kMaxLevels; ++l) tsearch[c][l] = tfuse[c][l] = 1e30;
+    for (int it = 0; it < 6; ++it) {
+        const int c = it % 3;
         for (int l = 0; l < NL; ++l) cfg[l] = kSearchCands[c];
         const size_t m0 = h->ev_marks.size();
         s = run_cfg(h, n, pairs, in_type, st, cfg.data(), false, true);
@@ -685,8 +690,13 @@ bdis_status autotune(bdis_handle *h, int n, const bdis_pair *pairs, int in_type,
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, h->ev_pool[ev], h->ev_pool[ev + 1]);
             if (e != cudaSuccess) return cuda_fail(h, e, "autotune events");
             const int kid = h->ev_marks[m].first;
-            if (kid == BDIS_K_SEARCH) tsearch[c][NL - 1 - ns++] = ms;
-            else if (kid == BDIS_K_FUSE) tfuse[c][NL - 1 - nf++] = ms;
+            if (kid == BDIS_K_SEARCH) {
+                double &t = tsearch[c][NL - 1 - ns++];
+                t = std::min(t, (double)ms);
+            } else if (kid == BDIS_K_FUSE) {
+                double &t = tfuse[c][NL - 1 - nf++];
+                t = std::min(t, (double)ms);
+            }
         }
         h->ev_marks.resize(m0);
     }
