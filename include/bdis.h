@@ -255,8 +255,8 @@ typedef enum {
     BDIS_OPT_PROFILE = 2,
     /* 1 (default): on the first call of a geometry (pair count and sizes),
      * time the candidate launch configurations (search patches per block,
-     * fusion tile size) level by level and keep the fastest; the call waits
-     * for the timing runs.  All configurations compute identical results.
+     * fusion tile size) level by level, each twice, and keep the fastest; the
+     * call waits for the timing runs.  All configurations compute identical results.
      * 0: the default configuration.  Never tunes while the stream is being
      * captured. */
     BDIS_OPT_AUTOTUNE = 3,
@@ -271,9 +271,11 @@ typedef enum {
      * stream order.  Same results. */
     BDIS_OPT_PDL = 5,
     /* Pyramid launches: 0 (default) two steps per launch (level l -> l+1 ->
-     * l+2, recomputing a 2-pixel halo of level l+1) when the call has at most
-     * 2^21 level-0 pixels, else one step per launch; 1 always one step;
-     * 2 always two steps where two coarser levels remain.  Same results. */
+     * l+2 with the gradients of l and l+1, recomputing a 2-pixel halo of level
+     * l+1; a launch whose l+1 is the coarsest level ends with its gradient)
+     * when the call has at most 2^21 level-0 pixels, else one step per launch;
+     * 1 always one step; 2 always two steps while a coarser level remains.
+     * Same results. */
     BDIS_OPT_PYRAMID_STEPS = 6,
     /* Extent of bdis_backward: 0 (default) the finest level, with the coarser
      * levels' state frozen (their propagated probability enters as a
