@@ -113,6 +113,7 @@ def lib():
         L.ob_check.argtypes = [C.POINTER(Params), C.c_int, C.c_int]
         L.ob_match.argtypes = [C.POINTER(Params), vp, vp, C.c_int, C.c_int, vp, vp, vp,
                                C.POINTER(Trace)]
+        L.ob_depth.argtypes = [vp, vp, C.c_long, C.c_double, vp, vp]
         assert L.ob_sizeof_patch() == PATCH_DTYPE.itemsize, "patch record layout mismatch"
         assert L.ob_sizeof_params() == C.sizeof(Params), "params layout mismatch"
         _lib = L
@@ -318,6 +319,17 @@ def match(p: Params, left: np.ndarray, right: np.ndarray, trace: bool = False):
             out["levels"].append({k: keep[(k, l)] for k in ("L", "R", "G", "D", "Q", "patches")}
                                  | {"sigma_r": tr.sigma_r[l]})
     return out
+
+
+def depth(disp, var, fb: float):
+    """Depth z = fb / d (Eq. 13) and its variance (fb)^2 / d^4 * var (Eq. 17);
+    NaN where d is not a positive finite number.  var may be None."""
+    d = np.ascontiguousarray(disp, dtype=np.float64)
+    v = None if var is None else np.ascontiguousarray(var, dtype=np.float64)
+    z = np.zeros_like(d)
+    zv = None if v is None else np.zeros_like(d)
+    lib().ob_depth(_ptr(d), _ptr(v), d.size, float(fb), _ptr(z), _ptr(zv))
+    return z, zv
 
 
 # ---------------------------------------------------------------- differentiable form

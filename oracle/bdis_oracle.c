@@ -824,6 +824,28 @@ int ob_match_u8(const ob_params *p, const uint8_t *L, const uint8_t *R, int w, i
     return rc;
 }
 
+/* ------------------------------------------------------------------ */
+/* depth (Eq. 13) and depth variance (Eq. 17)                           */
+/* ------------------------------------------------------------------ */
+
+/* Depth of a rectified pair from the fused finest-level disparity, Eq. 13:
+ * z = f b / d, with f the focal length (px) and b the baseline.  Its
+ * variance, Eq. 17: the fused disparity variance sum_k omega_k^2 sigma_k^2
+ * (the output var of ob_match) times (f b)^2 / d^4, the square of the slope
+ * of z(d).  A pixel whose disparity is not a positive finite number (NaN
+ * where the match is invalid) gets NaN in both.  var / depth_var may be
+ * NULL. */
+void ob_depth(const double *disp, const double *var, long n, double fb, double *depth,
+              double *depth_var)
+{
+    for (long i = 0; i < n; ++i) {
+        double d = disp[i];
+        int ok = isfinite(d) && d > 0.0;
+        depth[i] = ok ? fb / d : NAN;
+        if (depth_var) depth_var[i] = ok ? (fb * fb) / (d * d * d * d) * var[i] : NAN;
+    }
+}
+
 int ob_sizeof_patch(void) { return (int)sizeof(ob_patch); }
 int ob_sizeof_params(void) { return (int)sizeof(ob_params); }
 

@@ -111,11 +111,16 @@ def compare_outputs(gp, o, disp, var, valid, rec_gpu0):
         frac_within_tol=float((dd[both] <= D_TOL).mean()) if both.any() else 1.0,
         max_dd=float(dd[both].max()) if both.any() else 0.0,
         max_dd_outside_flips=float(dd[both & ~fp].max()) if (both & ~fp).any() else 0.0,
+        # reported, not gated: the pixels a flipped patch covers and the
+        # largest differences there (a flip moves a whole footprint)
+        flip_footprint_pixels=int(fp.sum()),
+        max_dd_inside_flips=float(dd[both & fp].max()) if (both & fp).any() else 0.0,
     )
     if gp.variance:
         vv = np.abs(var.astype(np.float64) - o["var"]) / np.maximum(np.abs(o["var"]), 1e-12)
         sel = both & ~fp
         m["var_max_rel_outside_flips"] = float(vv[sel].max()) if sel.any() else 0.0
+        m["var_max_rel_inside_flips"] = float(vv[both & fp].max()) if (both & fp).any() else 0.0
         m["var_frac_within"] = float((vv[both] <= V_RTOL).mean()) if both.any() else 1.0
     return m
 

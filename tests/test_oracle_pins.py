@@ -548,3 +548,188 @@ def test_default_parameters_match_paper():
     assert p.sigma_r_fixed == g["fixed_sigma_r_ablation"]["value"]
     assert p.pdf_iters == g["pdf_iterations"]["value"]
     assert p.pdf_resid == g["pdf_residual_threshold"]["value"]
+
+
+# ---------------------------------------------------------------- coarse-to-fine lookup
+
+# Coarse pixel X of level n+1 stands for the fine pixels 2X and 2X+1 of level
+# n (Fig. 1: each level halves the resolution), so its centre sits at fine
+# coordinate 2X + 1/2.  A disparity field that is linear at the fine level,
+# sampled at the coarse centres and halved (a disparity measured in coarse
+# pixels is half the fine one), must come back exactly from any coarse-to-
+# fine lookup that interpolates bilinearly: bilinear interpolation reproduces
+# linear functions.  A wrong coordinate map (x/2 instead of the centre
+# convention), a missing factor 2 or a patch centre other than the mean of
+# the patch's pixel coordinates all change the recovered values.
+
+def _fine_plane(a, b, c):
+    return lambda x, y: a * x + b * y + c
+
+
+def _coarse_samples(f, wc, hc, scale):
+    X = np.arange(wc, dtype=float)[None, :]
+    Y = np.arange(hc, dtype=float)[:, None]
+    return np.ascontiguousarray(f(2 * X + 0.5, 2 * Y + 0.5) * scale * np.ones((hc, wc)))
+
+
+def _interior(n_fine, n_coarse):
+    # fine coordinates whose coarse coordinate (x + 0.5)/2 - 0.5 lies in
+    # [0, n_coarse - 1]: no clamping
+    return lambda v: (v >= 0.5) & (v <= 2 * n_coarse - 1.5)
+
+
+@pytest.mark.parametrize("a,b,c", [(0.37, -0.21, 5.0), (-1.3, 0.8, 20.0)])
+def test_densify_fallback_recovers_linear_fine_field(a, b, c):
+    # nothing valid at this level: every pixel takes 2 * bilinear(D^(n+1))
+    p = oracle.make_params(patch=8, stride=4, levels=2)
+    w, h = 26, 18
+    wc, hc = (w + 1) // 2, (h + 1) // 2
+    f = _fine_plane(a, b, c)
+    Dc = _coarse_samples(f, wc, hc, 0.5)
+    rec = _grid_records(p, w, h)
+    D, Q, V, cnt = oracle.densify(p, rec, w, h, Dc=Dc)
+    xs, ys = np.meshgrid(np.arange(w, dtype=float), np.arange(h, dtype=float))
+    inner = _interior(w, wc)(xs) & _interior(h, hc)(ys)
+    assert inner.sum() > 0.7 * w * h
+    np.testing.assert_allclose(D[inner], f(xs, ys)[inner], rtol=0, atol=1e-12)
+    assert np.all(Q == 0.0) and np.all(cnt == 0)
+
+
+@pytest.mark.parametrize("P", [7, 8])
+def test_search_init_is_linear_coarse_field_at_patch_centre(P):
+    # the initial estimate of every patch is the fine field at the patch
+    # centre: the mean of its pixel coordinates, origin + (P - 1)/2
+    p = oracle.make_params(patch=P, stride=3, levels=2, iters=0, storage="f64")
+    w, h = 40, 27
+    wc, hc = (w + 1) // 2, (h + 1) // 2
+    f = _fine_plane(0.11, 0.29, 2.5)
+    Dc = _coarse_samples(f, wc, hc, 0.5)
+    rng = np.random.default_rng(P)
+    L = rng.uniform(0, 255, (h, w))
+    rec = oracle.search_level(p, L, L, oracle.sobel_x(L), Dc=Dc)
+    ox, oy = oracle.origins(w, P, 3), oracle.origins(h, P, 3)
+    cx = ox + (P - 1) / 2.0
+    cy = oy + (P - 1) / 2.0
+    CX, CY = np.meshgrid(cx, cy)
+    inner = _interior(w, wc)(CX) & _interior(h, hc)(CY)
+    assert inner.sum() >= 0.6 * inner.size
+    np.testing.assert_allclose(rec["dinit"][inner], f(CX, CY)[inner], rtol=0, atol=1e-12)
+    # with zero iterations the estimate is the initial value
+    np.testing.assert_allclose(rec["d"], rec["dinit"], rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("P", [7, 8])
+def test_inherited_probability_is_linear_coarse_map_at_patch_centre(P):
+    # Eq. 10 (reading): rho_k = Gamma_n pi_k + Q^(n+1)(centre); a probability
+    # carries no resolution factor, so the coarse map is sampled unscaled
+    p = oracle.make_params(patch=P, stride=3, levels=3)
+    w, h = 40, 27
+    wc, hc = (w + 1) // 2, (h + 1) // 2
+    g = _fine_plane(0.004, -0.003, 0.42)
+    Qc = _coarse_samples(g, wc, hc, 1.0)
+    rec = _grid_records(p, w, h)
+    rec["flags"] = 0
+    rec["E"] = np.array([0.0, 30, 30, 120, 120])
+    post = oracle.posterior(p, 1, rec, 1.0, Qc=Qc, w=w, h=h)
+    ox, oy = oracle.origins(w, P, 3), oracle.origins(h, P, 3)
+    CX, CY = np.meshgrid(ox + (P - 1) / 2.0, oy + (P - 1) / 2.0)
+    inner = _interior(w, wc)(CX) & _interior(h, hc)(CY)
+    w1 = oracle.gamma_weight(1, 3)
+    np.testing.assert_allclose(post["prop"][inner], g(CX, CY)[inner], rtol=0, atol=1e-14)
+    np.testing.assert_allclose((post["rho"] - w1 * post["pi"])[inner], g(CX, CY)[inner],
+                               rtol=0, atol=1e-14)
+
+
+# ---------------------------------------------------------------- sigma_r exact
+
+def _checker_quadratic(beta, dstar, c, w=96, h=24):
+    # left I = beta x^2; right = the left shifted by the integer d* plus the
+    # checkerboard c (-1)^(x+y).  With an even patch side every column of a
+    # patch holds as many +c as -c, so the checkerboard is orthogonal to the
+    # centred gradient 2 beta (x - xbar) (which has no y dependence) at any
+    # sample position, and the search converges on d* as without it.  At d*
+    # the residual is the checkerboard itself: E(0) = c^2 P^2 exactly.  At
+    # half-pixel offsets linear interpolation cancels the checkerboard, so
+    # E(+-1/2) = beta^2 S (the closed form of the quadratic image), which
+    # keeps the patch when beta^2 S > c^2 P^2.
+    L = synth.quadratic_image(w, h, beta)
+    X, Y = np.meshgrid(np.arange(w), np.arange(h))
+    R = synth.quadratic_image(w, h, beta, shift=dstar) + c * (-1.0) ** (X + Y)
+    return L, R, oracle.sobel_x(L)
+
+
+@pytest.mark.parametrize("c", [0.75, 1.5, 2.5])
+def test_sigma_r_pooled_exact_on_noise_free_checkerboard(c):
+    P, beta, dstar = 8, 1.2, 3
+    S = P * (P * (P * P - 1) / 12.0)
+    assert beta ** 2 * S > c * c * P * P
+    L, R, G = _checker_quadratic(beta, dstar, c)
+    p = oracle.make_params(patch=P, stride=4, levels=1, iters=3, storage="f64")
+    recs = []
+    for oy in (0, 4, 8, 16):
+        for ox in range(16, 80, 4):
+            r = oracle.search_patch(p, L, R, G, ox, oy, 2.0)
+            assert abs(r["d"] - dstar) < 1e-9
+            assert r["flags"] == 0, r["flags"]
+            assert abs(r["E"][0] - c * c * P * P) < 1e-6
+            assert abs(r["E"][1] - beta ** 2 * S) < 1e-6 * beta ** 2 * S
+            recs.append(r)
+    rec = np.array(recs, dtype=oracle.PATCH_DTYPE)
+    # pooled reading: sqrt(sum E_k(0) / (N P^2)) = c exactly (a P^2 - 1 in
+    # the denominator would give c * sqrt(64/63))
+    assert abs(oracle.sigma_r(p, rec) - c) < 1e-9
+    # a rejected patch with a large energy does not enter the sum
+    bad = rec[:1].copy()
+    bad["flags"] = oracle.F_SADDLE
+    bad["E"][0, 0] = 1e6
+    assert abs(oracle.sigma_r(p, np.concatenate([rec, bad])) - c) < 1e-9
+
+
+def test_sigma_r_literal_is_population_std_of_kept_energies():
+    p = oracle.make_params(sigma_r_mode="literal", sigma_r_floor=0.5)
+    rec = np.zeros(3, dtype=oracle.PATCH_DTYPE)
+    rec["E"][:, 0] = [10.0, 30.0, 5000.0]
+    rec["flags"] = [0, 0, oracle.F_MOVED]
+    # two kept patches: population std |E1 - E2| / 2 (the sample std would
+    # be |E1 - E2| / sqrt(2))
+    assert abs(oracle.sigma_r(p, rec) - 10.0) < 1e-12
+    rec["flags"] = 0
+    rec["E"][:, 0] = [1.0, 2.0, 6.0]
+    assert abs(oracle.sigma_r(p, rec) - float(np.std([1.0, 2.0, 6.0]))) < 1e-12
+    # equal energies: std 0, so the floor applies
+    rec["E"][:, 0] = 7.0
+    assert oracle.sigma_r(p, rec) == 0.5
+
+
+# ---------------------------------------------------------------- depth (Eq. 13, Eq. 17)
+
+def test_depth_is_inverse_disparity_and_variance_its_first_order_propagation():
+    rng = np.random.default_rng(9)
+    d = rng.uniform(0.5, 120.0, 400)
+    v = rng.uniform(0.0, 3.0, 400)
+    fb = 512.0 * 0.0042
+    z, zv = oracle.depth(d, v, fb)
+    # Eq. 13: z d = f b for every pixel
+    np.testing.assert_allclose(z * d, fb, rtol=1e-15)
+    # Eq. 17's depth factor is the squared slope of z(d): compare with the
+    # slope of the oracle's own depth by central differences (step 1e-5 d)
+    h = 1e-5 * d
+    zp, _ = oracle.depth(d + h, None, fb)
+    zm, _ = oracle.depth(d - h, None, fb)
+    slope = (zp - zm) / (2 * h)
+    np.testing.assert_allclose(zv, slope ** 2 * v, rtol=1e-8)
+    # doubling the disparity divides the depth by 2 and its variance by 16
+    z2, zv2 = oracle.depth(2 * d, v, fb)
+    np.testing.assert_allclose(z2, z / 2, rtol=1e-15)
+    np.testing.assert_allclose(zv2, zv / 16, rtol=1e-14)
+    # d = f b gives unit depth and unchanged variance / (f b)^2
+    z1, zv1 = oracle.depth(np.array([fb]), np.array([0.7]), fb)
+    assert z1[0] == 1.0 and abs(zv1[0] - 0.7 / fb ** 2) < 1e-15
+
+
+def test_depth_invalid_pixels_are_nan():
+    d = np.array([np.nan, 0.0, -3.0, np.inf, 5.0])
+    v = np.ones(5)
+    z, zv = oracle.depth(d, v, 10.0)
+    assert np.all(np.isnan(z[:4])) and np.all(np.isnan(zv[:4]))
+    assert z[4] == 2.0 and zv[4] == 100.0 / 625.0

@@ -306,24 +306,45 @@ def test_paper_preset_integer_shift(bd):
 
 
 def test_depth_kernel(bd):
+    # bdis_depth (Eq. 13, Eq. 17) against the oracle's depth, element by element
     import torch
     rng = np.random.default_rng(0)
     d = rng.uniform(0.5, 60.0, 100003).astype(np.float32)
     d[::7] = np.nan
     d[::11] = 0.0
     d[::13] = -1.0
+    d[::17] = np.inf
     v = rng.uniform(0.0, 2.0, d.size).astype(np.float32)
     fb = 512.0 * 0.005
     z, zv = bd.depth(torch.from_numpy(d).cuda(), torch.from_numpy(v).cuda(), fb=fb)
     z, zv = z.cpu().numpy(), zv.cpu().numpy()
-    ok = d > 0
-    d64 = d.astype(np.float64)
-    np.testing.assert_allclose(z[ok], fb / d64[ok], rtol=1e-6)
-    np.testing.assert_allclose(zv[ok], fb ** 2 / d64[ok] ** 4 * v[ok], rtol=1e-5)
-    assert np.isnan(z[~ok]).all() and np.isnan(zv[~ok]).all()
+    zo, zvo = oracle.depth(d, v, fb)
+    ok = np.isfinite(zo)
+    assert np.array_equal(ok, np.isfinite(z)) and np.array_equal(ok, np.isfinite(zv))
+    np.testing.assert_allclose(z[ok], zo[ok], rtol=1e-6)
+    np.testing.assert_allclose(zv[ok], zvo[ok], rtol=1e-5)
     z2, none = bd.depth(torch.from_numpy(d).cuda(), None, fb=fb)
     assert none is None and np.array_equal(np.nan_to_num(z2.cpu().numpy(), nan=-1),
                                            np.nan_to_num(z, nan=-1))
+
+
+def test_depth_of_a_match_against_the_oracle(bd):
+    # the depth and depth variance of a real disparity / variance output
+    import torch
+    pair = synth.config_pair("plain_640x480_var", seed=3)
+    m = bd.BDIS(patch=12, stride=6, levels=4, iters=8, variance=1)
+    disp, var, ok = m.match(torch.from_numpy(pair.left).cuda(), torch.from_numpy(pair.right).cuda())
+    z, zv = bd.depth(disp.reshape(-1), var.reshape(-1), fb=800.0 * 0.0055)
+    torch.cuda.synchronize()
+    dn, vn = disp.cpu().numpy().ravel(), var.cpu().numpy().ravel()
+    zo, zvo = oracle.depth(dn, vn, 800.0 * 0.0055)
+    z, zv = z.cpu().numpy(), zv.cpu().numpy()
+    fin = np.isfinite(zo)
+    assert fin.sum() > 0.5 * fin.size
+    assert np.array_equal(fin, np.isfinite(z))
+    np.testing.assert_allclose(z[fin], zo[fin], rtol=1e-6)
+    np.testing.assert_allclose(zv[fin], zvo[fin], rtol=1e-5, atol=1e-30)
+    m.close()
 
 
 def test_modes_outside_the_adjoint_are_rejected(bd):
