@@ -38,6 +38,12 @@ BATCH_PARAMS = dict(patch=8, stride=4, levels=3, iters=8, variance=0, storage="f
 L2_FLUSH_BYTES = 256 << 20   # larger than the 129 MB L2
 
 
+def bench_config(ws):
+    """The workload both arms measure (the reference arm prints the same)."""
+    return dict(WORKLOAD, parallelism=f"replicas x{ws} (one pair per rank)",
+                l2="flushed between timed steps (256 MiB write, outside the events)")
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -158,16 +164,31 @@ def algorithmic_bytes(kernel, w, h, prm):
     return _stage_bytes(kernel, w, h, prm)
 
 
-def _stage_bytes(kernel, w, h, prm):
+def fwd_bwd_bytes(w, h, prm):
+    """Algorithmic bytes of one differentiable step of one pair: the forward
+    (float level-0 images) plus the loss and the finest-level adjoint.  Per
+    level-0 pixel: loss reads L, R, D, valid (13 B) and writes dL/dD, dL/dI_l,
+    dL/dI_r (12 B); the adjoint reads dL/dD, the weight sums, L, R and the
+    gradient image (20 B) and accumulates into dL/dI_l, dL/dI_r (read + write,
+    16 B).  Per level-0 patch: patch record 64 B, fusion record 16 B, dL/dd_k
+    4 B."""
+    P, S = prm["patch"], prm["stride"]
+    fwd = sum(_stage_bytes(k, w, h, prm, level0_bytes=4) for k in ("pyramid", "search", "fuse"))
+    npch = level_geometry(w, h, P, S, 1)[0][2]
+    return fwd + w * h * (13 + 12 + 20 + 16) + npch * (64 + 16 + 4)
+
+
+def _stage_bytes(kernel, w, h, prm, level0_bytes=1):
     """Bytes one pass of `kernel` over all levels must move (per pair).
-    Image element sizes: level 0 u8, levels >= 1 and gradients the storage
-    type; patch record 64 B; fusion record 16 B; fused maps 8 B/px."""
+    Image element sizes: level 0 u8 (float in the differentiable form),
+    levels >= 1 and gradients the storage type; patch record 64 B; fusion
+    record 16 B; fused maps 8 B/px."""
     P, S, L = prm["patch"], prm["stride"], prm["levels"]
     b = 2 if prm["storage"] == "f16" else 4
     geo = level_geometry(w, h, P, S, L)
     tot = 0
     for l, (wl, hl, npch) in enumerate(geo):
-        img = 1 if l == 0 else b
+        img = level0_bytes if l == 0 else b
         px = wl * hl
         if kernel == "pyramid":
             nxt = geo[l + 1][0] * geo[l + 1][1] if l + 1 < L else 0
@@ -251,9 +272,74 @@ def measured_peaks():
 
 # ---------------------------------------------------------------- CPU baseline (oracle)
 
-def cpu_baseline(pair, prm, budget_s=12.0, gpu_out=None):
+def host_cpu():
+    """Usable host cores and the CPU model string."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu part")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return cores, f"{model or 'unknown'} ({platform.machine()})"
+
+
+def _oracle_worker(job):
+    """One host process: the oracle on its own pair until the wall budget."""
+    left, right, prm, budget = job
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import oracle
+    op = oracle.make_params(**prm)
+    runs, t0 = 0, time.perf_counter()
+    while True:
+        oracle.match(op, left, right)
+        runs += 1
+        if time.perf_counter() - t0 >= budget:
+            break
+    return runs, time.perf_counter() - t0
+
+
+def cpu_all_cores(prm, cores, budget_s=8.0):
+    """The oracle on every host core at once, one independent 640x480 pair
+    (G2, seed 100 + i) per process (the oracle itself is single-threaded),
+    until the wall budget: total pixels over the slowest process's time."""
+    import multiprocessing as mp
+
+    import synth
+    jobs = []
+    for i in range(cores):
+        pr = synth.g2_pair(640, 480, 100 + i)
+        jobs.append((pr.left, pr.right, dict(prm), budget_s))
+    ctx = mp.get_context("spawn")   # no fork after CUDA is initialised
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    runs = sum(r for r, _ in res)
+    el = max(t for _, t in res)
+    return {"value": round(runs * 640 * 480 / el / 1e6, 4), "unit": UNIT, "cores": cores,
+            "sample": f"{runs} full 640x480 pairs over {cores} processes (one pair each, "
+                      f"FP64 C oracle, 1 thread per process), {el:.1f} s wall"}
+
+
+def cpu_baseline(pair, prm, budget_s=12.0, gpu_out=None, all_cores=True):
     """The FP64 C oracle as it stands, one thread, on full pairs of the
-    workload until `budget_s` of CPU time is spent (at least one run)."""
+    workload until `budget_s` of CPU time is spent (at least one run); then
+    the same oracle on every host core (one process per core)."""
     import numpy as np
 
     import oracle
@@ -270,9 +356,13 @@ def cpu_baseline(pair, prm, budget_s=12.0, gpu_out=None):
         if el >= budget_s or runs >= 200:
             break
     px = pair.left.size * runs
+    cores, model = host_cpu()
     res = {"value": round(px / el / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
            "sample": f"{runs} full {pair.left.shape[1]}x{pair.left.shape[0]} pairs "
-                     f"(all {prm['levels']} levels, variance on), FP64 C, 1 thread, {el:.1f} s"}
+                     f"(all {prm['levels']} levels, variance on), FP64 C, 1 thread, {el:.1f} s",
+           "host_cores": cores, "cpu_model": model}
+    if all_cores and cores > 1:
+        res["all_cores"] = cpu_all_cores(prm, cores)
     if gpu_out is not None:
         from parity import compare_outputs
         disp, var, valid, rec0, gp = gpu_out
@@ -311,15 +401,17 @@ def run_reference(args):
     tot = sum(times)
     px = L.size * args.steps
     val = px / tot / 1e6
+    cores, model = host_cpu()
     sample = (f"each step a 640x{hc} crop of the 640x480 pair (full coarse-to-fine, variance on); "
-              f"FP64 C oracle, 1 thread")
+              f"FP64 C oracle, 1 thread of {cores} host cores ({model})")
     line = {"impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(tot / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(WORKLOAD, crop_h=hc),
+            "config": bench_config(ws),
             "cpu_baseline": {"value": round(val, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "crop_h": hc, "host_cores": cores,
+                             "cpu_model": model},
             "e2e": {"value": round(val, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -327,6 +419,39 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- ours
+
+def relaunch_distributed(n):
+    """`--gpus N` without a distributed environment: run this same command
+    under torch.distributed.run, one rank per GPU on this node."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node",
+           str(n), "--master-addr", "127.0.0.1", "--master-port", str(port),
+           os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
+def l2_copy_gbs(dev, stream, mib=16, reps=200):
+    """L2 bandwidth as a device-to-device copy of two mib-MiB buffers that
+    stay resident in the 129 MB L2 (read + write bytes, CUDA events, after
+    warm-up), the L2 counterpart of the HBM copy peak."""
+    import torch
+    a = torch.ones(mib << 18, dtype=torch.float32, device=dev)
+    b = torch.empty_like(a)
+    with torch.cuda.stream(stream):
+        for _ in range(20):
+            b.copy_(a)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            b.copy_(a)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return 2 * a.numel() * 4 * reps / (ms / 1e3) / 1e9
+
 
 def main():
     ap = argparse.ArgumentParser()
@@ -344,6 +469,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        return relaunch_distributed(args.gpus)
     if args.impl == "reference":
         return run_reference(args)
 
@@ -451,12 +578,19 @@ def main():
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
     per_step_bytes = algorithmic_bytes(dom, w, h, PARAMS)
     achieved = per_step_bytes / (kernels[dom]["ms_per_step"] / 1e3) / 1e9
+    l2_peak = l2_copy_gbs(dev, stream)
     roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 2),
                 "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 5),
                 "traffic": recorded_traffic(dom),
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
                 "algorithmic_bytes_per_step": per_step_bytes,
-                "launches_per_step": kernels[dom]["launches_per_step"]}
+                "launches_per_step": kernels[dom]["launches_per_step"],
+                "time_source": "CUDA events around each launch of the kernel (profiling pass of "
+                               "the same calls: plain launches, no graph)",
+                "l2": {"achieved": round(achieved, 2), "peak": round(l2_peak, 1), "unit": "GB/s",
+                       "frac": round(achieved / l2_peak, 5),
+                       "peak_source": "measured in bench.py: device copy of 2 x 16 MiB resident "
+                                      "in L2 (read + write bytes)"}}
     roofline_alu = None
     if "search" in kernels:
         fl = search_flops(w, h, PARAMS)
@@ -552,9 +686,7 @@ def main():
             "ms_per_step": round(dev_ms_max / args.steps, 5), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "fps": round(value / (w * h / 1e6), 2),
-            "config": dict(WORKLOAD, parallelism=f"replicas x{ws} (one pair per rank)",
-                           l2="flushed between timed steps (256 MiB write, outside the events)",
-                           graph="CUDA graph replay of the per-call launch sequence"),
+            "config": bench_config(ws),
             "gpu_launches": launches_per_step * args.steps,
             "form": form,
             "kernels": kernels,
@@ -613,8 +745,8 @@ def bench_fwd_bwd(bd, dev, stream, flush, rank, ws, steps=10, warmup=3):
             return
         arr = bd._grad_table(m, bufs)
         st = B.C.c_void_p(stream.cuda_stream)
-        B.check(B.lib().bdis_loss(m._h, B.C.c_float(0.1), arr, st), m._h)
-        B.check(B.lib().bdis_backward(m._h, arr, st), m._h)
+        B.check(B.lib().bdis_loss(m._h, None, B.C.c_float(0.1), arr, st), m._h)
+        B.check(B.lib().bdis_backward(m._h, None, arr, st), m._h)
 
     def run(fn, k):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -644,8 +776,21 @@ def bench_fwd_bwd(bd, dev, stream, flush, rank, ws, steps=10, warmup=3):
     t_fb_all = max_over_ranks(run(fwd_bwd, steps), ws, dev)
     m.close()
     px = n * w * h
+    by = n * fwd_bwd_bytes(w, h, DIFF_PARAMS)
+    pk = measured_peaks() or {}
+    hbm = pk.get("hbm_gbs", 6800.0)
+    l2 = l2_copy_gbs(dev, stream)
+    ach = by / (t_fb / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(ach / hbm, 4), "algorithmic_bytes_per_step": by,
+            "l2": {"achieved": round(ach, 1), "peak": round(l2, 1), "unit": "GB/s",
+                   "frac": round(ach / l2, 4)},
+            "scope": "whole fwd+bwd step (all its kernels): forward algorithmic bytes with float "
+                     "level-0 images plus the loss and finest-level adjoint bytes "
+                     "(bench.py fwd_bwd_bytes)"}
     return {"workload": "16 float pairs 640x480 (G1), P8 S4 L3, 8 iters, loss = L1 reprojection "
                         "+ 0.1 smoothness; grads w.r.t. both images and patch disparities",
+            "roofline": roof,
             "value": round(ws * px / (t_fb / 1e3) / 1e6, 2), "unit": UNIT,
             "ms_per_step": round(t_fb, 4), "fwd_only_value": round(ws * px / (t_f / 1e3) / 1e6, 2),
             "fwd_only_ms": round(t_f, 4), "mean_loss": round(loss, 5),
@@ -725,11 +870,16 @@ def bench_batched(bd, dev, stream, flush, rank, ws, steps=10, warmup=3, compare_
         t = kern["search"] / 1e3
         pk = measured_peaks() or {}
         hbm = pk.get("hbm_gbs", 6800.0)
+        l2 = l2_copy_gbs(dev, stream)
         roof = {"kernel": "search",
                 "alu": {"achieved": round(fl / t / 1e12, 3), "peak": round(alu_peak_tflops(), 2),
                         "unit": "TFLOP/s", "frac": round(fl / t / 1e12 / alu_peak_tflops(), 4)},
                 "hbm": {"achieved": round(by / t / 1e9, 1), "peak": hbm, "unit": "GB/s",
                         "frac": round(by / t / 1e9 / hbm, 4)},
+                "l2": {"achieved": round(by / t / 1e9, 1), "peak": round(l2, 1), "unit": "GB/s",
+                       "frac": round(by / t / 1e9 / l2, 4),
+                       "peak_source": "measured in bench.py: device copy of 2 x 16 MiB resident "
+                                      "in L2"},
                 "algorithmic_flops": fl, "algorithmic_bytes": by}
     return {"workload": "64 uneven pairs (24x640x480, 16x960x540, 16x1280x720, 8x1920x1080), "
                         "P8 S4 L3, 8 iters, fp16 pyramids",

@@ -186,8 +186,16 @@ bdis_status bdis_match_noalloc(const bdis_params *p, const uint8_t *left, const 
                                int w, int hgt, int pitch, float *disp, float *var,
                                uint8_t *valid, void *stream);
 
-/* Counters of the last call (synchronises `stream` to read them). */
+/* Counters of the last call (synchronises `stream` to read them).  The
+ * counters are filled in every case; the status is BDIS_ECUDA when a
+ * persistent-form call whose grid-barrier wait ran out has not been reported
+ * yet (barrier_timeouts = 1 if it was the last call). */
 bdis_status bdis_get_stats(bdis_handle *h, bdis_stats *out, void *stream);
+
+/* Waits until `stream` has finished the handle's calls and returns their
+ * device-side status: BDIS_ECUDA (reason in bdis_last_error) when a
+ * grid-barrier wait of a persistent-form call ran out, else BDIS_OK. */
+bdis_status bdis_wait(bdis_handle *h, void *stream);
 
 /* ---- differentiable form (finest level) ----
  * A forward on float images followed by a loss and its adjoint.  The
@@ -211,11 +219,35 @@ typedef struct {
 } bdis_pair_f32;
 
 /* Forward on float images (same pipeline as bdis_match; the level-0 images
- * are read as float).  Required before bdis_loss / bdis_backward. */
+ * are read as float).  Required before bdis_loss / bdis_backward.  Its state
+ * (pyramids, gradients, patch and fusion records, weight sums, sigma_r) stays
+ * in the handle until the handle's next call. */
 bdis_status bdis_match_f32(bdis_handle *h, const float *left, const float *right, int w, int hgt,
                            int pitch, float *disp, float *var, uint8_t *valid, void *stream);
 bdis_status bdis_match_batched_f32(bdis_handle *h, int n, const bdis_pair_f32 *pairs,
                                    void *stream);
+
+/* Caller-owned state of one differentiable forward (the saved tensors of an
+ * autograd graph).  A forward run into a bdis_saved keeps its state -- the
+ * pyramids, x-gradients, patch and fusion records, fusion-weight sums and
+ * sigma_r of every level (Sec. III-A..III-C), plus the caller's level-0
+ * image and output pointers -- in the object's own device memory, so any
+ * number of forwards on one handle can be differentiated later, each through
+ * its own state, in any order.
+ *   - bdis_saved_create ties the object to `h` (no CUDA call; the device
+ *     memory is allocated by the first forward into it, grows, never
+ *     shrinks) and bdis_saved_destroy frees it (synchronising the device).
+ *     A saved object outlives its handle only to be destroyed.
+ *   - bdis_match_batched_f32_saved is bdis_match_batched_f32 with the state
+ *     kept in `s`; running it again into the same `s` replaces the state.
+ *   - The caller keeps that forward's images and outputs (left, right, disp,
+ *     valid) unchanged until the last bdis_loss / bdis_backward on `s`.
+ *   - BDIS_EINVAL for an `s` created on another handle or holding no forward. */
+typedef struct bdis_saved bdis_saved;
+bdis_status bdis_saved_create(bdis_handle *h, bdis_saved **out);
+void bdis_saved_destroy(bdis_saved *s);
+bdis_status bdis_match_batched_f32_saved(bdis_handle *h, int n, const bdis_pair_f32 *pairs,
+                                         bdis_saved *s, void *stream);
 
 /* Per-pair gradient buffers (device, dense w*h unless stated). */
 typedef struct {
@@ -227,21 +259,25 @@ typedef struct {
                              held fixed (bdis_backward); may be NULL              */
 } bdis_grad;
 
-/* Loss of the last forward (bdis_match_f32 / _batched_f32), for every pair:
+/* Loss of a float forward -- the one kept in `s`, or with s == NULL the
+ * handle's last call (bdis_match_f32 / _batched_f32) -- for every pair:
  *   loss = ( sum_{valid x} |I_r(x - D(x)) - I_l(x)|
  *          + lambda sum_{valid 4-neighbour pairs} |D(p) - D(q)| ) / (w h)
  * (I_r sampled by clamped linear interpolation along x).  Writes loss,
  * g_disp, and the direct image terms: g_left is overwritten, g_right is
- * zeroed and then accumulated.  `g` has one entry per pair of that call. */
-bdis_status bdis_loss(bdis_handle *h, float lambda, const bdis_grad *g, void *stream);
+ * zeroed and then accumulated.  `g` has one entry per pair of that forward. */
+bdis_status bdis_loss(bdis_handle *h, const bdis_saved *s, float lambda, const bdis_grad *g,
+                      void *stream);
 
-/* Adjoint of the last forward: reads g_disp (from bdis_loss or from the
- * caller's own loss), ADDS dloss/dI_l and dloss/dI_r to g_left / g_right
- * (zero them first when g_disp comes from another loss) and writes
- * g_patch_disp.  Needs the pooled or fixed sigma_r (BDIS_EUNSUPPORTED for
- * LITERAL).  Image gradients are accumulated with float atomics, so their
- * last bits may differ from run to run. */
-bdis_status bdis_backward(bdis_handle *h, const bdis_grad *g, void *stream);
+/* Adjoint of a float forward (the one kept in `s`, or with s == NULL the
+ * handle's last call): reads g_disp (from bdis_loss or from the caller's own
+ * loss), ADDS dloss/dI_l and dloss/dI_r to g_left / g_right (zero them first
+ * when g_disp comes from another loss) and writes g_patch_disp.  Needs the
+ * pooled or fixed sigma_r (BDIS_EUNSUPPORTED for LITERAL).  Image gradients
+ * are accumulated with float atomics, so their last bits may differ from
+ * run to run.  The handle's backward scratch is shared by all its saved
+ * states: backward calls of one handle on different streams must not overlap. */
+bdis_status bdis_backward(bdis_handle *h, const bdis_saved *s, const bdis_grad *g, void *stream);
 
 /* ---- execution options ---- */
 
@@ -262,7 +298,11 @@ typedef enum {
     BDIS_OPT_AUTOTUNE = 3,
     /* Execution form: 0 (default) as chosen by the autotuner, 1 one launch per
      * stage, 2 persistent (every stage in one cooperative launch with grid
-     * barriers; 8-bit inputs, patch sizes 6, 8, 10, 12, 16).  Same results. */
+     * barriers; 8-bit inputs, patch sizes 6, 8, 10, 12, 16).  Same results.
+     * Every grid-barrier wait of the persistent form is bounded
+     * (BDIS_OPT_BARRIER_LIMIT); a wait that runs out lets the kernel finish
+     * with outputs that are not valid and is reported as BDIS_ECUDA by the
+     * next call on the handle, by bdis_get_stats and by bdis_wait. */
     BDIS_OPT_FORM = 4,
     /* 1 (default): launch each kernel of the launch sequence with
      * programmatic stream serialisation, so that it is scheduled while its
@@ -290,7 +330,15 @@ typedef enum {
      * kernels read the inputs and write the outputs in place over the
      * host-device link; 0, or any other buffer: staging copies through device
      * memory.  Same results. */
-    BDIS_OPT_HOST_MAPPED = 8
+    BDIS_OPT_HOST_MAPPED = 8,
+    /* Polls of one grid-barrier wait of the persistent form before it gives
+     * up (a poll is one L2 read and a 64 ns sleep): >= 1, default 2^22. */
+    BDIS_OPT_BARRIER_LIMIT = 9,
+    /* 1: test the timeout path of the persistent form -- no arrival completes
+     * a grid barrier, so every wait runs out after BDIS_OPT_BARRIER_LIMIT
+     * polls and the call is reported as failed (see BDIS_OPT_FORM).  0 (default):
+     * normal barriers.  Only for tests of the error reporting. */
+    BDIS_OPT_BARRIER_TEST = 10
 } bdis_option;
 
 bdis_status bdis_set_option(bdis_handle *h, int option, int value);

@@ -17,7 +17,7 @@ import numpy as np
 from . import _binding as B
 from ._binding import BdisError
 
-__all__ = ["BDIS", "BdisError", "default_params", "B", "_grad_table", "depth"]
+__all__ = ["BDIS", "BdisError", "default_params", "B", "_grad_table", "depth", "SavedState"]
 
 _STORAGE = {"f32": B.STORE_F32, "f16": B.STORE_F16}
 _SIGMA_R = {"pooled": B.SIGMA_R_POOLED, "literal": B.SIGMA_R_LITERAL, "fixed": B.SIGMA_R_FIXED}
@@ -65,8 +65,16 @@ class BDIS:
 
     def close(self):
         if getattr(self, "_h", None):
+            for sv in getattr(self, "_saved_pool", []):
+                sv.destroy()
+            self._saved_pool = []
             B.lib().bdis_destroy(self._h)
             self._h = None
+
+    def wait(self, stream=None):
+        """Wait for the handle's calls on `stream`; raises BdisError when a
+        persistent-form call's grid-barrier wait ran out."""
+        B.check(B.lib().bdis_wait(self._h, _stream_handle(stream)), self._h)
 
     def __del__(self):
         try:
@@ -189,16 +197,41 @@ class BDIS:
 
 # ---------------------------------------------------------------- differentiable form
 
+class SavedState:
+    """Caller-owned state of one differentiable forward (bdis_saved): the
+    forward's pyramids, gradients, records and weight sums live in this
+    object's device memory, plus the tensors of that forward (images and
+    outputs) that the loss and the adjoint read, kept alive here."""
+
+    def __init__(self, model: "BDIS"):
+        s = C.c_void_p()
+        B.check(B.lib().bdis_saved_create(model._h, C.byref(s)), model._h)
+        self._s = s
+        self.keep = None
+        self.shapes = None
+
+    @property
+    def handle(self):
+        return self._s
+
+    def destroy(self):
+        if getattr(self, "_s", None):
+            B.lib().bdis_saved_destroy(self._s)
+            self._s = None
+        self.keep = None
+
+
 def _f32_pair(l, r, d, v, m):
     h, w = l.shape
     return B.bdis_pair_f32(l.data_ptr(), r.data_ptr(), w, h, l.stride(0), d.data_ptr(),
                            v.data_ptr() if v is not None else None, m.data_ptr())
 
 
-def _match_f32(self, lefts, rights, outs=None, stream=None):
+def _match_f32(self, lefts, rights, outs=None, stream=None, saved=None):
     """Forward on float32 CUDA images (lists of (h, w) tensors); returns a list
     of (disp, var, valid) (preallocated `outs` are filled if given).
-    Required before loss_and_grad / backward."""
+    Required before loss_and_grad / backward.  With `saved` (a SavedState of
+    this model) the forward's state is kept there instead of in the handle."""
     import torch
     n = len(lefts)
     arr = (B.bdis_pair_f32 * n)()
@@ -216,11 +249,19 @@ def _match_f32(self, lefts, rights, outs=None, stream=None):
             m = torch.empty((h, w), dtype=torch.uint8, device=l.device)
         arr[i] = _f32_pair(l, r, d, v, m)
         res.append((d, v, m))
-    B.check(B.lib().bdis_match_batched_f32(self._h, n, arr, _stream_handle(stream)), self._h)
-    self._f32_shapes = [tuple(l.shape) for l in lefts]
     # the loss and the adjoint read the forward's images and outputs: keep
-    # them alive until the next forward on this handle
-    self._f32_keep = (list(lefts), list(rights), res)
+    # them alive as long as the state that points at them
+    keep = (list(lefts), list(rights), res)
+    shapes = [tuple(l.shape) for l in lefts]
+    if saved is None:
+        B.check(B.lib().bdis_match_batched_f32(self._h, n, arr, _stream_handle(stream)), self._h)
+        self._f32_shapes = shapes
+        self._f32_keep = keep
+    else:
+        B.check(B.lib().bdis_match_batched_f32_saved(self._h, n, arr, saved.handle,
+                                                     _stream_handle(stream)), self._h)
+        saved.shapes = shapes
+        saved.keep = keep
     return res
 
 
@@ -235,57 +276,106 @@ def _grad_table(self, bufs):
     return arr
 
 
-def _loss_and_grad(self, lam=0.1, stream=None):
-    """L1 reprojection + lam * smoothness of the last float forward and its
-    gradients.  Returns per pair dict(loss, g_disp, g_left, g_right,
-    g_patch_disp) (CUDA tensors)."""
+def _patch_grid(self, w, h):
+    """Level-0 patch grid (npx, npy) of a w x h pair (origins every S px plus
+    a ragged last one, so that every pixel is covered)."""
+    P, S = self.params.patch, self.params.stride
+
+    def n(x):
+        return (x - P) // S + 1 + (1 if (x - P) % S else 0)
+
+    return n(w), n(h)
+
+
+def _saved_ptr(saved):
+    return saved.handle if saved is not None else None
+
+
+def _loss_and_grad(self, lam=0.1, stream=None, saved=None):
+    """L1 reprojection + lam * smoothness of a float forward (the one kept in
+    `saved`, else the last one on the handle) and its gradients.  Returns per
+    pair dict(loss, g_disp, g_left, g_right, g_patch_disp) (CUDA tensors)."""
     import torch
     bufs = []
-    for i, (h, w) in enumerate(self._f32_shapes):
-        v = B.bdis_level_view()
-        B.check(B.lib().bdis_level_view_get(self._h, i, 0, C.byref(v)), self._h)
+    shapes = saved.shapes if saved is not None else self._f32_shapes
+    for (h, w) in shapes:
+        npx, npy = _patch_grid(self, w, h)
         dev = torch.device("cuda", torch.cuda.current_device())
         bufs.append(dict(loss=torch.empty(1, device=dev), g_disp=torch.empty((h, w), device=dev),
                          g_left=torch.empty((h, w), device=dev),
                          g_right=torch.empty((h, w), device=dev),
-                         g_patch_disp=torch.empty((v.npy, v.npx), device=dev)))
+                         g_patch_disp=torch.empty((npy, npx), device=dev)))
     arr = _grad_table(self, bufs)
     st = _stream_handle(stream)
-    B.check(B.lib().bdis_loss(self._h, C.c_float(lam), arr, st), self._h)
-    B.check(B.lib().bdis_backward(self._h, arr, st), self._h)
+    B.check(B.lib().bdis_loss(self._h, _saved_ptr(saved), C.c_float(lam), arr, st), self._h)
+    B.check(B.lib().bdis_backward(self._h, _saved_ptr(saved), arr, st), self._h)
     return bufs
 
 
-def _backward(self, g_disps, stream=None):
-    """Adjoint of the last float forward for caller-supplied dL/dD (list of
-    (h, w) tensors); returns (g_left, g_right, g_patch_disp) per pair."""
+def _backward(self, g_disps, stream=None, saved=None):
+    """Adjoint of a float forward (the one kept in `saved`, else the last one
+    on the handle) for caller-supplied dL/dD (list of (h, w) tensors);
+    returns (g_left, g_right, g_patch_disp) per pair."""
     import torch
     bufs = []
-    for i, gd in enumerate(g_disps):
+    for gd in g_disps:
         h, w = gd.shape
-        v = B.bdis_level_view()
-        B.check(B.lib().bdis_level_view_get(self._h, i, 0, C.byref(v)), self._h)
+        npx, npy = _patch_grid(self, w, h)
         bufs.append(dict(g_disp=torch.nan_to_num(gd.float(), nan=0.0).contiguous(),
                          g_left=torch.zeros((h, w), device=gd.device),
                          g_right=torch.zeros((h, w), device=gd.device),
-                         g_patch_disp=torch.empty((v.npy, v.npx), device=gd.device)))
+                         g_patch_disp=torch.empty((npy, npx), device=gd.device)))
     arr = _grad_table(self, bufs)
-    B.check(B.lib().bdis_backward(self._h, arr, _stream_handle(stream)), self._h)
+    B.check(B.lib().bdis_backward(self._h, _saved_ptr(saved), arr, _stream_handle(stream)),
+            self._h)
     return [(b["g_left"], b["g_right"], b["g_patch_disp"]) for b in bufs]
+
+
+def _take_saved(self) -> SavedState:
+    """A SavedState of this model: a released one if any (its device memory
+    and the handle's captured launch sequence are reused), else a new one."""
+    pool = self.__dict__.setdefault("_saved_pool", [])
+    return pool.pop() if pool else SavedState(self)
+
+
+def _release_saved(self, sv: SavedState):
+    if getattr(self, "_h", None) is None:
+        sv.destroy()
+        return
+    sv.keep = None
+    self.__dict__.setdefault("_saved_pool", []).append(sv)
 
 
 BDIS.match_f32 = _match_f32
 BDIS.loss_and_grad = _loss_and_grad
 BDIS.backward = _backward
+BDIS.saved_state = lambda self: SavedState(self)
+BDIS._take_saved = _take_saved
+BDIS._release_saved = _release_saved
 
 
 def disparity(model: "BDIS", left, right):
     """Differentiable dense disparity of one float32 pair (torch autograd).
     Returns (disp, valid); disp is NaN at invalid pixels and the gradient
-    flows to `left` and `right` through the library's adjoint.  The model's
-    handle keeps the forward state: run the backward before the next forward
-    on the same model."""
+    flows to `left` and `right` through the library's adjoint.  Each call's
+    forward state lives in its own SavedState held by the autograd graph, so
+    any number of forwards on one model can be differentiated, in any order;
+    the state returns to the model's pool when the graph is freed."""
     return _Disparity.apply(model, left, right)
+
+
+class _SavedLease:
+    """Ties a SavedState to an autograd graph: released to the model's pool
+    when the graph (and with it this object) is freed."""
+
+    def __init__(self, model, sv):
+        self.model, self.sv = model, sv
+
+    def __del__(self):
+        try:
+            self.model._release_saved(self.sv)
+        except Exception:
+            pass
 
 
 def _autograd_cls():
@@ -294,14 +384,17 @@ def _autograd_cls():
     class Disparity(torch.autograd.Function):
         @staticmethod
         def forward(ctx, model, left, right):
-            (d, _, m), = model.match_f32([left.detach().contiguous()], [right.detach().contiguous()])
+            sv = model._take_saved()
+            (d, _, m), = model.match_f32([left.detach().contiguous()],
+                                         [right.detach().contiguous()], saved=sv)
             ctx.model = model
+            ctx.lease = _SavedLease(model, sv)
             ctx.mark_non_differentiable(m)
             return d, m
 
         @staticmethod
         def backward(ctx, g_disp, g_valid):
-            (gl, gr, _), = ctx.model.backward([g_disp])
+            (gl, gr, _), = ctx.model.backward([g_disp], saved=ctx.lease.sv)
             return None, gl, gr
 
     return Disparity

@@ -87,6 +87,7 @@ class bdis_profile(C.Structure):
 OPT_GRAPH, OPT_PROFILE, OPT_AUTOTUNE, OPT_FORM, OPT_PDL, OPT_PYRAMID_STEPS, OPT_ADJOINT_LEVELS = (
     1, 2, 3, 4, 5, 6, 7)
 OPT_HOST_MAPPED = 8
+OPT_BARRIER_LIMIT, OPT_BARRIER_TEST = 9, 10
 KERNEL_NAMES = ["pyramid", "search", "fuse", "persistent", "upsample"]
 
 
@@ -104,14 +105,18 @@ EXPORTS = [
     ("bdis_match_host", C.c_int, [_h, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp]),
     ("bdis_match_batched", C.c_int, [_h, C.c_int, C.POINTER(bdis_pair), _vp]),
     ("bdis_get_stats", C.c_int, [_h, C.POINTER(bdis_stats), _vp]),
+    ("bdis_wait", C.c_int, [_h, _vp]),
     ("bdis_level_view_get", C.c_int, [_h, C.c_int, C.c_int, C.POINTER(bdis_level_view)]),
     ("bdis_copy", C.c_int, [_vp, _vp, C.c_size_t, _vp]),
     ("bdis_set_option", C.c_int, [_h, C.c_int, C.c_int]),
     ("bdis_get_profile", C.c_int, [_h, C.POINTER(bdis_profile), C.c_int]),
     ("bdis_match_f32", C.c_int, [_h, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp]),
     ("bdis_match_batched_f32", C.c_int, [_h, C.c_int, C.POINTER(bdis_pair_f32), _vp]),
-    ("bdis_loss", C.c_int, [_h, C.c_float, C.POINTER(bdis_grad), _vp]),
-    ("bdis_backward", C.c_int, [_h, C.POINTER(bdis_grad), _vp]),
+    ("bdis_saved_create", C.c_int, [_h, C.POINTER(C.c_void_p)]),
+    ("bdis_saved_destroy", None, [_vp]),
+    ("bdis_match_batched_f32_saved", C.c_int, [_h, C.c_int, C.POINTER(bdis_pair_f32), _vp, _vp]),
+    ("bdis_loss", C.c_int, [_h, _vp, C.c_float, C.POINTER(bdis_grad), _vp]),
+    ("bdis_backward", C.c_int, [_h, _vp, C.POINTER(bdis_grad), _vp]),
     ("bdis_match_noalloc", C.c_int, [C.POINTER(bdis_params), _vp, _vp, C.c_int, C.c_int, C.c_int,
                                      _vp, _vp, _vp, _vp]),
     ("bdis_depth", C.c_int, [_vp, _vp, C.c_longlong, C.c_float, _vp, _vp, _vp]),

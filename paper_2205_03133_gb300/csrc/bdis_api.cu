@@ -16,6 +16,18 @@
 
 using namespace bdis;
 
+// State of one differentiable forward kept by the caller (bdis_saved_create):
+// the forward ran with this object's device arena in place of the handle's,
+// so the pyramids, gradients, patch and fusion records, weight sums and
+// sigma_r it produced stay here until the object is reused or destroyed.
+struct bdis_saved {
+    bdis_handle *owner = nullptr;
+    char *arena = nullptr;
+    size_t arena_cap = 0;
+    std::vector<LevelDesc> descs;  // [level][pair] of that forward
+    int npairs = 0, levels = 0, in_type = -1;
+};
+
 struct bdis_handle {
     bdis_params p{};
     std::string err = "no error";
@@ -49,8 +61,19 @@ struct bdis_handle {
         bool mega;
     };
     std::map<std::string, Tuned> tuned;
-    int *err_flag = nullptr;  // timeout flag of the persistent form
+    int *err_flag = nullptr;  // timeout flag of the last persistent launch (device)
     bool last_persistent = false;
+    unsigned barrier_limit = kBarrierSpinLimit;  // BDIS_OPT_BARRIER_LIMIT
+    bool barrier_unreachable = false;            // BDIS_OPT_BARRIER_TEST
+    // sticky timeout word in mapped page-locked host memory: a persistent
+    // launch whose barrier wait ran out stores 1 there; the next call on the
+    // handle takes it (atomic exchange with 0) and fails
+    int *status_host = nullptr;
+    int *status_dev = nullptr;  // the device's address of the same word
+    // caller-owned forward states created on this handle, and the one whose
+    // arena the last call's descriptors point into (nullptr: the handle's own)
+    std::vector<bdis_saved *> saved;
+    bdis_saved *last_saved = nullptr;
     int form = 0;             // BDIS_OPT_FORM
     bool use_pdl = true;      // BDIS_OPT_PDL
     int pyr_steps = 0;        // BDIS_OPT_PYRAMID_STEPS
@@ -63,6 +86,7 @@ struct bdis_handle {
         int in_type = -1;
         cudaStream_t st = nullptr;
         char *arena = nullptr;
+        size_t arena_cap = 0;
         int opts = -1;
     } repeat;
     bool repeat_ok = false;
@@ -104,6 +128,10 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 bool finite_nonneg(float v) { return std::isfinite(v) && v >= 0.f; }
 
+}  // namespace
+
+namespace bdis {
+
 std::string check_params(const bdis_params &p) {
     if (p.patch < kMinPatch || p.patch > kMaxPatch) return "patch must be in [4, 16]";
     if (p.stride < 1 || p.stride > p.patch) return "stride must be in [1, patch]";
@@ -142,6 +170,10 @@ std::string check_pair(const bdis_params &p, const bdis_pair &q) {
         return "image too small: the coarsest level must be at least patch pixels per axis";
     return "";
 }
+
+}  // namespace bdis
+
+namespace {
 
 void fill_sgmm(const bdis_params &p, float *m) {
     // 1D factor of Eq. 8: m[a] = sum_{j<P} exp(-(a - j)^2 / (2 sigma_s^2)),
@@ -228,11 +260,13 @@ void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, const Leve
         v->assign(cnt, 0);
     const int F = p.finest_level;
     Bump b;
+    // the persistent form's barrier words sit at the start of the arena,
+    // whatever the pair count (they are cleared before every cooperative launch)
+    pl.off_bar = b.take(4 * sizeof(unsigned));
     pl.off_desc = b.take(sizeof(LevelDesc) * cnt);
     pl.off_stages = b.take(sizeof(LaunchArgs) * 3 * NL);
     pl.acc_count = 3 * cnt;
     pl.off_acc = b.take(sizeof(unsigned long long) * pl.acc_count);
-    pl.off_bar = b.take(4 * sizeof(unsigned));
     for (int l = 0; l < NL; ++l) {
         const int chunk = search_chunk(P, cfg[l].passes);
         int begin[W_COUNT] = {0, 0, 0, 0};
@@ -366,8 +400,8 @@ bdis_status ensure_arena(bdis_handle *h, size_t bytes) {
         cudaGetLastError();
         return fail(h, BDIS_ENOMEM, "cudaMalloc of the scratch arena failed");
     }
-    // zero once: the barrier state of the persistent form starts at zero and
-    // every call leaves its arrival counter at zero
+    // zeroed once (every element is written before it is read; the barrier
+    // words are also cleared before each persistent launch)
     e = cudaMemset(h->arena, 0, cap);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemset");
     h->arena_cap = cap;
@@ -554,7 +588,27 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
         m.nstages = (int)stages.size();
         m.bar = (unsigned *)(h->arena + pl.off_bar);
         m.err = (int *)(m.bar + 2);
-        cudaError_t e = timed(BDIS_K_PERSISTENT, [&] { return launch_mega(m, p.patch, st_type, grid, msm, st); });
+        m.spin_limit = h->barrier_limit;
+        m.unreachable = h->barrier_unreachable ? 1 : 0;
+        if (!h->status_host) {
+            cudaError_t e = cudaHostAlloc((void **)&h->status_host, sizeof(int),
+                                          cudaHostAllocMapped | cudaHostAllocPortable);
+            if (e == cudaSuccess) {
+                __atomic_store_n(h->status_host, 0, __ATOMIC_SEQ_CST);
+                e = cudaHostGetDevicePointer((void **)&h->status_dev, h->status_host, 0);
+            }
+            if (e != cudaSuccess) {
+                if (h->status_host) cudaFreeHost(h->status_host);
+                h->status_host = h->status_dev = nullptr;
+                cudaGetLastError();
+                return fail(h, BDIS_ENOMEM, "mapped page-locked status word unavailable");
+            }
+        }
+        m.err_host = h->status_dev;
+        // arrival counter, generation and timeout flag start at zero in every launch
+        cudaError_t e = cudaMemsetAsync(m.bar, 0, 4 * sizeof(unsigned), st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
+        e = timed(BDIS_K_PERSISTENT, [&] { return launch_mega(m, p.patch, st_type, grid, msm, st); });
         if (e != cudaSuccess) return cuda_fail(h, e, "persistent launch");
         h->descs = pl.descs;
         h->npairs = n;
@@ -748,7 +802,25 @@ int option_bits(const bdis_handle *h) {
            (h->form << 4) | (h->pyr_steps << 6);
 }
 
+// A persistent launch whose grid-barrier wait ran out has stored 1 in the
+// handle's mapped status word: the next call that looks at it (any call on
+// the handle; bdis_get_stats and bdis_wait after synchronising) takes the
+// word and fails.  That launch's outputs are not valid.
+bdis_status take_status(bdis_handle *h) {
+    if (!h->status_host) return BDIS_OK;
+    if (__atomic_exchange_n(h->status_host, 0, __ATOMIC_SEQ_CST) != 0)
+        return fail(h, BDIS_ECUDA,
+                    "a grid-barrier wait of an earlier persistent-form call ran out: that call's "
+                    "outputs are not valid");
+    return BDIS_OK;
+}
+
 bdis_status run(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, cudaStream_t st) {
+    {
+        const bdis_status ps = take_status(h);
+        if (ps != BDIS_OK) return ps;
+    }
+    h->last_saved = nullptr;
     // the same call as the last one, which replayed or captured a graph: replay it
     bdis_handle::Repeat &r = h->repeat;
     auto same_pair = [](const bdis_pair &x, const bdis_pair &y) {  // field by field (no padding)
@@ -756,7 +828,8 @@ bdis_status run(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, cuda
                x.disp == y.disp && x.var == y.var && x.valid == y.valid;
     };
     bool same = h->repeat_ok && h->graph_exec != nullptr && r.in_type == in_type && r.st == st &&
-                r.arena == h->arena && r.opts == option_bits(h) && (int)r.pairs.size() == n;
+                r.arena == h->arena && r.arena_cap == h->arena_cap && r.opts == option_bits(h) &&
+                (int)r.pairs.size() == n;
     for (int i = 0; i < n && same; ++i) same = same_pair(r.pairs[i], pairs[i]);
     if (same) {
         cudaError_t e = cudaGraphLaunch(h->graph_exec, st);
@@ -769,6 +842,7 @@ bdis_status run(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, cuda
         r.in_type = in_type;
         r.st = st;
         r.arena = h->arena;
+        r.arena_cap = h->arena_cap;
         r.opts = option_bits(h);
     } else {
         h->repeat_ok = false;
@@ -862,6 +936,7 @@ bdis_status bdis_create(const bdis_params *p, bdis_handle **out) {
 
 void bdis_destroy(bdis_handle *h) {
     if (!h) return;
+    for (bdis_saved *sv : h->saved) sv->owner = nullptr;  // they stay valid objects to destroy
     if (h->upload_done) {
         cudaEventSynchronize(h->upload_done);
         cudaEventDestroy(h->upload_done);
@@ -873,6 +948,10 @@ void bdis_destroy(bdis_handle *h) {
     if (h->pinned) cudaFreeHost(h->pinned);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     if (h->garena) cudaFree(h->garena);
+    if (h->status_host) {
+        cudaDeviceSynchronize();  // no launch may still write the word
+        cudaFreeHost(h->status_host);
+    }
     for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
     delete h;
 }
@@ -902,6 +981,15 @@ bdis_status bdis_set_option(bdis_handle *h, int option, int value) {
     }
     if (option == BDIS_OPT_HOST_MAPPED) {
         h->host_mapped = value != 0;
+        return BDIS_OK;
+    }
+    if (option == BDIS_OPT_BARRIER_LIMIT) {
+        if (value < 1) return fail(h, BDIS_EINVAL, "barrier limit must be >= 1 poll");
+        h->barrier_limit = (unsigned)value;
+        return BDIS_OK;
+    }
+    if (option == BDIS_OPT_BARRIER_TEST) {
+        h->barrier_unreachable = value != 0;
         return BDIS_OK;
     }
     if (option == BDIS_OPT_ADJOINT_LEVELS) {
@@ -1088,7 +1176,7 @@ bdis_status bdis_get_stats(bdis_handle *h, bdis_stats *out, void *stream) {
         }
     }
     out->persistent = h->last_persistent ? 1 : 0;
-    if (h->err_flag) {
+    if (h->last_persistent && h->err_flag) {
         e = cudaMemcpy(&out->barrier_timeouts, h->err_flag, sizeof(int), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(h, e, "stats copy");
     }
@@ -1100,7 +1188,15 @@ bdis_status bdis_get_stats(bdis_handle *h, bdis_stats *out, void *stream) {
         if (e != cudaSuccess) return cuda_fail(h, e, "stats copy");
         for (uint8_t b : v) out->valid_pixels += b;
     }
-    return BDIS_OK;
+    // the counters are filled either way; a timed-out barrier wait is an error
+    return take_status(h);
+}
+
+bdis_status bdis_wait(bdis_handle *h, void *stream) {
+    if (!h) return BDIS_EINVAL;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    return take_status(h);
 }
 
 bdis_status bdis_copy(void *dst, const void *src, size_t bytes, void *stream) {
@@ -1143,6 +1239,66 @@ bdis_status bdis_match_f32(bdis_handle *h, const float *left, const float *right
     return bdis_match_batched_f32(h, 1, &q, stream);
 }
 
+bdis_status bdis_saved_create(bdis_handle *h, bdis_saved **out) {
+    if (!out) return BDIS_EINVAL;
+    *out = nullptr;
+    if (!h) return BDIS_EINVAL;
+    bdis_saved *sv = new (std::nothrow) bdis_saved();
+    if (!sv) return fail(h, BDIS_ENOMEM, "out of host memory");
+    sv->owner = h;
+    h->saved.push_back(sv);
+    *out = sv;
+    return BDIS_OK;
+}
+
+void bdis_saved_destroy(bdis_saved *sv) {
+    if (!sv) return;
+    if (bdis_handle *h = sv->owner) {
+        h->saved.erase(std::remove(h->saved.begin(), h->saved.end(), sv), h->saved.end());
+        if (h->last_saved == sv) {  // the handle's last-call views pointed into this arena
+            h->last_saved = nullptr;
+            h->descs.clear();
+            h->npairs = 0;
+        }
+        h->repeat_ok = false;  // a replay must not reuse this arena's address
+    }
+    if (sv->arena) cudaFree(sv->arena);  // synchronises with work still using it
+    delete sv;
+}
+
+bdis_status bdis_match_batched_f32_saved(bdis_handle *h, int n, const bdis_pair_f32 *pairs,
+                                         bdis_saved *sv, void *stream) {
+    if (!h) return BDIS_EINVAL;
+    if (!sv) return fail(h, BDIS_EINVAL, "null saved state");
+    if (sv->owner != h) return fail(h, BDIS_EINVAL, "saved state created on another handle");
+    if (n < 1 || !pairs) return fail(h, BDIS_EINVAL, "need at least one pair");
+    std::vector<bdis_pair> q((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        const bdis_pair_f32 &f = pairs[i];
+        q[i] = bdis_pair{(const uint8_t *)f.left, (const uint8_t *)f.right, f.w, f.h, f.pitch,
+                         f.disp, f.var, f.valid};
+        std::string m = check_pair(h->p, q[i]);
+        if (!m.empty()) return fail(h, BDIS_EINVAL, "pair " + std::to_string(i) + ": " + m);
+    }
+    // the forward runs with the saved state's arena in place of the handle's
+    std::swap(h->arena, sv->arena);
+    std::swap(h->arena_cap, sv->arena_cap);
+    const bdis_status st = run(h, n, q.data(), E_F32, (cudaStream_t)stream);
+    std::swap(h->arena, sv->arena);
+    std::swap(h->arena_cap, sv->arena_cap);
+    if (st != BDIS_OK) {
+        sv->npairs = 0;
+        sv->descs.clear();
+        return st;
+    }
+    sv->descs = h->descs;
+    sv->npairs = h->npairs;
+    sv->levels = h->levels;
+    sv->in_type = h->in_type;
+    h->last_saved = sv;
+    return BDIS_OK;
+}
+
 namespace {
 
 // Backward plan: per-level launch arguments and work totals.
@@ -1153,13 +1309,30 @@ struct GradPlan {
     size_t zero_off = 0, zero_bytes = 0;  // gradient buffers of levels >= 1 (zeroed per call)
 };
 
+// The forward a loss or an adjoint differentiates: a caller-owned saved
+// state, or (sv == nullptr) the handle's last call.
+struct FwdView {
+    const std::vector<LevelDesc> *descs;
+    int npairs, levels, in_type;
+};
+
+bdis_status fwd_view(bdis_handle *h, const bdis_saved *sv, FwdView &v) {
+    if (sv != nullptr) {
+        if (sv->owner != h) return fail(h, BDIS_EINVAL, "saved state created on another handle");
+        v = FwdView{&sv->descs, sv->npairs, sv->levels, sv->in_type};
+    } else {
+        v = FwdView{&h->descs, h->npairs, h->levels, h->in_type};
+    }
+    if (v.npairs < 1 || v.in_type != E_F32)
+        return fail(h, BDIS_EINVAL, "no float-image forward to differentiate (call bdis_match_f32)");
+    return BDIS_OK;
+}
+
 // Builds and uploads the (level, pair) descriptors of the backward pass for
 // levels 0 .. nlev-1.
-bdis_status grad_setup(bdis_handle *h, const bdis_grad *g, bool need_loss, cudaStream_t st,
-                       int nlev, GradPlan &gp) {
+bdis_status grad_setup(bdis_handle *h, const FwdView &fv, const bdis_grad *g, bool need_loss,
+                       cudaStream_t st, int nlev, GradPlan &gp) {
     if (!g) return fail(h, BDIS_EINVAL, "null gradient table");
-    if (h->npairs < 1 || h->in_type != E_F32)
-        return fail(h, BDIS_EINVAL, "no float-image forward to differentiate (call bdis_match_f32)");
     const bdis_params &p = h->p;
     if (p.finest_level != 0 || p.weight_mode != BDIS_WEIGHT_BDIS || p.fast_exp != 0)
         return fail(h, BDIS_EUNSUPPORTED,
@@ -1167,7 +1340,7 @@ bdis_status grad_setup(bdis_handle *h, const bdis_grad *g, bool need_loss, cudaS
                     "(finest_level 0, BDIS weights, exact exponential)");
     if (nlev > 1 && p.storage != BDIS_STORE_F32)
         return fail(h, BDIS_EUNSUPPORTED, "the adjoint through every level needs FP32 pyramids");
-    const int n = h->npairs;
+    const int n = fv.npairs;
     for (int i = 0; i < n; ++i) {
         if (!g[i].g_disp || !g[i].g_left || !g[i].g_right)
             return fail(h, BDIS_EINVAL, "null gradient buffer");
@@ -1185,7 +1358,7 @@ bdis_status grad_setup(bdis_handle *h, const bdis_grad *g, bool need_loss, cudaS
         int begin[G_COUNT] = {0, 0};
         for (int i = 0; i < n; ++i) {
             const size_t k = (size_t)l * n + i;
-            const LevelDesc &d = h->descs[k];
+            const LevelDesc &d = (*fv.descs)[k];
             GradDesc &q = gd[k];
             q.w = d.w;
             q.h = d.h;
@@ -1245,7 +1418,7 @@ bdis_status grad_setup(bdis_handle *h, const bdis_grad *g, bool need_loss, cudaS
     for (int l = 0; l < nlev; ++l)
         for (int i = 0; i < n; ++i) {
             const size_t k = (size_t)l * n + i;
-            const LevelDesc &d = h->descs[k];
+            const LevelDesc &d = (*fv.descs)[k];
             GradDesc &q = gd[k];
             q.L = (const float *)d.L;
             q.R = (const float *)d.R;
@@ -1328,17 +1501,21 @@ bdis_status grad_setup(bdis_handle *h, const bdis_grad *g, bool need_loss, cudaS
 
 }  // namespace
 
-bdis_status bdis_loss(bdis_handle *h, float lambda, const bdis_grad *g, void *stream) {
+bdis_status bdis_loss(bdis_handle *h, const bdis_saved *sv, float lambda, const bdis_grad *g,
+                      void *stream) {
     if (!h) return BDIS_EINVAL;
     if (!std::isfinite(lambda) || lambda < 0.f) return fail(h, BDIS_EINVAL, "lambda must be >= 0");
     cudaStream_t st = (cudaStream_t)stream;
+    FwdView fv;
+    bdis_status s = fwd_view(h, sv, fv);
+    if (s != BDIS_OK) return s;
     GradPlan gp;
-    bdis_status s = grad_setup(h, g, true, st, 1, gp);
+    s = grad_setup(h, fv, g, true, st, 1, gp);
     if (s != BDIS_OK) return s;
     GradArgs a = gp.a[0];
     a.lambda = lambda;
-    for (int i = 0; i < h->npairs; ++i) {
-        const LevelDesc &d = h->descs[(size_t)i];
+    for (int i = 0; i < fv.npairs; ++i) {
+        const LevelDesc &d = (*fv.descs)[(size_t)i];
         cudaError_t e = cudaMemsetAsync(g[i].g_right, 0, sizeof(float) * (size_t)d.w * d.h, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
     }
@@ -1348,14 +1525,17 @@ bdis_status bdis_loss(bdis_handle *h, float lambda, const bdis_grad *g, void *st
     return BDIS_OK;
 }
 
-bdis_status bdis_backward(bdis_handle *h, const bdis_grad *g, void *stream) {
+bdis_status bdis_backward(bdis_handle *h, const bdis_saved *sv, const bdis_grad *g, void *stream) {
     if (!h) return BDIS_EINVAL;
     if (h->p.sigma_r_mode == BDIS_SIGMA_R_LITERAL)
         return fail(h, BDIS_EUNSUPPORTED, "no adjoint for the LITERAL sigma_r reading");
     cudaStream_t st = (cudaStream_t)stream;
-    const int nlev = h->adjoint_levels ? h->levels : 1;
+    FwdView fv;
+    bdis_status s = fwd_view(h, sv, fv);
+    if (s != BDIS_OK) return s;
+    const int nlev = h->adjoint_levels ? fv.levels : 1;
     GradPlan gp;
-    bdis_status s = grad_setup(h, g, false, st, nlev, gp);
+    s = grad_setup(h, fv, g, false, st, nlev, gp);
     if (s != BDIS_OK) return s;
     cudaError_t e;
     if (gp.zero_bytes > 0) {

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -110,12 +111,16 @@ struct LaunchArgs {
 struct MegaArgs {
     const LaunchArgs *stages;  // device array of nstages stage arguments
     int nstages;
-    unsigned *bar;             // [0] arrivals, [1] generation (both 0 initially)
-    int *err;                  // set to 1 when a barrier wait runs out
+    unsigned *bar;             // [0] arrivals, [1] generation (cleared before each launch)
+    int *err;                  // set to 1 when a barrier wait runs out (cleared before each launch)
+    int *err_host;             // mapped page-locked word of the handle: also set to 1 (sticky)
+    unsigned spin_limit;       // polls of one barrier wait before it gives up
+    int unreachable;           // test: no arrival completes a barrier, so every wait runs out
 };
 
-// Spin limit of one grid-barrier wait (well under a second); a wait that runs out
-// sets MegaArgs::err and lets the block continue, so the kernel always ends.
+// Default poll limit of one grid-barrier wait (a poll is one L2 read and a
+// 64 ns sleep); a wait that runs out sets MegaArgs::err and lets the block
+// continue, so the kernel always ends.
 constexpr unsigned kBarrierSpinLimit = 1u << 22;
 
 // ---- differentiable finest level (bdis_grad.cu)
@@ -160,6 +165,11 @@ struct GradArgs {
     int use_sgmm, use_c2f;
     float m[kMaxPatch];
 };
+
+// Argument checks shared by every entry point (bdis_api.cu): an empty string
+// when valid, else the reason.
+std::string check_params(const bdis_params &p);
+std::string check_pair(const bdis_params &p, const bdis_pair &q);
 
 cudaError_t launch_loss(const GradArgs &a, cudaStream_t s);        // + per-pair reduce
 cudaError_t launch_bwd_pix(const GradArgs &a, cudaStream_t s);

@@ -1045,23 +1045,29 @@ __device__ __forceinline__ void fuse_unit(const LaunchArgs &a, int unit, float4 
         patch_of(threadIdx.x, kx, ky);
         pre = posterior_load(a, D, kx, ky);
     }
-    // sigma_r of the pair from the search's exact sums (text after Eq. 6),
-    // by one thread (FP64 conversions), broadcast through shared memory
+    // sigma_r of the pair from the search's exact integer sums (text after
+    // Eq. 6), converted once to FP32 by one thread and broadcast through
+    // shared memory
     __shared__ float sr_sh;
     if (threadIdx.x == 0) {
         float sr;
-        const double S1 = (double)__ldcg(D.acc) / (double)kSigmaFix1;
-        const double S2 = (double)__ldcg(D.acc + 1);
-        const double S3 = (double)__ldcg(D.acc + 2);
+        const unsigned long long n = __ldcg(D.acc + 1);
+        const float S1 = __ull2float_rn(__ldcg(D.acc)) * (1.f / kSigmaFix1);  // sum E(0)
+        const float S2 = __ull2float_rn(n);                                  // kept patches
+        const float S3 = __ull2float_rn(__ldcg(D.acc + 2));                  // sum E(0)^2
         if (a.sigma_r_mode == BDIS_SIGMA_R_FIXED) {
             sr = a.sigma_r_fixed;
-        } else if (S2 == 0.0) {
+        } else if (n == 0ull) {
             sr = a.sigma_r_floor;
         } else if (a.sigma_r_mode == BDIS_SIGMA_R_LITERAL) {
-            const float mean = (float)(S1 / S2);
-            sr = fmaxf(sqrtf(fmaxf((float)(S3 / S2) - mean * mean, 0.f)), a.sigma_r_floor);
+            // population variance mean(E^2) - mean(E)^2, the square's
+            // rounding error taken back by an FMA
+            const float mean = S1 / S2;
+            const float sq = mean * mean;
+            const float var = (S3 / S2 - sq) - fmaf(mean, mean, -sq);
+            sr = fmaxf(sqrtf(fmaxf(var, 0.f)), a.sigma_r_floor);
         } else {
-            sr = fmaxf(sqrtf((float)(S1 / (S2 * (double)(P * P)))), a.sigma_r_floor);
+            sr = fmaxf(sqrtf(S1 / (S2 * (float)(P * P))), a.sigma_r_floor);
         }
         if (tile == 0) *D.sigma_r = sr;
         sr_sh = sr;
@@ -1316,24 +1322,29 @@ __global__ void __launch_bounds__(256) k_fuse(LaunchArgs a) {
 // Grid-wide barrier for a cooperative launch (all blocks co-resident).
 // Thread 0 of each block arrives on a counter; the last arrival resets it and
 // bumps the generation, the others wait for the generation to change.  Every
-// wait is bounded: past kBarrierSpinLimit polls the block records the timeout
-// and goes on, so the kernel always terminates.
-__device__ void grid_barrier(unsigned *bar, int *err) {
+// wait is bounded: past `limit` polls the block records the timeout and goes
+// on, so the kernel always terminates.  `unreachable` (a test of that path)
+// makes no arrival the last one, so every wait runs out.
+__device__ void grid_barrier(unsigned *bar, int *err, int *err_host, unsigned limit, int unreachable) {
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned *gen = bar + 1;
         const unsigned g = *gen;
         __threadfence();
         const unsigned arrived = atomicAdd(bar, 1u);
-        if (arrived == gridDim.x - 1) {
+        if (!unreachable && arrived == gridDim.x - 1) {
             atomicExch(bar, 0u);
             __threadfence();
             atomicAdd(bar + 1, 1u);
         } else {
             unsigned it = 0;
             while (*gen == g) {
-                if (++it > kBarrierSpinLimit) {
+                if (++it > limit) {
                     atomicOr(err, 1);
+                    if (err_host != nullptr) {
+                        *(volatile int *)err_host = 1;  // the host takes it on its next call
+                        __threadfence_system();
+                    }
                     break;
                 }
                 __nanosleep(64);
@@ -1388,7 +1399,7 @@ __global__ void __launch_bounds__(256) k_mega(MegaArgs m) {
         } else {
             for (int u = blockIdx.x; u < total; u += gridDim.x) upsample_unit(a, u);
         }
-        if (s + 1 < m.nstages) grid_barrier(m.bar, m.err);
+        if (s + 1 < m.nstages) grid_barrier(m.bar, m.err, m.err_host, m.spin_limit, m.unreachable);
     }
 }
 

@@ -62,30 +62,6 @@ int na_level_dim(int n, int l) {
 
 size_t na_align(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-bool na_params_ok(const bdis_params &p) {
-    auto fin = [](float v) { return std::isfinite(v); };
-    if (p.patch < kMinPatch || p.patch > kMaxPatch) return false;
-    if (p.stride < 1 || p.stride > p.patch) return false;
-    if (p.levels < 1 || p.levels > kMaxLevels || p.iters < 0 || p.iters > 1000) return false;
-    if (!(fin(p.sigma_s) && p.sigma_s > 0.f) || !(fin(p.window_step) && p.window_step > 0.f)) return false;
-    if (!(fin(p.conv_eps) && p.conv_eps >= 0.f)) return false;
-    if (!(fin(p.valid_gamma) && p.valid_gamma >= 0.f && p.valid_gamma <= 1.f)) return false;
-    if (!(fin(p.pix_thresh) && p.pix_thresh >= 0.f) || !fin(p.search_radius)) return false;
-    if (p.sigma_r_mode < 0 || p.sigma_r_mode > 2) return false;
-    if (!(fin(p.sigma_r_floor) && p.sigma_r_floor >= 0.f)) return false;
-    if (!(fin(p.sigma_r_fixed) && p.sigma_r_fixed > 0.f)) return false;
-    if (p.sigma_r_mode != BDIS_SIGMA_R_FIXED && !(p.sigma_r_floor > 0.f)) return false;
-    if ((p.variance != 0 && p.variance != 1) || p.pdf_iters < 0 || p.pdf_iters > 100) return false;
-    if (!(fin(p.pdf_resid) && p.pdf_resid >= 0.f)) return false;
-    if (p.storage != BDIS_STORE_F32 && p.storage != BDIS_STORE_F16) return false;
-    if (!(fin(p.hess_eps) && p.hess_eps >= 0.f)) return false;
-    if ((p.use_sgmm != 0 && p.use_sgmm != 1) || (p.use_c2f != 0 && p.use_c2f != 1)) return false;
-    if (p.weight_mode != BDIS_WEIGHT_BDIS && p.weight_mode != BDIS_WEIGHT_DIS) return false;
-    if (p.finest_level < 0 || p.finest_level >= p.levels || (p.fast_exp != 0 && p.fast_exp != 1))
-        return false;
-    return true;
-}
-
 // Resolves (once per device) the device address of the scratch array.
 bdis_status na_scratch(void **out) {
     int dev = 0;
@@ -112,10 +88,11 @@ extern "C" bdis_status bdis_match_noalloc(const bdis_params *pp, const uint8_t *
                                           void *stream) {
     if (!pp || !left || !right || !disp || !valid) return BDIS_EINVAL;
     const bdis_params p = *pp;
-    if (!na_params_ok(p)) return BDIS_EINVAL;
-    if (w < 1 || hgt < 1 || w > 32768 || hgt > 32768 || pitch < w) return BDIS_EINVAL;
+    // the same parameter and size checks as every other entry point
+    if (!check_params(p).empty()) return BDIS_EINVAL;
+    const bdis_pair q{left, right, w, hgt, pitch, disp, var, valid};
+    if (!check_pair(p, q).empty()) return BDIS_EINVAL;
     const int NL = p.levels, P = p.patch, S = p.stride;
-    if (na_level_dim(w, NL - 1) < P || na_level_dim(hgt, NL - 1) < P) return BDIS_EINVAL;
     // full resolution only: the upsampled form (finest_level > 0) needs bdis_match
     if (p.finest_level != 0) return BDIS_EUNSUPPORTED;
 
@@ -174,7 +151,14 @@ extern "C" bdis_status bdis_match_noalloc(const bdis_params *pp, const uint8_t *
     size_t smem;
     search_layout(P, S, tau, p.window_step, cfg.passes, band_pitch, band_cap, chunk_pitch, smem);
     const size_t fsmem = fuse_smem(P, S, cfg.tile_w, cfg.tile_h);
-    if (smem > 227 * 1024 || fsmem > 227 * 1024) return BDIS_EUNSUPPORTED;
+    int optin = 0, dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BDIS_ECUDA;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return BDIS_ECUDA;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+    // the search band and the fuse tile must fit the device's per-block limit
+    if (smem > (size_t)optin || fsmem > (size_t)optin) return BDIS_EUNSUPPORTED;
 
     void *scratch = nullptr;
     const bdis_status ss = na_scratch(&scratch);
@@ -216,13 +200,7 @@ extern "C" bdis_status bdis_match_noalloc(const bdis_params *pp, const uint8_t *
 
     // ---- launches (the same kernels as bdis_match)
     cudaStream_t st = (cudaStream_t)stream;
-    int optin = 0, dev = 0, sms = 1;
-    if (cudaGetDevice(&dev) != cudaSuccess) return BDIS_ECUDA;
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
     // the kernels' shared-memory limits are only ever raised, never lowered
-    (void)optin;
     if (prepare_search(P, smem) != cudaSuccess) return BDIS_ECUDA;
     if (prepare_fuse(fsmem) != cudaSuccess) return BDIS_ECUDA;
     k_noalloc_write_descs<<<1, 32, 0, st>>>(tab, d_descs);

@@ -53,6 +53,35 @@ def test_reference_arm_two_ranks_prints_once():
     assert len(lines) == 1 and lines[0]["impl"] == "reference" and lines[0]["n_gpus"] == 2
 
 
+def test_reference_arm_config_is_the_bench_workload():
+    sys.path.insert(0, ROOT)
+    import bench
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                        "--warmup", "3"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d, = _json_lines(r.stdout)
+    assert d["config"] == bench.bench_config(1)
+    assert d["cpu_baseline"]["host_cores"] >= 1 and d["cpu_baseline"]["cpu_model"]
+
+
+def test_gpus_flag_relaunches_under_torchrun():
+    # without a distributed environment, --gpus 2 starts two ranks itself
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2", "--steps",
+                        "1", "--warmup", "3"], cwd=ROOT, capture_output=True, text=True,
+                       timeout=900, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = _json_lines(r.stdout)
+    assert len(lines) == 1 and lines[0]["n_gpus"] == 2
+
+
+def test_all_core_oracle_baseline():
+    sys.path.insert(0, ROOT)
+    import bench
+    res = bench.cpu_all_cores(dict(bench.PARAMS), 2, budget_s=0.5)
+    assert res["cores"] == 2 and res["value"] > 0 and "2 processes" in res["sample"]
+
+
 def test_capture_digest_ignores_comments_only():
     sys.path.insert(0, ROOT)
     import bench

@@ -144,6 +144,81 @@ def test_autograd_function(bd):
     assert L.grad.abs().sum() > 0 and R.grad.abs().sum() > 0
 
 
+def test_two_forwards_then_backward_of_the_first(bd):
+    """Each disparity() forward keeps its state in its own caller-owned saved
+    state (bdis_saved), held by the autograd graph: after a second forward on
+    the same model, the first graph's backward still gives the first
+    forward's gradient, equal to that of a lone forward on a fresh model."""
+    import torch
+
+    def leaf(a):
+        return torch.from_numpy(a.astype(np.float32)).cuda().requires_grad_(True)
+
+    prs = [synth.g1_pair(96, 64, 7, d0=1.0, d1=3.0, amp=1.0, as_float=True),
+           synth.g1_pair(96, 64, 8, d0=1.5, d1=2.5, amp=1.0, as_float=True)]
+    kw = dict(patch=8, stride=4, levels=2, iters=30)
+    w = torch.linspace(0, 1, 96, device="cuda")[None, :].expand(64, 96)
+    m = bd.BDIS(**kw)
+    xs = [(leaf(p.left), leaf(p.right)) for p in prs]
+    outs = [bd.disparity(m, L, R) for L, R in xs]       # two forwards, one model
+    (torch.nan_to_num(outs[0][0], nan=0.0) * w).sum().backward()
+    (torch.nan_to_num(outs[1][0], nan=0.0) * w).sum().backward()
+    for (L, R), p in zip(xs, prs):
+        m1 = bd.BDIS(**kw)
+        L1, R1 = leaf(p.left), leaf(p.right)
+        d1, _ = bd.disparity(m1, L1, R1)
+        (torch.nan_to_num(d1, nan=0.0) * w).sum().backward()
+        torch.cuda.synchronize()
+        for a, b in ((L.grad, L1.grad), (R.grad, R1.grad)):
+            assert b.abs().sum() > 0
+            assert (a - b).abs().max().item() <= 1e-5 * b.abs().max().item()
+        m1.close()
+    m.close()
+
+
+def test_saved_states_through_the_c_abi(bd):
+    """bdis_match_batched_f32_saved keeps each forward in its own bdis_saved;
+    bdis_loss / bdis_backward differentiate the one they are given (NULL:
+    the handle's last call); a state of another handle is rejected."""
+    import ctypes as C
+    import torch
+    lib = bd.B.lib()
+    prs = [synth.g1_pair(96, 64, 11 + i, d0=1.0, d1=3.0, amp=1.0, as_float=True) for i in range(2)]
+    ims = [(torch.from_numpy(p.left.astype(np.float32)).cuda(),
+            torch.from_numpy(p.right.astype(np.float32)).cuda()) for p in prs]
+    kw = dict(patch=8, stride=4, levels=2, iters=30)
+    m = bd.BDIS(**kw)
+    s1, s2 = m.saved_state(), m.saved_state()
+    m.match_f32([ims[0][0]], [ims[0][1]], saved=s1)
+    m.match_f32([ims[1][0]], [ims[1][1]], saved=s2)
+    m.match_f32([ims[1][0]], [ims[0][1]])                  # a third forward, into the handle
+    g1, = m.loss_and_grad(0.1, saved=s1)
+    g2, = m.loss_and_grad(0.1, saved=s2)
+    g3, = m.loss_and_grad(0.1)
+    torch.cuda.synchronize()
+    for g, (L, R) in zip((g1, g2, g3), (ims[0], ims[1], (ims[1][0], ims[0][1]))):
+        ref = bd.BDIS(**kw)
+        ref.match_f32([L], [R])
+        gr, = ref.loss_and_grad(0.1)
+        torch.cuda.synchronize()
+        assert torch.equal(g["loss"], gr["loss"]) and torch.equal(g["g_disp"], gr["g_disp"])
+        # sums reduced across blocks (the sigma_r chain) and float atomics
+        # (image gradients): the last bits may differ from run to run
+        for k in ("g_patch_disp", "g_left", "g_right"):
+            assert (g[k] - gr[k]).abs().max() <= 1e-6 * gr[k].abs().max(), k
+        ref.close()
+    other = bd.BDIS(**kw)
+    arr = bd._grad_table(m, [g1])
+    rc = lib.bdis_backward(other._h, s1.handle, arr, None)
+    assert rc == bd.B.BDIS_EINVAL
+    empty = m.saved_state()
+    assert lib.bdis_backward(m._h, empty.handle, arr, None) == bd.B.BDIS_EINVAL
+    for sv in (s1, s2, empty):
+        sv.destroy()
+    other.close()
+    m.close()
+
+
 # ---------------------------------------------------------------- through every level
 
 def _gpu_ml(bd, kw, L32, R32, lam=0.1):

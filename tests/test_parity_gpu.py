@@ -260,6 +260,101 @@ def test_persistent_form_equals_launch_sequence(bd, kw, size):
         assert torch.equal(torch.nan_to_num(v1, nan=-1.0), torch.nan_to_num(v2, nan=-1.0))
 
 
+def test_persistent_form_after_batched_calls_on_one_handle(bd):
+    """The persistent form's barrier words sit at a fixed place in the arena
+    and are cleared before every cooperative launch, so plain and batched
+    calls of any pair count can alternate on one handle."""
+    import torch
+    kw = dict(patch=8, stride=4, levels=3, iters=8)
+    pairs = [synth.g1_pair(160 + 32 * i, 120, 40 + i) for i in range(4)]
+    Ls = [torch.from_numpy(p.left).cuda() for p in pairs]
+    Rs = [torch.from_numpy(p.right).cuda() for p in pairs]
+    ref = bd.BDIS(**kw)
+    ref.set_option(bd.B.OPT_FORM, 1)
+    want = [ref.match(Ls[i], Rs[i]) for i in range(2)]
+    torch.cuda.synchronize()
+    m = bd.BDIS(**kw)
+    m.set_option(bd.B.OPT_FORM, 2)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        got0 = m.match(Ls[0], Rs[0], stream=stream)          # one pair
+        m.match_batched(Ls, Rs, stream=stream)                # four pairs
+        got1 = m.match(Ls[1], Rs[1], stream=stream)          # one pair again
+    torch.cuda.synchronize()
+    st = m.stats(stream)
+    assert st["persistent"] == 1 and st["barrier_timeouts"] == 0
+    m.set_option(bd.B.OPT_FORM, 1)
+    with torch.cuda.stream(stream):
+        m.match_batched(Ls, Rs, stream=stream)                # launch form, n = 4
+        m.set_option(bd.B.OPT_FORM, 2)
+        got0b = m.match(Ls[0], Rs[0], stream=stream)
+    torch.cuda.synchronize()
+    assert m.stats(stream)["barrier_timeouts"] == 0
+    for (d, v, ok), (dw, vw, okw) in zip((got0, got1, got0b), (want[0], want[1], want[0])):
+        assert torch.equal(ok, okw)
+        assert torch.equal(torch.nan_to_num(d, nan=-1.0), torch.nan_to_num(dw, nan=-1.0))
+    m.close()
+    ref.close()
+
+
+def test_persistent_barrier_timeout_is_reported(bd):
+    """Every grid-barrier wait of the persistent form is bounded.  A wait that
+    runs out (forced here: with the test switch no arrival completes a
+    barrier) lets the kernel finish, and the call is reported as failed by
+    bdis_wait, by bdis_get_stats and by the next call on the handle; the
+    context and the handle stay usable."""
+    import ctypes as C
+    import torch
+    lib = bd.B.lib()
+    kw = dict(patch=8, stride=4, levels=2, iters=8)
+    pair = synth.g1_pair(160, 120, 5)
+    L = torch.from_numpy(pair.left).cuda()
+    R = torch.from_numpy(pair.right).cuda()
+    ref = bd.BDIS(**kw)
+    ref.set_option(bd.B.OPT_FORM, 1)
+    dw, _, okw = ref.match(L, R)
+    m = bd.BDIS(**kw)
+    m.set_option(bd.B.OPT_FORM, 2)
+    m.set_option(bd.B.OPT_BARRIER_LIMIT, 1024)
+    stream = torch.cuda.Stream()
+    sh = C.c_void_p(stream.cuda_stream)
+
+    def call():
+        d = torch.empty((120, 160), device="cuda")
+        ok = torch.empty((120, 160), dtype=torch.uint8, device="cuda")
+        rc = lib.bdis_match(m._h, L.data_ptr(), R.data_ptr(), 160, 120, 160, d.data_ptr(), None,
+                            ok.data_ptr(), sh)
+        return rc, d, ok
+
+    m.set_option(bd.B.OPT_BARRIER_TEST, 1)
+    rc, _, _ = call()
+    assert rc == bd.B.BDIS_OK                       # asynchronous: not known yet
+    assert lib.bdis_wait(m._h, sh) == bd.B.BDIS_ECUDA
+    assert b"grid-barrier" in lib.bdis_last_error(m._h)
+    assert lib.bdis_wait(m._h, sh) == bd.B.BDIS_OK  # reported once
+    s = bd.B.bdis_stats()
+    assert lib.bdis_get_stats(m._h, C.byref(s), sh) == bd.B.BDIS_OK
+    assert s.persistent == 1 and s.barrier_timeouts == 1
+    # the next call reports a timed-out call that nobody waited for
+    rc, _, _ = call()
+    assert rc == bd.B.BDIS_OK
+    stream.synchronize()
+    m.set_option(bd.B.OPT_BARRIER_TEST, 0)
+    rc, _, _ = call()
+    assert rc == bd.B.BDIS_ECUDA
+    # and then the handle works normally again
+    rc, d, ok = call()
+    assert rc == bd.B.BDIS_OK
+    assert lib.bdis_wait(m._h, sh) == bd.B.BDIS_OK
+    assert lib.bdis_get_stats(m._h, C.byref(s), sh) == bd.B.BDIS_OK
+    assert s.barrier_timeouts == 0
+    torch.cuda.synchronize()
+    assert torch.equal(ok, okw)
+    assert torch.equal(torch.nan_to_num(d, nan=-1.0), torch.nan_to_num(dw, nan=-1.0))
+    m.close()
+    ref.close()
+
+
 # ---------------------------------------------------------------- optional modes
 
 MODE_CASES = {

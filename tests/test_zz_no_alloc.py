@@ -17,12 +17,17 @@ from parity import D_FRAC, D_TOL, V_RTOL
 pytestmark = pytest.mark.gpu
 
 
-def _noalloc(bd, params, left, right):
+def _outputs(h, w):
+    import torch
+    return (torch.full((h, w), -7.0, dtype=torch.float32, device="cuda"),
+            torch.full((h, w), -7.0, dtype=torch.float32, device="cuda"),
+            torch.full((h, w), 9, dtype=torch.uint8, device="cuda"))
+
+
+def _noalloc(bd, params, left, right, out=None):
     import torch
     h, w = left.shape
-    d = torch.full((h, w), -7.0, dtype=torch.float32, device="cuda")
-    v = torch.full((h, w), -7.0, dtype=torch.float32, device="cuda")
-    ok = torch.full((h, w), 9, dtype=torch.uint8, device="cuda")
+    d, v, ok = out if out is not None else _outputs(h, w)
     st = bd.B.lib().bdis_match_noalloc(C.byref(params), left.data_ptr(), right.data_ptr(), w, h,
                                        left.stride(0), d.data_ptr(),
                                        v.data_ptr() if params.variance else None, ok.data_ptr(),
@@ -56,6 +61,9 @@ def test_noalloc_matches_bdis_match_on_two_calls():
          dict(patch=12, stride=6, levels=4, iters=8, variance=1)),
         (synth.config_pair("plain_320x240"),
          dict(patch=8, stride=4, levels=3, iters=8, variance=0, storage="f16")),
+        # the largest pair the static scratch is stated to hold
+        (synth.g1_pair(1280, 720, 21),
+         dict(patch=8, stride=4, levels=3, iters=8, variance=0, storage="f32")),
     ]
     for pair, kw in cases:
         L = torch.from_numpy(pair.left).cuda()
@@ -63,9 +71,19 @@ def test_noalloc_matches_bdis_match_on_two_calls():
         m = bd.BDIS(**kw)
         ref = m.match(L, R)
         torch.cuda.synchronize()
-        st, d, v, ok = _noalloc(bd, m.params, L, R)
-        assert st == bd.B.BDIS_OK
-        _compare(ref, (d, v if kw["variance"] else None, ok), kw["variance"])
+        h, w = pair.left.shape
+        outs = [_outputs(h, w), _outputs(h, w)]
+        for k in range(2):   # two calls in a row on the shared static scratch
+            torch.cuda.synchronize()
+            free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+            st, d, v, ok = _noalloc(bd, m.params, L, R, outs[k])
+            free1, reserved1 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+            assert st == bd.B.BDIS_OK
+            _compare(ref, (d, v if kw["variance"] else None, ok), kw["variance"])
+            if k == 1:
+                # the call allocates no device memory (the first call of a
+                # configuration may still load kernel code)
+                assert free1 == free0 and reserved1 == reserved0, (free0 - free1)
         m.close()
 
 
