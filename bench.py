@@ -572,7 +572,10 @@ def main():
         k["ms_per_step"] = round(k["ms_per_step"], 5)
         k["avg_launch_us"] = round(k["avg_launch_us"], 3)
     st = m.stats(stream)
-    form = "persistent" if st["persistent"] else "launch sequence (CUDA graph, programmatic dependent launch)"
+    form = {1: "persistent (every stage in one cooperative launch)",
+            2: "coarse levels in one cooperative launch, finer levels as a launch sequence "
+               "(CUDA graph, programmatic dependent launch)"}.get(
+        st["persistent"], "launch sequence (CUDA graph, programmatic dependent launch)")
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
     peaks = measured_peaks()
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0

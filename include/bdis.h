@@ -119,7 +119,8 @@ typedef struct {
     int valid_patches[8];    /* patches kept per level (all pairs)           */
     float sigma_r[8];        /* sigma_r per level of the first pair           */
     long long valid_pixels;  /* valid output pixels (all pairs)              */
-    int persistent;          /* 1 if the call ran in the persistent form      */
+    int persistent;          /* 1 if the call ran in the persistent form, 2 if
+                                its coarse levels ran in one cooperative launch */
     int barrier_timeouts;    /* persistent form: a grid-barrier wait ran out  */
 } bdis_stats;
 
@@ -256,7 +257,8 @@ typedef struct {
     float *g_left;        /* dloss/dI_l                                            */
     float *g_right;       /* dloss/dI_r                                            */
     float *g_patch_disp;  /* npx*npy level-0 patches: dloss/dd_k with the images
-                             held fixed (bdis_backward); may be NULL              */
+                             held fixed (bdis_backward), 0 for a rejected
+                             patch; may be NULL                                */
 } bdis_grad;
 
 /* Loss of a float forward -- the one kept in `s`, or with s == NULL the
@@ -297,8 +299,11 @@ typedef enum {
      * captured. */
     BDIS_OPT_AUTOTUNE = 3,
     /* Execution form: 0 (default) as chosen by the autotuner, 1 one launch per
-     * stage, 2 persistent (every stage in one cooperative launch with grid
-     * barriers; 8-bit inputs, patch sizes 6, 8, 10, 12, 16).  Same results.
+     * stage (the BDIS_OPT_COARSE_LEVELS coarsest levels excepted), 2
+     * persistent (every stage in one cooperative launch with grid barriers;
+     * 8-bit inputs, patch sizes 6, 8, 10, 12, 16).  The autotuner times the
+     * launch sequence, each number of coarse levels in one cooperative
+     * launch and the persistent form.  Same results in every form.
      * Every grid-barrier wait of the persistent form is bounded
      * (BDIS_OPT_BARRIER_LIMIT); a wait that runs out lets the kernel finish
      * with outputs that are not valid and is reported as BDIS_ECUDA by the
@@ -338,7 +343,15 @@ typedef enum {
      * a grid barrier, so every wait runs out after BDIS_OPT_BARRIER_LIMIT
      * polls and the call is reported as failed (see BDIS_OPT_FORM).  0 (default):
      * normal barriers.  Only for tests of the error reporting. */
-    BDIS_OPT_BARRIER_TEST = 10
+    BDIS_OPT_BARRIER_TEST = 10,
+    /* With BDIS_OPT_FORM 1: the number k of coarsest searched levels whose
+     * stages (their pyramid steps, searches and fusions) run as one
+     * cooperative launch with grid barriers between the stages, the finer
+     * levels as separate launches; 0 (default) none, at most
+     * levels - finest_level - 1; patch sizes 6, 8, 10, 12, 16.  The coarse
+     * levels' grids are small, so one launch replaces several short
+     * dependent ones.  Same results. */
+    BDIS_OPT_COARSE_LEVELS = 11
 } bdis_option;
 
 bdis_status bdis_set_option(bdis_handle *h, int option, int value);

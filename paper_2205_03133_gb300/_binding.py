@@ -87,7 +87,7 @@ class bdis_profile(C.Structure):
 OPT_GRAPH, OPT_PROFILE, OPT_AUTOTUNE, OPT_FORM, OPT_PDL, OPT_PYRAMID_STEPS, OPT_ADJOINT_LEVELS = (
     1, 2, 3, 4, 5, 6, 7)
 OPT_HOST_MAPPED = 8
-OPT_BARRIER_LIMIT, OPT_BARRIER_TEST = 9, 10
+OPT_BARRIER_LIMIT, OPT_BARRIER_TEST, OPT_COARSE_LEVELS = 9, 10, 11
 KERNEL_NAMES = ["pyramid", "search", "fuse", "persistent", "upsample"]
 
 

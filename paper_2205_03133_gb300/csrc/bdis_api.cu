@@ -56,13 +56,17 @@ struct bdis_handle {
     size_t garena_cap = 0;
     // autotuner: per-level launch configuration cached per geometry key
     bool autotune = true;
+    // execution form of a call: kFormLaunches, kFormPersistent, or k > 0:
+    // the k coarsest searched levels (with their pyramid steps) in one
+    // cooperative launch, the finer levels as separate launches
     struct Tuned {
         std::vector<LevelCfg> cfg;
-        bool mega;
+        int form;
     };
     std::map<std::string, Tuned> tuned;
-    int *err_flag = nullptr;  // timeout flag of the last persistent launch (device)
-    bool last_persistent = false;
+    int *err_flag = nullptr;  // timeout flag of the last cooperative launch (device)
+    int last_persistent = 0;  // bdis_stats::persistent of the last call
+    int coarse_levels = 0;    // BDIS_OPT_COARSE_LEVELS
     unsigned barrier_limit = kBarrierSpinLimit;  // BDIS_OPT_BARRIER_LIMIT
     bool barrier_unreachable = false;            // BDIS_OPT_BARRIER_TEST
     // sticky timeout word in mapped page-locked host memory: a persistent
@@ -442,13 +446,35 @@ int sm_count() {
 }
 
 const LevelCfg kDefaultCfg{2, 32, 16};
+constexpr int kFormLaunches = 0;
+constexpr int kFormPersistent = -1;
+
+// The mapped page-locked status word that cooperative launches set when a
+// grid-barrier wait runs out (allocated on first use).
+bdis_status ensure_status_word(bdis_handle *h) {
+    if (h->status_host) return BDIS_OK;
+    cudaError_t e = cudaHostAlloc((void **)&h->status_host, sizeof(int),
+                                  cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e == cudaSuccess) {
+        __atomic_store_n(h->status_host, 0, __ATOMIC_SEQ_CST);
+        e = cudaHostGetDevicePointer((void **)&h->status_dev, h->status_host, 0);
+    }
+    if (e != cudaSuccess) {
+        if (h->status_host) cudaFreeHost(h->status_host);
+        h->status_host = h->status_dev = nullptr;
+        cudaGetLastError();
+        return fail(h, BDIS_ENOMEM, "mapped page-locked status word unavailable");
+    }
+    return BDIS_OK;
+}
 const LevelCfg kSearchCands[3] = {{1, 32, 16}, {2, 64, 32}, {4, 32, 16}};
 
 // The whole coarse-to-fine pipeline for n pairs with per-level launch
 // configuration cfg.  graph: replay / capture allowed; prof: bracket each
 // launch with events (kernel id and level recorded in h->ev_marks).
 bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, cudaStream_t st,
-                    const LevelCfg *cfg, bool graph, bool prof, bool mega = false) {
+                    const LevelCfg *cfg, bool graph, bool prof, int mform = kFormLaunches) {
+    const bool mega = mform == kFormPersistent;
     const bdis_params &p = h->p;
     const int NL = p.levels;
     Plan pl;
@@ -536,9 +562,13 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
     std::vector<char> host((size_t)blob, 0);
     std::memcpy(host.data(), pl.descs.data(), dbytes);
     std::memcpy(host.data() + (pl.off_stages - pl.off_desc), stages.data(), sbytes);
-    // graph key: descriptors and stage arguments (launch parameters are baked
-    // into a captured graph)
-    const std::vector<char> key = host;
+    // graph key: descriptors, stage arguments and the execution form with its
+    // barrier settings (launch parameters are baked into a captured graph)
+    std::vector<char> key = host;
+    {
+        const unsigned extra[3] = {(unsigned)mform, h->barrier_limit, h->barrier_unreachable ? 1u : 0u};
+        key.insert(key.end(), (const char *)extra, (const char *)extra + sizeof(extra));
+    }
     const bool same = h->last_upload.size() == host.size() &&
                       std::memcmp(h->last_upload.data(), host.data(), host.size()) == 0;
     if (!same) {
@@ -590,25 +620,14 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
         m.err = (int *)(m.bar + 2);
         m.spin_limit = h->barrier_limit;
         m.unreachable = h->barrier_unreachable ? 1 : 0;
-        if (!h->status_host) {
-            cudaError_t e = cudaHostAlloc((void **)&h->status_host, sizeof(int),
-                                          cudaHostAllocMapped | cudaHostAllocPortable);
-            if (e == cudaSuccess) {
-                __atomic_store_n(h->status_host, 0, __ATOMIC_SEQ_CST);
-                e = cudaHostGetDevicePointer((void **)&h->status_dev, h->status_host, 0);
-            }
-            if (e != cudaSuccess) {
-                if (h->status_host) cudaFreeHost(h->status_host);
-                h->status_host = h->status_dev = nullptr;
-                cudaGetLastError();
-                return fail(h, BDIS_ENOMEM, "mapped page-locked status word unavailable");
-            }
-        }
+        s = ensure_status_word(h);
+        if (s != BDIS_OK) return s;
         m.err_host = h->status_dev;
         // arrival counter, generation and timeout flag start at zero in every launch
         cudaError_t e = cudaMemsetAsync(m.bar, 0, 4 * sizeof(unsigned), st);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
-        e = timed(BDIS_K_PERSISTENT, [&] { return launch_mega(m, p.patch, st_type, grid, msm, st); });
+        e = timed(BDIS_K_PERSISTENT,
+                  [&] { return launch_mega(m, p.patch, st_type, grid, msm, false, st); });
         if (e != cudaSuccess) return cuda_fail(h, e, "persistent launch");
         h->descs = pl.descs;
         h->npairs = n;
@@ -616,9 +635,46 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
         h->in_type = in_type;
         h->d_descs = d_descs;
         h->err_flag = m.err;
-        h->last_persistent = true;
+        h->last_persistent = 1;
         h->repeat_ok = false;
         return BDIS_OK;
+    }
+
+    // Coarse levels in one cooperative launch (mform = k > 0): the pyramid
+    // stages that start at level >= NL - k and the search and fuse stages of
+    // levels >= NL - k, which are consecutive in the stage list.  Their grids
+    // are small, so one launch with grid barriers between the stages replaces
+    // several short dependent launches.
+    size_t cm_first = stages.size(), cm_count = 0;
+    int cm_grid = 0;
+    size_t cm_smem = 0;
+    MegaArgs cm{};
+    if (mform > 0 && mega_supported(p.patch)) {
+        const int lmin = NL - mform;
+        for (size_t k = 0; k < stages.size(); ++k) {
+            const LaunchArgs &a = stages[k];
+            const bool in = a.kind != 3 && a.level >= lmin && lmin > F;
+            if (in && cm_count == 0) cm_first = k;
+            if (in) ++cm_count;
+        }
+        int umax = 0;
+        for (size_t k = cm_first; k < cm_first + cm_count; ++k) umax = std::max(umax, stages[k].total);
+        cm_smem = std::max(kPyr2SmemBytes, std::max(smax, fmax));
+        cm_grid = std::min(mega_grid(p.patch, st_type, cm_smem), std::max(1, umax));
+        if (cm_count < 2 || cm_grid < 1) {
+            cm_first = stages.size();
+            cm_count = 0;
+        } else {
+            s = ensure_status_word(h);
+            if (s != BDIS_OK) return s;
+            cm.stages = (const LaunchArgs *)(h->arena + pl.off_stages) + cm_first;
+            cm.nstages = (int)cm_count;
+            cm.bar = (unsigned *)(h->arena + pl.off_bar);
+            cm.err = (int *)(cm.bar + 2);
+            cm.spin_limit = h->barrier_limit;
+            cm.unreachable = h->barrier_unreachable ? 1 : 0;
+            cm.err_host = h->status_dev;
+        }
     }
 
     auto launch_all = [&]() -> bdis_status {
@@ -626,6 +682,28 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
         for (size_t k = 0; k < stages.size(); ++k) {
             const LaunchArgs &a = stages[k];
             const int itype = stage_itype[k];
+            if (k == cm_first) {
+                e = cudaMemsetAsync(cm.bar, 0, 4 * sizeof(unsigned), st);
+                if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
+                // with programmatic serialisation where the runtime accepts it
+                // on a cooperative launch (remembered per process)
+                static int pdl_ok = -1;
+                const bool try_pdl = h->use_pdl && pdl_ok != 0;
+                e = timed(BDIS_K_PERSISTENT, [&] {
+                    cudaError_t r = launch_mega(cm, p.patch, st_type, cm_grid, cm_smem, try_pdl, st);
+                    if (r != cudaSuccess && try_pdl) {
+                        cudaGetLastError();
+                        r = launch_mega(cm, p.patch, st_type, cm_grid, cm_smem, false, st);
+                        if (r == cudaSuccess) pdl_ok = 0;
+                    } else if (r == cudaSuccess && try_pdl) {
+                        pdl_ok = 1;
+                    }
+                    return r;
+                });
+                if (e != cudaSuccess) return cuda_fail(h, e, "coarse-level cooperative launch");
+                k += cm_count - 1;
+                continue;
+            }
             if (a.kind == 0 || a.kind == 4) {
                 e = timed(BDIS_K_PYRAMID, [&] {
                     return a.kind == 4 ? launch_pyramid2(a, itype, st_type, st)
@@ -679,21 +757,23 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
             s = launch_all();
             cudaGraph_t g = nullptr;
             cudaError_t e2 = cudaStreamEndCapture(st, &g);
-            if (s != BDIS_OK) {
-                if (g) cudaGraphDestroy(g);
-                return s;
+            if (s == BDIS_OK && e2 == cudaSuccess) {
+                e2 = cudaGraphInstantiate(&h->graph_exec, g, 0);
+                if (e2 != cudaSuccess) h->graph_exec = nullptr;
             }
-            if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
-            e2 = cudaGraphInstantiate(&h->graph_exec, g, 0);
-            cudaGraphDestroy(g);
-            if (e2 != cudaSuccess) {
-                h->graph_exec = nullptr;
-                return cuda_fail(h, e2, "cudaGraphInstantiate");
+            if (g) cudaGraphDestroy(g);
+            if (s == BDIS_OK && e2 == cudaSuccess) {
+                h->graph_descs = key;
+                e2 = cudaGraphLaunch(h->graph_exec, st);
+                if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaGraphLaunch");
+                h->repeat_ok = true;
+            } else {
+                // a launch that cannot be captured or instantiated (nothing
+                // has run yet): issue the same launches directly
+                cudaGetLastError();
+                s = launch_all();
+                if (s != BDIS_OK) return s;
             }
-            h->graph_descs = key;
-            e2 = cudaGraphLaunch(h->graph_exec, st);
-            if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaGraphLaunch");
-            h->repeat_ok = true;
         }
     } else {
         s = launch_all();
@@ -704,7 +784,8 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
     h->levels = NL;
     h->in_type = in_type;
     h->d_descs = d_descs;
-    h->last_persistent = false;
+    h->last_persistent = cm_count > 0 ? 2 : 0;
+    if (cm_count > 0) h->err_flag = cm.err;
     return BDIS_OK;
 }
 
@@ -770,18 +851,18 @@ bdis_status autotune(bdis_handle *h, int n, const bdis_pair *pairs, int in_type,
 
 // Mean device time of `reps` back-to-back calls of one form (events).
 bdis_status time_form(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, cudaStream_t st,
-                      const LevelCfg *cfg, bool mega, int reps, float &ms) {
+                      const LevelCfg *cfg, int mform, int reps, float &ms) {
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(h, cudaGetLastError(), "cudaEventCreate");
     if (cudaEventCreate(&e1) != cudaSuccess) {
         cudaEventDestroy(e0);
         return cuda_fail(h, cudaGetLastError(), "cudaEventCreate");
     }
-    bdis_status s = run_cfg(h, n, pairs, in_type, st, cfg, true, false, mega);  // warm / capture
+    bdis_status s = run_cfg(h, n, pairs, in_type, st, cfg, true, false, mform);  // warm / capture
     if (s == BDIS_OK) {
         cudaEventRecord(e0, st);
         for (int r = 0; r < reps && s == BDIS_OK; ++r)
-            s = run_cfg(h, n, pairs, in_type, st, cfg, true, false, mega);
+            s = run_cfg(h, n, pairs, in_type, st, cfg, true, false, mform);
         cudaEventRecord(e1, st);
         cudaError_t e = cudaEventSynchronize(e1);
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
@@ -799,7 +880,8 @@ bdis_status run_tuned(bdis_handle *h, int n, const bdis_pair *pairs, int in_type
 
 int option_bits(const bdis_handle *h) {
     return (h->use_graph ? 1 : 0) | (h->profile ? 2 : 0) | (h->use_pdl ? 4 : 0) | (h->autotune ? 8 : 0) |
-           (h->form << 4) | (h->pyr_steps << 6);
+           (h->form << 4) | (h->pyr_steps << 6) | (h->coarse_levels << 8) |
+           (h->barrier_unreachable ? 1 << 12 : 0);
 }
 
 // A persistent launch whose grid-barrier wait ran out has stored 1 in the
@@ -867,26 +949,42 @@ bdis_status run_tuned(bdis_handle *h, int n, const bdis_pair *pairs, int in_type
         if (h->autotune && !capturing) {
             bdis_status s = autotune(h, n, pairs, in_type, st, t.cfg);
             if (s != BDIS_OK) return s;
-            // one persistent launch against the launch sequence, for 8-bit inputs
-            t.mega = false;
-            if (in_type == E_U8 && mega_supported(h->p.patch) && st != nullptr) {
-                float tm = 0.f, tp = 0.f;
-                s = time_form(h, n, pairs, in_type, st, t.cfg.data(), false, 5, tm);
+            // the execution forms against each other: the launch sequence, the
+            // k coarsest levels in one cooperative launch (k = 1 .. while a
+            // finer searched level remains), and, for 8-bit inputs, every
+            // stage in one persistent launch
+            t.form = kFormLaunches;
+            if (mega_supported(h->p.patch) && st != nullptr) {
+                float best = 0.f;
+                s = time_form(h, n, pairs, in_type, st, t.cfg.data(), kFormLaunches, 5, best);
                 if (s != BDIS_OK) return s;
-                s = time_form(h, n, pairs, in_type, st, t.cfg.data(), true, 5, tp);
-                if (s == BDIS_OK) t.mega = tp < tm;
-                else h->err = "no persistent form";
+                std::vector<int> cands;
+                for (int k = 1; h->p.levels - k > h->p.finest_level; ++k) cands.push_back(k);
+                if (in_type == E_U8) cands.push_back(kFormPersistent);
+                for (int f : cands) {
+                    float tf = 0.f;
+                    s = time_form(h, n, pairs, in_type, st, t.cfg.data(), f, 5, tf);
+                    if (s != BDIS_OK) {  // a form that cannot run here is skipped
+                        cudaGetLastError();
+                        continue;
+                    }
+                    if (tf < best) {
+                        best = tf;
+                        t.form = f;
+                    }
+                }
             }
             h->tuned[key] = t;
         } else {
             t.cfg.assign((size_t)h->p.levels, kDefaultCfg);
-            t.mega = false;
+            t.form = kFormLaunches;
         }
     }
-    bool mega = t.mega;
-    if (h->form == 1) mega = false;
-    if (h->form == 2) mega = in_type == E_U8 && mega_supported(h->p.patch);
-    return run_cfg(h, n, pairs, in_type, st, t.cfg.data(), true, h->profile, mega);
+    int form = t.form;
+    if (h->form == 1) form = h->coarse_levels;
+    if (h->form == 2) form = (in_type == E_U8 && mega_supported(h->p.patch)) ? kFormPersistent
+                                                                              : kFormLaunches;
+    return run_cfg(h, n, pairs, in_type, st, t.cfg.data(), true, h->profile, form);
 }
 
 }  // namespace
@@ -990,6 +1088,12 @@ bdis_status bdis_set_option(bdis_handle *h, int option, int value) {
     }
     if (option == BDIS_OPT_BARRIER_TEST) {
         h->barrier_unreachable = value != 0;
+        return BDIS_OK;
+    }
+    if (option == BDIS_OPT_COARSE_LEVELS) {
+        if (value < 0 || value >= h->p.levels - h->p.finest_level)
+            return fail(h, BDIS_EINVAL, "coarse levels must be in [0, levels - finest_level - 1]");
+        h->coarse_levels = value;
         return BDIS_OK;
     }
     if (option == BDIS_OPT_ADJOINT_LEVELS) {
@@ -1175,7 +1279,7 @@ bdis_status bdis_get_stats(bdis_handle *h, bdis_stats *out, void *stream) {
             }
         }
     }
-    out->persistent = h->last_persistent ? 1 : 0;
+    out->persistent = h->last_persistent;
     if (h->last_persistent && h->err_flag) {
         e = cudaMemcpy(&out->barrier_timeouts, h->err_flag, sizeof(int), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(h, e, "stats copy");

@@ -416,7 +416,8 @@ __device__ __forceinline__ void patch_adjoint_half(const GradDesc &g, const bdis
 #pragma unroll
     for (int i = 0; i < 5; ++i) gdt = fmaf(gE[i], dEdd[i], gdt);
     const float vF = -gdt / Fd;
-    if (active_patch && gl == 0 && g.gPatch) g.gPatch[kk] = gdt;
+    // a rejected patch does not reach the output: its gradient is 0
+    if (k < g.npx * g.npy && gl == 0 && g.gPatch) g.gPatch[kk] = active_patch ? gdt : 0.f;
     const int P2 = P * P;
     float *cLrow = g.cpatch + ((size_t)kk * 2 * P + (row_on ? gl : 0)) * P;
     float *cGrow = cLrow + P2;
@@ -597,7 +598,8 @@ __global__ void __launch_bounds__(256) k_bwd_patch(GradArgs a) {
 #pragma unroll
         for (int i = 0; i < 5; ++i) gdt = fmaf(gE[i], dEdd[i], gdt);
         const float vF = -gdt / Fd;
-        if (active_patch && gl == 0 && g.gPatch) g.gPatch[kk] = gdt;
+        // a rejected patch does not reach the output: its gradient is 0
+        if (k < g.npx * g.npy && gl == 0 && g.gPatch) g.gPatch[kk] = active_patch ? gdt : 0.f;
         // this row's template and gradient-image terms (gathered per pixel
         // by k_bwd_gather); a rejected patch contributes zeros
         float *cLrow = g.cpatch + ((size_t)kk * 2 * P + (row_on ? gl : 0)) * P;

@@ -198,7 +198,10 @@ cudaError_t prepare_fuse(size_t smem_bytes);
 // co-resident blocks (0 if unavailable).
 bool mega_supported(int P);
 int mega_grid(int P, int st_type, size_t smem);
-cudaError_t launch_mega(const MegaArgs &m, int P, int st_type, int grid, size_t smem, cudaStream_t s);
+// pdl: also allow programmatic stream serialisation (the kernel waits in
+// pdl_wait() before touching memory)
+cudaError_t launch_mega(const MegaArgs &m, int P, int st_type, int grid, size_t smem, bool pdl,
+                        cudaStream_t s);
 constexpr size_t kPyrSmemBytes = sizeof(float) * (2 * 36 * 76 + 2 * 36 * 36);
 constexpr size_t kPyr2SmemBytes = sizeof(float) * (2 * 44 * 76 + 2 * 20 * 36 + 2 * 44 * 36);
 // Raise (never lower) the dynamic shared-memory limit of every search instance.

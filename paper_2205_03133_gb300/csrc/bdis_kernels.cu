@@ -1360,6 +1360,7 @@ __device__ void grid_barrier(unsigned *bar, int *err, int *err_host, unsigned li
 template <int P, typename TG>
 __global__ void __launch_bounds__(256) k_mega(MegaArgs m) {
     extern __shared__ __align__(16) float smem[];
+    pdl_wait();
     for (int s = 0; s < m.nstages; ++s) {
         const LaunchArgs &a = m.stages[s];
         const int total = a.total;
@@ -1401,6 +1402,7 @@ __global__ void __launch_bounds__(256) k_mega(MegaArgs m) {
         }
         if (s + 1 < m.nstages) grid_barrier(m.bar, m.err, m.err_host, m.spin_limit, m.unreachable);
     }
+    pdl_release();
 }
 
 const void *mega_kernel(int P, int st_type) {
@@ -1502,7 +1504,8 @@ int mega_grid(int P, int st_type, size_t smem) {
     return nb * num_sms();
 }
 
-cudaError_t launch_mega(const MegaArgs &m, int P, int st_type, int grid, size_t smem, cudaStream_t s) {
+cudaError_t launch_mega(const MegaArgs &m, int P, int st_type, int grid, size_t smem, bool pdl,
+                        cudaStream_t s) {
     const void *f = mega_kernel(P, st_type);
     if (f == nullptr || grid < 1) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
@@ -1510,11 +1513,13 @@ cudaError_t launch_mega(const MegaArgs &m, int P, int st_type, int grid, size_t 
     cfg.blockDim = dim3(256);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 2 : 1;
     void *args[] = {(void *)&m};
     return cudaLaunchKernelExC(&cfg, f, args);
 }

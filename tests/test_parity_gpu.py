@@ -297,6 +297,66 @@ def test_persistent_form_after_batched_calls_on_one_handle(bd):
     ref.close()
 
 
+@pytest.mark.parametrize("kw,size", [
+    (dict(patch=12, stride=6, levels=4, iters=8, variance=1), (640, 480)),
+    (dict(patch=8, stride=4, levels=3, iters=8, storage="f16"), (320, 240)),
+    (dict(patch=10, stride=4, levels=6, iters=12, finest_level=1, variance=1), (640, 480)),
+])
+def test_coarse_levels_in_one_launch_equal_launch_sequence(bd, kw, size):
+    """The k coarsest levels in one cooperative launch (grid barriers between
+    their stages) give bitwise the outputs, records and images of one launch
+    per stage, for every k, on graph replay too."""
+    import torch
+    w, h = size
+    pair = synth.g2_pair(w, h, 13) if kw.get("variance") else synth.g1_pair(w, h, 13)
+    L = torch.from_numpy(pair.left).cuda()
+    R = torch.from_numpy(pair.right).cuda()
+    nl = kw["levels"] - kw.get("finest_level", 0)
+    ref = None
+    for k in range(nl):
+        m = bd.BDIS(**kw)
+        m.set_option(bd.B.OPT_FORM, 1)
+        m.set_option(bd.B.OPT_COARSE_LEVELS, k)
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            for _ in range(3):   # capture, then replays
+                d, v, ok = m.match(L, R, stream=stream)
+        torch.cuda.synchronize()
+        st = m.stats(stream)
+        assert st["persistent"] == (2 if k > 0 else 0) and st["barrier_timeouts"] == 0
+        got = [torch.nan_to_num(d, nan=-1.0), ok] + ([torch.nan_to_num(v, nan=-1.0)] if v is not None else [])
+        recs = [m.level_view(0, l)["patches"] for l in range(kw.get("finest_level", 0), kw["levels"])]
+        if ref is None:
+            ref, ref_recs = got, recs
+        else:
+            for a, b in zip(ref, got):
+                assert torch.equal(a, b), k
+            for a, b in zip(ref_recs, recs):
+                assert a.tobytes() == b.tobytes(), k
+        m.close()
+
+
+def test_coarse_levels_in_one_launch_float_forward(bd):
+    """The float-image (differentiable) forward in the same form, and its
+    gradient, equal those of the launch sequence."""
+    import torch
+    pr = synth.g1_pair(320, 240, 17, d0=1.0, d1=3.0, amp=1.0, as_float=True)
+    L = torch.from_numpy(pr.left.astype(np.float32)).cuda()
+    R = torch.from_numpy(pr.right.astype(np.float32)).cuda()
+    outs = []
+    for k in (0, 2):
+        m = bd.BDIS(patch=8, stride=4, levels=3, iters=8)
+        m.set_option(bd.B.OPT_FORM, 1)
+        m.set_option(bd.B.OPT_COARSE_LEVELS, k)
+        (d, _, ok), = m.match_f32([L], [R])
+        g, = m.loss_and_grad(0.1)
+        torch.cuda.synchronize()
+        outs.append((torch.nan_to_num(d, nan=-1.0), ok, g["loss"], g["g_disp"]))
+        m.close()
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+
+
 def test_persistent_barrier_timeout_is_reported(bd):
     """Every grid-barrier wait of the persistent form is bounded.  A wait that
     runs out (forced here: with the test switch no arrival completes a
