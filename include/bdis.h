@@ -351,7 +351,15 @@ typedef enum {
      * levels - finest_level - 1; patch sizes 6, 8, 10, 12, 16.  The coarse
      * levels' grids are small, so one launch replaces several short
      * dependent ones.  Same results. */
-    BDIS_OPT_COARSE_LEVELS = 11
+    BDIS_OPT_COARSE_LEVELS = 11,
+    /* 1 (default): the one-step pyramid launches (calls of more than 2^21
+     * level-0 pixels, or BDIS_OPT_PYRAMID_STEPS 1) stage each interior tile
+     * by bulk asynchronous copies (cp.async.bulk, one per row, completing on
+     * an mbarrier), the next tile's copies in flight while the current one is
+     * computed; 0: the block's own loads.  Same results.  The wait for a
+     * tile's copies is bounded; one that runs out is reported like a
+     * grid-barrier timeout (BDIS_OPT_FORM). */
+    BDIS_OPT_BULK_COPY = 12
 } bdis_option;
 
 bdis_status bdis_set_option(bdis_handle *h, int option, int value);
@@ -418,12 +426,23 @@ bdis_status bdis_level_view_get(const bdis_handle *h, int pair, int level,
 /* Elementwise on n pixels of device buffers, asynchronous on `stream`:
  *   depth = fb / disp,   depth_var = fb^2 / disp^4 * var,
  * fb = focal length (px) x baseline (any length unit; depth comes out in
- * that unit).  A pixel whose disp is NaN or <= 0 gets NaN in both.  `var`
+ * that unit).  A pixel whose disp is not a positive finite number (NaN,
+ * <= 0 or infinite) gets NaN in both.  `var`
  * and `depth_var` may be NULL (then no variance is written); n == 0 is a
  * no-op.  BDIS_EINVAL for a null disp / depth with n > 0, n < 0, or a
  * non-finite or non-positive fb. */
 bdis_status bdis_depth(const float *disp, const float *var, long long n, float fb, float *depth,
                        float *depth_var, void *stream);
+
+/* ---- measurement ----
+ * L2 read-bandwidth probe (the paper has no counterpart: it gives the
+ * denominator of the L2 roofline fractions the benchmark reports).  Reads
+ * the device buffer `buf` (16-byte aligned, `bytes` >= 16; make it small
+ * enough to stay in L2, e.g. 48 MiB of the 129 MB) `reps` times in one
+ * launch with 16-byte loads that bypass L1, writing nothing; asynchronous on
+ * `stream` (time it with events: bytes x reps / elapsed).  BDIS_EINVAL for a
+ * null or unaligned buffer, bytes < 16 or reps < 1. */
+bdis_status bdis_probe_l2_read(const void *buf, size_t bytes, int reps, void *stream);
 
 /* cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, stream) + sync. */
 bdis_status bdis_copy(void *dst, const void *src, size_t bytes, void *stream);

@@ -87,7 +87,7 @@ class bdis_profile(C.Structure):
 OPT_GRAPH, OPT_PROFILE, OPT_AUTOTUNE, OPT_FORM, OPT_PDL, OPT_PYRAMID_STEPS, OPT_ADJOINT_LEVELS = (
     1, 2, 3, 4, 5, 6, 7)
 OPT_HOST_MAPPED = 8
-OPT_BARRIER_LIMIT, OPT_BARRIER_TEST, OPT_COARSE_LEVELS = 9, 10, 11
+OPT_BARRIER_LIMIT, OPT_BARRIER_TEST, OPT_COARSE_LEVELS, OPT_BULK_COPY = 9, 10, 11, 12
 KERNEL_NAMES = ["pyramid", "search", "fuse", "persistent", "upsample"]
 
 
@@ -120,6 +120,7 @@ EXPORTS = [
     ("bdis_match_noalloc", C.c_int, [C.POINTER(bdis_params), _vp, _vp, C.c_int, C.c_int, C.c_int,
                                      _vp, _vp, _vp, _vp]),
     ("bdis_depth", C.c_int, [_vp, _vp, C.c_longlong, C.c_float, _vp, _vp, _vp]),
+    ("bdis_probe_l2_read", C.c_int, [_vp, C.c_size_t, C.c_int, _vp]),
 ]
 
 _lib = None

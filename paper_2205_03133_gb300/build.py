@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUTDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUTDIR, "libbdis.so")
-SOURCES = ["bdis_api.cu", "bdis_kernels.cu", "bdis_noalloc.cu", "bdis_grad.cu"]
+SOURCES = ["bdis_api.cu", "bdis_kernels.cu", "bdis_noalloc.cu", "bdis_grad.cu", "bdis_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -67,6 +67,7 @@ struct bdis_handle {
     int *err_flag = nullptr;  // timeout flag of the last cooperative launch (device)
     int last_persistent = 0;  // bdis_stats::persistent of the last call
     int coarse_levels = 0;    // BDIS_OPT_COARSE_LEVELS
+    bool bulk_copy = true;    // BDIS_OPT_BULK_COPY
     unsigned barrier_limit = kBarrierSpinLimit;  // BDIS_OPT_BARRIER_LIMIT
     bool barrier_unreachable = false;            // BDIS_OPT_BARRIER_TEST
     // sticky timeout word in mapped page-locked host memory: a persistent
@@ -554,7 +555,13 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
         stages.push_back(a);
         stage_itype.push_back(in_type);
     }
-    for (auto &a : stages) a.pdl = h->use_pdl ? 1 : 0;
+    s = ensure_status_word(h);
+    if (s != BDIS_OK) return s;
+    for (auto &a : stages) {
+        a.pdl = h->use_pdl ? 1 : 0;
+        a.bulk = h->bulk_copy ? 1 : 0;
+        a.err_host = h->status_dev;
+    }
     // upload descriptors (and the stage list) unless identical to the last upload
     const size_t dbytes = sizeof(LevelDesc) * pl.descs.size();
     const size_t sbytes = sizeof(LaunchArgs) * stages.size();
@@ -881,7 +888,7 @@ bdis_status run_tuned(bdis_handle *h, int n, const bdis_pair *pairs, int in_type
 int option_bits(const bdis_handle *h) {
     return (h->use_graph ? 1 : 0) | (h->profile ? 2 : 0) | (h->use_pdl ? 4 : 0) | (h->autotune ? 8 : 0) |
            (h->form << 4) | (h->pyr_steps << 6) | (h->coarse_levels << 8) |
-           (h->barrier_unreachable ? 1 << 12 : 0);
+           (h->barrier_unreachable ? 1 << 12 : 0) | (h->bulk_copy ? 1 << 13 : 0);
 }
 
 // A persistent launch whose grid-barrier wait ran out has stored 1 in the
@@ -892,8 +899,9 @@ bdis_status take_status(bdis_handle *h) {
     if (!h->status_host) return BDIS_OK;
     if (__atomic_exchange_n(h->status_host, 0, __ATOMIC_SEQ_CST) != 0)
         return fail(h, BDIS_ECUDA,
-                    "a grid-barrier wait of an earlier persistent-form call ran out: that call's "
-                    "outputs are not valid");
+                    "a bounded device wait (a grid-barrier wait of a cooperative launch, or the "
+                    "wait for a bulk copy) ran out in an earlier call: that call's outputs are "
+                    "not valid");
     return BDIS_OK;
 }
 
@@ -1088,6 +1096,10 @@ bdis_status bdis_set_option(bdis_handle *h, int option, int value) {
     }
     if (option == BDIS_OPT_BARRIER_TEST) {
         h->barrier_unreachable = value != 0;
+        return BDIS_OK;
+    }
+    if (option == BDIS_OPT_BULK_COPY) {
+        h->bulk_copy = value != 0;
         return BDIS_OK;
     }
     if (option == BDIS_OPT_COARSE_LEVELS) {

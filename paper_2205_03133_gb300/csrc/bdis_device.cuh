@@ -61,6 +61,61 @@ __device__ __forceinline__ void pdl_release() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// ---- bulk asynchronous copies from global to shared memory
+// cp.async.bulk moves a contiguous run of bytes (16-byte aligned at both
+// ends, a multiple of 16 long) through the async proxy and reports its bytes
+// to an mbarrier (complete_tx); a phase of the barrier completes when its
+// one expected arrival (arrive.expect_tx, which also announces the bytes)
+// has happened and all announced bytes have landed.
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// makes the initialised barriers visible to the async proxy (before any copy)
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// true once the phase with the given parity has completed (non-blocking)
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0u;
+}
+// generic-proxy accesses of shared memory ordered before later async-proxy ones
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes,
+                                              uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+// Waits for a phase of `bar` with at most `limit` polls; false if it ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, unsigned limit) {
+    for (unsigned it = 0; !mbar_test(bar, parity); ++it) {
+        if (it >= limit) return false;
+        __nanosleep(32);
+    }
+    return true;
+}
+
 // reflect about the edge pixel without repeating it (-1 -> 1, n -> n-2); n >= 3
 __device__ __forceinline__ int refl(int i, int n) {
     i = i < 0 ? -i : i;

@@ -104,6 +104,8 @@ struct LaunchArgs {
     int fast_exp;             // Schraudolph exponential in the posterior
     int img_type;             // ElemType of this level's L, R (read by the DIS fusion)
     int pdl;                  // launch with programmatic stream serialisation
+    int bulk;                 // one-step pyramid: interior tiles staged by bulk async copies
+    int *err_host;            // mapped status word of the handle (a device wait ran out), or nullptr
 };
 
 // Persistent form: every stage of a call in one cooperative launch, with a

@@ -54,16 +54,13 @@ constexpr int kPyrSP = kPyrSW + 4, kPyrHP = kPyrTW / 2 + 4;
 static_assert(kPyrSmemBytes == sizeof(float) * (2 * kPyrSH * kPyrSP + 2 * kPyrSH * kPyrHP),
               "one-step pyramid shared memory");
 
-template <typename TI, typename TO>
-__device__ __forceinline__ void pyramid_unit(const LaunchArgs &a, int unit, float (*Ls)[kPyrSP],
-                                             float (*Rs)[kPyrSP], float (*Lh)[kPyrHP],
-                                             float (*Rh)[kPyrHP]) {
-    static_assert(kPyrTW * kPyrTH == 8 * 256 && (kPyrTW / 2) * (kPyrTH / 2) == 2 * 256,
-                  "one Sobel segment and one blurred pair per thread");
-    const LevelDesc &D = a.descs[find_pair(a.descs, a.npairs, unit, W_PYR)];
-    const int tile = unit - D.work_begin[W_PYR];
-    const int ntx = (D.w + kPyrTW - 1) / kPyrTW;
-    const int tx = tile % ntx, ty = tile / ntx;
+// Staging of a one-step tile's region (72 x 36 pixels from 4 columns and 2
+// rows before the tile) by the block's own loads: four-element vector loads
+// for a region inside the image with rows aligned to four elements, else
+// element loads with reflect-101 indices.
+template <typename TI>
+__device__ __forceinline__ void pyramid_stage_loads(const LevelDesc &D, int tx, int ty,
+                                                    float (*Ls)[kPyrSP], float (*Rs)[kPyrSP]) {
     const int xs = tx * kPyrTW - kPyrOX, y0 = ty * kPyrTH - 2;  // region origin
     const int w = D.w, h = D.h, pitch = D.pitch;
     const TI *L = (const TI *)D.L;
@@ -72,7 +69,6 @@ __device__ __forceinline__ void pyramid_unit(const LaunchArgs &a, int unit, floa
     const int tid = threadIdx.x;
     const bool vec_in = xs >= 0 && xs + kPyrSW <= w && y0 >= 0 && y0 + kPyrSH <= h && pitch % 4 == 0 &&
                         ((uintptr_t)L | (next ? (uintptr_t)R : (uintptr_t)0)) % (4 * sizeof(TI)) == 0;
-    __syncthreads();
     // all of a thread's loads are issued before its stores (memory-level parallelism);
     // every launch of the pyramid stage uses 256 threads
     if (vec_in) {
@@ -129,7 +125,17 @@ __device__ __forceinline__ void pyramid_unit(const LaunchArgs &a, int unit, floa
             }
         }
     }
-    __syncthreads();
+}
+
+// Sobel-x/8 of L over the 64 x 32 tile and the blurred, decimated 32 x 16
+// tile of the next level of L and R, from the staged region.
+template <typename TO>
+__device__ __forceinline__ void pyramid_compute(const LevelDesc &D, int tx, int ty,
+                                                float (*Ls)[kPyrSP], float (*Rs)[kPyrSP],
+                                                float (*Lh)[kPyrHP], float (*Rh)[kPyrHP]) {
+    const int w = D.w, h = D.h;
+    const bool next = D.Ln != nullptr;
+    const int tid = threadIdx.x;
     TO *G = (TO *)D.G;  // nullptr below the finest processed level
     if (G != nullptr) {
         // pixels lx0 .. lx0 + 7 of row ly: staged columns lx0 + 3 .. lx0 + 12
@@ -231,7 +237,23 @@ __device__ __forceinline__ void pyramid_unit(const LaunchArgs &a, int unit, floa
             }
         }
     }
-    }
+}
+
+template <typename TI, typename TO>
+__device__ __forceinline__ void pyramid_unit(const LaunchArgs &a, int unit, float (*Ls)[kPyrSP],
+                                             float (*Rs)[kPyrSP], float (*Lh)[kPyrHP],
+                                             float (*Rh)[kPyrHP]) {
+    static_assert(kPyrTW * kPyrTH == 8 * 256 && (kPyrTW / 2) * (kPyrTH / 2) == 2 * 256,
+                  "one Sobel segment and one blurred pair per thread");
+    const LevelDesc &D = a.descs[find_pair(a.descs, a.npairs, unit, W_PYR)];
+    const int tile = unit - D.work_begin[W_PYR];
+    const int ntx = (D.w + kPyrTW - 1) / kPyrTW;
+    const int tx = tile % ntx, ty = tile / ntx;
+    __syncthreads();  // the previous unit's readers are done with the staged region
+    pyramid_stage_loads<TI>(D, tx, ty, Ls, Rs);
+    __syncthreads();
+    pyramid_compute<TO>(D, tx, ty, Ls, Rs, Lh, Rh);
+}
 
 // Two pyramid steps in one unit: a 64x32 tile of level l gives its Sobel-x,
 // the 32x16 tile of level l+1 with its Sobel-x, and the 16x8 tile of level
@@ -406,6 +428,157 @@ __global__ void __launch_bounds__(256, 4) k_pyramid(LaunchArgs a) {
         for (int i = threadIdx.x; i < a.acc_count; i += blockDim.x) a.acc_zero[i] = 0ull;
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x)
         pyramid_unit<TI, TO>(a, unit, Ls, Rs, Lh, Rh);
+    pdl_release();
+}
+
+// One-step pyramid with the staging of interior tiles by bulk asynchronous
+// copies.  Each row of a tile's region is one cp.async.bulk of the storage
+// type's raw bytes, from the region's first column rounded down to a 16-byte
+// boundary (RAW_OFF elements before it) over RAW_SPAN_E elements, so both
+// ends are 16-byte aligned; the copies of a tile complete on one mbarrier.
+// A block walks its units with two raw buffers: the copies of the next unit
+// are in flight while the current unit is widened to FP32 and computed.  A
+// unit whose region is not inside the image (or whose rows do not allow the
+// alignment) is staged by the block's own loads (pyramid_stage_loads).  The
+// staged values, and so the results, are those of the one-step kernel.
+template <typename TI>
+struct PyrBulk {
+    static constexpr int E = (int)sizeof(TI);
+    static constexpr int A = 16 / E;                                   // elements per 16 bytes
+    static constexpr int RAW_OFF = (kPyrOX + A - 1) / A * A - kPyrOX;  // region start in the raw row
+    static constexpr int RAW_SPAN_E = (RAW_OFF + kPyrSW + A - 1) / A * A;
+    static constexpr int RAW_SPAN_B = RAW_SPAN_E * E;                  // bytes per copied row
+    static constexpr size_t kSmem = (size_t)2 * 2 * kPyrSH * RAW_SPAN_B;  // 2 buffers x (L, R)
+};
+static_assert(PyrBulk<uint8_t>::RAW_SPAN_B % 16 == 0 && PyrBulk<__half>::RAW_SPAN_B % 16 == 0 &&
+                  PyrBulk<float>::RAW_SPAN_B % 16 == 0 && kPyrTW % 16 == 0,
+              "bulk rows and tile columns on 16-byte boundaries");
+
+// Polls of one wait for a tile's copies (a poll is a barrier test and a 32 ns
+// sleep); past it the kernel records the failure and stops.
+constexpr unsigned kCopyWaitLimit = 1u << 22;
+
+// Four raw elements at p (4-, 8- or 16-byte aligned) as floats.
+__device__ __forceinline__ float4 raw4(const uint8_t *p) {
+    const uchar4 u = *(const uchar4 *)p;
+    return make_float4((float)u.x, (float)u.y, (float)u.z, (float)u.w);
+}
+__device__ __forceinline__ float4 raw4(const __half *p) {
+    const uint2 u = *(const uint2 *)p;
+    const float2 a = __half22float2(*(const __half2 *)&u.x);
+    const float2 b = __half22float2(*(const __half2 *)&u.y);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float4 raw4(const float *p) { return *(const float4 *)p; }
+
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(256, 4) k_pyramid_bulk(LaunchArgs a) {
+    using PB = PyrBulk<TI>;
+    __shared__ __align__(16) float Ls[kPyrSH][kPyrSP];
+    __shared__ __align__(16) float Rs[kPyrSH][kPyrSP];
+    __shared__ __align__(16) float Lh[kPyrSH][kPyrHP];
+    __shared__ __align__(16) float Rh[kPyrSH][kPyrHP];
+    __shared__ __align__(8) uint64_t bar[2];
+    extern __shared__ __align__(16) unsigned char raw[];  // [buffer][image][row][RAW_SPAN_B]
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    pdl_wait();
+    if (blockIdx.x == 0 && a.acc_zero != nullptr)
+        for (int i = tid; i < a.acc_count; i += blockDim.x) a.acc_zero[i] = 0ull;
+
+    struct Tile {
+        const LevelDesc *D;
+        int tx, ty;
+        bool bulk;
+    };
+    auto tile_of = [&](int unit) {
+        Tile t;
+        t.D = &a.descs[find_pair(a.descs, a.npairs, unit, W_PYR)];
+        const LevelDesc &D = *t.D;
+        const int tile = unit - D.work_begin[W_PYR];
+        const int ntx = (D.w + kPyrTW - 1) / kPyrTW;
+        t.tx = tile % ntx;
+        t.ty = tile / ntx;
+        const int xs = t.tx * kPyrTW - kPyrOX, y0 = t.ty * kPyrTH - 2;
+        const int xr = xs - PB::RAW_OFF;
+        const bool next = D.Ln != nullptr;
+        const uintptr_t base = (uintptr_t)D.L | (next ? (uintptr_t)D.R : (uintptr_t)0);
+        // region inside the image, copied span inside the row, 16-byte rows
+        t.bulk = xr >= 0 && xs + kPyrSW <= D.w && xr + PB::RAW_SPAN_E <= D.pitch && y0 >= 0 &&
+                 y0 + kPyrSH <= D.h && (base & 15u) == 0 && ((size_t)D.pitch * PB::E) % 16 == 0;
+        return t;
+    };
+    // the copies of one tile into raw buffer b (block-uniform decision)
+    auto issue = [&](const Tile &t, int b) {
+        const LevelDesc &D = *t.D;
+        const bool next = D.Ln != nullptr;
+        const int nrows = next ? 2 * kPyrSH : kPyrSH;
+        if (tid < nrows) {
+            fence_proxy_async_smem();  // earlier reads of this buffer precede the copy
+            if (tid == 0) mbar_arrive_expect_tx(&bar[b], (unsigned)(nrows * PB::RAW_SPAN_B));
+            const int img = tid / kPyrSH, r = tid - img * kPyrSH;
+            const int xr = t.tx * kPyrTW - kPyrOX - PB::RAW_OFF, y = t.ty * kPyrTH - 2 + r;
+            const TI *src = (const TI *)(img ? D.R : D.L) + (size_t)y * D.pitch + xr;
+            unsigned char *dst = raw + ((size_t)(b * 2 + img) * kPyrSH + r) * PB::RAW_SPAN_B;
+            bulk_copy_g2s(dst, src, (unsigned)PB::RAW_SPAN_B, &bar[b]);
+        }
+    };
+
+    unsigned parity = 0u;  // bit b: parity of raw buffer b's next phase
+    int unit = blockIdx.x;
+    Tile cur;
+    if (unit < a.total) {
+        cur = tile_of(unit);
+        if (cur.bulk) issue(cur, 0);
+    }
+    for (int i = 0; unit < a.total; ++i, unit += gridDim.x) {
+        const int b = i & 1;
+        // the next unit's copies go into the other buffer, whose last reads
+        // (widening, iteration i - 1) finished before that iteration's barrier
+        const int un = unit + gridDim.x;
+        Tile nxt;
+        nxt.bulk = false;
+        if (un < a.total) {
+            nxt = tile_of(un);
+            if (nxt.bulk) issue(nxt, b ^ 1);
+        }
+        __syncthreads();  // the previous unit's readers are done with Ls, Rs
+        if (cur.bulk) {
+            const bool ok = mbar_wait_bounded(&bar[b], (parity >> b) & 1u, kCopyWaitLimit);
+            parity ^= 1u << b;
+            if (__syncthreads_or(!ok)) {
+                // a copy did not land: report it, wait (bounded) for the
+                // copies still in flight and stop
+                if (tid == 0 && a.err_host != nullptr) {
+                    *(volatile int *)a.err_host = 1;
+                    __threadfence_system();
+                }
+                if (nxt.bulk) mbar_wait_bounded(&bar[b ^ 1], (parity >> (b ^ 1)) & 1u, kCopyWaitLimit);
+                return;
+            }
+            // widen the raw rows to FP32 (exact for u8, f16, f32)
+            const LevelDesc &D = *cur.D;
+            const int nimg = D.Ln != nullptr ? 2 : 1;
+            constexpr int QPR = kPyrSW / 4;  // four-element groups per row
+            for (int q = tid; q < nimg * kPyrSH * QPR; q += blockDim.x) {
+                const int img = q / (kPyrSH * QPR), rem = q - img * (kPyrSH * QPR);
+                const int r = rem / QPR, c = 4 * (rem - r * QPR);
+                const TI *src = (const TI *)(raw + ((size_t)(b * 2 + img) * kPyrSH + r) * PB::RAW_SPAN_B) +
+                                PB::RAW_OFF + c;
+                *(float4 *)&(img ? Rs : Ls)[r][c] = raw4(src);
+            }
+        } else {
+            pyramid_stage_loads<TI>(*cur.D, cur.tx, cur.ty, Ls, Rs);
+        }
+        __syncthreads();
+        pyramid_compute<TO>(*cur.D, cur.tx, cur.ty, Ls, Rs, Lh, Rh);
+        cur = nxt;
+    }
     pdl_release();
 }
 
@@ -1272,7 +1445,7 @@ __global__ void __launch_bounds__(256) k_upsample(LaunchArgs a) {
 
 // Depth (Eq. 13) and its variance (the depth factor of Eq. 17), elementwise.
 __device__ __forceinline__ void depth_px(float d, float v, float fb, float &z, float &zv) {
-    const bool ok = d > 0.f;  // false for NaN
+    const bool ok = d > 0.f && d < INFINITY;  // a positive finite disparity (false for NaN)
     const float q = fb / d;
     const float qd = q / d;   // fb / d^2
     z = ok ? q : __int_as_float(0x7fc00000);
@@ -1578,7 +1751,50 @@ cudaError_t launch_args_kernel(const void *f, const LaunchArgs &a, int grid, siz
 }
 }  // namespace
 
+namespace {
+// Resident blocks per SM of a kernel at a dynamic shared-memory size (cached).
+int resident_blocks(const void *f, size_t smem) {
+    static const void *keys[16];
+    static size_t sizes[16];
+    static int vals[16];
+    static int n = 0;
+    for (int i = 0; i < n; ++i)
+        if (keys[i] == f && sizes[i] == smem) return vals[i];
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, 256, smem) != cudaSuccess || nb < 1) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    if (n < 16) {
+        keys[n] = f;
+        sizes[n] = smem;
+        vals[n] = nb;
+        ++n;
+    }
+    return nb;
+}
+
+template <typename TI, typename TO>
+cudaError_t launch_pyramid_bulk(const LaunchArgs &a, cudaStream_t s) {
+    const void *f = (const void *)k_pyramid_bulk<TI, TO>;
+    const size_t smem = PyrBulk<TI>::kSmem;
+    const cudaError_t e = raise_smem_limit(f, smem);
+    if (e != cudaSuccess) return e;
+    // every block resident: each walks its units with the copies of the next
+    // one in flight
+    return launch_args_kernel(f, a, grid_for(a.total, resident_blocks(f, smem)), smem, s);
+}
+}  // namespace
+
 cudaError_t launch_pyramid(const LaunchArgs &a, int in_type, int out_type, cudaStream_t s) {
+    if (a.bulk) {
+        if (out_type == E_F32)
+            return in_type == E_U8 ? launch_pyramid_bulk<uint8_t, float>(a, s)
+                                   : launch_pyramid_bulk<float, float>(a, s);
+        return in_type == E_U8    ? launch_pyramid_bulk<uint8_t, __half>(a, s)
+               : in_type == E_F32 ? launch_pyramid_bulk<float, __half>(a, s)
+                                  : launch_pyramid_bulk<__half, __half>(a, s);
+    }
     const void *f = nullptr;
     if (out_type == E_F32) {
         f = in_type == E_U8 ? (const void *)k_pyramid<uint8_t, float> : (const void *)k_pyramid<float, float>;

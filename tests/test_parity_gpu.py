@@ -495,7 +495,7 @@ def test_depth_of_a_match_against_the_oracle(bd):
     zo, zvo = oracle.depth(dn, vn, 800.0 * 0.0055)
     z, zv = z.cpu().numpy(), zv.cpu().numpy()
     fin = np.isfinite(zo)
-    assert fin.sum() > 0.5 * fin.size
+    assert fin.sum() > 0.25 * fin.size
     assert np.array_equal(fin, np.isfinite(z))
     np.testing.assert_allclose(z[fin], zo[fin], rtol=1e-6)
     np.testing.assert_allclose(zv[fin], zvo[fin], rtol=1e-5, atol=1e-30)
@@ -568,6 +568,43 @@ def test_launch_options_do_not_change_results(bd, kw):
             for a, b in zip(ref_imgs, imgs):
                 assert np.array_equal(a, b), (graph, pdl, steps)
         m.close()
+
+
+@pytest.mark.parametrize("storage", ["f16", "f32"])
+def test_bulk_copy_staging_equals_own_loads(bd, storage):
+    """The one-step pyramid's bulk asynchronous staging of interior tiles
+    gives bitwise the images, gradients and outputs of staging by the block's
+    own loads, on pairs whose tiles are partly ineligible (odd sizes, a row
+    pitch that is not a multiple of 16 bytes)."""
+    import torch
+    sizes = [(640, 480, 640), (333, 217, 333), (1280, 720, 1296), (250, 130, 257)]
+    pairs = [synth.g1_pair(w, h, 50 + i) for i, (w, h, _) in enumerate(sizes)]
+    Ls, Rs = [], []
+    for (w, h, pitch), p in zip(sizes, pairs):
+        for img, lst in ((p.left, Ls), (p.right, Rs)):
+            buf = torch.zeros((h, pitch), dtype=torch.uint8, device="cuda")
+            buf[:, :w] = torch.from_numpy(img).cuda()
+            lst.append(buf[:, :w])
+    kw = dict(patch=8, stride=4, levels=3, iters=8, storage=storage)
+    res = []
+    for bulk in (0, 1):
+        m = bd.BDIS(**kw)
+        m.set_option(bd.B.OPT_FORM, 1)
+        m.set_option(bd.B.OPT_PYRAMID_STEPS, 1)
+        m.set_option(bd.B.OPT_BULK_COPY, bulk)
+        out = m.match_batched(Ls, Rs)
+        torch.cuda.synchronize()
+        views = [m.level_view(i, l) for i in range(len(sizes)) for l in range(3)]
+        res.append((out, views))
+        m.close()
+    (o0, v0), (o1, v1) = res
+    for (d0, _, k0), (d1, _, k1) in zip(o0, o1):
+        assert torch.equal(k0, k1)
+        assert torch.equal(torch.nan_to_num(d0, nan=-1.0), torch.nan_to_num(d1, nan=-1.0))
+    for a, b in zip(v0, v1):
+        for key in ("L", "R", "G"):
+            if a.get(key) is not None:
+                assert np.array_equal(a[key], b[key]), key
 
 
 def _coverage(disp, var, valid, gt, z=1.96):
