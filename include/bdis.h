@@ -352,11 +352,12 @@ typedef enum {
      * levels' grids are small, so one launch replaces several short
      * dependent ones.  Same results. */
     BDIS_OPT_COARSE_LEVELS = 11,
-    /* 1 (default): the one-step pyramid launches (calls of more than 2^21
-     * level-0 pixels, or BDIS_OPT_PYRAMID_STEPS 1) stage each interior tile
-     * by bulk asynchronous copies (cp.async.bulk, one per row, completing on
-     * an mbarrier), the next tile's copies in flight while the current one is
-     * computed; 0: the block's own loads.  Same results.  The wait for a
+    /* 1: the one-step pyramid launches (calls of more than 2^21 level-0
+     * pixels, or BDIS_OPT_PYRAMID_STEPS 1) stage each interior tile by bulk
+     * asynchronous copies (cp.async.bulk, one per row, completing on an
+     * mbarrier), the next tile's copies in flight while the current one is
+     * computed; 0 (default, faster on GB300): the block's own loads.  Same
+     * results.  The wait for a
      * tile's copies is bounded; one that runs out is reported like a
      * grid-barrier timeout (BDIS_OPT_FORM). */
     BDIS_OPT_BULK_COPY = 12

@@ -67,7 +67,7 @@ struct bdis_handle {
     int *err_flag = nullptr;  // timeout flag of the last cooperative launch (device)
     int last_persistent = 0;  // bdis_stats::persistent of the last call
     int coarse_levels = 0;    // BDIS_OPT_COARSE_LEVELS
-    bool bulk_copy = true;    // BDIS_OPT_BULK_COPY
+    bool bulk_copy = false;   // BDIS_OPT_BULK_COPY
     unsigned barrier_limit = kBarrierSpinLimit;  // BDIS_OPT_BARRIER_LIMIT
     bool barrier_unreachable = false;            // BDIS_OPT_BARRIER_TEST
     // sticky timeout word in mapped page-locked host memory: a persistent

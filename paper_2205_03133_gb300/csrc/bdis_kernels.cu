@@ -788,6 +788,9 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
         // correlations of gt with the row at integer offsets base and base + 1;
         // they change only when d crosses an integer, so the warp recomputes
         // them only when one of its patches did.
+        // The state of a step is d alone: once no patch of the warp has moved
+        // (d bitwise unchanged), every remaining step would repeat the same
+        // values, so the loop stops with the result of all `iters` steps.
         float d = dinit, dlast = 0.f;
         int offc = INT_MIN;
         float At = 0.f, Bt = 0.f;
@@ -809,11 +812,15 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
                 offc = off;
             }
             const float s = fmaf(t, Bt - At, At);
+            bool still = true;
             if (!flat) {
                 const float delta = (s - cT) * invH;
-                d = fminf(fmaxf(d + delta, -dlim), dlim);
+                const float dn = fminf(fmaxf(d + delta, -dlim), dlim);
+                still = dn == d;
+                d = dn;
                 dlast = delta;
             }
+            if (__all_sync(0xffffffffu, still)) break;
         }
 
         // window energies.  E(0) in two passes; for the four offsets the
@@ -829,26 +836,29 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
         // (general h: one split per offset; h = 1/2: the +-2h samples are the
         // centre samples one column over and -h is +h one column over, so two
         // interpolated rows cover all five)
-        float su[4], suu[4], suc[4];
+        float su[4], suu[4];
         float sa = 0.f;
         const bool half = h == 0.5f;
         // S0: columns -1 .. P at d (the centre samples are S0[1 .. P]);
         // Sp (h = 1/2 only): columns 0 .. P at d + 1/2
         float S0[P + 2], Sp[P + 1];
-        {
-            float v0[P + 3];
-            load_vals(base0 - 1, v0);
+        float v0[P + 3];
+        load_vals(base0 - 1, v0);
 #pragma unroll
-            for (int j = 0; j < P + 2; ++j) S0[j] = fmaf(t0, v0[j + 1] - v0[j], v0[j]);
-        }
+        for (int j = 0; j < P + 2; ++j) S0[j] = fmaf(t0, v0[j + 1] - v0[j], v0[j]);
         if (half) {
+            // the columns of d + 1/2 start at base0 or base0 - 1 (the half
+            // pixel moves the split by at most one column), both held in v0
             int offp;
             float tp;
             split_shift(d + 0.5f, offp, tp);
-            float vp[P + 2];
-            load_vals(ox + offp, vp);
+            const bool same = offp == off0;
 #pragma unroll
-            for (int j = 0; j < P + 1; ++j) Sp[j] = fmaf(tp, vp[j + 1] - vp[j], vp[j]);
+            for (int j = 0; j < P + 1; ++j) {
+                const float a0 = same ? v0[j + 1] : v0[j];
+                const float a1 = same ? v0[j + 2] : v0[j + 1];
+                Sp[j] = fmaf(tp, a1 - a0, a0);
+            }
         }
 #pragma unroll
         for (int j = 0; j < P; ++j) sa += row_on ? S0[j + 1] - T[j] : 0.f;
@@ -868,8 +878,10 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
         // window energies.  E(0) in two passes; for the four offsets the
         // differences dE_k = E(delta_k) - E(0) directly from the sample
         // differences u_j = s_kj - s_0j (the template cancels):
-        //   dE_k = sum u^2 - (sum u)^2 / N + 2 sum u (a_0j - mean a_0),
-        // which keeps full relative precision when dE_k << E(0).
+        //   dE_k = sum u^2 - (sum u)^2 / N + 2 sum u (a_0j - mean a_0)
+        //        = sum u (u + 2 c_j) - (sum u)^2 / N,  c_j the centred residual,
+        // which keeps full relative precision when dE_k << E(0); two group
+        // sums per offset.
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             float sk[P];
@@ -886,17 +898,15 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
 #pragma unroll
                 for (int j = 0; j < P; ++j) sk[j] = fmaf(t, v[j + 1] - v[j], v[j]);
             }
-            float p1 = 0.f, p2 = 0.f, p3 = 0.f;
+            float p1 = 0.f, p2 = 0.f;
 #pragma unroll
             for (int j = 0; j < P; ++j) {
                 const float uj = row_on ? sk[j] - S0[j + 1] : 0.f;
                 p1 += uj;
-                p2 = fmaf(uj, uj, p2);
-                p3 = fmaf(uj, T[j], p3);
+                p2 = fmaf(uj, fmaf(2.f, T[j], uj), p2);
             }
             su[k] = p1;
             suu[k] = p2;
-            suc[k] = p3;
         }
         float E[5];  // E[0] = E(0); E[k] = E(delta_k) - E(0)
         E[0] = group_sum<G>(e0);
@@ -904,8 +914,7 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
         for (int k = 0; k < 4; ++k) {
             const float S1 = group_sum<G>(su[k]);
             const float S2 = group_sum<G>(suu[k]);
-            const float S3 = group_sum<G>(suc[k]);
-            E[k + 1] = fmaxf(S2 - S1 * S1 * invN, 0.f) + 2.f * S3;
+            E[k + 1] = fmaf(-S1 * invN, S1, S2);
         }
 
         if (active && gl == 0) {
