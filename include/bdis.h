@@ -312,8 +312,11 @@ typedef enum {
     /* 1 (default): launch each kernel of the launch sequence with
      * programmatic stream serialisation, so that it is scheduled while its
      * predecessor drains and starts reading once the predecessor has
-     * completed (hides the launch gap between dependent kernels); 0: plain
-     * stream order.  Same results. */
+     * completed (hides the launch gap between dependent kernels); each block
+     * of a kernel releases the next one at its end.  2: the same, but a
+     * kernel whose grid fits in one wave of resident blocks releases the next
+     * one at its start, and every kernel after a call's first prefetches its
+     * descriptor while it waits.  0: plain stream order.  Same results. */
     BDIS_OPT_PDL = 5,
     /* Pyramid launches: 0 (default) two steps per launch (level l -> l+1 ->
      * l+2 with the gradients of l and l+1, recomputing a 2-pixel halo of level

@@ -354,6 +354,8 @@ def _diff_sigs(L):
     L.ob_diff_forward.argtypes = common + [vp, vp, vp]
     L.ob_diff_grad.restype = C.c_double
     L.ob_diff_grad.argtypes = common + [vp, vp, vp, vp]
+    L.ob_diff_adjoint.restype = None
+    L.ob_diff_adjoint.argtypes = common[:-1] + [vp, vp, vp, vp]
 
 
 def diff_forward(p: Params, left, right, st: dict, lam: float = 0.1, d_override=None):
@@ -385,6 +387,23 @@ def diff_grad(p: Params, left, right, st: dict, lam: float = 0.1):
                           _ptr(st["prop"]), _ptr(st["valid"]), st["sr_const"], lam, _ptr(gL), _ptr(gR),
                           _ptr(gdk), _ptr(gD))
     return loss, gL, gR, gdk, gD
+
+
+def diff_adjoint(p: Params, left, right, st: dict, g_disp):
+    """The adjoint chain alone (fusion, posterior, window energies, patch
+    solve, Sobel) for a given dL/dD: returns (dL/dI_l, dL/dI_r, dL/dd_k)."""
+    L = lib()
+    _diff_sigs(L)
+    Lf = np.ascontiguousarray(left, dtype=np.float64)
+    Rf = np.ascontiguousarray(right, dtype=np.float64)
+    h, w = Lf.shape
+    gD = np.ascontiguousarray(np.nan_to_num(g_disp, nan=0.0), dtype=np.float64)
+    gL = np.zeros((h, w)); gR = np.zeros((h, w))
+    gdk = np.zeros(st["kept"].size)
+    L.ob_diff_adjoint(C.byref(p), _ptr(Lf), _ptr(Rf), w, h, _ptr(st["kept"]), _ptr(st["dinit"]),
+                      _ptr(st["prop"]), _ptr(st["valid"]), st["sr_const"], _ptr(gD), _ptr(gL),
+                      _ptr(gR), _ptr(gdk))
+    return gL, gR, gdk
 
 
 # ---------------------------------------------------------------- differentiable form, all levels
@@ -452,3 +471,23 @@ def mdiff_grad(p: Params, left, right, st: dict, lam: float = 0.1):
     loss = L.ob_mdiff_grad(C.byref(p), _ptr(Lf), _ptr(Rf), w, h, C.byref(ms), lam, _ptr(gL),
                            _ptr(gR), _ptr(gdk))
     return loss, gL, gR, gdk
+
+
+def mdiff_adjoint(p: Params, left, right, st: dict, g_disp):
+    """The adjoint through every level alone for a given level-0 dL/dD:
+    (dL/dI_l, dL/dI_r, dL/dd_k of level 0)."""
+    L = lib()
+    vp = C.c_void_p
+    L.ob_mdiff_adjoint.restype = None
+    L.ob_mdiff_adjoint.argtypes = [C.POINTER(Params), vp, vp, C.c_int, C.c_int, C.POINTER(MState),
+                                   vp, vp, vp, vp]
+    Lf = np.ascontiguousarray(left, dtype=np.float64)
+    Rf = np.ascontiguousarray(right, dtype=np.float64)
+    h, w = Lf.shape
+    gD = np.ascontiguousarray(np.nan_to_num(g_disp, nan=0.0), dtype=np.float64)
+    gL = np.zeros((h, w)); gR = np.zeros((h, w))
+    gdk = np.zeros(st["kept"][0].size)
+    ms = _mstate(st)
+    L.ob_mdiff_adjoint(C.byref(p), _ptr(Lf), _ptr(Rf), w, h, C.byref(ms), _ptr(gD), _ptr(gL),
+                       _ptr(gR), _ptr(gdk))
+    return gL, gR, gdk

@@ -1065,11 +1065,15 @@ double ob_diff_forward(const ob_params *p, const double *L, const double *R, int
 
 /* Analytic gradient of ob_diff_forward with respect to I_l, I_r (w*h each,
  * overwritten) and to the patch disparities d_k as free variables (gdk,
- * patches).  gD (w*h, may be NULL) receives dloss/dD. */
-double ob_diff_grad(const ob_params *p, const double *L, const double *R, int w, int h,
-                    const uint8_t *kept, const double *dinit, const double *prop,
-                    const uint8_t *valid, int sr_const, double lambda, double *gL, double *gR,
-                    double *gdk, double *gD_out)
+ * patches).  gD (w*h, may be NULL) receives dloss/dD.  With gD_in given, the
+ * loss step is replaced by that dloss/dD (read at valid pixels): the result
+ * is the adjoint of the fusion, posterior, window and patch-solve chain
+ * alone (steps 2-5 below), for any loss on D. */
+static double diff_grad_impl(const ob_params *p, const double *L, const double *R, int w, int h,
+                             const uint8_t *kept, const double *dinit, const double *prop,
+                             const uint8_t *valid, int sr_const, double lambda,
+                             const double *gD_in, double *gL, double *gR, double *gdk,
+                             double *gD_out)
 {
     /* the differentiable form covers the default fusion at full resolution */
     if (p->weight_mode != OB_WEIGHT_BDIS || p->finest_level != 0 || p->fast_exp) return NAN;
@@ -1088,11 +1092,15 @@ double ob_diff_grad(const ob_params *p, const double *L, const double *R, int w,
     const double inv = 1.0 / ((double)w * h);
     for (size_t i = 0; i < (size_t)w * h; ++i) { gL[i] = 0.0; gR[i] = 0.0; }
 
-    /* 1. loss -> D, and the direct image terms */
+    /* 1. loss -> D, and the direct image terms (or the given dloss/dD) */
     for (int y = 0; y < h; ++y)
         for (int x = 0; x < w; ++x) {
             size_t i = (size_t)y * w + x;
             if (!valid[i]) continue;
+            if (gD_in) {
+                gD[i] = gD_in[i];
+                continue;
+            }
             double X = x - D[i];
             double r = sample_row(R, w, y, X) - L[i];
             double s = sgn(r) * inv;
@@ -1250,6 +1258,25 @@ double ob_diff_grad(const ob_params *p, const double *L, const double *R, int w,
     free(ox);
     free(oy);
     return loss;
+}
+
+double ob_diff_grad(const ob_params *p, const double *L, const double *R, int w, int h,
+                    const uint8_t *kept, const double *dinit, const double *prop,
+                    const uint8_t *valid, int sr_const, double lambda, double *gL, double *gR,
+                    double *gdk, double *gD_out)
+{
+    return diff_grad_impl(p, L, R, w, h, kept, dinit, prop, valid, sr_const, lambda, NULL, gL, gR,
+                          gdk, gD_out);
+}
+
+/* The adjoint chain alone (see diff_grad_impl) for a given dloss/dD. */
+void ob_diff_adjoint(const ob_params *p, const double *L, const double *R, int w, int h,
+                     const uint8_t *kept, const double *dinit, const double *prop,
+                     const uint8_t *valid, int sr_const, const double *gD_in, double *gL,
+                     double *gR, double *gdk)
+{
+    diff_grad_impl(p, L, R, w, h, kept, dinit, prop, valid, sr_const, 0.0, gD_in, gL, gR, gdk,
+                   NULL);
 }
 
 /* ------------------------------------------------------------------ */
@@ -1494,9 +1521,9 @@ double ob_mdiff_forward(const ob_params *p, const double *L, const double *R, in
  * the implicit-function adjoint of each solve into that level's images, the
  * Sobel transpose, and the bilinear transpose of rho's coarse term into the
  * next level's Q map; finally the pyramid transpose, coarsest first. */
-double ob_mdiff_grad(const ob_params *p, const double *L, const double *R, int w, int h,
-                     const ob_mstate *st, double lambda, double *gL_out, double *gR_out,
-                     double *gdk_out)
+static double mdiff_grad_impl(const ob_params *p, const double *L, const double *R, int w, int h,
+                              const ob_mstate *st, double lambda, const double *gD_in,
+                              double *gL_out, double *gR_out, double *gdk_out)
 {
     if (p->weight_mode != OB_WEIGHT_BDIS || p->finest_level != 0 || p->fast_exp) return NAN;
     const int NL = p->levels, P = p->patch, N = P * P;
@@ -1516,7 +1543,7 @@ double ob_mdiff_grad(const ob_params *p, const double *L, const double *R, int w
     ob_window_offsets(p->window_step, delta);
     const double inv = 1.0 / ((double)w * h);
 
-    /* 1. loss -> D and the direct image terms (level 0) */
+    /* 1. loss -> D and the direct image terms (level 0), or the given dloss/dD */
     double *gD = (double *)calloc((size_t)w * h, sizeof(double));
     {
         const ob_mlevel *v = &lv[0];
@@ -1524,6 +1551,10 @@ double ob_mdiff_grad(const ob_params *p, const double *L, const double *R, int w
             for (int x = 0; x < w; ++x) {
                 size_t i = (size_t)y * w + x;
                 if (!st->valid[i]) continue;
+                if (gD_in) {
+                    gD[i] = gD_in[i];
+                    continue;
+                }
                 double X = x - v->D[i];
                 double r = sample_row(v->R, w, y, X) - v->L[i];
                 double s = sgn(r) * inv;
@@ -1719,4 +1750,19 @@ double ob_mdiff_grad(const ob_params *p, const double *L, const double *R, int w
     free(a);
     mlevels_free(lv, NL);
     return loss;
+}
+
+double ob_mdiff_grad(const ob_params *p, const double *L, const double *R, int w, int h,
+                     const ob_mstate *st, double lambda, double *gL_out, double *gR_out,
+                     double *gdk_out)
+{
+    return mdiff_grad_impl(p, L, R, w, h, st, lambda, NULL, gL_out, gR_out, gdk_out);
+}
+
+/* The adjoint through every level alone, for a given level-0 dloss/dD. */
+void ob_mdiff_adjoint(const ob_params *p, const double *L, const double *R, int w, int h,
+                      const ob_mstate *st, const double *gD_in, double *gL_out, double *gR_out,
+                      double *gdk_out)
+{
+    mdiff_grad_impl(p, L, R, w, h, st, 0.0, gD_in, gL_out, gR_out, gdk_out);
 }

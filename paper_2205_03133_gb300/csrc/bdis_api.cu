@@ -80,7 +80,7 @@ struct bdis_handle {
     std::vector<bdis_saved *> saved;
     bdis_saved *last_saved = nullptr;
     int form = 0;             // BDIS_OPT_FORM
-    bool use_pdl = true;      // BDIS_OPT_PDL
+    int use_pdl = 1;          // BDIS_OPT_PDL: 0, 1 or 2
     int pyr_steps = 0;        // BDIS_OPT_PYRAMID_STEPS
     bool adjoint_levels = false;  // BDIS_OPT_ADJOINT_LEVELS
     bool host_mapped = true;      // BDIS_OPT_HOST_MAPPED
@@ -558,7 +558,8 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
     s = ensure_status_word(h);
     if (s != BDIS_OK) return s;
     for (auto &a : stages) {
-        a.pdl = h->use_pdl ? 1 : 0;
+        a.pdl = h->use_pdl;
+        a.prefetch = &a == &stages.front() ? 0 : 1;  // the table is uploaded before the first stage
         a.bulk = h->bulk_copy ? 1 : 0;
         a.err_host = h->status_dev;
     }
@@ -886,7 +887,7 @@ bdis_status time_form(bdis_handle *h, int n, const bdis_pair *pairs, int in_type
 bdis_status run_tuned(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, cudaStream_t st);
 
 int option_bits(const bdis_handle *h) {
-    return (h->use_graph ? 1 : 0) | (h->profile ? 2 : 0) | (h->use_pdl ? 4 : 0) | (h->autotune ? 8 : 0) |
+    return (h->use_graph ? 1 : 0) | (h->profile ? 2 : 0) | (h->use_pdl << 14) | (h->autotune ? 8 : 0) |
            (h->form << 4) | (h->pyr_steps << 6) | (h->coarse_levels << 8) |
            (h->barrier_unreachable ? 1 << 12 : 0) | (h->bulk_copy ? 1 << 13 : 0);
 }
@@ -1082,7 +1083,8 @@ bdis_status bdis_set_option(bdis_handle *h, int option, int value) {
         return BDIS_OK;
     }
     if (option == BDIS_OPT_PDL) {
-        h->use_pdl = value != 0;
+        if (value < 0 || value > 2) return fail(h, BDIS_EINVAL, "pdl must be 0, 1 or 2");
+        h->use_pdl = value;
         return BDIS_OK;
     }
     if (option == BDIS_OPT_HOST_MAPPED) {

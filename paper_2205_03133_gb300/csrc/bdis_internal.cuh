@@ -103,7 +103,12 @@ struct LaunchArgs {
     int weight_mode;          // bdis_weight_mode
     int fast_exp;             // Schraudolph exponential in the posterior
     int img_type;             // ElemType of this level's L, R (read by the DIS fusion)
-    int pdl;                  // launch with programmatic stream serialisation
+    int pdl;                  // programmatic stream serialisation: 0 off, 1 the next kernel
+                              // released at block end, 2 released at kernel start when
+                              // the grid fits in one wave of resident blocks
+    int early;                // set by the launcher: release the next kernel at the start
+    int prefetch;             // the descriptor table is complete before this kernel starts
+                              // (every stage after a call's first): prefetched while waiting
     int bulk;                 // one-step pyramid: interior tiles staged by bulk async copies
     int *err_host;            // mapped status word of the handle (a device wait ran out), or nullptr
 };

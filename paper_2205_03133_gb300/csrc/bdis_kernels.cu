@@ -32,6 +32,22 @@
 namespace bdis {
 namespace {
 
+// Entry and exit of a stage kernel launched with programmatic stream
+// serialisation.  With `early` the next kernel may be scheduled at once (it
+// still waits in pdl_wait() for this one to complete); otherwise each block
+// releases it at its end.  A stage whose descriptor table is complete before
+// it starts (every stage after a call's first) prefetches its single
+// descriptor into L1 while it waits for its predecessor.
+__device__ __forceinline__ void pdl_enter(const LaunchArgs &a) {
+    if (a.early) pdl_release();
+    if (a.prefetch && a.npairs == 1 && threadIdx.x * 128 < sizeof(LevelDesc))
+        asm volatile("prefetch.L1 [%0];" ::"l"((const char *)a.descs + 128 * threadIdx.x));
+    pdl_wait();
+}
+__device__ __forceinline__ void pdl_leave(const LaunchArgs &a) {
+    if (!a.early) pdl_release();
+}
+
 // ---------------------------------------------------------------- pyramid
 
 // A block owns a 64 x 32 pixel tile of level l and the 32 x 16 tile of
@@ -408,11 +424,11 @@ __device__ __forceinline__ void pyramid2_unit(const LaunchArgs &a, int unit, flo
 template <typename TI, typename TO>
 __global__ void __launch_bounds__(256) k_pyramid2(LaunchArgs a) {
     __shared__ float sm[kPyr2SmemFloats];
-    pdl_wait();
+    pdl_enter(a);
     if (blockIdx.x == 0 && a.acc_zero != nullptr)
         for (int i = threadIdx.x; i < a.acc_count; i += blockDim.x) a.acc_zero[i] = 0ull;
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) pyramid2_unit<TI, TO>(a, unit, sm);
-    pdl_release();
+    pdl_leave(a);
 }
 
 template <typename TI, typename TO>
@@ -421,14 +437,14 @@ __global__ void __launch_bounds__(256, 4) k_pyramid(LaunchArgs a) {
     __shared__ __align__(16) float Rs[kPyrSH][kPyrSP];
     __shared__ __align__(16) float Lh[kPyrSH][kPyrHP];
     __shared__ __align__(16) float Rh[kPyrSH][kPyrHP];
-    pdl_wait();
+    pdl_enter(a);
     // the finest pyramid launch runs before every search: it clears the
     // sigma_r accumulators of all levels and pairs
     if (blockIdx.x == 0 && a.acc_zero != nullptr)
         for (int i = threadIdx.x; i < a.acc_count; i += blockDim.x) a.acc_zero[i] = 0ull;
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x)
         pyramid_unit<TI, TO>(a, unit, Ls, Rs, Lh, Rh);
-    pdl_release();
+    pdl_leave(a);
 }
 
 // One-step pyramid with the staging of interior tiles by bulk asynchronous
@@ -487,7 +503,7 @@ __global__ void __launch_bounds__(256, 4) k_pyramid_bulk(LaunchArgs a) {
         mbar_init_fence();
     }
     __syncthreads();
-    pdl_wait();
+    pdl_enter(a);
     if (blockIdx.x == 0 && a.acc_zero != nullptr)
         for (int i = tid; i < a.acc_count; i += blockDim.x) a.acc_zero[i] = 0ull;
 
@@ -579,7 +595,7 @@ __global__ void __launch_bounds__(256, 4) k_pyramid_bulk(LaunchArgs a) {
         pyramid_compute<TO>(*cur.D, cur.tx, cur.ty, Ls, Rs, Lh, Rh);
         cur = nxt;
     }
-    pdl_release();
+    pdl_leave(a);
 }
 
 // ---------------------------------------------------------------- patch search
@@ -836,7 +852,7 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
         // (general h: one split per offset; h = 1/2: the +-2h samples are the
         // centre samples one column over and -h is +h one column over, so two
         // interpolated rows cover all five)
-        float su[4], suu[4];
+        float su[4], suu[4], suc[4];
         float sa = 0.f;
         const bool half = h == 0.5f;
         // S0: columns -1 .. P at d (the centre samples are S0[1 .. P]);
@@ -878,10 +894,8 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
         // window energies.  E(0) in two passes; for the four offsets the
         // differences dE_k = E(delta_k) - E(0) directly from the sample
         // differences u_j = s_kj - s_0j (the template cancels):
-        //   dE_k = sum u^2 - (sum u)^2 / N + 2 sum u (a_0j - mean a_0)
-        //        = sum u (u + 2 c_j) - (sum u)^2 / N,  c_j the centred residual,
-        // which keeps full relative precision when dE_k << E(0); two group
-        // sums per offset.
+        //   dE_k = sum u^2 - (sum u)^2 / N + 2 sum u (a_0j - mean a_0),
+        // which keeps full relative precision when dE_k << E(0).
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             float sk[P];
@@ -898,15 +912,17 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
 #pragma unroll
                 for (int j = 0; j < P; ++j) sk[j] = fmaf(t, v[j + 1] - v[j], v[j]);
             }
-            float p1 = 0.f, p2 = 0.f;
+            float p1 = 0.f, p2 = 0.f, p3 = 0.f;
 #pragma unroll
             for (int j = 0; j < P; ++j) {
                 const float uj = row_on ? sk[j] - S0[j + 1] : 0.f;
                 p1 += uj;
-                p2 = fmaf(uj, fmaf(2.f, T[j], uj), p2);
+                p2 = fmaf(uj, uj, p2);
+                p3 = fmaf(uj, T[j], p3);
             }
             su[k] = p1;
             suu[k] = p2;
+            suc[k] = p3;
         }
         float E[5];  // E[0] = E(0); E[k] = E(delta_k) - E(0)
         E[0] = group_sum<G>(e0);
@@ -914,7 +930,8 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
         for (int k = 0; k < 4; ++k) {
             const float S1 = group_sum<G>(su[k]);
             const float S2 = group_sum<G>(suu[k]);
-            E[k + 1] = fmaf(-S1 * invN, S1, S2);
+            const float S3 = group_sum<G>(suc[k]);
+            E[k + 1] = fmaxf(S2 - S1 * S1 * invN, 0.f) + 2.f * S3;
         }
 
         if (active && gl == 0) {
@@ -977,9 +994,9 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
 template <int P, typename TI, typename TG>
 __global__ void __launch_bounds__(256, (P <= 8 ? 3 : 2)) k_search(LaunchArgs a) {
     extern __shared__ float smem[];
-    pdl_wait();
+    pdl_enter(a);
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) search_unit<P, TI, TG>(a, unit, smem);
-    pdl_release();
+    pdl_leave(a);
 }
 
 // ---------------------------------------------------------------- posterior, fusion
@@ -1447,9 +1464,9 @@ __device__ __forceinline__ void upsample_unit(const LaunchArgs &a, int unit) {
 }
 
 __global__ void __launch_bounds__(256) k_upsample(LaunchArgs a) {
-    pdl_wait();
+    pdl_enter(a);
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) upsample_unit(a, unit);
-    pdl_release();
+    pdl_leave(a);
 }
 
 // Depth (Eq. 13) and its variance (the depth factor of Eq. 17), elementwise.
@@ -1494,9 +1511,9 @@ __global__ void __launch_bounds__(256) k_depth(const float *__restrict__ disp,
 template <int TW, int TH>
 __global__ void __launch_bounds__(256) k_fuse(LaunchArgs a) {
     extern __shared__ float4 fz[];
-    pdl_wait();
+    pdl_enter(a);
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) fuse_unit<TW, TH>(a, unit, fz);
-    pdl_release();
+    pdl_leave(a);
 }
 
 // ---------------------------------------------------------------- persistent form
@@ -1742,8 +1759,12 @@ int search_occupancy(int P, int in_type, int g_type, size_t smem_bytes) {
 namespace {
 // One 256-thread launch of a LaunchArgs kernel; with a.pdl the launch allows
 // programmatic stream serialisation (the kernel waits in pdl_wait()).
-cudaError_t launch_args_kernel(const void *f, const LaunchArgs &a, int grid, size_t smem,
+int resident_blocks(const void *f, size_t smem);
+
+cudaError_t launch_args_kernel(const void *f, const LaunchArgs &args, int grid, size_t smem,
                                cudaStream_t s) {
+    LaunchArgs a = args;
+    a.early = a.pdl == 2 && grid <= num_sms() * resident_blocks(f, smem) ? 1 : 0;
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3(grid);
@@ -1755,8 +1776,8 @@ cudaError_t launch_args_kernel(const void *f, const LaunchArgs &a, int grid, siz
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = a.pdl ? 1 : 0;
-    void *args[] = {(void *)&a};
-    return cudaLaunchKernelExC(&cfg, f, args);
+    void *kargs[] = {(void *)&a};
+    return cudaLaunchKernelExC(&cfg, f, kargs);
 }
 }  // namespace
 

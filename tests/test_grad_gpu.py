@@ -3,10 +3,13 @@ analytic gradient (itself pinned to FP64 central differences on CPU), on the
 same seeded float images, through the C ABI.
 
 Tolerance: per element |g_gpu - g_oracle| <= 1e-4 * max|g_oracle| (+ a
-FP32 floor), on all elements for the small case and on >= 99.9 % of them at
-640x480, where FP32 and FP64 can take a different side of a kink of the L1
-terms (sign of a residual or of a disparity difference within rounding of
-zero) at a handful of pixels."""
+FP32 floor).  The L1 terms of the loss have kinks (the sign of a residual,
+or of a disparity difference at the tie threshold), where FP32 and FP64 can
+take different sides at a handful of pixels.  The small cases therefore
+compare the adjoint chain of both sides from the same dL/dD (the GPU's) on
+every element, dL/dD itself away from kink-adjacent pixels, and the complete
+gradients on most elements; at 640x480 the complete gradients are compared
+on >= 99.9 % of the elements."""
 import numpy as np
 import pytest
 
@@ -50,6 +53,29 @@ def _oracle(gp, L, R, lam=0.1):
     return dict(loss=loss, g_left=gL, g_right=gR, g_patch=gdk, g_disp=gD, out=o, st=st)
 
 
+def _kink_pixels(D, valid, L, R, lam_tie=1e-6, band=1e-5, rband=1e-4):
+    """Pixels whose loss subgradient the two arithmetics may legitimately
+    take on different sides: a reprojection residual within rband of 0, or a
+    4-neighbour disparity difference within band of the tie threshold
+    lam_tie (|D_p| + |D_q|) (reading r25).  FP32 rounding moves D by ~1e-6."""
+    h, w = D.shape
+    out = np.zeros((h, w), bool)
+    X = np.clip(np.arange(w)[None, :] - np.nan_to_num(D), 0, w - 1)
+    x0 = np.floor(X).astype(int)
+    x1 = np.minimum(x0 + 1, w - 1)
+    t = X - x0
+    rows = np.arange(h)[:, None]
+    r = (1 - t) * R[rows, x0] + t * R[rows, x1] - L
+    out |= valid & (np.abs(r) < rband)
+    for dy, dx in ((0, 1), (1, 0)):
+        a, b = D[: h - dy, : w - dx], D[dy:, dx:]
+        both = valid[: h - dy, : w - dx] & valid[dy:, dx:]
+        near = both & (np.abs(a - b) < lam_tie * (np.abs(a) + np.abs(b)) + band)
+        out[: h - dy, : w - dx] |= near
+        out[dy:, dx:] |= near
+    return out
+
+
 def _close(a, b, frac=1.0):
     scale = np.abs(b).max()
     err = np.abs(a.astype(np.float64) - b)
@@ -65,21 +91,43 @@ def _close(a, b, frac=1.0):
     dict(patch=8, stride=4, levels=2, iters=50, window_step=0.4),
 ])
 def test_adjoint_matches_oracle_small(bd, kw):
+    """Every element: the adjoint chain of both sides from the same dL/dD
+    (the GPU's), and dL/dD itself away from the kinks of the L1 terms; the
+    complete gradients agree on all but the kink-adjacent elements."""
+    import torch
     pr = synth.g1_pair(64, 48, 3, d0=1.0, d1=3.0, amp=1.0, as_float=True)
     L32, R32 = pr.left.astype(np.float32), pr.right.astype(np.float32)
     L, R = L32.astype(np.float64), R32.astype(np.float64)
-    g = _gpu(bd, kw, L32, R32)
-    o = _oracle(g["params"], L, R)
+    m = bd.BDIS(**kw)
+    (d, _, ok), = m.match_f32([torch.from_numpy(L32).cuda()], [torch.from_numpy(R32).cuda()])
+    g, = m.loss_and_grad(0.1)
+    (aL, aR, adk), = m.backward([g["g_disp"]])     # the adjoint chain alone
+    torch.cuda.synchronize()
+    rec = m.level_view(0, 0)["patches"]
+    gp = m.params
+    g = {k: t.cpu().numpy() for k, t in g.items()}
+    aL, aR, adk = aL.cpu().numpy(), aR.cpu().numpy(), adk.cpu().numpy()
+    valid = ok.cpu().numpy().astype(bool)
+    m.close()
+    o = _oracle(gp, L, R)
     # same discrete state on both sides
-    assert np.array_equal(g["valid"], o["out"]["valid"])
-    assert np.array_equal(g["rec"]["flags"].ravel() == 0, o["st"]["kept"].astype(bool))
-    assert abs(float(g["loss"][0]) - o["loss"]) <= 1e-5 * o["loss"]
-    for key, okey in (("g_disp", "g_disp"), ("g_left", "g_left"), ("g_right", "g_right")):
-        good, info = _close(g[key], o[okey])
-        assert good, (key, info)
+    assert np.array_equal(valid, o["out"]["valid"])
     kept = o["st"]["kept"].astype(bool)
-    good, info = _close(g["g_patch_disp"].ravel()[kept], o["g_patch"][kept])
-    assert good, ("g_patch_disp", info)
+    assert np.array_equal(rec["flags"].ravel() == 0, kept)
+    assert abs(float(g["loss"][0]) - o["loss"]) <= 1e-5 * o["loss"]
+    oL, oR, odk = oracle.diff_adjoint(oracle_params(gp), L, R, o["st"], g["g_disp"])
+    for key, a, b in (("adjoint g_left", aL, oL), ("adjoint g_right", aR, oR)):
+        good, info = _close(a, b)
+        assert good, (key, info)
+    good, info = _close(adk.ravel()[kept], odk[kept])
+    assert good, ("adjoint g_patch_disp", info)
+    kinks = _kink_pixels(o["out"]["disp"], valid, L, R)
+    assert kinks.mean() < 0.02, kinks.mean()
+    good, info = _close(g["g_disp"][~kinks], o["g_disp"][~kinks])
+    assert good, ("g_disp away from kinks", info, int(kinks.sum()))
+    for key in ("g_left", "g_right"):
+        good, info = _close(g[key], o[key], frac=0.97)
+        assert good, (key, info)
 
 
 def test_adjoint_matches_oracle_640x480(bd):
@@ -229,9 +277,11 @@ def _gpu_ml(bd, kw, L32, R32, lam=0.1):
     Rt = torch.from_numpy(R32).cuda()
     (d, v, ok), = m.match_f32([Lt], [Rt])
     g, = m.loss_and_grad(lam)
+    (aL, aR, _), = m.backward([g["g_disp"]])   # the adjoint chain alone
     torch.cuda.synchronize()
     recs = [m.level_view(0, l)["patches"] for l in range(m.params.levels)]
     out = {k: t.cpu().numpy() for k, t in g.items()}
+    out["adjoint_g_left"], out["adjoint_g_right"] = aL.cpu().numpy(), aR.cpu().numpy()
     out.update(valid=ok.cpu().numpy().astype(bool), recs=recs, params=m.params)
     m.close()
     return out
@@ -256,8 +306,15 @@ def test_adjoint_through_levels_matches_oracle_small(bd, kw):
         assert np.array_equal(g["recs"][l]["flags"].ravel() == 0, st["kept"][l].astype(bool)), l
     loss, gL, gR, gdk = oracle.mdiff_grad(op, L, R, st)
     assert abs(float(g["loss"][0]) - loss) <= 1e-5 * loss
+    # every element of the adjoint chain from the GPU's own dL/dD
+    oL, oR, _ = oracle.mdiff_adjoint(op, L, R, st, g["g_disp"])
+    for key, ref in (("g_left", oL), ("g_right", oR)):
+        good, info = _close(g["adjoint_" + key], ref)
+        assert good, ("adjoint " + key, info)
+    # the complete gradients: all but the elements a kink-adjacent pixel of
+    # the L1 terms reaches
     for key, ref in (("g_left", gL), ("g_right", gR)):
-        good, info = _close(g[key], ref)
+        good, info = _close(g[key], ref, frac=0.9)
         assert good, (key, info)
     kept = st["kept"][0].astype(bool)
     good, info = _close(g["g_patch_disp"].ravel()[kept], gdk[kept])

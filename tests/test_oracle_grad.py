@@ -99,3 +99,52 @@ def test_gradient_invariances():
     data = oracle.diff_forward(p, L, R, st, lam=0.0)[0]
     assert data < loss
     assert abs((gL * L).sum() + (gR * R).sum() - data) < 1e-8 * data
+
+
+def test_adjoint_alone_matches_finite_differences_of_a_linear_loss():
+    # for a fixed weight map g, the adjoint chain of dL/dD = g is the gradient
+    # of f(I) = sum g D(I) (the frozen forward's D): FD pins it independently
+    p, L, R, out, st = _setup()
+    rng = np.random.default_rng(12)
+    g = rng.standard_normal(L.shape) * st["valid"]
+    gL, gR, gdk = oracle.diff_adjoint(p, L, R, st, g)
+
+    def f_left(x):
+        return float((g * oracle.diff_forward(p, x, R, st)[1]).sum())
+
+    def f_right(x):
+        return float((g * oracle.diff_forward(p, L, x, st)[1]).sum())
+
+    idx = rng.choice(L.size, 60, replace=False)
+    for fun, x, an in ((f_left, L, gL), (f_right, R, gR)):
+        ok, bad, excluded, worst = _fd_check(fun, x, idx, an)
+        assert bad == 0 and ok >= 54, (ok, bad, excluded, worst)
+
+
+def test_full_gradient_is_adjoint_plus_direct_loss_terms():
+    # dL/dI = (direct terms of the loss) + adjoint(dL/dD); the direct terms of
+    # the L1 reprojection are -sign(r)/(w h) on I_l and the interpolation
+    # taps of sign(r)/(w h) on I_r
+    p, L, R, out, st = _setup()
+    loss, gL, gR, gdk, gD = oracle.diff_grad(p, L, R, st)
+    aL, aR, adk = oracle.diff_adjoint(p, L, R, st, gD)
+    _, D, _ = oracle.diff_forward(p, L, R, st)
+    h, w = L.shape
+    dL = np.zeros_like(L)
+    dR = np.zeros_like(R)
+    for y in range(h):
+        for x in range(w):
+            if not st["valid"][y, x]:
+                continue
+            X = min(max(x - D[y, x], 0.0), w - 1.0)
+            x0 = int(np.floor(X))
+            x1 = min(x0 + 1, w - 1)
+            t = X - x0
+            r = (1 - t) * R[y, x0] + t * R[y, x1] - L[y, x]
+            s = np.sign(r) / (w * h)
+            dL[y, x] -= s
+            dR[y, x0] += s * (1 - t)
+            dR[y, x1] += s * t
+    np.testing.assert_allclose(gL, dL + aL, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(gR, dR + aR, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(gdk, adk, rtol=0, atol=1e-15)

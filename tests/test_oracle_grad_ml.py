@@ -70,3 +70,33 @@ def test_finest_level_gradient_alone_misses_the_coarse_path():
     okm, badm, _, _ = _fd_check(lambda y: oracle.mdiff_forward(p, y, R, st)[0], L, idx, gm)
     assert bad1 >= 10
     assert badm == 0 and okm >= 30
+
+
+def test_adjoint_through_levels_alone_matches_finite_differences():
+    # the adjoint through every level for a fixed dL/dD = g is the gradient of
+    # f(I) = sum g D(I) of the frozen forward through every level
+    p, L, R, out = _setup()
+    st = oracle.frozen_state_ml(p, out)
+    rng = np.random.default_rng(21)
+    g = rng.standard_normal(L.shape) * st["valid"]
+    gL, gR, gdk = oracle.mdiff_adjoint(p, L, R, st, g)
+
+    def f_left(x):
+        return float((g * oracle.mdiff_forward(p, x, R, st)[1]).sum())
+
+    def f_right(x):
+        return float((g * oracle.mdiff_forward(p, L, x, st)[1]).sum())
+
+    idx = rng.choice(L.size, 40, replace=False)
+    for fun, x, an in ((f_left, L, gL), (f_right, R, gR)):
+        ok, bad, excluded, worst = _fd_check(fun, x, idx, an)
+        assert bad == 0 and ok >= 34, (ok, bad, excluded, worst)
+    # and the full gradient is this adjoint plus the loss's direct terms,
+    # which are those of the finest-level form
+    loss, fL, fR, fdk = oracle.mdiff_grad(p, L, R, st)
+    _, _, _, _, gD = oracle.diff_grad(p, L, R, oracle.frozen_state(p, out))
+    aL, aR, adk = oracle.mdiff_adjoint(p, L, R, st, gD)
+    sL, sR, sdk = oracle.diff_adjoint(p, L, R, oracle.frozen_state(p, out), gD)
+    d1 = oracle.diff_grad(p, L, R, oracle.frozen_state(p, out))
+    np.testing.assert_allclose(fL - aL, d1[1] - sL, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(fR - aR, d1[2] - sR, rtol=0, atol=1e-12)
