@@ -116,6 +116,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity
     return true;
 }
 
+// x / d for 0 <= x < 2^22 and d >= 1 from the correctly rounded reciprocal
+// r = 1/d: floor((x + 1/2) r) is exact there (the half step keeps the product
+// at least 1/(2d) away from the next integer, more than its rounding error),
+// four instructions where an integer division by a run-time divisor takes
+// about twenty.
+__device__ __forceinline__ int udiv_small(int x, float r) {
+    return (int)__fmul_rn(__fadd_rn((float)x, 0.5f), r);
+}
+__device__ __forceinline__ float recip(int d) { return __frcp_rn((float)d); }
+
 // reflect about the edge pixel without repeating it (-1 -> 1, n -> n-2); n >= 3
 __device__ __forceinline__ int refl(int i, int n) {
     i = i < 0 ? -i : i;

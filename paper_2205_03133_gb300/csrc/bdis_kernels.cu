@@ -264,7 +264,7 @@ __device__ __forceinline__ void pyramid_unit(const LaunchArgs &a, int unit, floa
     const LevelDesc &D = a.descs[find_pair(a.descs, a.npairs, unit, W_PYR)];
     const int tile = unit - D.work_begin[W_PYR];
     const int ntx = (D.w + kPyrTW - 1) / kPyrTW;
-    const int tx = tile % ntx, ty = tile / ntx;
+    const int ty = udiv_small(tile, recip(ntx)), tx = tile - ty * ntx;
     __syncthreads();  // the previous unit's readers are done with the staged region
     pyramid_stage_loads<TI>(D, tx, ty, Ls, Rs);
     __syncthreads();
@@ -303,7 +303,7 @@ __device__ __forceinline__ void pyramid2_unit(const LaunchArgs &a, int unit, flo
     const LevelDesc &E = a.descs2[pi];    // level l+1 (its Ln, Rn: level l+2)
     const int tile = unit - D.work_begin[W_PYR];
     const int ntx = (D.w + kPyrTW - 1) / kPyrTW;
-    const int tx = tile % ntx, ty = tile / ntx;
+    const int ty = udiv_small(tile, recip(ntx)), tx = tile - ty * ntx;
     const int x0 = tx * kPyrTW - 6, y0 = ty * kPyrTH - 6;  // level-l region origin
     const int X0 = tx * (kPyrTW / 2) - 2, Y0 = ty * (kPyrTH / 2) - 2;  // level-(l+1) region origin
     const int w = D.w, h = D.h, pitch = D.pitch;
@@ -518,8 +518,8 @@ __global__ void __launch_bounds__(256, 4) k_pyramid_bulk(LaunchArgs a) {
         const LevelDesc &D = *t.D;
         const int tile = unit - D.work_begin[W_PYR];
         const int ntx = (D.w + kPyrTW - 1) / kPyrTW;
-        t.tx = tile % ntx;
-        t.ty = tile / ntx;
+        t.ty = udiv_small(tile, recip(ntx));
+        t.tx = tile - t.ty * ntx;
         const int xs = t.tx * kPyrTW - kPyrOX, y0 = t.ty * kPyrTH - 2;
         const int xr = xs - PB::RAW_OFF;
         const bool next = D.Ln != nullptr;
@@ -852,7 +852,7 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
         // (general h: one split per offset; h = 1/2: the +-2h samples are the
         // centre samples one column over and -h is +h one column over, so two
         // interpolated rows cover all five)
-        float su[4], suu[4], suc[4];
+        float su[4], suu[4];
         float sa = 0.f;
         const bool half = h == 0.5f;
         // S0: columns -1 .. P at d (the centre samples are S0[1 .. P]);
@@ -894,8 +894,10 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
         // window energies.  E(0) in two passes; for the four offsets the
         // differences dE_k = E(delta_k) - E(0) directly from the sample
         // differences u_j = s_kj - s_0j (the template cancels):
-        //   dE_k = sum u^2 - (sum u)^2 / N + 2 sum u (a_0j - mean a_0),
-        // which keeps full relative precision when dE_k << E(0).
+        //   dE_k = sum u^2 - (sum u)^2 / N + 2 sum u (a_0j - mean a_0)
+        //        = sum u (u + 2 c_j) - (sum u)^2 / N,  c_j the centred residual,
+        // which keeps full relative precision when dE_k << E(0); two group
+        // sums per offset.
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             float sk[P];
@@ -912,17 +914,15 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
 #pragma unroll
                 for (int j = 0; j < P; ++j) sk[j] = fmaf(t, v[j + 1] - v[j], v[j]);
             }
-            float p1 = 0.f, p2 = 0.f, p3 = 0.f;
+            float p1 = 0.f, p2 = 0.f;
 #pragma unroll
             for (int j = 0; j < P; ++j) {
                 const float uj = row_on ? sk[j] - S0[j + 1] : 0.f;
                 p1 += uj;
-                p2 = fmaf(uj, uj, p2);
-                p3 = fmaf(uj, T[j], p3);
+                p2 = fmaf(uj, fmaf(2.f, T[j], uj), p2);
             }
             su[k] = p1;
             suu[k] = p2;
-            suc[k] = p3;
         }
         float E[5];  // E[0] = E(0); E[k] = E(delta_k) - E(0)
         E[0] = group_sum<G>(e0);
@@ -930,8 +930,7 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
         for (int k = 0; k < 4; ++k) {
             const float S1 = group_sum<G>(su[k]);
             const float S2 = group_sum<G>(suu[k]);
-            const float S3 = group_sum<G>(suc[k]);
-            E[k + 1] = fmaxf(S2 - S1 * S1 * invN, 0.f) + 2.f * S3;
+            E[k + 1] = fmaf(-S1 * invN, S1, S2);
         }
 
         if (active && gl == 0) {
@@ -944,22 +943,14 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
             // saddle: E(0) above the smallest off-centre energy (a tie keeps)
             const float dmin = fminf(fminf(E[1], E[2]), fminf(E[3], E[4]));
             if (dmin < 0.f) f |= BDIS_F_SADDLE;
-            bdis_patch_record rec;
-            rec.d = d;
-            rec.dinit = dinit;
-            rec.dlast = dlast;
-            rec.H = H;
-#pragma unroll
-            for (int k = 0; k < 5; ++k) rec.E[k] = E[k];
-            rec.cT = cT;
-            rec.flags = f;
-            rec.nout = (uint16_t)nout_all;
-            rec.pdf_flags = 0;
-            rec.pi = 0.f;
-            rec.rho = 0.f;
-            rec.sig2 = 0.f;
-            rec.mu = mean0;
-            D.rec[(size_t)py * D.npx + kx] = rec;
+            // the 64-byte record as four 16-byte stores (layout of bdis_patch_record:
+            // d dinit dlast H | E0..E3 | E4 cT flags nout+pdf_flags | pi rho sig2 mu)
+            static_assert(sizeof(bdis_patch_record) == 64, "record layout");
+            float4 *rp = (float4 *)(D.rec + (size_t)py * D.npx + kx);
+            rp[0] = make_float4(d, dinit, dlast, H);
+            rp[1] = make_float4(E[0], E[1], E[2], E[3]);
+            rp[2] = make_float4(E[4], cT, __uint_as_float(f), __uint_as_float((uint32_t)nout_all & 0xffffu));
+            rp[3] = make_float4(0.f, 0.f, 0.f, mean0);
             const bool kept = f == 0u;
             pe[3 * kk] = kept ? E[0] : 0.f;
             pe[3 * kk + 1] = kept ? 1.f : 0.f;
@@ -1188,10 +1179,11 @@ __device__ __forceinline__ float4 posterior_of(const LaunchArgs &a, const LevelD
 
 // Covering patch indices of pixel coordinate x along one axis: regular k
 // with kS <= x < kS + P, plus the ragged one.
-__device__ __forceinline__ void cover(int x, int n, int P, int S, int kreg, int np, int &lo,
+// rS = 1/S (udiv_small).
+__device__ __forceinline__ void cover(int x, int n, int P, int S, float rS, int kreg, int np, int &lo,
                                       int &hi, bool &ext) {
-    lo = x - P + 1 > 0 ? (x - P + 1 + S - 1) / S : 0;
-    hi = min(kreg - 1, x / S);
+    lo = x - P + 1 > 0 ? udiv_small(x - P + 1 + S - 1, rS) : 0;
+    hi = min(kreg - 1, udiv_small(x, rS));
     ext = np > kreg && x >= n - P;
 }
 
@@ -1219,22 +1211,24 @@ __device__ __forceinline__ void fuse_unit(const LaunchArgs &a, int unit, float4 
     // as far as the compiler knows, which would reload its fields per pixel
     const LevelDesc D = a.descs[find_pair(a.descs, a.npairs, unit, W_FUSE)];
     const int tile = unit - D.work_begin[W_FUSE];
-    const int tx = tile % D.tiles_x, ty = tile / D.tiles_x;
+    const int ty = udiv_small(tile, recip(D.tiles_x)), tx = tile - ty * D.tiles_x;
+    const float rS = recip(S);
     const int x0 = tx * TW, y0 = ty * TH;
     const int x1 = min(x0 + TW, D.w) - 1, y1 = min(y0 + TH, D.h) - 1;
     // patches overlapping the tile
     int kxlo, kxhi, kylo, kyhi, tmp;
     bool kxext, kyext, bext;
-    cover(x0, D.w, P, S, D.kxreg, D.npx, kxlo, tmp, bext);
-    cover(x1, D.w, P, S, D.kxreg, D.npx, tmp, kxhi, kxext);
-    cover(y0, D.h, P, S, D.kyreg, D.npy, kylo, tmp, bext);
-    cover(y1, D.h, P, S, D.kyreg, D.npy, tmp, kyhi, kyext);
+    cover(x0, D.w, P, S, rS, D.kxreg, D.npx, kxlo, tmp, bext);
+    cover(x1, D.w, P, S, rS, D.kxreg, D.npx, tmp, kxhi, kxext);
+    cover(y0, D.h, P, S, rS, D.kyreg, D.npy, kylo, tmp, bext);
+    cover(y1, D.h, P, S, rS, D.kyreg, D.npy, tmp, kyhi, kyext);
     const int nkxr = max(0, kxhi - kxlo + 1), nkyr = max(0, kyhi - kylo + 1);
     const int nkx = nkxr + (kxext ? 1 : 0);
     const int nky = nkyr + (kyext ? 1 : 0);
+    const float rnkx = recip(nkx);
     // the first patch's posterior inputs are loaded before sigma_r is known
     auto patch_of = [&](int i, int &kx, int &ky) {
-        const int ix = i % nkx, iy = i / nkx;
+        const int iy = udiv_small(i, rnkx), ix = i - iy * nkx;
         kx = ix < nkxr ? kxlo + ix : D.npx - 1;
         ky = iy < nkyr ? kylo + iy : D.npy - 1;
     };
@@ -1294,7 +1288,7 @@ __device__ __forceinline__ void fuse_unit(const LaunchArgs &a, int unit, float4 
         const int klo = col ? kxlo : kylo, nr = col ? nkxr : nkyr, nt = col ? nkx : nky;
         int lo = 0, hi = -1;
         bool ext = false;
-        if (xy < n) cover(xy, n, P, S, kreg, np, lo, hi, ext);
+        if (xy < n) cover(xy, n, P, S, rS, kreg, np, lo, hi, ext);
         const int cnt = xy < n ? max(0, hi - lo + 1) + (ext ? 1 : 0) : 0;
         float *mrow = col ? cxm[c] : cym[c];
         for (int q = 0; q < cnt; ++q) {
@@ -1509,7 +1503,7 @@ __global__ void __launch_bounds__(256) k_depth(const float *__restrict__ disp,
 }
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(256) k_fuse(LaunchArgs a) {
+__global__ void __launch_bounds__(256, 4) k_fuse(LaunchArgs a) {
     extern __shared__ float4 fz[];
     pdl_enter(a);
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) fuse_unit<TW, TH>(a, unit, fz);
