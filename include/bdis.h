@@ -293,7 +293,7 @@ typedef enum {
     BDIS_OPT_PROFILE = 2,
     /* 1 (default): on the first call of a geometry (pair count and sizes),
      * time the candidate launch configurations (search patches per block,
-     * fusion tile size) level by level, each twice, and keep the fastest; the
+     * fusion tile size) level by level, each five times, and keep the fastest; the
      * call waits for the timing runs.  All configurations compute identical results.
      * 0: the default configuration.  Never tunes while the stream is being
      * captured. */

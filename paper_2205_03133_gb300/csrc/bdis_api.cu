@@ -813,12 +813,13 @@ bdis_status autotune(bdis_handle *h, int n, const bdis_pair *pairs, int in_type,
     std::vector<LevelCfg> cfg((size_t)NL, kDefaultCfg);
     bdis_status s = run_cfg(h, n, pairs, in_type, st, cfg.data(), false, false);  // warm-up
     if (s != BDIS_OK) return s;
-    // every candidate is timed twice (interleaved) and keeps its faster run,
-    // so that one noisy timing does not decide a level's configuration
+    // every candidate is timed five times (interleaved) and keeps its fastest
+    // run, so that noisy timings of short launches do not decide a level's
+    // configuration
     double tsearch[3][kMaxLevels], tfuse[3][kMaxLevels];
     for (int c = 0; c < 3; ++c)
         for (int l = 0; l < kMaxLevels; ++l) tsearch[c][l] = tfuse[c][l] = 1e30;
-    for (int it = 0; it < 6; ++it) {
+    for (int it = 0; it < 15; ++it) {
         const int c = it % 3;
         for (int l = 0; l < NL; ++l) cfg[l] = kSearchCands[c];
         const size_t m0 = h->ev_marks.size();

