@@ -804,9 +804,6 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
         // correlations of gt with the row at integer offsets base and base + 1;
         // they change only when d crosses an integer, so the warp recomputes
         // them only when one of its patches did.
-        // The state of a step is d alone: once no patch of the warp has moved
-        // (d bitwise unchanged), every remaining step would repeat the same
-        // values, so the loop stops with the result of all `iters` steps.
         float d = dinit, dlast = 0.f;
         int offc = INT_MIN;
         float At = 0.f, Bt = 0.f;
@@ -828,15 +825,11 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
                 offc = off;
             }
             const float s = fmaf(t, Bt - At, At);
-            bool still = true;
             if (!flat) {
                 const float delta = (s - cT) * invH;
-                const float dn = fminf(fmaxf(d + delta, -dlim), dlim);
-                still = dn == d;
-                d = dn;
+                d = fminf(fmaxf(d + delta, -dlim), dlim);
                 dlast = delta;
             }
-            if (__all_sync(0xffffffffu, still)) break;
         }
 
         // window energies.  E(0) in two passes; for the four offsets the
