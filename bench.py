@@ -572,7 +572,10 @@ def main():
         if prof.launches[i]:
             kernels[name] = {"launches_per_step": prof.launches[i] // n_prof,
                              "ms_per_step": prof.ms[i] / n_prof,
-                             "avg_launch_us": prof.ms[i] / prof.launches[i] * 1e3}
+                             "avg_launch_us": prof.ms[i] / prof.launches[i] * 1e3,
+                             "us_per_launch_by_level": {
+                                 str(l): round(prof.ms_level[i][l] / prof.launches_level[i][l] * 1e3, 3)
+                                 for l in range(8) if prof.launches_level[i][l]}}
     launches_per_step = sum(k["launches_per_step"] for k in kernels.values())
     tot_k = sum(k["ms_per_step"] for k in kernels.values())
     for k in kernels.values():

@@ -377,6 +377,10 @@ enum { BDIS_K_PYRAMID = 0, BDIS_K_SEARCH = 1, BDIS_K_FUSE = 2, BDIS_K_PERSISTENT
 typedef struct {
     int launches[BDIS_K_COUNT];   /* launches per kernel since the last reset */
     double ms[BDIS_K_COUNT];      /* summed CUDA-event time per kernel (ms)   */
+    int launches_level[BDIS_K_COUNT][8];  /* the same per pyramid level of the  */
+    double ms_level[BDIS_K_COUNT][8];     /* launch (a pyramid launch counts at
+                                             the level it reads; a persistent
+                                             launch at its first stage's level) */
 } bdis_profile;
 
 /* Per-kernel launch counts and event times accumulated while

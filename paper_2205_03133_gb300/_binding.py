@@ -81,7 +81,8 @@ class bdis_grad(C.Structure):
 
 
 class bdis_profile(C.Structure):
-    _fields_ = [("launches", C.c_int * 5), ("ms", C.c_double * 5)]
+    _fields_ = [("launches", C.c_int * 5), ("ms", C.c_double * 5),
+                ("launches_level", (C.c_int * 8) * 5), ("ms_level", (C.c_double * 8) * 5)]
 
 
 OPT_GRAPH, OPT_PROFILE, OPT_AUTOTUNE, OPT_FORM, OPT_PDL, OPT_PYRAMID_STEPS, OPT_ADJOINT_LEVELS = (

@@ -98,9 +98,11 @@ struct bdis_handle {
     // per-kernel event timing
     bool profile = false;
     std::vector<cudaEvent_t> ev_pool;
-    std::vector<std::pair<int, size_t>> ev_marks;  // (kernel id, index of start event)
+    std::vector<std::pair<int, size_t>> ev_marks;  // (kernel id + 16 level, index of start event)
     int prof_launches[BDIS_K_COUNT] = {0};
     double prof_ms[BDIS_K_COUNT] = {0};
+    int prof_launches_level[BDIS_K_COUNT][kMaxLevels] = {{0}};
+    double prof_ms_level[BDIS_K_COUNT][kMaxLevels] = {{0}};
 };
 
 namespace {
@@ -697,7 +699,7 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
                 // on a cooperative launch (remembered per process)
                 static int pdl_ok = -1;
                 const bool try_pdl = h->use_pdl && pdl_ok != 0;
-                e = timed(BDIS_K_PERSISTENT, [&] {
+                e = timed(BDIS_K_PERSISTENT + 16 * stages[cm_first].level, [&] {
                     cudaError_t r = launch_mega(cm, p.patch, st_type, cm_grid, cm_smem, try_pdl, st);
                     if (r != cudaSuccess && try_pdl) {
                         cudaGetLastError();
@@ -713,7 +715,7 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
                 continue;
             }
             if (a.kind == 0 || a.kind == 4) {
-                e = timed(BDIS_K_PYRAMID, [&] {
+                e = timed(BDIS_K_PYRAMID + 16 * a.level, [&] {
                     return a.kind == 4 ? launch_pyramid2(a, itype, st_type, st)
                                        : launch_pyramid(a, itype, st_type, st);
                 });
@@ -722,13 +724,14 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
                 const size_t sm = ssm[a.level];
                 const int occ = search_occupancy(p.patch, itype, st_type, sm);
                 const int grid = std::max(1, std::min(a.total, sm_count() * occ));
-                e = timed(BDIS_K_SEARCH, [&] { return launch_search(a, itype, st_type, sm, grid, st); });
+                e = timed(BDIS_K_SEARCH + 16 * a.level,
+                          [&] { return launch_search(a, itype, st_type, sm, grid, st); });
                 if (e != cudaSuccess) return cuda_fail(h, e, "search launch");
             } else if (a.kind == 2) {
-                e = timed(BDIS_K_FUSE, [&] { return launch_fuse(a, fsm[a.level], st); });
+                e = timed(BDIS_K_FUSE + 16 * a.level, [&] { return launch_fuse(a, fsm[a.level], st); });
                 if (e != cudaSuccess) return cuda_fail(h, e, "fuse launch");
             } else {
-                e = timed(BDIS_K_UPSAMPLE, [&] { return launch_upsample(a, st); });
+                e = timed(BDIS_K_UPSAMPLE + 16 * a.level, [&] { return launch_upsample(a, st); });
                 if (e != cudaSuccess) return cuda_fail(h, e, "upsample launch");
             }
         }
@@ -833,7 +836,7 @@ bdis_status autotune(bdis_handle *h, int n, const bdis_pair *pairs, int in_type,
             cudaError_t e = cudaEventSynchronize(h->ev_pool[ev + 1]);
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, h->ev_pool[ev], h->ev_pool[ev + 1]);
             if (e != cudaSuccess) return cuda_fail(h, e, "autotune events");
-            const int kid = h->ev_marks[m].first;
+            const int kid = h->ev_marks[m].first & 15;
             if (kid == BDIS_K_SEARCH) {
                 double &t = tsearch[c][NL - 1 - ns++];
                 t = std::min(t, (double)ms);
@@ -1130,16 +1133,27 @@ bdis_status bdis_get_profile(bdis_handle *h, bdis_profile *out, int reset) {
         cudaError_t e = cudaEventSynchronize(h->ev_pool[mk.second + 1]);
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, h->ev_pool[mk.second], h->ev_pool[mk.second + 1]);
         if (e != cudaSuccess) return cuda_fail(h, e, "profile events");
-        h->prof_launches[mk.first] += 1;
-        h->prof_ms[mk.first] += ms;
+        const int kid = mk.first & 15, lvl = mk.first >> 4;
+        h->prof_launches[kid] += 1;
+        h->prof_ms[kid] += ms;
+        h->prof_launches_level[kid][lvl] += 1;
+        h->prof_ms_level[kid][lvl] += ms;
     }
     h->ev_marks.clear();
     for (int k = 0; k < BDIS_K_COUNT; ++k) {
         out->launches[k] = h->prof_launches[k];
         out->ms[k] = h->prof_ms[k];
+        for (int l = 0; l < kMaxLevels; ++l) {
+            out->launches_level[k][l] = h->prof_launches_level[k][l];
+            out->ms_level[k][l] = h->prof_ms_level[k][l];
+        }
         if (reset) {
             h->prof_launches[k] = 0;
             h->prof_ms[k] = 0.0;
+            for (int l = 0; l < kMaxLevels; ++l) {
+                h->prof_launches_level[k][l] = 0;
+                h->prof_ms_level[k][l] = 0.0;
+            }
         }
     }
     return BDIS_OK;
