@@ -46,8 +46,13 @@ typedef enum {
 } bdis_status;
 
 /* Storage type of the pyramid levels 1..L-1 and of the x-gradient images.
- * Level 0 is the caller's 8-bit image.  Arithmetic is FP32 in every case. */
-typedef enum { BDIS_STORE_F32 = 0, BDIS_STORE_F16 = 1 } bdis_storage;
+ * Level 0 is the caller's 8-bit image.  Arithmetic is FP32 in every case.
+ * U8: the pyramid levels as 8-bit integers (the FP32 blur rounded to the
+ * nearest integer, ties to even, within 0..255) and the gradients as FP16
+ * (Sobel-x/8 of 8-bit values is a multiple of 1/8 within +-127.5, which
+ * FP16 holds exactly).  Not available to the persistent and cooperative
+ * forms, to the adjoint through every level and to bdis_match_noalloc. */
+typedef enum { BDIS_STORE_F32 = 0, BDIS_STORE_F16 = 1, BDIS_STORE_U8 = 2 } bdis_storage;
 
 /* Reading of the dynamic scale sigma_r^(n) (text after Eq. 6):
  * POOLED  sqrt(sum_valid E_k(0) / (N_valid P^2)) -- the default;

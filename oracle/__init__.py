@@ -26,7 +26,7 @@ _lock = threading.Lock()
 _lib = None
 
 MAX_LEVELS = 8
-STORE = {"f64": 0, "f32": 1, "f16": 2}
+STORE = {"f64": 0, "f32": 1, "f16": 2, "u8": 3}
 SIGMA_R = {"pooled": 0, "literal": 1, "fixed": 2}
 WEIGHT = {"bdis": 0, "dis": 1}
 
@@ -83,6 +83,8 @@ def lib():
         vp = C.c_void_p
         L.ob_round_f16.restype = C.c_double
         L.ob_round_f16.argtypes = [C.c_double]
+        L.ob_round_u8.restype = C.c_double
+        L.ob_round_u8.argtypes = [C.c_double]
         L.ob_level_dim.argtypes = [C.c_int, C.c_int]
         L.ob_origins.argtypes = [C.c_int, C.c_int, C.c_int, vp]
         L.ob_gamma_weight.restype = C.c_double
@@ -169,6 +171,10 @@ def upsample_output(Df, Vf, okf, f: int, w: int, h: int):
 
 def round_f16(v: float) -> float:
     return lib().ob_round_f16(float(v))
+
+
+def round_u8(v: float) -> float:
+    return lib().ob_round_u8(float(v))
 
 
 def pyr_down(img: np.ndarray, storage: str = "f64") -> np.ndarray:

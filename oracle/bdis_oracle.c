@@ -35,8 +35,9 @@
 
 #define OB_MAX_LEVELS 8
 
-/* storage emulation for the pyramid and gradient images */
-enum { OB_STORE_F64 = 0, OB_STORE_F32 = 1, OB_STORE_F16 = 2 };
+/* storage emulation for the pyramid and gradient images; U8: pyramid images
+ * stored as 8-bit integers, gradients as binary16 */
+enum { OB_STORE_F64 = 0, OB_STORE_F32 = 1, OB_STORE_F16 = 2, OB_STORE_U8 = 3 };
 enum { OB_SIGMA_R_POOLED = 0, OB_SIGMA_R_LITERAL = 1, OB_SIGMA_R_FIXED = 2 };
 /* fusion weights: BDIS (Eq. 12, sGMM x probability) or DIS (Eq. 2, inverse
  * photometric residual) */
@@ -119,11 +120,27 @@ double ob_round_f16(double v)
     return copysign(q * ulp, v);
 }
 
+/* An 8-bit image value: the nearest integer, ties to even, clamped to
+ * [0, 255]. */
+double ob_round_u8(double v)
+{
+    double q = nearbyint(v); /* default rounding mode: nearest, ties even */
+    return q < 0.0 ? 0.0 : (q > 255.0 ? 255.0 : q);
+}
+
+/* Rounding of a stored pyramid image value. */
 double ob_round_storage(double v, int storage)
 {
     if (storage == OB_STORE_F32) return (double)(float)v;
     if (storage == OB_STORE_F16) return ob_round_f16(v);
+    if (storage == OB_STORE_U8) return ob_round_u8(v);
     return v;
+}
+
+/* Rounding of a stored gradient value (binary16 with 8-bit images). */
+static double round_grad_storage(double v, int storage)
+{
+    return ob_round_storage(v, storage == OB_STORE_U8 ? OB_STORE_F16 : storage);
 }
 
 /* ------------------------------------------------------------------ */
@@ -233,7 +250,7 @@ void ob_sobel_x(const double *src, int w, int h, double *g, int storage)
                 acc += wr[j + 1] * (src[(size_t)yy * w + reflect101(x + 1, w)] -
                                     src[(size_t)yy * w + reflect101(x - 1, w)]);
             }
-            g[(size_t)y * w + x] = ob_round_storage(acc / 8.0, storage);
+            g[(size_t)y * w + x] = round_grad_storage(acc / 8.0, storage);
         }
 }
 

@@ -19,7 +19,7 @@ from ._binding import BdisError
 
 __all__ = ["BDIS", "BdisError", "default_params", "B", "_grad_table", "depth", "SavedState"]
 
-_STORAGE = {"f32": B.STORE_F32, "f16": B.STORE_F16}
+_STORAGE = {"f32": B.STORE_F32, "f16": B.STORE_F16, "u8": B.STORE_U8}
 _SIGMA_R = {"pooled": B.SIGMA_R_POOLED, "literal": B.SIGMA_R_LITERAL, "fixed": B.SIGMA_R_FIXED}
 _WEIGHT = {"bdis": B.WEIGHT_BDIS, "dis": B.WEIGHT_DIS}
 
@@ -185,11 +185,11 @@ class BDIS:
         if level > 0:
             out["D"] = cp(v.D, np.float32, (v.h, v.w))
             out["Q"] = cp(v.Q, np.float32, (v.h, v.w))
-            dt = np.float16 if v.storage == B.STORE_F16 else np.float32
+            dt = {B.STORE_F16: np.float16, B.STORE_U8: np.uint8}.get(v.storage, np.float32)
             pitch = v.image_pitch
             for key, ptr in (("L", v.left), ("R", v.right)):
                 out[key] = cp(ptr, dt, (v.h, pitch))[:, :v.w].astype(np.float64)
-        gdt = np.float16 if self.params.storage == B.STORE_F16 else np.float32
+        gdt = np.float32 if self.params.storage == B.STORE_F32 else np.float16
         out["G"] = (cp(v.grad, gdt, (v.h, v.grad_pitch))[:, :v.w].astype(np.float64)
                     if v.grad else None)
         return out

@@ -14,7 +14,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "libbdis.so")
 
 BDIS_OK, BDIS_EINVAL, BDIS_ENOMEM, BDIS_ECUDA, BDIS_EUNSUPPORTED = range(5)
-STORE_F32, STORE_F16 = 0, 1
+STORE_F32, STORE_F16, STORE_U8 = 0, 1, 2
 SIGMA_R_POOLED, SIGMA_R_LITERAL, SIGMA_R_FIXED = 0, 1, 2
 WEIGHT_BDIS, WEIGHT_DIS = 0, 1
 

@@ -158,7 +158,8 @@ std::string check_params(const bdis_params &p) {
     if (p.variance != 0 && p.variance != 1) return "variance must be 0 or 1";
     if (p.pdf_iters < 0 || p.pdf_iters > 100) return "pdf_iters must be in [0, 100]";
     if (!finite_nonneg(p.pdf_resid)) return "pdf_resid must be >= 0";
-    if (p.storage != BDIS_STORE_F32 && p.storage != BDIS_STORE_F16) return "bad storage";
+    if (p.storage != BDIS_STORE_F32 && p.storage != BDIS_STORE_F16 && p.storage != BDIS_STORE_U8)
+        return "bad storage";
     if (!finite_nonneg(p.hess_eps)) return "hess_eps must be >= 0";
     if (p.use_sgmm != 0 && p.use_sgmm != 1) return "use_sgmm must be 0 or 1";
     if (p.use_c2f != 0 && p.use_c2f != 1) return "use_c2f must be 0 or 1";
@@ -260,7 +261,8 @@ struct Bump {
 void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, const LevelCfg *cfg,
                  Plan &pl, bool wsum) {
     const int NL = p.levels, P = p.patch, S = p.stride;
-    const size_t esz = p.storage == BDIS_STORE_F16 ? 2 : 4;
+    const size_t esz = elem_size(image_type_of(p.storage));  // pyramid images
+    const size_t gsz = elem_size(grad_type_of(p.storage));   // gradients
     const size_t cnt = (size_t)NL * n;
     pl.descs.assign(cnt, LevelDesc{});
     for (auto *v : {&pl.oG, &pl.oL, &pl.oR, &pl.oD, &pl.oQ, &pl.oV, &pl.oW, &pl.oRec, &pl.oFuse, &pl.oSr})
@@ -300,9 +302,10 @@ void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, const Leve
                 d.work_begin[q] = begin[q];
                 begin[q] += units[q];
             }
-            const size_t gp = align_up((size_t)d.w * esz, 128) / esz;
-            d.gpitch = (int)gp;
-            if (searched) pl.oG[k] = b.take(gp * esz * d.h);
+            const size_t gp = align_up((size_t)d.w * esz, 128) / esz;   // image pitch
+            const size_t ggp = align_up((size_t)d.w * gsz, 128) / gsz;  // gradient pitch
+            d.gpitch = (int)ggp;
+            if (searched) pl.oG[k] = b.take(ggp * gsz * d.h);
             if (l == F && F > 0 && p.variance) pl.oV[k] = b.take(sizeof(float) * (size_t)d.w * d.h);
             if (l == 0) {
                 d.pitch = pairs[i].pitch;
@@ -503,7 +506,8 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
         if (e == cudaSuccess) e = prepare_fuse(fmax);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute");
     }
-    const int st_type = p.storage == BDIS_STORE_F16 ? E_F16 : E_F32;
+    const int st_type = image_type_of(p.storage);  // pyramid levels 1..L-1
+    const int g_type = grad_type_of(p.storage);    // gradients
     LevelDesc *d_descs = (LevelDesc *)(h->arena + pl.off_desc);
     // stage list: the pyramid levels, then (search, fuse) per level coarse to fine
     std::vector<LaunchArgs> stages;
@@ -618,6 +622,8 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
         return cudaSuccess;
     };
 
+    if (mega && p.storage == BDIS_STORE_U8)
+        return fail(h, BDIS_EUNSUPPORTED, "no persistent form with 8-bit pyramids");
     if (mega) {
         // persistent form: one cooperative launch runs every stage
         const size_t msm = std::max(kPyr2SmemBytes, std::max(smax, fmax));
@@ -659,7 +665,7 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
     int cm_grid = 0;
     size_t cm_smem = 0;
     MegaArgs cm{};
-    if (mform > 0 && mega_supported(p.patch)) {
+    if (mform > 0 && mega_supported(p.patch) && p.storage != BDIS_STORE_U8) {
         const int lmin = NL - mform;
         for (size_t k = 0; k < stages.size(); ++k) {
             const LaunchArgs &a = stages[k];
@@ -716,16 +722,16 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
             }
             if (a.kind == 0 || a.kind == 4) {
                 e = timed(BDIS_K_PYRAMID + 16 * a.level, [&] {
-                    return a.kind == 4 ? launch_pyramid2(a, itype, st_type, st)
-                                       : launch_pyramid(a, itype, st_type, st);
+                    return a.kind == 4 ? launch_pyramid2(a, itype, st_type, g_type, st)
+                                       : launch_pyramid(a, itype, st_type, g_type, st);
                 });
                 if (e != cudaSuccess) return cuda_fail(h, e, "pyramid launch");
             } else if (a.kind == 1) {
                 const size_t sm = ssm[a.level];
-                const int occ = search_occupancy(p.patch, itype, st_type, sm);
+                const int occ = search_occupancy(p.patch, itype, g_type, sm);
                 const int grid = std::max(1, std::min(a.total, sm_count() * occ));
                 e = timed(BDIS_K_SEARCH + 16 * a.level,
-                          [&] { return launch_search(a, itype, st_type, sm, grid, st); });
+                          [&] { return launch_search(a, itype, g_type, sm, grid, st); });
                 if (e != cudaSuccess) return cuda_fail(h, e, "search launch");
             } else if (a.kind == 2) {
                 e = timed(BDIS_K_FUSE + 16 * a.level, [&] { return launch_fuse(a, fsm[a.level], st); });
@@ -967,7 +973,7 @@ bdis_status run_tuned(bdis_handle *h, int n, const bdis_pair *pairs, int in_type
             // finer searched level remains), and, for 8-bit inputs, every
             // stage in one persistent launch
             t.form = kFormLaunches;
-            if (mega_supported(h->p.patch) && st != nullptr) {
+            if (mega_supported(h->p.patch) && h->p.storage != BDIS_STORE_U8 && st != nullptr) {
                 float best = 0.f;
                 s = time_form(h, n, pairs, in_type, st, t.cfg.data(), kFormLaunches, 5, best);
                 if (s != BDIS_OK) return s;
@@ -995,7 +1001,8 @@ bdis_status run_tuned(bdis_handle *h, int n, const bdis_pair *pairs, int in_type
     }
     int form = t.form;
     if (h->form == 1) form = h->coarse_levels;
-    if (h->form == 2) form = (in_type == E_U8 && mega_supported(h->p.patch)) ? kFormPersistent
+    if (h->form == 2) form = (in_type == E_U8 && mega_supported(h->p.patch) &&
+                              h->p.storage != BDIS_STORE_U8) ? kFormPersistent
                                                                               : kFormLaunches;
     return run_cfg(h, n, pairs, in_type, st, t.cfg.data(), true, h->profile, form);
 }
@@ -1497,7 +1504,7 @@ bdis_status grad_setup(bdis_handle *h, const FwdView &fv, const bdis_grad *g, bo
             q.h = d.h;
             q.pitch = d.pitch;
             q.gpitch = d.gpitch;
-            q.gtype = p.storage == BDIS_STORE_F16 ? E_F16 : E_F32;
+            q.gtype = grad_type_of(p.storage);
             q.npx = d.npx;
             q.npy = d.npy;
             q.kxreg = d.kxreg;

@@ -14,6 +14,10 @@ __device__ __forceinline__ float ldf(const __half *p) { return __half2float(__ld
 
 __device__ __forceinline__ void stf(float *p, float v) { *p = v; }
 __device__ __forceinline__ void stf(__half *p, float v) { *p = __float2half_rn(v); }
+// an 8-bit image value: nearest integer, ties to even, within 0..255
+__device__ __forceinline__ void stf(uint8_t *p, float v) {
+    *p = (uint8_t)__float2uint_rn(fminf(fmaxf(v, 0.f), 255.f));
+}
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
@@ -49,6 +53,10 @@ __device__ __forceinline__ void st8(__half *p, const float *v) {
 // Two consecutive values; p aligned to two elements.
 __device__ __forceinline__ void st2(float *p, float a, float b) { *(float2 *)p = make_float2(a, b); }
 __device__ __forceinline__ void st2(__half *p, float a, float b) { *(__half2 *)p = __floats2half2_rn(a, b); }
+__device__ __forceinline__ void st2(uint8_t *p, float a, float b) {
+    *(uchar2 *)p = make_uchar2((uint8_t)__float2uint_rn(fminf(fmaxf(a, 0.f), 255.f)),
+                               (uint8_t)__float2uint_rn(fminf(fmaxf(b, 0.f), 255.f)));
+}
 
 // Programmatic dependent launch.  A kernel launched with programmatic stream
 // serialisation may start while its predecessor on the stream still runs;

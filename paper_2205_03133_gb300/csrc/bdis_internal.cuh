@@ -43,6 +43,13 @@ constexpr float kSigmaFix1 = 65536.f;
 // Element types of the level images.
 enum ElemType { E_U8 = 0, E_F32 = 1, E_F16 = 2 };
 
+// Element type of the stored pyramid levels 1..L-1 and of the gradients.
+inline int image_type_of(int storage) {
+    return storage == BDIS_STORE_F16 ? E_F16 : storage == BDIS_STORE_U8 ? E_U8 : E_F32;
+}
+inline int grad_type_of(int storage) { return storage == BDIS_STORE_F32 ? E_F32 : E_F16; }
+inline size_t elem_size(int type) { return type == E_U8 ? 1 : type == E_F16 ? 2 : 4; }
+
 // One (pair, level).  All pointers are device pointers.
 struct alignas(16) LevelDesc {
     const void *L, *R;        // level images (level 0: caller's 8-bit images)
@@ -187,9 +194,11 @@ cudaError_t launch_bwd_sobel(const GradArgs &a, cudaStream_t s);
 cudaError_t launch_bwd_pyr(const GradArgs &a, cudaStream_t s);   // pyramid transpose into this level
 
 // Kernel launchers (bdis_kernels.cu).  Each returns cudaGetLastError().
-cudaError_t launch_pyramid(const LaunchArgs &a, int in_type, int out_type, cudaStream_t s);
+// in_type: the images the launch reads; img_type: the next levels it
+// writes; g_type: the gradients it writes.
+cudaError_t launch_pyramid(const LaunchArgs &a, int in_type, int img_type, int g_type, cudaStream_t s);
 // Two pyramid steps (level l -> l+1 -> l+2, with both gradients) per launch.
-cudaError_t launch_pyramid2(const LaunchArgs &a, int in_type, int out_type, cudaStream_t s);
+cudaError_t launch_pyramid2(const LaunchArgs &a, int in_type, int img_type, int g_type, cudaStream_t s);
 cudaError_t launch_search(const LaunchArgs &a, int in_type, int g_type, size_t smem, int grid,
                           cudaStream_t s);
 cudaError_t launch_fuse(const LaunchArgs &a, size_t smem, cudaStream_t s);

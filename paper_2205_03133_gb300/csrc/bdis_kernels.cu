@@ -145,14 +145,14 @@ __device__ __forceinline__ void pyramid_stage_loads(const LevelDesc &D, int tx, 
 
 // Sobel-x/8 of L over the 64 x 32 tile and the blurred, decimated 32 x 16
 // tile of the next level of L and R, from the staged region.
-template <typename TO>
+template <typename TN, typename TG>
 __device__ __forceinline__ void pyramid_compute(const LevelDesc &D, int tx, int ty,
                                                 float (*Ls)[kPyrSP], float (*Rs)[kPyrSP],
                                                 float (*Lh)[kPyrHP], float (*Rh)[kPyrHP]) {
     const int w = D.w, h = D.h;
     const bool next = D.Ln != nullptr;
     const int tid = threadIdx.x;
-    TO *G = (TO *)D.G;  // nullptr below the finest processed level
+    TG *G = (TG *)D.G;  // nullptr below the finest processed level
     if (G != nullptr) {
         // pixels lx0 .. lx0 + 7 of row ly: staged columns lx0 + 3 .. lx0 + 12
         // of rows ly + 1 .. ly + 3.  A quarter warp takes eight rows of one
@@ -180,7 +180,7 @@ __device__ __forceinline__ void pyramid_compute(const LevelDesc &D, int tx, int 
                                   (u[2][j + 2] - u[2][j]);
                 g[j] = acc * 0.125f;
             }
-            TO *gp = G + (size_t)y * D.gpitch + x;
+            TG *gp = G + (size_t)y * D.gpitch + x;
             if (x + 8 <= w && (((uintptr_t)gp) & 15u) == 0) {
                 st8(gp, g);
             } else {
@@ -236,10 +236,10 @@ __device__ __forceinline__ void pyramid_compute(const LevelDesc &D, int tx, int 
                     aR0 += k[j] * r2.x;
                     aR1 += k[j] * r2.y;
                 }
-                TO *lp = (TO *)D.Ln + (size_t)Y * D.pitchn + X;
-                TO *rp = (TO *)D.Rn + (size_t)Y * D.pitchn + X;
+                TN *lp = (TN *)D.Ln + (size_t)Y * D.pitchn + X;
+                TN *rp = (TN *)D.Rn + (size_t)Y * D.pitchn + X;
                 const float s = 1.f / 256.f;
-                if (X + 1 < D.wn && ((((uintptr_t)lp) | ((uintptr_t)rp)) & (2 * sizeof(TO) - 1)) == 0) {
+                if (X + 1 < D.wn && ((((uintptr_t)lp) | ((uintptr_t)rp)) & (2 * sizeof(TN) - 1)) == 0) {
                     st2(lp, aL0 * s, aL1 * s);
                     st2(rp, aR0 * s, aR1 * s);
                 } else {
@@ -255,7 +255,7 @@ __device__ __forceinline__ void pyramid_compute(const LevelDesc &D, int tx, int 
     }
 }
 
-template <typename TI, typename TO>
+template <typename TI, typename TN, typename TG>
 __device__ __forceinline__ void pyramid_unit(const LaunchArgs &a, int unit, float (*Ls)[kPyrSP],
                                              float (*Rs)[kPyrSP], float (*Lh)[kPyrHP],
                                              float (*Rh)[kPyrHP], int &hint) {
@@ -268,7 +268,7 @@ __device__ __forceinline__ void pyramid_unit(const LaunchArgs &a, int unit, floa
     __syncthreads();  // the previous unit's readers are done with the staged region
     pyramid_stage_loads<TI>(D, tx, ty, Ls, Rs);
     __syncthreads();
-    pyramid_compute<TO>(D, tx, ty, Ls, Rs, Lh, Rh);
+    pyramid_compute<TN, TG>(D, tx, ty, Ls, Rs, Lh, Rh);
 }
 
 // Two pyramid steps in one unit: a 64x32 tile of level l gives its Sobel-x,
@@ -287,10 +287,11 @@ static_assert(kPyr2SmemFloats * sizeof(float) == kPyr2SmemBytes, "two-step pyram
 template <typename TO>
 __device__ __forceinline__ float round_to(float v) {
     if constexpr (sizeof(TO) == 2) return __half2float(__float2half_rn(v));
+    if constexpr (sizeof(TO) == 1) return (float)__float2uint_rn(fminf(fmaxf(v, 0.f), 255.f));
     return v;
 }
 
-template <typename TI, typename TO>
+template <typename TI, typename TN, typename TG>
 __device__ __forceinline__ void pyramid2_unit(const LaunchArgs &a, int unit, float *sm) {
     float(*Ls)[kPyr2SW] = (float(*)[kPyr2SW])sm;
     float(*Rs)[kPyr2SW] = Ls + kPyr2SH;
@@ -336,7 +337,7 @@ __device__ __forceinline__ void pyramid2_unit(const LaunchArgs &a, int unit, flo
     }
     __syncthreads();
     // Sobel-x/8 of level l over the 64x32 tile
-    TO *G = (TO *)D.G;
+    TG *G = (TG *)D.G;
     for (int i = threadIdx.x; G != nullptr && i < kPyrTW * kPyrTH; i += blockDim.x) {
         const int ly = i / kPyrTW, lx = i - ly * kPyrTW;
         const int x = x0 + 6 + lx, y = y0 + 6 + ly;
@@ -377,17 +378,17 @@ __device__ __forceinline__ void pyramid2_unit(const LaunchArgs &a, int unit, flo
             accR += k5[j] * Rh[cy + j - 2][mx];
         }
         const float vL = accL * (1.f / 256.f), vR = accR * (1.f / 256.f);
-        Lm[my][mx] = round_to<TO>(vL);
-        Rm[my][mx] = round_to<TO>(vR);
+        Lm[my][mx] = round_to<TN>(vL);
+        Rm[my][mx] = round_to<TN>(vR);
         const bool own = mx >= 2 && mx < 2 + kPyrTW / 2 && my >= 2 && my < 2 + kPyrTH / 2;
         if (own && X < w1 && Y < h1) {
-            stf((TO *)D.Ln + (size_t)Y * D.pitchn + X, vL);
-            stf((TO *)D.Rn + (size_t)Y * D.pitchn + X, vR);
+            stf((TN *)D.Ln + (size_t)Y * D.pitchn + X, vL);
+            stf((TN *)D.Rn + (size_t)Y * D.pitchn + X, vR);
         }
     }
     __syncthreads();
     // Sobel-x/8 of level l+1 over its 32x16 tile
-    TO *G1 = (TO *)E.G;
+    TG *G1 = (TG *)E.G;
     for (int i = threadIdx.x; G1 != nullptr && i < (kPyrTW / 2) * (kPyrTH / 2); i += blockDim.x) {
         const int ly = i / (kPyrTW / 2), lx = i - ly * (kPyrTW / 2);
         const int X = X0 + 2 + lx, Y = Y0 + 2 + ly;
@@ -416,22 +417,22 @@ __device__ __forceinline__ void pyramid2_unit(const LaunchArgs &a, int unit, flo
             accL += k5[j] * sl;
             accR += k5[j] * sr;
         }
-        stf((TO *)E.Ln + (size_t)Y * E.pitchn + X, accL * (1.f / 256.f));
-        stf((TO *)E.Rn + (size_t)Y * E.pitchn + X, accR * (1.f / 256.f));
+        stf((TN *)E.Ln + (size_t)Y * E.pitchn + X, accL * (1.f / 256.f));
+        stf((TN *)E.Rn + (size_t)Y * E.pitchn + X, accR * (1.f / 256.f));
     }
 }
 
-template <typename TI, typename TO>
+template <typename TI, typename TN, typename TG>
 __global__ void __launch_bounds__(256) k_pyramid2(LaunchArgs a) {
     __shared__ float sm[kPyr2SmemFloats];
     pdl_enter(a);
     if (blockIdx.x == 0 && a.acc_zero != nullptr)
         for (int i = threadIdx.x; i < a.acc_count; i += blockDim.x) a.acc_zero[i] = 0ull;
-    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) pyramid2_unit<TI, TO>(a, unit, sm);
+    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) pyramid2_unit<TI, TN, TG>(a, unit, sm);
     pdl_leave(a);
 }
 
-template <typename TI, typename TO>
+template <typename TI, typename TN, typename TG>
 __global__ void __launch_bounds__(256, 4) k_pyramid(LaunchArgs a) {
     __shared__ __align__(16) float Ls[kPyrSH][kPyrSP];
     __shared__ __align__(16) float Rs[kPyrSH][kPyrSP];
@@ -444,7 +445,7 @@ __global__ void __launch_bounds__(256, 4) k_pyramid(LaunchArgs a) {
         for (int i = threadIdx.x; i < a.acc_count; i += blockDim.x) a.acc_zero[i] = 0ull;
     int hint = -1;
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x)
-        pyramid_unit<TI, TO>(a, unit, Ls, Rs, Lh, Rh, hint);
+        pyramid_unit<TI, TN, TG>(a, unit, Ls, Rs, Lh, Rh, hint);
     pdl_leave(a);
 }
 
@@ -488,7 +489,7 @@ __device__ __forceinline__ float4 raw4(const __half *p) {
 }
 __device__ __forceinline__ float4 raw4(const float *p) { return *(const float4 *)p; }
 
-template <typename TI, typename TO>
+template <typename TI, typename TN, typename TG>
 __global__ void __launch_bounds__(256, 4) k_pyramid_bulk(LaunchArgs a) {
     using PB = PyrBulk<TI>;
     __shared__ __align__(16) float Ls[kPyrSH][kPyrSP];
@@ -593,7 +594,7 @@ __global__ void __launch_bounds__(256, 4) k_pyramid_bulk(LaunchArgs a) {
             pyramid_stage_loads<TI>(*cur.D, cur.tx, cur.ty, Ls, Rs);
         }
         __syncthreads();
-        pyramid_compute<TO>(*cur.D, cur.tx, cur.ty, Ls, Rs, Lh, Rh);
+        pyramid_compute<TN, TG>(*cur.D, cur.tx, cur.ty, Ls, Rs, Lh, Rh);
         cur = nxt;
     }
     pdl_leave(a);
@@ -1569,17 +1570,17 @@ __global__ void __launch_bounds__(256) k_mega(MegaArgs m) {
             float(*Rh)[kPyrHP] = Lh + kPyrSH;
             if (a.level == 0) {
                 for (int u = blockIdx.x; u < total; u += gridDim.x)
-                    pyramid_unit<uint8_t, TG>(a, u, Ls, Rs, Lh, Rh, hint);
+                    pyramid_unit<uint8_t, TG, TG>(a, u, Ls, Rs, Lh, Rh, hint);
             } else {
-                for (int u = blockIdx.x; u < total; u += gridDim.x) pyramid_unit<TG, TG>(a, u, Ls, Rs, Lh, Rh, hint);
+                for (int u = blockIdx.x; u < total; u += gridDim.x) pyramid_unit<TG, TG, TG>(a, u, Ls, Rs, Lh, Rh, hint);
             }
         } else if (a.kind == 4) {
             if (blockIdx.x == 0 && a.acc_zero != nullptr)
                 for (int i = threadIdx.x; i < a.acc_count; i += blockDim.x) a.acc_zero[i] = 0ull;
             if (a.level == 0) {
-                for (int u = blockIdx.x; u < total; u += gridDim.x) pyramid2_unit<uint8_t, TG>(a, u, smem);
+                for (int u = blockIdx.x; u < total; u += gridDim.x) pyramid2_unit<uint8_t, TG, TG>(a, u, smem);
             } else {
-                for (int u = blockIdx.x; u < total; u += gridDim.x) pyramid2_unit<TG, TG>(a, u, smem);
+                for (int u = blockIdx.x; u < total; u += gridDim.x) pyramid2_unit<TG, TG, TG>(a, u, smem);
             }
         } else if (a.kind == 1) {
             if (a.level == 0) {
@@ -1801,9 +1802,9 @@ int resident_blocks(const void *f, size_t smem) {
     return nb;
 }
 
-template <typename TI, typename TO>
+template <typename TI, typename TN, typename TG>
 cudaError_t launch_pyramid_bulk(const LaunchArgs &a, cudaStream_t s) {
-    const void *f = (const void *)k_pyramid_bulk<TI, TO>;
+    const void *f = (const void *)k_pyramid_bulk<TI, TN, TG>;
     const size_t smem = PyrBulk<TI>::kSmem;
     const cudaError_t e = raise_smem_limit(f, smem);
     if (e != cudaSuccess) return e;
@@ -1811,37 +1812,56 @@ cudaError_t launch_pyramid_bulk(const LaunchArgs &a, cudaStream_t s) {
     // one in flight
     return launch_args_kernel(f, a, grid_for(a.total, resident_blocks(f, smem)), smem, s);
 }
+
+// The (read, next level, gradient) element types of a pyramid launch: FP32
+// or FP16 pyramids with gradients of the same type, or 8-bit pyramids with
+// FP16 gradients; the images read are the level-0 input (8-bit or FP32) or
+// the stored type.
+#define BDIS_PYR_TYPES(X)                                                                  \
+    X(E_U8, E_F32, E_F32, uint8_t, float, float)                                           \
+    X(E_F32, E_F32, E_F32, float, float, float)                                            \
+    X(E_U8, E_F16, E_F16, uint8_t, __half, __half)                                         \
+    X(E_F32, E_F16, E_F16, float, __half, __half)                                          \
+    X(E_F16, E_F16, E_F16, __half, __half, __half)                                         \
+    X(E_U8, E_U8, E_F16, uint8_t, uint8_t, __half)                                         \
+    X(E_F32, E_U8, E_F16, float, uint8_t, __half)
+
+const void *pyramid_kernel(int in_type, int img_type, int g_type) {
+#define BDIS_PYR_CASE(a, b, c, TI, TN, TG) \
+    if (in_type == a && img_type == b && g_type == c) return (const void *)k_pyramid<TI, TN, TG>;
+    BDIS_PYR_TYPES(BDIS_PYR_CASE)
+#undef BDIS_PYR_CASE
+    return nullptr;
+}
+
+const void *pyramid2_kernel(int in_type, int img_type, int g_type) {
+#define BDIS_PYR_CASE(a, b, c, TI, TN, TG) \
+    if (in_type == a && img_type == b && g_type == c) return (const void *)k_pyramid2<TI, TN, TG>;
+    BDIS_PYR_TYPES(BDIS_PYR_CASE)
+#undef BDIS_PYR_CASE
+    return nullptr;
+}
+
+cudaError_t launch_pyramid_bulk_typed(const LaunchArgs &a, int in_type, int img_type, int g_type,
+                                      cudaStream_t s) {
+#define BDIS_PYR_CASE(a_, b, c, TI, TN, TG) \
+    if (in_type == a_ && img_type == b && g_type == c) return launch_pyramid_bulk<TI, TN, TG>(a, s);
+    BDIS_PYR_TYPES(BDIS_PYR_CASE)
+#undef BDIS_PYR_CASE
+    return cudaErrorInvalidValue;
+}
 }  // namespace
 
-cudaError_t launch_pyramid(const LaunchArgs &a, int in_type, int out_type, cudaStream_t s) {
-    if (a.bulk) {
-        if (out_type == E_F32)
-            return in_type == E_U8 ? launch_pyramid_bulk<uint8_t, float>(a, s)
-                                   : launch_pyramid_bulk<float, float>(a, s);
-        return in_type == E_U8    ? launch_pyramid_bulk<uint8_t, __half>(a, s)
-               : in_type == E_F32 ? launch_pyramid_bulk<float, __half>(a, s)
-                                  : launch_pyramid_bulk<__half, __half>(a, s);
-    }
-    const void *f = nullptr;
-    if (out_type == E_F32) {
-        f = in_type == E_U8 ? (const void *)k_pyramid<uint8_t, float> : (const void *)k_pyramid<float, float>;
-    } else {
-        f = in_type == E_U8    ? (const void *)k_pyramid<uint8_t, __half>
-            : in_type == E_F32 ? (const void *)k_pyramid<float, __half>
-                               : (const void *)k_pyramid<__half, __half>;
-    }
+cudaError_t launch_pyramid(const LaunchArgs &a, int in_type, int img_type, int g_type, cudaStream_t s) {
+    if (a.bulk) return launch_pyramid_bulk_typed(a, in_type, img_type, g_type, s);
+    const void *f = pyramid_kernel(in_type, img_type, g_type);
+    if (f == nullptr) return cudaErrorInvalidValue;
     return launch_args_kernel(f, a, grid_for(a.total, 8), 0, s);
 }
 
-cudaError_t launch_pyramid2(const LaunchArgs &a, int in_type, int out_type, cudaStream_t s) {
-    const void *f = nullptr;
-    if (out_type == E_F32) {
-        f = in_type == E_U8 ? (const void *)k_pyramid2<uint8_t, float> : (const void *)k_pyramid2<float, float>;
-    } else {
-        f = in_type == E_U8    ? (const void *)k_pyramid2<uint8_t, __half>
-            : in_type == E_F32 ? (const void *)k_pyramid2<float, __half>
-                               : (const void *)k_pyramid2<__half, __half>;
-    }
+cudaError_t launch_pyramid2(const LaunchArgs &a, int in_type, int img_type, int g_type, cudaStream_t s) {
+    const void *f = pyramid2_kernel(in_type, img_type, g_type);
+    if (f == nullptr) return cudaErrorInvalidValue;
     return launch_args_kernel(f, a, grid_for(a.total, 8), 0, s);
 }
 

@@ -93,8 +93,9 @@ extern "C" bdis_status bdis_match_noalloc(const bdis_params *pp, const uint8_t *
     const bdis_pair q{left, right, w, hgt, pitch, disp, var, valid};
     if (!check_pair(p, q).empty()) return BDIS_EINVAL;
     const int NL = p.levels, P = p.patch, S = p.stride;
-    // full resolution only: the upsampled form (finest_level > 0) needs bdis_match
-    if (p.finest_level != 0) return BDIS_EUNSUPPORTED;
+    // full resolution and FP32 / FP16 pyramids only (the upsampled form and
+    // 8-bit pyramids need bdis_match)
+    if (p.finest_level != 0 || p.storage == BDIS_STORE_U8) return BDIS_EUNSUPPORTED;
 
     // ---- layout inside the scratch array (no heap use)
     DescTable tab;
@@ -250,7 +251,8 @@ extern "C" bdis_status bdis_match_noalloc(const bdis_params *pp, const uint8_t *
         a.total = units[l][W_PYR];
         a.acc_zero = l == 0 ? (unsigned long long *)(base + off_acc) : nullptr;
         a.acc_count = l == 0 ? 3 * kMaxLevels : 0;
-        if (launch_pyramid(a, l == 0 ? E_U8 : st_type, st_type, st) != cudaSuccess) return BDIS_ECUDA;
+        if (launch_pyramid(a, l == 0 ? E_U8 : st_type, st_type, st_type, st) != cudaSuccess)
+            return BDIS_ECUDA;
     }
     for (int l = NL - 1; l >= 0; --l) {
         a.descs = d_descs + l;

@@ -33,7 +33,7 @@ V_RTOL = 1e-3
 # twice that: the variance gate of this mode is 5e-3.
 V_RTOL_DIS = 5e-3
 
-STORE_NAMES = {0: "f32", 1: "f16"}
+STORE_NAMES = {0: "f32", 1: "f16", 2: "u8"}
 
 
 def oracle_params(gp, storage_override=None):

@@ -733,3 +733,24 @@ def test_depth_invalid_pixels_are_nan():
     z, zv = oracle.depth(d, v, 10.0)
     assert np.all(np.isnan(z[:4])) and np.all(np.isnan(zv[:4]))
     assert z[4] == 2.0 and zv[4] == 100.0 / 625.0
+
+
+# ---------------------------------------------------------------- 8-bit storage
+
+def test_round_u8_is_numpy_rint_clipped():
+    # numpy's rint rounds half to even; the stored value is clipped to 0..255
+    vals = np.concatenate([np.arange(-3, 259, 0.25), np.arange(0, 256) + 0.5,
+                           np.random.default_rng(1).uniform(-10, 270, 3000)])
+    for v in vals:
+        assert oracle.round_u8(v) == float(np.clip(np.rint(v), 0, 255)), v
+
+
+def test_pyr_down_u8_storage_rounds_each_level_and_gradient_is_exact_f16():
+    rng = np.random.default_rng(2)
+    img = rng.integers(0, 256, (18, 22)).astype(float)
+    a = oracle.pyr_down(img, "u8")
+    b = np.clip(np.rint(oracle.pyr_down(img, "f64")), 0, 255)
+    assert np.array_equal(a, b)
+    # Sobel/8 of an 8-bit image is a multiple of 1/8 within +-127.5, which
+    # binary16 holds exactly: the stored gradient equals the exact one
+    np.testing.assert_array_equal(oracle.sobel_x(a, "u8"), oracle.sobel_x(a, "f64"))

@@ -111,6 +111,56 @@ def test_ragged_and_parameter_cases(bd, w, h, kw):
     _check_pair(bd, kw, pair)
 
 
+def test_pyramid_and_gradient_u8(bd):
+    # 8-bit pyramid levels (nearest integer, ties to even) and FP16 gradients
+    pair = synth.g1_pair(250, 130, 4)
+    kw = dict(patch=12, stride=4, levels=3, iters=8, storage="u8")
+    g = _run(bd, kw, pair.left, pair.right)
+    o = oracle.match(oracle_params(g["params"]), pair.left, pair.right, trace=True)
+    for l in range(3):
+        gv, ov = g["levels"][l], o["levels"][l]
+        keys = ("G", "L", "R") if l > 0 else ("G",)
+        for k in keys:
+            diff = np.abs(gv[k] - ov[k])
+            # equal except where the FP32 blur and the FP64 one round to
+            # different integers (a value within rounding of a half step)
+            assert (diff > 0).mean() <= 0.01, (l, k, (diff > 0).mean())
+            assert diff.max() <= (1.0 if k != "G" else 0.5), (l, k, diff.max())
+        if l > 0:
+            assert np.array_equal(gv["L"], np.round(gv["L"]))  # integers 0..255
+            assert gv["L"].min() >= 0 and gv["L"].max() <= 255
+
+
+@pytest.mark.parametrize("name,kw", [
+    ("plain_640x480_var", dict(patch=12, stride=6, levels=4, iters=8, variance=1, storage="u8")),
+    ("plain_320x240", dict(patch=8, stride=4, levels=3, iters=8, storage="u8")),
+])
+def test_u8_storage_workload_parity(bd, name, kw):
+    m = {}
+    _check_pair(bd, kw, synth.config_pair(name), m)
+    print(name, "u8 storage", m)
+
+
+def test_u8_storage_batched_equals_plain(bd):
+    import torch
+    sizes = [(160, 120), (97, 61), (256, 144)]
+    pairs = [synth.g1_pair(w, h, 200 + i) for i, (w, h) in enumerate(sizes)]
+    kw = dict(patch=8, stride=4, levels=2, iters=8, variance=1, storage="u8")
+    m = bd.BDIS(**kw)
+    Ls = [torch.from_numpy(p.left).cuda() for p in pairs]
+    Rs = [torch.from_numpy(p.right).cuda() for p in pairs]
+    res = m.match_batched(Ls, Rs)
+    torch.cuda.synchronize()
+    for i in range(len(pairs)):
+        one = bd.BDIS(**kw)
+        d, v, ok = one.match(Ls[i], Rs[i])
+        torch.cuda.synchronize()
+        assert torch.equal(ok, res[i][2])
+        assert torch.equal(torch.nan_to_num(d, nan=-1.0), torch.nan_to_num(res[i][0], nan=-1.0))
+        one.close()
+    m.close()
+
+
 def test_surgical_like_small(bd):
     pair = synth.g2_pair(320, 240, 5)
     _check_pair(bd, dict(patch=12, stride=6, levels=3, iters=8, variance=1), pair)
@@ -514,6 +564,37 @@ def test_modes_outside_the_adjoint_are_rejected(bd):
             m.loss_and_grad(0.1)
         assert e.value.status == bd.B.BDIS_EUNSUPPORTED
         m.close()
+
+
+def test_u8_storage_outside_the_cooperative_forms(bd):
+    # 8-bit pyramids have no persistent or coarse-level cooperative form: those
+    # options fall back to the launch sequence; the allocation-free entry
+    # point rejects them
+    import ctypes as C
+    import torch
+    pair = synth.g1_pair(160, 120, 8)
+    L = torch.from_numpy(pair.left).cuda()
+    R = torch.from_numpy(pair.right).cuda()
+    ref = bd.BDIS(patch=8, stride=4, levels=3, storage="u8")
+    d0, _, ok0 = ref.match(L, R)
+    for opt, val in ((bd.B.OPT_FORM, 2), (bd.B.OPT_COARSE_LEVELS, 2)):
+        m = bd.BDIS(patch=8, stride=4, levels=3, storage="u8")
+        if opt == bd.B.OPT_COARSE_LEVELS:
+            m.set_option(bd.B.OPT_FORM, 1)
+        m.set_option(opt, val)
+        d, _, ok = m.match(L, R)
+        torch.cuda.synchronize()
+        assert m.stats()["persistent"] == 0
+        assert torch.equal(ok, ok0)
+        assert torch.equal(torch.nan_to_num(d, nan=-1.0), torch.nan_to_num(d0, nan=-1.0))
+        m.close()
+    p = bd._params(patch=8, stride=4, levels=3, storage="u8")
+    out = torch.empty((120, 160), device="cuda")
+    okb = torch.empty((120, 160), dtype=torch.uint8, device="cuda")
+    rc = bd.B.lib().bdis_match_noalloc(C.byref(p), L.data_ptr(), R.data_ptr(), 160, 120, 160,
+                                        out.data_ptr(), None, okb.data_ptr(), None)
+    assert rc == bd.B.BDIS_EUNSUPPORTED
+    ref.close()
 
 
 def test_noalloc_rejects_finest_level(bd):
