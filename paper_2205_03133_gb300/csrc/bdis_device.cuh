@@ -156,17 +156,6 @@ __device__ __forceinline__ int find_pair(const LevelDesc *d, int n, int unit, in
     return lo;
 }
 
-// The same, starting from a hint (the pair of the block's previous unit: a
-// block walks its units in increasing order, so the hint usually holds and
-// costs two loads instead of a binary search).
-__device__ __forceinline__ int find_pair_from(const LevelDesc *d, int n, int unit, int kind, int &hint) {
-    const int h = hint;
-    if (!(h >= 0 && h < n && d[h].work_begin[kind] <= unit &&
-          (h + 1 >= n || d[h + 1].work_begin[kind] > unit)))
-        hint = find_pair(d, n, unit, kind);
-    return hint;
-}
-
 // Bilinear lookup of a coarse map at fine position (x, y): coarse
 // coordinate (x + 0.5)/2 - 0.5, clamped to the map.
 __device__ __forceinline__ float coarse_bilin(const float *__restrict__ m, int wc, int hc,

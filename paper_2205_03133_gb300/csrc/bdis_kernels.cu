@@ -258,10 +258,10 @@ __device__ __forceinline__ void pyramid_compute(const LevelDesc &D, int tx, int 
 template <typename TI, typename TN, typename TG>
 __device__ __forceinline__ void pyramid_unit(const LaunchArgs &a, int unit, float (*Ls)[kPyrSP],
                                              float (*Rs)[kPyrSP], float (*Lh)[kPyrHP],
-                                             float (*Rh)[kPyrHP], int &hint) {
+                                             float (*Rh)[kPyrHP]) {
     static_assert(kPyrTW * kPyrTH == 8 * 256 && (kPyrTW / 2) * (kPyrTH / 2) == 2 * 256,
                   "one Sobel segment and one blurred pair per thread");
-    const LevelDesc &D = a.descs[find_pair_from(a.descs, a.npairs, unit, W_PYR, hint)];
+    const LevelDesc &D = a.descs[find_pair(a.descs, a.npairs, unit, W_PYR)];
     const int tile = unit - D.work_begin[W_PYR];
     const int ntx = (D.w + kPyrTW - 1) / kPyrTW;
     const int ty = udiv_small(tile, recip(ntx)), tx = tile - ty * ntx;
@@ -443,9 +443,8 @@ __global__ void __launch_bounds__(256, 4) k_pyramid(LaunchArgs a) {
     // sigma_r accumulators of all levels and pairs
     if (blockIdx.x == 0 && a.acc_zero != nullptr)
         for (int i = threadIdx.x; i < a.acc_count; i += blockDim.x) a.acc_zero[i] = 0ull;
-    int hint = -1;
     for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x)
-        pyramid_unit<TI, TN, TG>(a, unit, Ls, Rs, Lh, Rh, hint);
+        pyramid_unit<TI, TN, TG>(a, unit, Ls, Rs, Lh, Rh);
     pdl_leave(a);
 }
 
@@ -637,7 +636,7 @@ __device__ __forceinline__ void block_minmax(float &lo, float &hi, float *red) {
 // of a warp executes the same instruction stream.  The groups of a warp take
 // patches spaced so that their rows fall in different shared-memory banks.
 template <int P, typename TI, typename TG>
-__device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float *smem, int &hint) {
+__device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float *smem) {
 
     constexpr int G = P <= 8 ? 8 : 16;
     constexpr int N = P * P;
@@ -665,7 +664,7 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
     const int margin = (int)ceilf(a.tau) + (int)ceilf(2.f * h) + 3;
 
 
-    const LevelDesc &D = a.descs[find_pair_from(a.descs, a.npairs, unit, W_SEARCH, hint)];
+    const LevelDesc &D = a.descs[find_pair(a.descs, a.npairs, unit, W_SEARCH)];
     const int u = unit - D.work_begin[W_SEARCH];
     const int py = udiv_small(u, recip(D.nchunks)), ch = u - py * D.nchunks;
     const int oy = origin(py, D.h, P, S, D.kyreg);
@@ -981,8 +980,7 @@ template <int P, typename TI, typename TG>
 __global__ void __launch_bounds__(256, (P <= 8 ? 3 : 2)) k_search(LaunchArgs a) {
     extern __shared__ float smem[];
     pdl_enter(a);
-    int hint = -1;
-    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) search_unit<P, TI, TG>(a, unit, smem, hint);
+    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) search_unit<P, TI, TG>(a, unit, smem);
     pdl_leave(a);
 }
 
@@ -1200,7 +1198,7 @@ __device__ __forceinline__ void cover(int x, int n, int P, int S, float rS, int 
 // and covering patch row, sums over the covering patch columns; then per
 // pixel, sums over the covering patch rows.
 template <int TW, int TH>
-__device__ __forceinline__ void fuse_unit(const LaunchArgs &a, int unit, float4 *fz, int &hint) {
+__device__ __forceinline__ void fuse_unit(const LaunchArgs &a, int unit, float4 *fz) {
     // fz: nkx * nky posteriors, then nky * TW column sums (dynamic shared memory).
     // The tile size is a compile-time constant (32x16 or 64x32), so the pixel
     // index arithmetic is shifts and masks.
@@ -1211,7 +1209,7 @@ __device__ __forceinline__ void fuse_unit(const LaunchArgs &a, int unit, float4 
 
     // the descriptor is copied to registers: the pixel stores could alias it
     // as far as the compiler knows, which would reload its fields per pixel
-    const LevelDesc D = a.descs[find_pair_from(a.descs, a.npairs, unit, W_FUSE, hint)];
+    const LevelDesc D = a.descs[find_pair(a.descs, a.npairs, unit, W_FUSE)];
     const int tile = unit - D.work_begin[W_FUSE];
     const int ty = udiv_small(tile, recip(D.tiles_x)), tx = tile - ty * D.tiles_x;
     const float rS = recip(S);
@@ -1508,8 +1506,7 @@ template <int TW, int TH>
 __global__ void __launch_bounds__(256, 4) k_fuse(LaunchArgs a) {
     extern __shared__ float4 fz[];
     pdl_enter(a);
-    int hint = -1;
-    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) fuse_unit<TW, TH>(a, unit, fz, hint);
+    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) fuse_unit<TW, TH>(a, unit, fz);
     pdl_leave(a);
 }
 
@@ -1559,7 +1556,6 @@ __global__ void __launch_bounds__(256) k_mega(MegaArgs m) {
     pdl_wait();
     for (int s = 0; s < m.nstages; ++s) {
         const LaunchArgs &a = m.stages[s];
-        int hint = -1;
         const int total = a.total;
         if (a.kind == 0) {
             if (blockIdx.x == 0 && a.acc_zero != nullptr)
@@ -1570,9 +1566,9 @@ __global__ void __launch_bounds__(256) k_mega(MegaArgs m) {
             float(*Rh)[kPyrHP] = Lh + kPyrSH;
             if (a.level == 0) {
                 for (int u = blockIdx.x; u < total; u += gridDim.x)
-                    pyramid_unit<uint8_t, TG, TG>(a, u, Ls, Rs, Lh, Rh, hint);
+                    pyramid_unit<uint8_t, TG, TG>(a, u, Ls, Rs, Lh, Rh);
             } else {
-                for (int u = blockIdx.x; u < total; u += gridDim.x) pyramid_unit<TG, TG, TG>(a, u, Ls, Rs, Lh, Rh, hint);
+                for (int u = blockIdx.x; u < total; u += gridDim.x) pyramid_unit<TG, TG, TG>(a, u, Ls, Rs, Lh, Rh);
             }
         } else if (a.kind == 4) {
             if (blockIdx.x == 0 && a.acc_zero != nullptr)
@@ -1584,15 +1580,15 @@ __global__ void __launch_bounds__(256) k_mega(MegaArgs m) {
             }
         } else if (a.kind == 1) {
             if (a.level == 0) {
-                for (int u = blockIdx.x; u < total; u += gridDim.x) search_unit<P, uint8_t, TG>(a, u, smem, hint);
+                for (int u = blockIdx.x; u < total; u += gridDim.x) search_unit<P, uint8_t, TG>(a, u, smem);
             } else {
-                for (int u = blockIdx.x; u < total; u += gridDim.x) search_unit<P, TG, TG>(a, u, smem, hint);
+                for (int u = blockIdx.x; u < total; u += gridDim.x) search_unit<P, TG, TG>(a, u, smem);
             }
         } else if (a.kind == 2) {
             if (a.tile_w == 64) {
-                for (int u = blockIdx.x; u < total; u += gridDim.x) fuse_unit<64, 32>(a, u, (float4 *)smem, hint);
+                for (int u = blockIdx.x; u < total; u += gridDim.x) fuse_unit<64, 32>(a, u, (float4 *)smem);
             } else {
-                for (int u = blockIdx.x; u < total; u += gridDim.x) fuse_unit<32, 16>(a, u, (float4 *)smem, hint);
+                for (int u = blockIdx.x; u < total; u += gridDim.x) fuse_unit<32, 16>(a, u, (float4 *)smem);
             }
         } else {
             for (int u = blockIdx.x; u < total; u += gridDim.x) upsample_unit(a, u);
