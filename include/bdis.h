@@ -360,14 +360,21 @@ typedef enum {
      * levels' grids are small, so one launch replaces several short
      * dependent ones.  Same results. */
     BDIS_OPT_COARSE_LEVELS = 11,
-    /* 1: the one-step pyramid launches (calls of more than 2^21 level-0
+    /* Bit flags, 0 (default, faster on GB300): every stage stages its
+     * shared-memory tiles by the block's own loads.
+     * Bit 1: the one-step pyramid launches (calls of more than 2^21 level-0
      * pixels, or BDIS_OPT_PYRAMID_STEPS 1) stage each interior tile by bulk
      * asynchronous copies (cp.async.bulk, one per row, completing on an
      * mbarrier), the next tile's copies in flight while the current one is
-     * computed; 0 (default, faster on GB300): the block's own loads.  Same
-     * results.  The wait for a
-     * tile's copies is bounded; one that runs out is reported like a
-     * grid-barrier timeout (BDIS_OPT_FORM). */
+     * computed.
+     * Bit 2: the search launches (patch sizes 8 and 12; others ignore the
+     * bit) copy the right-image band of each block whose band window lies
+     * inside the image by one cp.async.bulk per patch row, issued before
+     * the left-image and gradient bands are loaded, then widen it to FP32
+     * in shared memory.
+     * Same results in every case.  The wait for a block's copies is
+     * bounded; one that runs out is reported like a grid-barrier timeout
+     * (BDIS_OPT_FORM).  Values outside 0..3: BDIS_EINVAL. */
     BDIS_OPT_BULK_COPY = 12
 } bdis_option;
 

@@ -67,7 +67,7 @@ struct bdis_handle {
     int *err_flag = nullptr;  // timeout flag of the last cooperative launch (device)
     int last_persistent = 0;  // bdis_stats::persistent of the last call
     int coarse_levels = 0;    // BDIS_OPT_COARSE_LEVELS
-    bool bulk_copy = false;   // BDIS_OPT_BULK_COPY
+    int bulk_copy = 0;        // BDIS_OPT_BULK_COPY (bit 1 pyramid, bit 2 search band)
     unsigned barrier_limit = kBarrierSpinLimit;  // BDIS_OPT_BARRIER_LIMIT
     bool barrier_unreachable = false;            // BDIS_OPT_BARRIER_TEST
     // sticky timeout word in mapped page-locked host memory: a persistent
@@ -490,7 +490,7 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
     size_t ssm[kMaxLevels], fsm[kMaxLevels], smax = 0, fmax = 0;
     for (int l = 0; l < NL; ++l) {
         search_layout(p.patch, p.stride, tau_at(p), p.window_step, cfg[l].passes, bpitch[l], bcap[l],
-                      cpitch[l], ssm[l]);
+                      cpitch[l], ssm[l], (h->bulk_copy & 2) != 0);
         fsm[l] = fuse_smem(p.patch, p.stride, cfg[l].tile_w, cfg[l].tile_h);
         smax = std::max(smax, ssm[l]);
         fmax = std::max(fmax, fsm[l]);
@@ -566,7 +566,7 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
     for (auto &a : stages) {
         a.pdl = h->use_pdl;
         a.prefetch = &a == &stages.front() ? 0 : 1;  // the table is uploaded before the first stage
-        a.bulk = h->bulk_copy ? 1 : 0;
+        a.bulk = h->bulk_copy;
         a.err_host = h->status_dev;
     }
     // upload descriptors (and the stage list) unless identical to the last upload
@@ -728,7 +728,7 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
                 if (e != cudaSuccess) return cuda_fail(h, e, "pyramid launch");
             } else if (a.kind == 1) {
                 const size_t sm = ssm[a.level];
-                const int occ = search_occupancy(p.patch, itype, g_type, sm);
+                const int occ = search_occupancy(p.patch, itype, g_type, sm, (a.bulk & 2) != 0);
                 const int grid = std::max(1, std::min(a.total, sm_count() * occ));
                 e = timed(BDIS_K_SEARCH + 16 * a.level,
                           [&] { return launch_search(a, itype, g_type, sm, grid, st); });
@@ -899,7 +899,7 @@ bdis_status run_tuned(bdis_handle *h, int n, const bdis_pair *pairs, int in_type
 int option_bits(const bdis_handle *h) {
     return (h->use_graph ? 1 : 0) | (h->profile ? 2 : 0) | (h->use_pdl << 14) | (h->autotune ? 8 : 0) |
            (h->form << 4) | (h->pyr_steps << 6) | (h->coarse_levels << 8) |
-           (h->barrier_unreachable ? 1 << 12 : 0) | (h->bulk_copy ? 1 << 13 : 0);
+           (h->barrier_unreachable ? 1 << 12 : 0) | ((h->bulk_copy & 1) << 13) | ((h->bulk_copy & 2) << 15);
 }
 
 // A persistent launch whose grid-barrier wait ran out has stored 1 in the
@@ -1112,7 +1112,8 @@ bdis_status bdis_set_option(bdis_handle *h, int option, int value) {
         return BDIS_OK;
     }
     if (option == BDIS_OPT_BULK_COPY) {
-        h->bulk_copy = value != 0;
+        if (value < 0 || value > 3) return fail(h, BDIS_EINVAL, "bulk copy option must be 0..3");
+        h->bulk_copy = value;
         return BDIS_OK;
     }
     if (option == BDIS_OPT_COARSE_LEVELS) {

@@ -116,7 +116,7 @@ struct LaunchArgs {
     int early;                // set by the launcher: release the next kernel at the start
     int prefetch;             // the descriptor table is complete before this kernel starts
                               // (every stage after a call's first): prefetched while waiting
-    int bulk;                 // one-step pyramid: interior tiles staged by bulk async copies
+    int bulk;                 // bit 1: one-step pyramid tiles, bit 2: search bands, by bulk async copies
     int *err_host;            // mapped status word of the handle (a device wait ran out), or nullptr
 };
 
@@ -206,8 +206,9 @@ cudaError_t launch_upsample(const LaunchArgs &a, cudaStream_t s);
 cudaError_t launch_depth(const float *disp, const float *var, long long n, float fb, float *depth,
                          float *depth_var, cudaStream_t s);
 // Shared-memory layout of the search (band pitch and capacity, chunk pitch, bytes).
+// bulk: with the raw area of the right band's bulk staging (BDIS_OPT_BULK_COPY bit 2)
 void search_layout(int P, int S, float tau, float window_step, int passes, int &band_pitch,
-                   int &band_cap, int &chunk_pitch, size_t &bytes);
+                   int &band_cap, int &chunk_pitch, size_t &bytes, bool bulk = false);
 size_t fuse_smem(int P, int S, int tile_w, int tile_h);
 cudaError_t prepare_fuse(size_t smem_bytes);
 // Persistent form: available for the patch sizes with an instance; grid =
@@ -223,7 +224,7 @@ constexpr size_t kPyr2SmemBytes = sizeof(float) * (2 * 44 * 76 + 2 * 20 * 36 + 2
 // Raise (never lower) the dynamic shared-memory limit of every search instance.
 cudaError_t prepare_search(int P, size_t smem_bytes);
 // Number of resident search blocks per SM for (P, image type, gradient type, smem).
-int search_occupancy(int P, int in_type, int g_type, size_t smem_bytes);
+int search_occupancy(int P, int in_type, int g_type, size_t smem_bytes, bool bulk = false);
 bool search_supported(int P);
 int search_group(int P);      // lanes per patch
 int search_chunk(int P, int passes);  // patches per chunk

@@ -601,6 +601,21 @@ __global__ void __launch_bounds__(256, 4) k_pyramid_bulk(LaunchArgs a) {
 
 // ---------------------------------------------------------------- patch search
 
+// Raw row pitch in bytes of the search's bulk band staging for element size
+// esz: the band capacity rounded up to 16 bytes, plus 16.
+__host__ __device__ __forceinline__ size_t search_raw_pitch(int band_cap, int esz) {
+    return ((size_t)band_cap * esz + 15) / 16 * 16 + 16;
+}
+
+// The mbarrier of the bulk band staging: at the first 16-byte boundary past
+// the right band, the left and gradient bands, the chunk's estimates and
+// sigma_r terms and the reduction scratch (the layout of search_unit); the
+// raw rows follow 16 bytes later.
+__device__ __forceinline__ uint64_t *search_bulk_bar(float *smem, int P, int bp, int cp, int chunk) {
+    const size_t off = sizeof(float) * ((size_t)P * bp + 2 * (size_t)P * cp + 4 * (size_t)chunk + 16);
+    return (uint64_t *)((char *)smem + (off + 15) / 16 * 16);
+}
+
 // Block-wide min and max (all threads get the result).
 __device__ __forceinline__ void block_minmax(float &lo, float &hi, float *red) {
 #pragma unroll
@@ -635,8 +650,14 @@ __device__ __forceinline__ void block_minmax(float &lo, float &hi, float *red) {
 // xor shuffles inside the group; the iteration count is fixed, so every lane
 // of a warp executes the same instruction stream.  The groups of a warp take
 // patches spaced so that their rows fall in different shared-memory banks.
-template <int P, typename TI, typename TG>
-__device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float *smem) {
+// With BULK and bit 2 of a.bulk, a band window inside the image is instead
+// copied row by row by cp.async.bulk into a raw area behind the band
+// (search_layout), then widened to FP32 in shared memory; the values staged,
+// and so the results, are the same.  Returns false if the wait for those
+// copies ran out (reported through a.err_host; the block stops).
+template <int P, typename TI, typename TG, bool BULK>
+__device__ __forceinline__ bool search_unit(const LaunchArgs &a, int unit, float *smem,
+                                            unsigned &bphase) {
 
     constexpr int G = P <= 8 ? 8 : 16;
     constexpr int N = P * P;
@@ -717,11 +738,38 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
     // column window of the right band
     dhi = fminf(fmaxf(dhi, -(float)(2 * w)), (float)(2 * w));
     dlo = fminf(fmaxf(dlo, -(float)(2 * w)), (float)(2 * w));
-    const int xlo = cx0 - (int)ceilf(dhi) - margin;
+    int xlo = cx0 - (int)ceilf(dhi) - margin;
     const int xhi = cx0 + cw - (int)floorf(dlo) + margin;
-    const int wwin = min(xhi - xlo, cap);
+    int wwin = min(xhi - xlo, cap);
+    // bulk staging of the right band (block-uniform decision): the window
+    // starts at a 16-byte boundary at or left of xlo and lies inside the
+    // image (no clamping), the copied span (the window rounded up to 16
+    // bytes) inside the image row, rows 16-byte aligned
+    constexpr int kE = (int)sizeof(TI), kA = 16 / kE;
+    bool bulk_band = false;
+    unsigned char *raw = nullptr;
+    uint64_t *bbar = nullptr;
+    if (BULK && (a.bulk & 2) != 0) {
+        const int xa = xlo >= 0 ? xlo / kA * kA : -1;
+        const int wb = min(xhi - xa, cap);
+        const int span = (wb + kA - 1) / kA * kA;
+        if (xa >= 0 && xhi <= w && xa + span <= w && ((uintptr_t)R & 15u) == 0 &&
+            ((size_t)D.pitch * kE) % 16 == 0) {
+            bulk_band = true;
+            xlo = xa;
+            wwin = wb;
+            bbar = search_bulk_bar(smem, P, bp, cp, a.chunk);
+            raw = (unsigned char *)(bbar + 2);
+            if (tid < P) {
+                fence_proxy_async_smem();  // the last unit's widening reads precede the copy
+                if (tid == 0) mbar_arrive_expect_tx(bbar, (unsigned)(P * span * kE));
+                bulk_copy_g2s(raw + (size_t)tid * search_raw_pitch(cap, kE),
+                              R + (size_t)(oy + tid) * D.pitch + xa, (unsigned)(span * kE), bbar);
+            }
+        }
+    }
     // staging: the P rows of a column are loaded together (memory-level parallelism)
-    for (int c = tid; c < wwin; c += blockDim.x) {
+    for (int c = bulk_band ? wwin : tid; c < wwin; c += blockDim.x) {
         const int col = clampi(xlo + c, 0, w - 1);
         float v[P];
 #pragma unroll
@@ -740,6 +788,35 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
         for (int r = 0; r < P; ++r) {
             Lb[r * cp + c] = vl[r];
             Gb[r * cp + c] = vg[r];
+        }
+    }
+    if (bulk_band) {
+        const unsigned par = bphase & 1u;
+        const bool ok = mbar_wait_bounded(bbar, par, kCopyWaitLimit);
+        bphase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            // the copies did not land: report it, wait (bounded) once more
+            // for them to finish writing shared memory, and stop
+            if (tid == 0 && a.err_host != nullptr) {
+                *(volatile int *)a.err_host = 1;
+                __threadfence_system();
+            }
+            mbar_wait_bounded(bbar, par, kCopyWaitLimit);
+            return false;
+        }
+        // widen to FP32: four raw elements per step (the copied span covers
+        // the window rounded up to four), stored up to the window's end
+        const int ng = (wwin + 3) >> 2;
+        const size_t rpb = search_raw_pitch(cap, kE);
+        const float rng = recip(ng);
+        for (int i = tid; i < P * ng; i += blockDim.x) {
+            const int r = udiv_small(i, rng), g = i - r * ng, c = 4 * g;
+            const float4 f = raw4((const TI *)(raw + (size_t)r * rpb) + c);
+            float *dst = Rb + r * bp + c;
+            dst[0] = f.x;
+            if (c + 1 < wwin) dst[1] = f.y;
+            if (c + 2 < wwin) dst[2] = f.z;
+            if (c + 3 < wwin) dst[3] = f.w;
         }
     }
     __syncthreads();
@@ -974,13 +1051,24 @@ __device__ __forceinline__ void search_unit(const LaunchArgs &a, int unit, float
             atomicAdd(D.acc + 2, s3);
         }
     }
-    }
+    return true;
+}
 
-template <int P, typename TI, typename TG>
+// BULK: the instance with the bulk band staging (BDIS_OPT_BULK_COPY bit 2;
+// compiled for P = 8 and 12), a kernel of its own so that the default
+// instances keep their register allocation.
+template <int P, typename TI, typename TG, bool BULK>
 __global__ void __launch_bounds__(256, (P <= 8 ? 3 : 2)) k_search(LaunchArgs a) {
-    extern __shared__ float smem[];
+    extern __shared__ __align__(16) float smem[];
+    if (BULK && (a.bulk & 2) != 0 && threadIdx.x == 0) {
+        mbar_init(search_bulk_bar(smem, P, a.band_pitch, a.chunk_pitch, a.chunk), 1);
+        mbar_init_fence();
+    }
+    // (the unit's first barrier orders the initialisation before any use)
     pdl_enter(a);
-    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) search_unit<P, TI, TG>(a, unit, smem);
+    unsigned bphase = 0u;
+    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x)
+        if (!search_unit<P, TI, TG, BULK>(a, unit, smem, bphase)) break;
     pdl_leave(a);
 }
 
@@ -1579,10 +1667,11 @@ __global__ void __launch_bounds__(256) k_mega(MegaArgs m) {
                 for (int u = blockIdx.x; u < total; u += gridDim.x) pyramid2_unit<TG, TG, TG>(a, u, smem);
             }
         } else if (a.kind == 1) {
+            unsigned ph = 0u;  // (no bulk staging in the persistent form)
             if (a.level == 0) {
-                for (int u = blockIdx.x; u < total; u += gridDim.x) search_unit<P, uint8_t, TG>(a, u, smem);
+                for (int u = blockIdx.x; u < total; u += gridDim.x) search_unit<P, uint8_t, TG, false>(a, u, smem, ph);
             } else {
-                for (int u = blockIdx.x; u < total; u += gridDim.x) search_unit<P, TG, TG>(a, u, smem);
+                for (int u = blockIdx.x; u < total; u += gridDim.x) search_unit<P, TG, TG, false>(a, u, smem, ph);
             }
         } else if (a.kind == 2) {
             if (a.tile_w == 64) {
@@ -1613,19 +1702,23 @@ const void *mega_kernel(int P, int st_type) {
 // ---------------------------------------------------------------- dispatch
 
 // (image type, gradient type): (u8, f32), (u8, f16), (f32, f32), (f32, f16), (f16, f16)
-template <int P>
+template <int P, bool BULK = false>
 const void *search_fn(int in_type, int g_type) {
     if (in_type == E_U8)
-        return g_type == E_F32 ? (const void *)k_search<P, uint8_t, float>
-                               : (const void *)k_search<P, uint8_t, __half>;
+        return g_type == E_F32 ? (const void *)k_search<P, uint8_t, float, BULK>
+                               : (const void *)k_search<P, uint8_t, __half, BULK>;
     if (in_type == E_F32)
-        return g_type == E_F32 ? (const void *)k_search<P, float, float>
-                               : (const void *)k_search<P, float, __half>;
-    if (in_type == E_F16 && g_type == E_F16) return (const void *)k_search<P, __half, __half>;
+        return g_type == E_F32 ? (const void *)k_search<P, float, float, BULK>
+                               : (const void *)k_search<P, float, __half, BULK>;
+    if (in_type == E_F16 && g_type == E_F16) return (const void *)k_search<P, __half, __half, BULK>;
     return nullptr;
 }
 
-const void *search_kernel(int P, int in_type, int g_type) {
+// bulk: the instance with the bulk band staging where one is compiled (P = 8
+// and 12), else the default one (same results)
+const void *search_kernel(int P, int in_type, int g_type, bool bulk) {
+    if (bulk && P == 8) return search_fn<8, true>(in_type, g_type);
+    if (bulk && P == 12) return search_fn<12, true>(in_type, g_type);
     switch (P) {
         case 4: return search_fn<4>(in_type, g_type);
         case 5: return search_fn<5>(in_type, g_type);
@@ -1667,7 +1760,7 @@ cudaError_t raise_smem_limit(const void *f, size_t bytes);
 bool search_supported(int P) { return P >= kMinPatch && P <= kMaxPatch; }
 
 void search_layout(int P, int S, float tau, float window_step, int passes, int &band_pitch,
-                   int &band_cap, int &chunk_pitch, size_t &bytes) {
+                   int &band_cap, int &chunk_pitch, size_t &bytes, bool bulk) {
     const int chunk = search_chunk(P, passes);
     const int cw = (chunk - 1) * S + P;
     const int margin = (int)ceilf(tau) + (int)ceilf(2.f * window_step) + 3;
@@ -1675,6 +1768,9 @@ void search_layout(int P, int S, float tau, float window_step, int passes, int &
     band_pitch = (band_cap + 31) / 32 * 32 + 1;  // rows land in different banks
     chunk_pitch = cw | 1;
     bytes = sizeof(float) * ((size_t)P * band_pitch + 2 * (size_t)P * chunk_pitch + 4 * (size_t)chunk + 16);
+    // bulk staging of the right band: a 16-byte aligned mbarrier slot, then P
+    // raw rows of the widest storage type (FP32)
+    if (bulk) bytes = (bytes + 15) / 16 * 16 + 16 + (size_t)P * search_raw_pitch(band_cap, 4);
 }
 
 size_t fuse_smem(int P, int S, int tile_w, int tile_h) {
@@ -1732,18 +1828,19 @@ cudaError_t raise_smem_limit(const void *f, size_t bytes) {
 cudaError_t prepare_search(int P, size_t smem_bytes) {
     const int combos[5][2] = {{E_U8, E_F32}, {E_U8, E_F16}, {E_F32, E_F32}, {E_F32, E_F16},
                               {E_F16, E_F16}};
-    for (const auto &c : combos) {
-        const void *f = search_kernel(P, c[0], c[1]);
-        if (f == nullptr) return cudaErrorInvalidValue;
-        cudaError_t e = raise_smem_limit(f, smem_bytes);
-        if (e != cudaSuccess) return e;
-    }
+    for (const auto &c : combos)
+        for (const bool bulk : {false, true}) {
+            const void *f = search_kernel(P, c[0], c[1], bulk);
+            if (f == nullptr) return cudaErrorInvalidValue;
+            cudaError_t e = raise_smem_limit(f, smem_bytes);
+            if (e != cudaSuccess) return e;
+        }
     return cudaSuccess;
 }
 
-int search_occupancy(int P, int in_type, int g_type, size_t smem_bytes) {
+int search_occupancy(int P, int in_type, int g_type, size_t smem_bytes, bool bulk) {
     int nb = 0;
-    const void *f = search_kernel(P, in_type, g_type);
+    const void *f = search_kernel(P, in_type, g_type, bulk);
     if (f == nullptr) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, 256, smem_bytes) != cudaSuccess)
         return 1;
@@ -1849,7 +1946,7 @@ cudaError_t launch_pyramid_bulk_typed(const LaunchArgs &a, int in_type, int img_
 }  // namespace
 
 cudaError_t launch_pyramid(const LaunchArgs &a, int in_type, int img_type, int g_type, cudaStream_t s) {
-    if (a.bulk) return launch_pyramid_bulk_typed(a, in_type, img_type, g_type, s);
+    if (a.bulk & 1) return launch_pyramid_bulk_typed(a, in_type, img_type, g_type, s);
     const void *f = pyramid_kernel(in_type, img_type, g_type);
     if (f == nullptr) return cudaErrorInvalidValue;
     return launch_args_kernel(f, a, grid_for(a.total, 8), 0, s);
@@ -1863,7 +1960,7 @@ cudaError_t launch_pyramid2(const LaunchArgs &a, int in_type, int img_type, int 
 
 cudaError_t launch_search(const LaunchArgs &a, int in_type, int g_type, size_t smem, int grid,
                           cudaStream_t s) {
-    const void *f = search_kernel(a.P, in_type, g_type);
+    const void *f = search_kernel(a.P, in_type, g_type, (a.bulk & 2) != 0);
     if (f == nullptr) return cudaErrorInvalidValue;
     return launch_args_kernel(f, a, grid, smem, s);
 }

@@ -688,6 +688,47 @@ def test_bulk_copy_staging_equals_own_loads(bd, storage):
                 assert np.array_equal(a[key], b[key]), key
 
 
+
+@pytest.mark.parametrize("patch,storage", [(8, "f16"), (8, "u8"), (12, "f32"), (12, "f16")])
+def test_bulk_search_band_equals_own_loads(bd, patch, storage):
+    """The search's bulk asynchronous staging of the right-image band
+    (BDIS_OPT_BULK_COPY bit 2) gives bitwise the records and outputs of
+    staging by the block's own loads, on pairs where some bands are
+    ineligible (near the image edges, odd widths, row pitches that are not a
+    multiple of 16 bytes), alone and together with the pyramid's (value 3)."""
+    import torch
+    sizes = [(640, 480, 640), (333, 217, 333), (1280, 720, 1296), (250, 130, 257)]
+    pairs = [synth.g1_pair(w, h, 70 + i) for i, (w, h, _) in enumerate(sizes)]
+    Ls, Rs = [], []
+    for (w, h, pitch), p in zip(sizes, pairs):
+        for img, lst in ((p.left, Ls), (p.right, Rs)):
+            buf = torch.zeros((h, pitch), dtype=torch.uint8, device="cuda")
+            buf[:, :w] = torch.from_numpy(img).cuda()
+            lst.append(buf[:, :w])
+    kw = dict(patch=patch, stride=patch // 2, levels=3, iters=8, storage=storage, variance=1)
+    res = []
+    for bulk in (0, 2, 3):
+        m = bd.BDIS(**kw)
+        m.set_option(bd.B.OPT_FORM, 1)
+        m.set_option(bd.B.OPT_BULK_COPY, bulk)
+        out = m.match_batched(Ls, Rs)
+        torch.cuda.synchronize()
+        views = [m.level_view(i, l) for i in range(len(sizes)) for l in range(3)]
+        one = m.match(Ls[0], Rs[0])
+        torch.cuda.synchronize()
+        assert m.stats()["barrier_timeouts"] == 0
+        res.append((out + [one], views))
+        m.close()
+    (o0, v0) = res[0]
+    for o1, v1 in res[1:]:
+        for (d0, q0, k0), (d1, q1, k1) in zip(o0, o1):
+            assert torch.equal(k0, k1)
+            assert torch.equal(torch.nan_to_num(d0, nan=-1.0), torch.nan_to_num(d1, nan=-1.0))
+            assert torch.equal(torch.nan_to_num(q0, nan=-1.0), torch.nan_to_num(q1, nan=-1.0))
+        for a, b in zip(v0, v1):
+            assert np.array_equal(a["patches"].view(np.uint8), b["patches"].view(np.uint8))
+
+
 def _coverage(disp, var, valid, gt, z=1.96):
     v = valid.astype(bool) & np.isfinite(var) & (var > 0)
     e = np.abs(disp[v].astype(np.float64) - gt[v])
