@@ -375,7 +375,13 @@ typedef enum {
      * Same results in every case.  The wait for a block's copies is
      * bounded; one that runs out is reported like a grid-barrier timeout
      * (BDIS_OPT_FORM).  Values outside 0..3: BDIS_EINVAL. */
-    BDIS_OPT_BULK_COPY = 12
+    BDIS_OPT_BULK_COPY = 12,
+    /* Search chunk of every level: 0 (default) as tuned (or the default
+     * configuration with BDIS_OPT_AUTOTUNE 0); 1..4 that many passes of the
+     * block's lane groups per chunk (32 patches per pass for patch sizes up
+     * to 8, 16 above).  Same results: the sigma_r sums are exact integers, so
+     * the chunking does not change them.  Other values: BDIS_EINVAL. */
+    BDIS_OPT_SEARCH_PASSES = 13
 } bdis_option;
 
 bdis_status bdis_set_option(bdis_handle *h, int option, int value);

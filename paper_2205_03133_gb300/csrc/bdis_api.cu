@@ -82,6 +82,7 @@ struct bdis_handle {
     int form = 0;             // BDIS_OPT_FORM
     int use_pdl = 1;          // BDIS_OPT_PDL: 0, 1 or 2
     int pyr_steps = 0;        // BDIS_OPT_PYRAMID_STEPS
+    int search_passes = 0;    // BDIS_OPT_SEARCH_PASSES (0: tuned)
     bool adjoint_levels = false;  // BDIS_OPT_ADJOINT_LEVELS
     bool host_mapped = true;      // BDIS_OPT_HOST_MAPPED
     // repeat of the previous call: same pairs, stream, options and arena ->
@@ -473,7 +474,7 @@ bdis_status ensure_status_word(bdis_handle *h) {
     }
     return BDIS_OK;
 }
-const LevelCfg kSearchCands[3] = {{1, 32, 16}, {2, 64, 32}, {4, 32, 16}};
+const LevelCfg kSearchCands[4] = {{1, 32, 16}, {2, 64, 32}, {4, 32, 16}, {3, 64, 32}};
 
 // The whole coarse-to-fine pipeline for n pairs with per-level launch
 // configuration cfg.  graph: replay / capture allowed; prof: bracket each
@@ -825,11 +826,11 @@ bdis_status autotune(bdis_handle *h, int n, const bdis_pair *pairs, int in_type,
     // every candidate is timed five times (interleaved) and keeps its fastest
     // run, so that noisy timings of short launches do not decide a level's
     // configuration
-    double tsearch[3][kMaxLevels], tfuse[3][kMaxLevels];
-    for (int c = 0; c < 3; ++c)
+    double tsearch[4][kMaxLevels], tfuse[4][kMaxLevels];
+    for (int c = 0; c < 4; ++c)
         for (int l = 0; l < kMaxLevels; ++l) tsearch[c][l] = tfuse[c][l] = 1e30;
-    for (int it = 0; it < 15; ++it) {
-        const int c = it % 3;
+    for (int it = 0; it < 20; ++it) {
+        const int c = it % 4;
         for (int l = 0; l < NL; ++l) cfg[l] = kSearchCands[c];
         const size_t m0 = h->ev_marks.size();
         s = run_cfg(h, n, pairs, in_type, st, cfg.data(), false, true);
@@ -856,7 +857,7 @@ bdis_status autotune(bdis_handle *h, int n, const bdis_pair *pairs, int in_type,
     best.assign((size_t)NL, kDefaultCfg);
     for (int l = h->p.finest_level; l < NL; ++l) {
         int bs = 0, bf = 0;
-        for (int c = 1; c < 3; ++c) {
+        for (int c = 1; c < 4; ++c) {
             if (tsearch[c][l] < tsearch[bs][l]) bs = c;
             if (tfuse[c][l] < tfuse[bf][l]) bf = c;
         }
@@ -898,7 +899,7 @@ bdis_status run_tuned(bdis_handle *h, int n, const bdis_pair *pairs, int in_type
 
 int option_bits(const bdis_handle *h) {
     return (h->use_graph ? 1 : 0) | (h->profile ? 2 : 0) | (h->use_pdl << 14) | (h->autotune ? 8 : 0) |
-           (h->form << 4) | (h->pyr_steps << 6) | (h->coarse_levels << 8) |
+           (h->form << 4) | (h->pyr_steps << 6) | (h->search_passes << 18) | (h->coarse_levels << 8) |
            (h->barrier_unreachable ? 1 << 12 : 0) | ((h->bulk_copy & 1) << 13) | ((h->bulk_copy & 2) << 15);
 }
 
@@ -999,6 +1000,8 @@ bdis_status run_tuned(bdis_handle *h, int n, const bdis_pair *pairs, int in_type
             t.form = kFormLaunches;
         }
     }
+    if (h->search_passes > 0)
+        for (auto &c : t.cfg) c.passes = h->search_passes;
     int form = t.form;
     if (h->form == 1) form = h->coarse_levels;
     if (h->form == 2) form = (in_type == E_U8 && mega_supported(h->p.patch) &&
@@ -1129,6 +1132,11 @@ bdis_status bdis_set_option(bdis_handle *h, int option, int value) {
     if (option == BDIS_OPT_PYRAMID_STEPS) {
         if (value < 0 || value > 2) return fail(h, BDIS_EINVAL, "pyramid steps must be 0, 1 or 2");
         h->pyr_steps = value;
+        return BDIS_OK;
+    }
+    if (option == BDIS_OPT_SEARCH_PASSES) {
+        if (value < 0 || value > 4) return fail(h, BDIS_EINVAL, "search passes must be 0..4");
+        h->search_passes = value;
         return BDIS_OK;
     }
     return fail(h, BDIS_EINVAL, "unknown option");

@@ -681,7 +681,8 @@ __device__ __forceinline__ bool search_unit(const LaunchArgs &a, int unit, float
     // patch spacing between the groups of a warp (a power of two dividing 16)
     int sp = (32 / GPW) / S;
     sp = sp >= 16 ? 16 : sp >= 8 ? 8 : sp >= 4 ? 4 : sp >= 2 ? 2 : 1;
-    sp = min(sp, 8 * (a.chunk / (8 * GPW)));  // must divide 8 x passes
+    // must divide the chunk's 8 x passes warp slots
+    for (const int ns = 8 * (a.chunk / (8 * GPW)); ns % sp != 0;) sp >>= 1;
     const int margin = (int)ceilf(a.tau) + (int)ceilf(2.f * h) + 3;
 
 
@@ -777,7 +778,33 @@ __device__ __forceinline__ bool search_unit(const LaunchArgs &a, int unit, float
 #pragma unroll
         for (int r = 0; r < P; ++r) Rb[r * bp + c] = v[r];
     }
-    for (int c = kEarlyLG ? tid + blockDim.x : tid; c < cw; c += blockDim.x) {
+    // four columns per step where the rows allow aligned vector loads
+    // (P <= 8: no early column; block-uniform decision)
+    int c_first = kEarlyLG ? tid + blockDim.x : tid;
+    if (!kEarlyLG && (cx0 & 3) == 0 && (D.pitch & 3) == 0 && (D.gpitch & 3) == 0 &&
+        (((uintptr_t)L | (uintptr_t)Gi) & 15u) == 0) {
+        const int nq = cw >> 2;
+        for (int q = tid; q < nq; q += blockDim.x) {
+            const int c = 4 * q;
+            float4 v[P];
+#pragma unroll
+            for (int r = 0; r < P; ++r) v[r] = raw4(L + (size_t)(oy + r) * D.pitch + cx0 + c);
+#pragma unroll
+            for (int r = 0; r < P; ++r) {
+                float *d = Lb + r * cp + c;
+                d[0] = v[r].x; d[1] = v[r].y; d[2] = v[r].z; d[3] = v[r].w;
+            }
+#pragma unroll
+            for (int r = 0; r < P; ++r) v[r] = raw4(Gi + (size_t)(oy + r) * D.gpitch + cx0 + c);
+#pragma unroll
+            for (int r = 0; r < P; ++r) {
+                float *d = Gb + r * cp + c;
+                d[0] = v[r].x; d[1] = v[r].y; d[2] = v[r].z; d[3] = v[r].w;
+            }
+        }
+        c_first = 4 * nq + tid;
+    }
+    for (int c = c_first; c < cw; c += blockDim.x) {
         float vl[P], vg[P];
 #pragma unroll
         for (int r = 0; r < P; ++r) {
@@ -823,9 +850,12 @@ __device__ __forceinline__ bool search_unit(const LaunchArgs &a, int unit, float
 
     const int passes = a.chunk / (8 * GPW);
     for (int pass = 0; pass < passes; ++pass) {
-        // pass p holds the chunk slots [p * 8 * GPW, (p + 1) * 8 * GPW): none
-        // is a patch once they start past the chunk's last one (block-uniform)
-        if (pass * 8 * GPW >= nk) break;
+        // the slot of warp u, group q is (u / sp) sp GPW + u % sp + sp q,
+        // increasing in u for q = 0, so the pass's smallest slot is that of
+        // its first warp's first group; once it is past the chunk's last
+        // patch, so is every slot of this pass and the later ones
+        // (block-uniform).  With sp > 8 a pass's slots are not contiguous.
+        if (((pass * 8) / sp) * (sp * GPW) + (pass * 8) % sp >= nk) break;
         const int uu = pass * 8 + warp;
         const int kk = (uu / sp) * (sp * GPW) + (uu % sp) + sp * q;  // patch slot in chunk
         const bool active = kk < nk;

@@ -75,6 +75,13 @@ def test_host_side_argument_checks(lib):
     # level views before any call
     v = B.bdis_level_view()
     assert lib.bdis_level_view_get(m._h, 0, 0, C.byref(v)) == B.BDIS_EINVAL
+    # option ranges
+    for opt, good, bad in ((B.OPT_BULK_COPY, (0, 1, 2, 3), (-1, 4)),
+                           (B.OPT_SEARCH_PASSES, (0, 1, 2, 3, 4), (-1, 5))):
+        for val in good:
+            assert lib.bdis_set_option(m._h, opt, val) == B.BDIS_OK, (opt, val)
+        for val in bad:
+            assert lib.bdis_set_option(m._h, opt, val) == B.BDIS_EINVAL, (opt, val)
 
 
 def test_mode_parameter_checks(lib):

@@ -105,6 +105,9 @@ def test_pyramid_and_gradient_f16(bd):
     (160, 120, dict(patch=8, stride=4, levels=2, iters=0)),
     (64, 48, dict(patch=4, stride=1, levels=2, iters=8)),          # smallest patch, densest grid
     (96, 80, dict(patch=16, stride=1, levels=1, iters=6, variance=1)),  # 256 patches per pixel
+    # stride 1 with 16 lanes per patch: the groups of a warp are 16 patches
+    # apart, and level 1 (82 x 49) ends each patch row with a chunk of 9
+    (163, 97, dict(patch=10, stride=1, levels=2, iters=6, variance=1)),
 ])
 def test_ragged_and_parameter_cases(bd, w, h, kw):
     pair = synth.g1_pair(w, h, w * 7 + h)
@@ -727,6 +730,44 @@ def test_bulk_search_band_equals_own_loads(bd, patch, storage):
             assert torch.equal(torch.nan_to_num(q0, nan=-1.0), torch.nan_to_num(q1, nan=-1.0))
         for a, b in zip(v0, v1):
             assert np.array_equal(a["patches"].view(np.uint8), b["patches"].view(np.uint8))
+
+
+
+@pytest.mark.parametrize("kw,size", [
+    (dict(patch=12, stride=6, levels=3, iters=8, variance=1, storage="f32"), (333, 217)),
+    (dict(patch=8, stride=4, levels=3, iters=8, variance=0, storage="f16"), (641, 359)),
+    (dict(patch=10, stride=1, levels=2, iters=6, variance=1, storage="f32"), (163, 97)),
+])
+def test_search_chunking_does_not_change_results(bd, kw, size):
+    """Every search chunking (BDIS_OPT_SEARCH_PASSES 1..4 passes of the
+    block's lane groups, so 16 to 128 patches per block) gives bitwise the
+    same records and outputs: the patches are independent and the sigma_r
+    sums are exact integers.  The stride-1 case puts the groups of a warp 16
+    patches apart, which a 3-pass chunk must still cover exactly once."""
+    import torch
+    w, h = size
+    p = synth.g1_pair(w, h, 91)
+    L = torch.from_numpy(p.left).cuda()
+    R = torch.from_numpy(p.right).cuda()
+    res = []
+    for passes in (1, 2, 3, 4):
+        m = bd.BDIS(**kw)
+        m.set_option(bd.B.OPT_FORM, 1)
+        m.set_option(bd.B.OPT_SEARCH_PASSES, passes)
+        d, v, k = m.match(L, R)
+        torch.cuda.synchronize()
+        views = [m.level_view(0, l) for l in range(kw["levels"])]
+        res.append(((d, v, k), views))
+        m.close()
+    (d0, v0, k0), w0 = res[0]
+    for (d1, v1, k1), w1 in res[1:]:
+        assert torch.equal(k0, k1)
+        assert torch.equal(torch.nan_to_num(d0, nan=-1.0), torch.nan_to_num(d1, nan=-1.0))
+        if v0 is not None:
+            assert torch.equal(torch.nan_to_num(v0, nan=-1.0), torch.nan_to_num(v1, nan=-1.0))
+        for a, b in zip(w0, w1):
+            assert np.array_equal(a["patches"].view(np.uint8), b["patches"].view(np.uint8))
+            assert a["sigma_r"] == b["sigma_r"]
 
 
 def _coverage(disp, var, valid, gt, z=1.96):
