@@ -381,7 +381,13 @@ typedef enum {
      * block's lane groups per chunk (32 patches per pass for patch sizes up
      * to 8, 16 above).  Same results: the sigma_r sums are exact integers, so
      * the chunking does not change them.  Other values: BDIS_EINVAL. */
-    BDIS_OPT_SEARCH_PASSES = 13
+    BDIS_OPT_SEARCH_PASSES = 13,
+    /* Fusion tile of every level: 0 (default) as tuned (or the default
+     * configuration with BDIS_OPT_AUTOTUNE 0); 1 32x16, 2 64x32, 3 64x64
+     * pixels.  Same results: each pixel's sums run over its covering
+     * patches in the same order whatever the tile.  Other values:
+     * BDIS_EINVAL. */
+    BDIS_OPT_FUSE_TILE = 14
 } bdis_option;
 
 bdis_status bdis_set_option(bdis_handle *h, int option, int value);

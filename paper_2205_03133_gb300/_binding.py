@@ -89,7 +89,7 @@ OPT_GRAPH, OPT_PROFILE, OPT_AUTOTUNE, OPT_FORM, OPT_PDL, OPT_PYRAMID_STEPS, OPT_
     1, 2, 3, 4, 5, 6, 7)
 OPT_HOST_MAPPED = 8
 OPT_BARRIER_LIMIT, OPT_BARRIER_TEST, OPT_COARSE_LEVELS, OPT_BULK_COPY = 9, 10, 11, 12
-OPT_SEARCH_PASSES = 13
+OPT_SEARCH_PASSES, OPT_FUSE_TILE = 13, 14
 KERNEL_NAMES = ["pyramid", "search", "fuse", "persistent", "upsample"]
 
 

@@ -83,6 +83,7 @@ struct bdis_handle {
     int use_pdl = 1;          // BDIS_OPT_PDL: 0, 1 or 2
     int pyr_steps = 0;        // BDIS_OPT_PYRAMID_STEPS
     int search_passes = 0;    // BDIS_OPT_SEARCH_PASSES (0: tuned)
+    int fuse_tile = 0;        // BDIS_OPT_FUSE_TILE (0: tuned)
     bool adjoint_levels = false;  // BDIS_OPT_ADJOINT_LEVELS
     bool host_mapped = true;      // BDIS_OPT_HOST_MAPPED
     // repeat of the previous call: same pairs, stream, options and arena ->
@@ -474,7 +475,7 @@ bdis_status ensure_status_word(bdis_handle *h) {
     }
     return BDIS_OK;
 }
-const LevelCfg kSearchCands[4] = {{1, 32, 16}, {2, 64, 32}, {4, 32, 16}, {3, 64, 32}};
+const LevelCfg kSearchCands[4] = {{1, 32, 16}, {2, 64, 32}, {4, 64, 64}, {3, 64, 32}};
 
 // The whole coarse-to-fine pipeline for n pairs with per-level launch
 // configuration cfg.  graph: replay / capture allowed; prof: bracket each
@@ -899,7 +900,7 @@ bdis_status run_tuned(bdis_handle *h, int n, const bdis_pair *pairs, int in_type
 
 int option_bits(const bdis_handle *h) {
     return (h->use_graph ? 1 : 0) | (h->profile ? 2 : 0) | (h->use_pdl << 14) | (h->autotune ? 8 : 0) |
-           (h->form << 4) | (h->pyr_steps << 6) | (h->search_passes << 18) | (h->coarse_levels << 8) |
+           (h->form << 4) | (h->pyr_steps << 6) | (h->search_passes << 18) | (h->fuse_tile << 21) | (h->coarse_levels << 8) |
            (h->barrier_unreachable ? 1 << 12 : 0) | ((h->bulk_copy & 1) << 13) | ((h->bulk_copy & 2) << 15);
 }
 
@@ -1002,6 +1003,13 @@ bdis_status run_tuned(bdis_handle *h, int n, const bdis_pair *pairs, int in_type
     }
     if (h->search_passes > 0)
         for (auto &c : t.cfg) c.passes = h->search_passes;
+    if (h->fuse_tile > 0) {
+        const int tw[3] = {32, 64, 64}, th[3] = {16, 32, 64};
+        for (auto &c : t.cfg) {
+            c.tile_w = tw[h->fuse_tile - 1];
+            c.tile_h = th[h->fuse_tile - 1];
+        }
+    }
     int form = t.form;
     if (h->form == 1) form = h->coarse_levels;
     if (h->form == 2) form = (in_type == E_U8 && mega_supported(h->p.patch) &&
@@ -1132,6 +1140,11 @@ bdis_status bdis_set_option(bdis_handle *h, int option, int value) {
     if (option == BDIS_OPT_PYRAMID_STEPS) {
         if (value < 0 || value > 2) return fail(h, BDIS_EINVAL, "pyramid steps must be 0, 1 or 2");
         h->pyr_steps = value;
+        return BDIS_OK;
+    }
+    if (option == BDIS_OPT_FUSE_TILE) {
+        if (value < 0 || value > 3) return fail(h, BDIS_EINVAL, "fuse tile must be 0..3");
+        h->fuse_tile = value;
         return BDIS_OK;
     }
     if (option == BDIS_OPT_SEARCH_PASSES) {

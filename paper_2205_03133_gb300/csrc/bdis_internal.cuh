@@ -26,7 +26,7 @@ constexpr int kUpUnitPixels = 1024;
 
 // Largest pixel tile of the fused posterior / densify kernel.
 constexpr int kFuseTileWMax = 64;
-constexpr int kFuseTileHMax = 32;
+constexpr int kFuseTileHMax = 64;
 
 // Launch configuration of one level (chosen by the autotuner): search passes
 // per block (a block's chunk is passes x groups patches) and fuse tile size.

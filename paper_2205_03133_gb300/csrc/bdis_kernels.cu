@@ -13,7 +13,7 @@
 //               rejection flags (Sec. III-B, Sec. IV technical details), and the
 //               sums of the dynamic sigma_r (text after Eq. 6), accumulated in
 //               exact 64-bit fixed point
-//   k_fuse      per 32x16 or 64x32 pixel tile: window posterior (Eq. 5-6),
+//   k_fuse      per 32x16, 64x32 or 64x64 pixel tile: window posterior (Eq. 5-6),
 //               coarse-to-fine rho (Eq. 10-11) and PDF fit (Eq. 14-16) of the
 //               patches overlapping the tile, then the sGMM fusion gather
 //               (Eq. 8-9, Eq. 12) and pixel variance (Eq. 17)
@@ -1318,7 +1318,7 @@ __device__ __forceinline__ void cover(int x, int n, int P, int S, float rS, int 
 template <int TW, int TH>
 __device__ __forceinline__ void fuse_unit(const LaunchArgs &a, int unit, float4 *fz) {
     // fz: nkx * nky posteriors, then nky * TW column sums (dynamic shared memory).
-    // The tile size is a compile-time constant (32x16 or 64x32), so the pixel
+    // The tile size is a compile-time constant (32x16, 64x32 or 64x64), so the pixel
     // index arithmetic is shifts and masks.
     __shared__ int cxlo[kFuseTileWMax], cxn[kFuseTileWMax], cxr[kFuseTileWMax];
     __shared__ int cylo[kFuseTileHMax], cyn[kFuseTileHMax], cyr[kFuseTileHMax];
@@ -1704,7 +1704,9 @@ __global__ void __launch_bounds__(256) k_mega(MegaArgs m) {
                 for (int u = blockIdx.x; u < total; u += gridDim.x) search_unit<P, TG, TG, false>(a, u, smem, ph);
             }
         } else if (a.kind == 2) {
-            if (a.tile_w == 64) {
+            if (a.tile_w == 64 && a.tile_h == 64) {
+                for (int u = blockIdx.x; u < total; u += gridDim.x) fuse_unit<64, 64>(a, u, (float4 *)smem);
+            } else if (a.tile_w == 64) {
                 for (int u = blockIdx.x; u < total; u += gridDim.x) fuse_unit<64, 32>(a, u, (float4 *)smem);
             } else {
                 for (int u = blockIdx.x; u < total; u += gridDim.x) fuse_unit<32, 16>(a, u, (float4 *)smem);
@@ -1809,8 +1811,9 @@ size_t fuse_smem(int P, int S, int tile_w, int tile_h) {
 }
 
 cudaError_t prepare_fuse(size_t smem_bytes) {
-    const cudaError_t e = raise_smem_limit((const void *)k_fuse<32, 16>, smem_bytes);
-    return e != cudaSuccess ? e : raise_smem_limit((const void *)k_fuse<64, 32>, smem_bytes);
+    cudaError_t e = raise_smem_limit((const void *)k_fuse<32, 16>, smem_bytes);
+    if (e == cudaSuccess) e = raise_smem_limit((const void *)k_fuse<64, 32>, smem_bytes);
+    return e != cudaSuccess ? e : raise_smem_limit((const void *)k_fuse<64, 64>, smem_bytes);
 }
 
 bool mega_supported(int P) { return mega_kernel(P, E_F32) != nullptr; }
@@ -1996,7 +1999,8 @@ cudaError_t launch_search(const LaunchArgs &a, int in_type, int g_type, size_t s
 }
 
 cudaError_t launch_fuse(const LaunchArgs &a, size_t smem, cudaStream_t s) {
-    const void *f = a.tile_w == 64 ? (const void *)k_fuse<64, 32> : (const void *)k_fuse<32, 16>;
+    const void *f = a.tile_w == 64 ? (a.tile_h == 64 ? (const void *)k_fuse<64, 64> : (const void *)k_fuse<64, 32>)
+                                   : (const void *)k_fuse<32, 16>;
     return launch_args_kernel(f, a, grid_for(a.total, 8), smem, s);
 }
 

@@ -77,7 +77,8 @@ def test_host_side_argument_checks(lib):
     assert lib.bdis_level_view_get(m._h, 0, 0, C.byref(v)) == B.BDIS_EINVAL
     # option ranges
     for opt, good, bad in ((B.OPT_BULK_COPY, (0, 1, 2, 3), (-1, 4)),
-                           (B.OPT_SEARCH_PASSES, (0, 1, 2, 3, 4), (-1, 5))):
+                           (B.OPT_SEARCH_PASSES, (0, 1, 2, 3, 4), (-1, 5)),
+                           (B.OPT_FUSE_TILE, (0, 1, 2, 3), (-1, 4))):
         for val in good:
             assert lib.bdis_set_option(m._h, opt, val) == B.BDIS_OK, (opt, val)
         for val in bad:

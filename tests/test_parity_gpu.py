@@ -740,9 +740,10 @@ def test_bulk_search_band_equals_own_loads(bd, patch, storage):
 ])
 def test_search_chunking_does_not_change_results(bd, kw, size):
     """Every search chunking (BDIS_OPT_SEARCH_PASSES 1..4 passes of the
-    block's lane groups, so 16 to 128 patches per block) gives bitwise the
-    same records and outputs: the patches are independent and the sigma_r
-    sums are exact integers.  The stride-1 case puts the groups of a warp 16
+    block's lane groups, so 16 to 128 patches per block) and every fusion
+    tile (BDIS_OPT_FUSE_TILE 32x16, 64x32, 64x64) gives bitwise the same
+    records and outputs: the patches are independent, the sigma_r sums are
+    exact integers and each pixel's fusion sums run in the same order.  The stride-1 case puts the groups of a warp 16
     patches apart, which a 3-pass chunk must still cover exactly once."""
     import torch
     w, h = size
@@ -750,10 +751,11 @@ def test_search_chunking_does_not_change_results(bd, kw, size):
     L = torch.from_numpy(p.left).cuda()
     R = torch.from_numpy(p.right).cuda()
     res = []
-    for passes in (1, 2, 3, 4):
+    for passes, tile in ((1, 1), (2, 2), (3, 3), (4, 1), (2, 3)):
         m = bd.BDIS(**kw)
         m.set_option(bd.B.OPT_FORM, 1)
         m.set_option(bd.B.OPT_SEARCH_PASSES, passes)
+        m.set_option(bd.B.OPT_FUSE_TILE, tile)
         d, v, k = m.match(L, R)
         torch.cuda.synchronize()
         views = [m.level_view(0, l) for l in range(kw["levels"])]
