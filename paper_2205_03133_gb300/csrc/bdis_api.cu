@@ -54,6 +54,10 @@ struct bdis_handle {
     // scratch of the backward pass (grows, never shrinks)
     char *garena = nullptr;
     size_t garena_cap = 0;
+    // the gradient-descriptor table the backward scratch holds (its bytes,
+    // uploaded at the start of garena); a call whose table is these bytes or
+    // a prefix of them skips the upload and the wait for the staging buffer
+    std::vector<char> last_grad_upload;
     // autotuner: per-level launch configuration cached per geometry key
     bool autotune = true;
     // execution form of a call: kFormLaunches, kFormPersistent, or k > 0:
@@ -1567,6 +1571,7 @@ bdis_status grad_setup(bdis_handle *h, const FwdView &fv, const bdis_grad *g, bo
             cudaFree(h->garena);
             h->garena = nullptr;
             h->garena_cap = 0;
+            h->last_grad_upload.clear();
         }
         const size_t cap = align_up(bytes + bytes / 4, 1 << 20);
         if (cudaMalloc((void **)&h->garena, cap) != cudaSuccess) {
@@ -1630,16 +1635,22 @@ bdis_status grad_setup(bdis_handle *h, const FwdView &fv, const bdis_grad *g, bo
             if (q.wsum == nullptr) return fail(h, BDIS_EINVAL, "forward kept no fusion weights");
         }
     const size_t tbytes = sizeof(GradDesc) * cnt;
-    bdis_status s = ensure_pinned(h, std::max(tbytes, h->last_upload.size()));
-    if (s != BDIS_OK) return s;
-    cudaError_t e = cudaEventSynchronize(h->upload_done);
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
-    std::memcpy(h->pinned, gd.data(), tbytes);
     GradDesc *d_desc = (GradDesc *)(base + off_desc);
-    e = cudaMemcpyAsync(d_desc, h->pinned, tbytes, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(h, e, "gradient descriptor upload");
-    e = cudaEventRecord(h->upload_done, st);
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
+    const bool same = h->last_grad_upload.size() >= tbytes &&
+                      std::memcmp(h->last_grad_upload.data(), gd.data(), tbytes) == 0;
+    if (!same) {
+        bdis_status s = ensure_pinned(h, std::max(tbytes, h->last_upload.size()));
+        if (s != BDIS_OK) return s;
+        cudaError_t e = cudaEventSynchronize(h->upload_done);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
+        std::memcpy(h->pinned, gd.data(), tbytes);
+        e = cudaMemcpyAsync(d_desc, h->pinned, tbytes, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "gradient descriptor upload");
+        e = cudaEventRecord(h->upload_done, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
+        const char *tb = (const char *)gd.data();
+        h->last_grad_upload.assign(tb, tb + tbytes);
+    }
     double gsum = 0.0;
     for (int m = 0; m < p.levels; ++m) gsum += std::ldexp(1.0, m);
     for (int l = 0; l < nlev; ++l) {
@@ -1676,11 +1687,6 @@ bdis_status bdis_loss(bdis_handle *h, const bdis_saved *sv, float lambda, const 
     if (s != BDIS_OK) return s;
     GradArgs a = gp.a[0];
     a.lambda = lambda;
-    for (int i = 0; i < fv.npairs; ++i) {
-        const LevelDesc &d = (*fv.descs)[(size_t)i];
-        cudaError_t e = cudaMemsetAsync(g[i].g_right, 0, sizeof(float) * (size_t)d.w * d.h, st);
-        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
-    }
     a.total = gp.tot[0][G_PIX];
     cudaError_t e = launch_loss(a, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "loss launch");

@@ -145,6 +145,16 @@ __global__ void __launch_bounds__(256) k_loss(GradArgs a) {
     }
 }
 
+// Zeroes every pair's dL/dI_r buffer (w h floats) before k_loss scatters
+// into it: one launch over the pixels of all pairs.
+__global__ void __launch_bounds__(256) k_zero_gr(GradArgs a) {
+    for (int unit = blockIdx.x; unit < a.total; unit += gridDim.x) {
+        const GradDesc &g = a.descs[find_pair_g(a.descs, a.npairs, unit, G_PIX)];
+        const int idx = (unit - g.work_begin[G_PIX]) * blockDim.x + threadIdx.x;
+        if (idx < g.w * g.h) g.gR[idx] = 0.f;
+    }
+}
+
 // One block per pair: loss = sum of the partials / (w h), in a fixed order.
 __global__ void __launch_bounds__(256) k_loss_reduce(GradArgs a) {
     __shared__ float red[32];
@@ -797,6 +807,9 @@ int ggrid(int total) {
 }  // namespace
 
 cudaError_t launch_loss(const GradArgs &a, cudaStream_t s) {
+    k_zero_gr<<<ggrid(a.total), 256, 0, s>>>(a);
+    cudaError_t z = cudaGetLastError();
+    if (z != cudaSuccess) return z;
     k_loss<<<ggrid(a.total), 256, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

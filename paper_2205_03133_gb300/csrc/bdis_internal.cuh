@@ -185,7 +185,7 @@ struct GradArgs {
 std::string check_params(const bdis_params &p);
 std::string check_pair(const bdis_params &p, const bdis_pair &q);
 
-cudaError_t launch_loss(const GradArgs &a, cudaStream_t s);        // + per-pair reduce
+cudaError_t launch_loss(const GradArgs &a, cudaStream_t s);        // zeroes dL/dI_r; + per-pair reduce
 cudaError_t launch_bwd_pix(const GradArgs &a, cudaStream_t s);
 cudaError_t launch_bwd_dens(const GradArgs &a, cudaStream_t s);    // + sigma_r adjoint
 cudaError_t launch_bwd_patch(const GradArgs &a, cudaStream_t s);
