@@ -378,12 +378,15 @@ __device__ __forceinline__ void patch_adjoint_half(const GradDesc &g, const bdis
     float t0, tp;
     split_shift(d, off0, t0);
     split_shift(d + 0.5f, offp, tp);
-    const int b0 = ox + off0 - 1, bp = ox + offp;
+    const int b0 = ox + off0 - 1;
+    // the d + 1/2 row starts at b0 + 1 (offp == off0) or b0 (offp == off0 - 1):
+    // its values are the d row's, one column over or not
+    const bool right = offp == off0;
     float v0[P + 3], vp[P + 2];
 #pragma unroll
     for (int q = 0; q < P + 3; ++q) v0[q] = __ldg(Rrow + clampi(b0 + q, 0, g.w - 1));
 #pragma unroll
-    for (int q = 0; q < P + 2; ++q) vp[q] = __ldg(Rrow + clampi(bp + q, 0, g.w - 1));
+    for (int q = 0; q < P + 2; ++q) vp[q] = right ? v0[q + 1] : v0[q];
     // tap (value, slope) of offset i at pixel j: row, first index, phase
     auto tap = [&](int i, int j, float &v, float &sl) {
         const float *r = (i == 1 || i == 2) ? vp : v0;
@@ -464,18 +467,25 @@ __device__ __forceinline__ void patch_adjoint_half(const GradDesc &g, const bdis
         cLrow[j] = -tsum - cF;
         cGrow[j] = vF * ((v00 - T[j]) - mres);
     }
-    // a clamped column's weight lands on the edge column, as in tap_row()
+    // one atomic per column: the d + 1/2 row starts one column right of
+    // the d row's first column (offp == off0) or at it (offp == off0 - 1,
+    // the half pixel moving the split left), so its adjoints add onto the
+    // d row's columns b0 .. b0 + P + 2.  A clamped column's weight lands on
+    // the edge column, as in tap_row().
     float *gRrow = g.gR + (size_t)row * g.w;
 #pragma unroll
-    for (int q = 0; q < P + 3; ++q)
-        if (a0[q] != 0.f) atomicAdd(gRrow + clampi(b0 + q, 0, g.w - 1), a0[q]);
-#pragma unroll
-    for (int q = 0; q < P + 2; ++q)
-        if (ap[q] != 0.f) atomicAdd(gRrow + clampi(bp + q, 0, g.w - 1), ap[q]);
+    for (int c = 0; c < P + 3; ++c) {
+        const float pr = c >= 1 ? ap[c - 1] : 0.f;
+        const float pl = c < P + 2 ? ap[c] : 0.f;
+        const float v = a0[c] + (right ? pr : pl);
+        if (v != 0.f) atomicAdd(gRrow + clampi(b0 + c, 0, g.w - 1), v);
+    }
 }
 
+// P <= 8: three blocks per SM (80 registers, a few spilled values) hide more
+// of the record and row-load latency than two without spills.
 template <int P>
-__global__ void __launch_bounds__(256) k_bwd_patch(GradArgs a) {
+__global__ void __launch_bounds__(256, (P <= 8 ? 3 : 1)) k_bwd_patch(GradArgs a) {
     constexpr int G = P <= 8 ? 8 : 16;
     constexpr int N = P * P;
     constexpr int SEGN = P + kSegExtra;
