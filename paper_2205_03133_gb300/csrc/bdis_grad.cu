@@ -483,9 +483,10 @@ __device__ __forceinline__ void patch_adjoint_half(const GradDesc &g, const bdis
 }
 
 // P <= 8: three blocks per SM (80 registers, a few spilled values) hide more
-// of the record and row-load latency than two without spills.
+// of the record and row-load latency than two without spills; larger patches
+// keep two (128 registers).
 template <int P>
-__global__ void __launch_bounds__(256, (P <= 8 ? 3 : 1)) k_bwd_patch(GradArgs a) {
+__global__ void __launch_bounds__(256, (P <= 8 ? 3 : 2)) k_bwd_patch(GradArgs a) {
     constexpr int G = P <= 8 ? 8 : 16;
     constexpr int N = P * P;
     constexpr int SEGN = P + kSegExtra;
