@@ -271,6 +271,9 @@ void plan_layout(const bdis_params &p, int n, const bdis_pair *pairs, const Leve
     const size_t gsz = elem_size(grad_type_of(p.storage));   // gradients
     const size_t cnt = (size_t)NL * n;
     pl.descs.assign(cnt, LevelDesc{});
+    // every byte defined (padding included): the table keys the upload skip
+    // and the graph replay bytewise
+    std::memset(pl.descs.data(), 0, sizeof(LevelDesc) * cnt);
     for (auto *v : {&pl.oG, &pl.oL, &pl.oR, &pl.oD, &pl.oQ, &pl.oV, &pl.oW, &pl.oRec, &pl.oFuse, &pl.oSr})
         v->assign(cnt, 0);
     const int F = p.finest_level;
@@ -1514,7 +1517,10 @@ bdis_status grad_setup(bdis_handle *h, const FwdView &fv, const bdis_grad *g, bo
     }
     gp.nlev = nlev;
     const size_t cnt = (size_t)nlev * n;
-    std::vector<GradDesc> gd(cnt, GradDesc{});
+    std::vector<GradDesc> gd(cnt);
+    // every byte defined (padding included): the table is compared bytewise
+    // with the last upload
+    std::memset(gd.data(), 0, sizeof(GradDesc) * cnt);
     Bump b;
     const size_t off_desc = b.take(sizeof(GradDesc) * cnt);
     std::vector<size_t> oDw(cnt), oG(cnt), od(cnt), opi(cnt), osp(cnt), oce(cnt), olp(cnt), ocp(cnt);
