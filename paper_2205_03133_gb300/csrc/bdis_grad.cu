@@ -695,12 +695,14 @@ __global__ void __launch_bounds__(256) k_bwd_gather(GradArgs a) {
         const GradDesc &g = a.descs[find_pair_g(a.descs, a.npairs, unit, G_PIX)];
         const int idx = (unit - g.work_begin[G_PIX]) * blockDim.x + threadIdx.x;
         if (idx >= g.w * g.h) continue;
-        const int x = idx % g.w, y = idx / g.w;
-        const int kxlo = x - P + 1 > 0 ? (x - P + 1 + S - 1) / S : 0;
-        const int kxhi = min(g.kxreg - 1, x / S);
+        const int y = idx / g.w, x = idx - y * g.w;
+        // x, y < 2^22: exact divisions by S through its rounded reciprocal
+        const float rS = recip(S);
+        const int kxlo = x - P + 1 > 0 ? udiv_small(x - P + S, rS) : 0;
+        const int kxhi = min(g.kxreg - 1, udiv_small(x, rS));
         const bool kxext = g.npx > g.kxreg && x >= g.w - P;
-        const int kylo = y - P + 1 > 0 ? (y - P + 1 + S - 1) / S : 0;
-        const int kyhi = min(g.kyreg - 1, y / S);
+        const int kylo = y - P + 1 > 0 ? udiv_small(y - P + S, rS) : 0;
+        const int kyhi = min(g.kyreg - 1, udiv_small(y, rS));
         const bool kyext = g.npy > g.kyreg && y >= g.h - P;
         const int nkx = kxhi - kxlo + 1 + (kxext ? 1 : 0);
         const int nky = kyhi - kylo + 1 + (kyext ? 1 : 0);
