@@ -344,13 +344,15 @@ typedef enum {
      * host-device link; 0, or any other buffer: staging copies through device
      * memory.  Same results. */
     BDIS_OPT_HOST_MAPPED = 8,
-    /* Polls of one grid-barrier wait of the persistent form before it gives
-     * up (a poll is one L2 read and a 64 ns sleep): >= 1, default 2^22. */
+    /* Polls of one grid-barrier wait of the persistent form, and of one wait
+     * for bulk copies (BDIS_OPT_BULK_COPY), before it gives up (a poll is one
+     * read and a short sleep): >= 1, default 2^22. */
     BDIS_OPT_BARRIER_LIMIT = 9,
-    /* 1: test the timeout path of the persistent form -- no arrival completes
-     * a grid barrier, so every wait runs out after BDIS_OPT_BARRIER_LIMIT
-     * polls and the call is reported as failed (see BDIS_OPT_FORM).  0 (default):
-     * normal barriers.  Only for tests of the error reporting. */
+    /* 1: test the timeout paths -- no arrival completes a grid barrier of the
+     * persistent form, and every wait for bulk copies expects 16 bytes that
+     * no copy delivers, so each wait runs out after BDIS_OPT_BARRIER_LIMIT
+     * polls and the call is reported as failed (see BDIS_OPT_FORM).  0
+     * (default): normal waits.  Only for tests of the error reporting. */
     BDIS_OPT_BARRIER_TEST = 10,
     /* With BDIS_OPT_FORM 1: the number k of coarsest searched levels whose
      * stages (their pyramid steps, searches and fusions) run as one

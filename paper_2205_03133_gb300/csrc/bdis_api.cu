@@ -577,6 +577,8 @@ bdis_status run_cfg(bdis_handle *h, int n, const bdis_pair *pairs, int in_type, 
         a.prefetch = &a == &stages.front() ? 0 : 1;  // the table is uploaded before the first stage
         a.bulk = h->bulk_copy;
         a.err_host = h->status_dev;
+        a.copy_limit = h->barrier_limit;
+        a.copy_test = h->barrier_unreachable ? 1 : 0;
     }
     // upload descriptors (and the stage list) unless identical to the last upload
     const size_t dbytes = sizeof(LevelDesc) * pl.descs.size();

@@ -118,6 +118,9 @@ struct LaunchArgs {
                               // (every stage after a call's first): prefetched while waiting
     int bulk;                 // bit 1: one-step pyramid tiles, bit 2: search bands, by bulk async copies
     int *err_host;            // mapped status word of the handle (a device wait ran out), or nullptr
+    unsigned copy_limit;      // polls of a bulk-copy wait before it gives up (0: the default)
+    int copy_test;            // test switch: each bulk-copy wait expects 16 bytes that no copy
+                              // delivers, so it runs out (BDIS_OPT_BARRIER_TEST)
 };
 
 // Persistent form: every stage of a call in one cooperative launch, with a

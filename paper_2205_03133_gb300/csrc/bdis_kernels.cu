@@ -474,6 +474,11 @@ static_assert(PyrBulk<uint8_t>::RAW_SPAN_B % 16 == 0 && PyrBulk<__half>::RAW_SPA
 // Polls of one wait for a tile's copies (a poll is a barrier test and a 32 ns
 // sleep); past it the kernel records the failure and stops.
 constexpr unsigned kCopyWaitLimit = 1u << 22;
+__device__ __forceinline__ unsigned copy_limit(const LaunchArgs &a) {
+    return a.copy_limit != 0u ? a.copy_limit : kCopyWaitLimit;
+}
+// bytes a wait expects beyond those its copies deliver (the test switch)
+__device__ __forceinline__ unsigned copy_extra(const LaunchArgs &a) { return a.copy_test ? 16u : 0u; }
 
 // Four raw elements at p (4-, 8- or 16-byte aligned) as floats.
 __device__ __forceinline__ float4 raw4(const uint8_t *p) {
@@ -537,7 +542,7 @@ __global__ void __launch_bounds__(256, 4) k_pyramid_bulk(LaunchArgs a) {
         const int nrows = next ? 2 * kPyrSH : kPyrSH;
         if (tid < nrows) {
             fence_proxy_async_smem();  // earlier reads of this buffer precede the copy
-            if (tid == 0) mbar_arrive_expect_tx(&bar[b], (unsigned)(nrows * PB::RAW_SPAN_B));
+            if (tid == 0) mbar_arrive_expect_tx(&bar[b], (unsigned)(nrows * PB::RAW_SPAN_B) + copy_extra(a));
             const int img = tid / kPyrSH, r = tid - img * kPyrSH;
             const int xr = t.tx * kPyrTW - kPyrOX - PB::RAW_OFF, y = t.ty * kPyrTH - 2 + r;
             const TI *src = (const TI *)(img ? D.R : D.L) + (size_t)y * D.pitch + xr;
@@ -566,7 +571,7 @@ __global__ void __launch_bounds__(256, 4) k_pyramid_bulk(LaunchArgs a) {
         }
         __syncthreads();  // the previous unit's readers are done with Ls, Rs
         if (cur.bulk) {
-            const bool ok = mbar_wait_bounded(&bar[b], (parity >> b) & 1u, kCopyWaitLimit);
+            const bool ok = mbar_wait_bounded(&bar[b], (parity >> b) & 1u, copy_limit(a));
             parity ^= 1u << b;
             if (__syncthreads_or(!ok)) {
                 // a copy did not land: report it, wait (bounded) for the
@@ -575,7 +580,7 @@ __global__ void __launch_bounds__(256, 4) k_pyramid_bulk(LaunchArgs a) {
                     *(volatile int *)a.err_host = 1;
                     __threadfence_system();
                 }
-                if (nxt.bulk) mbar_wait_bounded(&bar[b ^ 1], (parity >> (b ^ 1)) & 1u, kCopyWaitLimit);
+                if (nxt.bulk) mbar_wait_bounded(&bar[b ^ 1], (parity >> (b ^ 1)) & 1u, copy_limit(a));
                 return;
             }
             // widen the raw rows to FP32 (exact for u8, f16, f32)
@@ -763,7 +768,7 @@ __device__ __forceinline__ bool search_unit(const LaunchArgs &a, int unit, float
             raw = (unsigned char *)(bbar + 2);
             if (tid < P) {
                 fence_proxy_async_smem();  // the last unit's widening reads precede the copy
-                if (tid == 0) mbar_arrive_expect_tx(bbar, (unsigned)(P * span * kE));
+                if (tid == 0) mbar_arrive_expect_tx(bbar, (unsigned)(P * span * kE) + copy_extra(a));
                 bulk_copy_g2s(raw + (size_t)tid * search_raw_pitch(cap, kE),
                               R + (size_t)(oy + tid) * D.pitch + xa, (unsigned)(span * kE), bbar);
             }
@@ -819,7 +824,7 @@ __device__ __forceinline__ bool search_unit(const LaunchArgs &a, int unit, float
     }
     if (bulk_band) {
         const unsigned par = bphase & 1u;
-        const bool ok = mbar_wait_bounded(bbar, par, kCopyWaitLimit);
+        const bool ok = mbar_wait_bounded(bbar, par, copy_limit(a));
         bphase ^= 1u;
         if (__syncthreads_or(!ok)) {
             // the copies did not land: report it, wait (bounded) once more
@@ -828,7 +833,7 @@ __device__ __forceinline__ bool search_unit(const LaunchArgs &a, int unit, float
                 *(volatile int *)a.err_host = 1;
                 __threadfence_system();
             }
-            mbar_wait_bounded(bbar, par, kCopyWaitLimit);
+            mbar_wait_bounded(bbar, par, copy_limit(a));
             return false;
         }
         // widen to FP32: four raw elements per step (the copied span covers

@@ -772,6 +772,52 @@ def test_search_chunking_does_not_change_results(bd, kw, size):
             assert a["sigma_r"] == b["sigma_r"]
 
 
+
+def test_bulk_copy_wait_timeout_is_reported(bd):
+    """Every wait for bulk asynchronous copies (the one-step pyramid's tiles
+    and the search's bands) is bounded.  A wait that runs out (forced here:
+    with the test switch each wait expects 16 bytes that no copy delivers)
+    stops the block after its copies have landed, and the call is reported
+    as failed by bdis_wait; the handle then works normally again, with the
+    outputs of a handle that never used the copies."""
+    import ctypes as C
+    import torch
+    lib = bd.B.lib()
+    kw = dict(patch=8, stride=4, levels=3, iters=8, storage="f16")
+    pair = synth.g1_pair(640, 480, 6)
+    L = torch.from_numpy(pair.left).cuda()
+    R = torch.from_numpy(pair.right).cuda()
+    ref = bd.BDIS(**kw)
+    ref.set_option(bd.B.OPT_FORM, 1)
+    dw, _, okw = ref.match(L, R)
+    torch.cuda.synchronize()
+    m = bd.BDIS(**kw)
+    for opt, val in ((bd.B.OPT_FORM, 1), (bd.B.OPT_AUTOTUNE, 0), (bd.B.OPT_PYRAMID_STEPS, 1),
+                     (bd.B.OPT_BULK_COPY, 3), (bd.B.OPT_BARRIER_LIMIT, 4096)):
+        m.set_option(opt, val)
+    stream = torch.cuda.Stream()
+    sh = C.c_void_p(stream.cuda_stream)
+    d = torch.empty((480, 640), device="cuda")
+    ok = torch.empty((480, 640), dtype=torch.uint8, device="cuda")
+
+    def call():
+        return lib.bdis_match(m._h, L.data_ptr(), R.data_ptr(), 640, 480, 640, d.data_ptr(), None,
+                              ok.data_ptr(), sh)
+
+    m.set_option(bd.B.OPT_BARRIER_TEST, 1)
+    assert call() == bd.B.BDIS_OK                    # asynchronous: not known yet
+    assert lib.bdis_wait(m._h, sh) == bd.B.BDIS_ECUDA
+    assert b"bulk copy" in lib.bdis_last_error(m._h)
+    assert lib.bdis_wait(m._h, sh) == bd.B.BDIS_OK   # reported once
+    m.set_option(bd.B.OPT_BARRIER_TEST, 0)
+    assert call() == bd.B.BDIS_OK
+    assert lib.bdis_wait(m._h, sh) == bd.B.BDIS_OK
+    assert torch.equal(ok, okw)
+    assert torch.equal(torch.nan_to_num(d, nan=-1.0), torch.nan_to_num(dw, nan=-1.0))
+    m.close()
+    ref.close()
+
+
 def _coverage(disp, var, valid, gt, z=1.96):
     v = valid.astype(bool) & np.isfinite(var) & (var > 0)
     e = np.abs(disp[v].astype(np.float64) - gt[v])
