@@ -413,7 +413,7 @@ typedef struct {
  * BDIS_OPT_PROFILE is on (waits for the recorded events); reset != 0 clears. */
 bdis_status bdis_get_profile(bdis_handle *h, bdis_profile *out, int reset);
 
-/* ---- inspection of the last call's intermediate buffers (tests) ---- */
+/* ---- inspection of the last call's intermediate buffers (diagnostics; the parity tests read every level through it) ---- */
 
 /* Per-patch record, as written by the search and posterior stages. */
 typedef struct {
@@ -455,6 +455,16 @@ typedef struct {
 bdis_status bdis_level_view_get(const bdis_handle *h, int pair, int level,
                                 bdis_level_view *out);
 
+/* Companion of bdis_level_view_get for callers without a CUDA runtime of
+ * their own (the Python binding): copies `bytes` between any two addresses
+ * the device can reach (host, page-locked or device; e.g. a level view's
+ * device pointers into a host buffer the caller owns) with
+ * cudaMemcpyAsync(..., cudaMemcpyDefault) on `stream` (NULL: the legacy
+ * default stream) and waits for it.  Nothing is allocated or kept.
+ * BDIS_EINVAL for a null pointer with bytes > 0; BDIS_ECUDA if the copy
+ * fails (bad address, or an error of an earlier asynchronous call). */
+bdis_status bdis_copy(void *dst, const void *src, size_t bytes, void *stream);
+
 /* ---- depth (Eq. 13) and depth variance (Eq. 17) ---- */
 
 /* Elementwise on n pixels of device buffers, asynchronous on `stream`:
@@ -478,8 +488,6 @@ bdis_status bdis_depth(const float *disp, const float *var, long long n, float f
  * null or unaligned buffer, bytes < 16 or reps < 1. */
 bdis_status bdis_probe_l2_read(const void *buf, size_t bytes, int reps, void *stream);
 
-/* cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, stream) + sync. */
-bdis_status bdis_copy(void *dst, const void *src, size_t bytes, void *stream);
 
 #ifdef __cplusplus
 }

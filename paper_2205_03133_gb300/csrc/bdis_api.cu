@@ -1371,6 +1371,7 @@ bdis_status bdis_wait(bdis_handle *h, void *stream) {
 }
 
 bdis_status bdis_copy(void *dst, const void *src, size_t bytes, void *stream) {
+    if (bytes == 0) return BDIS_OK;
     if (!dst || !src) return BDIS_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st) != cudaSuccess) return BDIS_ECUDA;
